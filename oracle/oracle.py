@@ -1,0 +1,242 @@
+"""Python driver of the FP64 C oracle (erq_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Follows arXiv 2409.09913:
+
+* ``centroids`` / ``rotate``   -- local centring (Section 5.1) and o' = P^{-1}(o_r - c)
+  (Section 3.3 workflow), readings R1/R2 of erq_oracle.c.
+* ``quantize``                  -- Algorithm 1 (Section 3.1).
+* ``build_index``               -- IVF index: clusters from an input assignment
+  (Section 4.1), codes and per-vector factors (Section 5.1 metrics paragraph).
+* ``search``                    -- probe, Eq. 3.3 + Eq. (eq:dis to ip) estimates, top-k',
+  exact re-rank, top-k.
+* ``estimate_rows`` / ``backward`` -- estimated distances of given pairs and their
+  gradient w.r.t. the raw query.
+* ``brute_force_quantize``      -- exhaustive argmax of Eq. 3.2 (optimization) over the
+  whole grid G, for tiny D and B (pin for Algorithm 1).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import functools
+import itertools
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "lib", "centroids", "rotate", "quantize", "build_index", "search", "estimate_rows",
+    "backward", "centroid_dists", "brute_force_quantize", "exact_knn", "num_threads",
+    "stored_factors",
+]
+
+_lib = None
+_P = np.ctypeslib.ndpointer
+_f32 = _P(np.float32, flags="C_CONTIGUOUS")
+_f64 = _P(np.float64, flags="C_CONTIGUOUS")
+_i32 = _P(np.int32, flags="C_CONTIGUOUS")
+_i64 = _P(np.int64, flags="C_CONTIGUOUS")
+_u8 = _P(np.uint8, flags="C_CONTIGUOUS")
+
+
+class _Opt:
+    """ndpointer that also accepts None."""
+
+    def __init__(self, dtype):
+        self.base = _P(dtype, flags="C_CONTIGUOUS")
+
+    def from_param(self, obj):
+        if obj is None:
+            return None
+        return self.base.from_param(obj)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        L.orc_centroids.argtypes = [_f32, ct.c_int64, ct.c_int, _i32, ct.c_int, _f32]
+        L.orc_rotate.argtypes = [_f32, _Opt(np.float32), _Opt(np.int32), ct.c_int64, ct.c_int, _f32, _f32]
+        L.orc_quantize_batch.argtypes = [_f32, ct.c_int64, ct.c_int, ct.c_int, _u8, _f64]
+        L.orc_search.argtypes = [ct.c_int, ct.c_int, ct.c_int, _f32, _f32, _i64, _i64, _u8, _f64, _f32,
+                                 _f64, ct.c_int64, _i32, _Opt(np.int32), ct.c_int, ct.c_int, ct.c_int,
+                                 _i64, _f64, _Opt(np.int64), _Opt(np.float64), _Opt(np.int32)]
+        L.orc_centroid_dists.argtypes = [_f32, ct.c_int, ct.c_int, _f64, ct.c_int64, _f64]
+        L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
+                                        _i64, _i32, _f64]
+        L.orc_backward.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
+                                   _i64, _i32, _f64, _f64]
+        L.orc_num_threads.restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def centroids(X, assign, nlist):
+    X = _c32(X)
+    C = np.empty((nlist, X.shape[1]), np.float32)
+    lib().orc_centroids(X, X.shape[0], X.shape[1], np.ascontiguousarray(assign, np.int32), nlist, C)
+    return C
+
+
+def rotate(X, P, C=None, assign=None):
+    """Rows of fl32(P^T (x - c)) accumulated in FP64 (reading R2)."""
+    X = _c32(X)
+    out = np.empty_like(X)
+    lib().orc_rotate(X, None if C is None else _c32(C),
+                     None if assign is None else np.ascontiguousarray(assign, np.int32),
+                     X.shape[0], X.shape[1], _c32(P), out)
+    return out
+
+
+def quantize(Rp, B):
+    """Algorithm 1 on each row.  Returns (codes uint8 [n,d], stats float64 [n,5]);
+    stats = (<ybar,|o'|>, ||ybar||^2, v_max, ||o'||^2, events)."""
+    Rp = _c32(np.atleast_2d(Rp))
+    n, d = Rp.shape
+    codes = np.empty((n, d), np.uint8)
+    stats = np.empty((n, 5), np.float64)
+    lib().orc_quantize_batch(Rp, n, d, int(B), codes, stats)
+    return codes, stats
+
+
+def stored_factors(stats):
+    """The two FP32 per-vector factors held by an index, from the FP64 stats:
+    f_add = ||o'||^2 and f_res = -2 ||o'||^2 / <ybar, |o'|> (0 when o' = 0), so that
+    est = f_add + ||q_r - c||^2 + f_res * <ybar, P^T (q_r - c)>  (Eq. 3.3 with
+    Eq. (eq:dis to ip), ||ybar|| cancelling)."""
+    ip, nr2 = stats[:, 0], stats[:, 3]
+    f_add = nr2.astype(np.float32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f_res = np.where(nr2 > 0, (-2.0 * nr2) / ip, 0.0).astype(np.float32)
+    return f_add, f_res
+
+
+def build_index(X, P, assign, nlist, B, centroids_in=None):
+    """IVF + extended-RaBitQ index, all in FP64 (Sections 3.3, 4.1).
+
+    Centroids are the cluster means (reading R1) unless ``centroids_in`` is
+    given (e.g. c = 0, the un-centred setting of Section 2.2)."""
+    X = _c32(X)
+    assign = np.ascontiguousarray(assign, np.int32)
+    n, d = X.shape
+    C = centroids(X, assign, nlist) if centroids_in is None else _c32(centroids_in)
+    Rp = rotate(X, P, C, assign)
+    order = np.argsort(assign, kind="stable").astype(np.int64)
+    counts = np.bincount(assign, minlength=nlist).astype(np.int64)
+    list_off = np.zeros(nlist + 1, np.int64)
+    list_off[1:] = np.cumsum(counts)
+    codes, stats = quantize(Rp[order], B)
+    row_of = np.empty(n, np.int64)
+    row_of[order] = np.arange(n, dtype=np.int64)
+    return dict(d=d, B=int(B), nlist=int(nlist), P=_c32(P), C=C, Cp=rotate(C, P), list_off=list_off,
+                list_ids=order, codes=codes, stats=stats, X=X, assign=assign, row_of=row_of,
+                Rp=Rp)
+
+
+def _q64(Q):
+    return np.ascontiguousarray(np.atleast_2d(Q), dtype=np.float64)
+
+
+def search(ix, Q, k, kprime=0, nprobe=None, probe=None):
+    """Batched search; returns dict(ids, dists, cand_ids, cand_est, probe).
+
+    ``nprobe``: int or per-query array; ``probe``: optional explicit [nq, maxp]
+    probe lists (then nprobe per query defaults to maxp)."""
+    Q = _q64(Q)
+    nq = Q.shape[0]
+    if probe is not None:
+        probe = np.ascontiguousarray(probe, np.int32)
+        maxp = probe.shape[1]
+        npr = np.full(nq, maxp, np.int32) if nprobe is None else np.broadcast_to(
+            np.asarray(nprobe, np.int32), (nq,)).copy()
+    else:
+        npr = np.broadcast_to(np.asarray(ix["nlist"] if nprobe is None else nprobe, np.int32), (nq,)).copy()
+        maxp = int(npr.max()) if nq else 1
+    kp = kprime if kprime > 0 else k
+    ids = np.empty((nq, k), np.int64)
+    dists = np.empty((nq, k), np.float64)
+    cand_ids = np.empty((nq, kp), np.int64)
+    cand_est = np.empty((nq, kp), np.float64)
+    probe_out = np.full((nq, maxp), -1, np.int32)
+    lib().orc_search(ix["d"], ix["B"], ix["nlist"], ix["P"], ix["C"], ix["list_off"], ix["list_ids"],
+                     ix["codes"], ix["stats"], ix["X"], Q, nq, np.ascontiguousarray(npr), probe, maxp,
+                     int(kprime), int(k), ids, dists, cand_ids, cand_est, probe_out)
+    return dict(ids=ids, dists=dists, cand_ids=cand_ids, cand_est=cand_est, probe=probe_out)
+
+
+def _rows_and_clusters(ix, ids):
+    ids = np.asarray(ids, np.int64)
+    rows = np.where(ids >= 0, ix["row_of"][np.maximum(ids, 0)], -1).astype(np.int64)
+    cl = np.repeat(np.arange(ix["nlist"], dtype=np.int32), np.diff(ix["list_off"]))
+    return np.ascontiguousarray(rows), np.ascontiguousarray(cl)
+
+
+def estimate_rows(ix, Q, ids):
+    """Estimated squared distance of query i to each original id in ids[i, :]."""
+    Q = _q64(Q)
+    ids = np.atleast_2d(ids)
+    rows, cl = _rows_and_clusters(ix, ids)
+    out = np.empty(ids.shape, np.float64)
+    lib().orc_estimate_rows(ix["d"], ix["B"], ix["P"], ix["C"], ix["codes"], ix["stats"], Q, Q.shape[0],
+                            ids.shape[1], rows, cl, out)
+    return out
+
+
+def backward(ix, Q, ids, g):
+    """sum_j g[i,j] * d est(q_i, ids[i,j]) / d q_i  (FP64)."""
+    Q = _q64(Q)
+    ids = np.atleast_2d(ids)
+    rows, cl = _rows_and_clusters(ix, ids)
+    out = np.empty(Q.shape, np.float64)
+    lib().orc_backward(ix["d"], ix["B"], ix["P"], ix["C"], ix["codes"], ix["stats"], Q, Q.shape[0],
+                       ids.shape[1], rows, cl, np.ascontiguousarray(g, np.float64), out)
+    return out
+
+
+def centroid_dists(C, Q):
+    Q = _q64(Q)
+    C = _c32(C)
+    out = np.empty((Q.shape[0], C.shape[0]), np.float64)
+    lib().orc_centroid_dists(C, C.shape[0], C.shape[1], Q, Q.shape[0], out)
+    return out
+
+
+def exact_knn(X, Q, k):
+    """Exact k nearest rows by FP64 squared distance, ties by id (ground truth)."""
+    X64 = np.asarray(X, np.float64)
+    ids = np.empty((len(Q), k), np.int64)
+    dd = np.empty((len(Q), k), np.float64)
+    for i, q in enumerate(np.asarray(Q, np.float64)):
+        d2 = ((X64 - q) ** 2).sum(1)
+        o = np.lexsort((np.arange(len(X64)), d2))[:k]
+        ids[i], dd[i] = o, d2[o]
+    return ids, dd
+
+
+@functools.lru_cache(maxsize=16)
+def _grid(d, B):
+    levels = np.arange(2 ** B, dtype=np.float64) - (2 ** B - 1) / 2.0   # Eq. (equ:shift)
+    grid = np.array(list(itertools.product(levels, repeat=d)), dtype=np.float64)
+    return grid, np.linalg.norm(grid, axis=1)
+
+
+def brute_force_quantize(op, B):
+    """argmax over the whole grid G of <y/||y||, o'> (Eq. 3.2, optimization) by
+    enumeration of all 2^(B*D) grid vectors.  Returns (best cosine, list of
+    ybar_u codes that reach it within 4 ulp)."""
+    op = np.asarray(op, np.float64)
+    grid, gnorm = _grid(op.shape[0], int(B))
+    cos = grid @ op / gnorm / np.linalg.norm(op)
+    best = cos.max()
+    tol = 4 * np.spacing(abs(best))
+    hits = grid[cos >= best - tol] + (2 ** B - 1) / 2.0
+    return best, hits.astype(np.int64)
