@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput of batched extended-RaBitQ IVF search on one GB300.
+
+Workload (default): 1,000,000 x 960 FP32 vectors from a 256-component Gaussian
+mixture with per-component per-dimension scales ~U(0.5, 2), 4,096 IVF clusters
+(Lloyd k-means, 10 iterations on a 262,144-row sample), B = 5 bits/dim,
+10,000 queries from the same mixture, top-10 after exact re-rank of the
+estimated top-k'.  nprobe is the smallest of {16, 32, 64, 128, 256} that reaches
+recall@10 >= 0.95 against exact FP32 kNN.  A step is one erq_search of the
+whole 10,000-query batch (query rotation, centroid probe, probe inversion,
+estimator scan with per-item top-k', merge, exact re-rank).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "QPS at recall@10>=0.95 (batched IVF search, 1 GB300)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="erq", choices=["erq", "reference"])
+    ap.add_argument("--workload", default="ivf_n1m_d960_nlist4096")
+    ap.add_argument("--B", type=int, default=5)
+    ap.add_argument("--precision", default="auto", help="fp32 | fp16 | fp8 | auto (best meeting recall)")
+    ap.add_argument("--nprobe", type=int, default=0, help="0 = smallest meeting the recall target")
+    ap.add_argument("--rerank-k", type=int, default=20)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--recall", type=float, default=0.95)
+    ap.add_argument("--cpu-sample", type=int, default=16, help="queries in the timed oracle sample")
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of N and nq (smoke runs only)")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- data
+def make_workload(args, rank=0):
+    cfg = S.WORKLOADS[args.workload]
+    n = int(cfg["n"] * args.scale)
+    nq = int(cfg["nq"] * args.scale)
+    d = cfg["d"]
+    X, _ = S.mixture(n, d, cfg["n_comp"], cfg["data_seed"], scale=cfg.get("scale", "unit"),
+                     normalize=cfg.get("normalize", False))
+    Q, _ = S.mixture(nq, d, cfg["n_comp"], cfg["query_seed"] + 1000 * rank, comp_seed=cfg["data_seed"],
+                     scale=cfg.get("scale", "unit"), normalize=cfg.get("normalize", False))
+    P = S.random_orthogonal(d, cfg["p_seed"])
+    return cfg, X, Q, P
+
+
+def ivf_assign(cfg, X, args, device):
+    nlist = cfg["nlist"]
+    if nlist == 1:
+        return np.zeros(len(X), np.int32)
+    sample = min(len(X), cfg.get("kmeans_sample", 262_144))
+    return S.kmeans_assign_torch(X, nlist, cfg.get("kmeans_iters", 10), 17, sample=sample, device=device)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                mhz.append(float(r[0]))
+                mx = float(r[1])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"],
+                "bf16_tflops_sustained": j.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def ffma_peak_tflops(sm_mhz):
+    """FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops per cycle at the clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- oracle sample
+def oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, rank_queries):
+    """Bounded CPU sample: the FP64 oracle over the probed clusters of
+    ``rank_queries`` queries (all of them present, so its answer is the full
+    index's).  Returns (partial index, query rows)."""
+    import oracle
+    C = oracle.centroids(X, assign, cfg["nlist"])
+    Qs = Q[:rank_queries]
+    cd = oracle.centroid_dists(C, Qs)
+    probed = np.unique(np.argsort(cd, axis=1, kind="stable")[:, :nprobe])
+    rows = np.nonzero(np.isin(assign, probed))[0]
+    ox = oracle.build_index(X[rows], P, assign[rows], cfg["nlist"], args.B, centroids_in=C)
+    return ox, Qs, rows
+
+
+def time_oracle(ox, Qs, args, nprobe, kp, reps=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.search(ox, Qs, args.k, kprime=kp, nprobe=nprobe)
+    return (time.perf_counter() - t0) / reps
+
+
+# ----------------------------------------------------------------------------- main
+def run_reference(args):
+    """FP64 oracle on host cores, a bounded sample of the workload per step."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg, X, Q, P = make_workload(args)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    assign = ivf_assign(cfg, X, args, dev)
+    nprobe = args.nprobe or 32
+    kp = max(args.k, args.rerank_k)
+    import oracle
+    ox, Qs, _ = oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, args.cpu_sample)
+    for _ in range(args.warmup):
+        time_oracle(ox, Qs[:2], args, nprobe, kp)
+    times = [time_oracle(ox, Qs, args, nprobe, kp) for _ in range(args.steps)]
+    qps = len(Qs) / statistics.mean(times)
+    cores = min(oracle.num_threads(), len(Qs))
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "nprobe": nprobe, "B": args.B,
+                                             "rerank_k": kp, "k": args.k},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe {nprobe}"},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2409_09913_gb300 import build as erq_build
+    erq_build.build()
+    from paper_2409_09913_gb300 import erq
+
+    t0 = time.perf_counter()
+    cfg, X, Q, P = make_workload(args, rank)
+    assign = ivf_assign(cfg, X, args, dev)
+    t_data = time.perf_counter() - t0
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ix = erq.build_index(Xd, torch.from_numpy(P).to(dev), args.B, cfg["nlist"],
+                         assign=torch.from_numpy(assign).to(dev))
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t1
+
+    # exact ground truth (FP32 GEMM, measurement helper only)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    xn = (Xd * Xd).sum(1)
+    gt = torch.empty((len(Q), args.k), dtype=torch.int64, device=dev)
+    for s0 in range(0, len(Q), 1024):
+        q = Qd[s0:s0 + 1024]
+        best_d = best_i = None
+        for x0 in range(0, len(X), 1 << 18):
+            d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
+            v, i = torch.topk(d, args.k, dim=1, largest=False)
+            i = i + x0
+            if best_d is None:
+                best_d, best_i = v, i
+            else:
+                cat_d, cat_i = torch.cat([best_d, v], 1), torch.cat([best_i, i], 1)
+                best_d, j = torch.topk(cat_d, args.k, dim=1, largest=False)
+                best_i = torch.gather(cat_i, 1, j)
+        gt[s0:s0 + len(q)] = best_i
+    gt_np = gt.cpu().numpy()
+    del xn
+
+    def recall(ids):
+        ids = ids.cpu().numpy()
+        return float(np.mean([len(set(a) & set(b)) / args.k for a, b in zip(ids, gt_np)]))
+
+    kp = max(args.k, args.rerank_k)
+    precisions = ["fp32", "fp16", "fp8"] if args.precision == "auto" else [args.precision]
+    sweep = {}
+    chosen = {}
+    for prec in precisions:
+        for p in ([args.nprobe] if args.nprobe else cfg.get("nprobes", (16, 32, 64, 128, 256))):
+            try:
+                ids, _ = ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec)
+            except erq.ErqError as e:
+                sweep[prec] = f"unavailable: {e}"
+                break
+            torch.cuda.synchronize()
+            r = recall(ids)
+            sweep.setdefault(prec, {})[p] = r
+            if r >= args.recall:
+                chosen[prec] = p
+                break
+
+    results = {}
+    for prec, p in chosen.items():
+        def step():
+            ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = erq.kernel_launches()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(args.steps):
+                step()
+            e1.record(st)
+            torch.cuda.synchronize()
+        launches = erq.kernel_launches() - launches0
+        ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        # phase split and work counters from one extra timed search
+        ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True)
+        phases = ix.timing()
+        work = ix.stats()
+        results[prec] = dict(nprobe=p, ms=ms, qps=len(Q) * world / (ms / 1e3), recall=sweep[prec][p],
+                             phases=phases, work=work, clocks=clk.summary(), launches=launches)
+
+    if not results:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": None, "error": "recall target not reached",
+                              "sweep": sweep}), flush=True)
+        return 1
+    best = max(results, key=lambda k: results[k]["qps"])
+    R = results[best]
+
+    # end to end through the C ABI from pinned host buffers
+    Qh = torch.from_numpy(Q).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best)
+    e2e_s = (time.perf_counter() - te) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (the code scan)
+    peaks = measured_peaks()
+    D, B = cfg["d"], args.B
+    scan_s = R["phases"]["scan"] / 1e3
+    flops = 2.0 * D * R["work"]["pairs"]
+    bytes_alg = (B * D / 8 + 8) * R["work"]["rows"] + len(Q) * D * 4
+    sm_mhz = R["clocks"]["sm_mhz"] or 2070.0
+    if best == "fp32":
+        peak_c, unit_c, bound_c = ffma_peak_tflops(sm_mhz), "TFLOP/s", "alu"
+    else:
+        peak_c = peaks["bf16_tflops"] * (2.0 if best == "fp8" else 1.0)
+        unit_c, bound_c = "TFLOP/s", "tensor"
+    t_c = flops / (peak_c * 1e12)
+    t_m = bytes_alg / (peaks["hbm_gbs"] * 1e9)
+    if t_c >= t_m:
+        roof = {"bound": bound_c, "achieved": flops / scan_s / 1e12, "peak": peak_c, "unit": unit_c,
+                "frac": (flops / scan_s / 1e12) / peak_c, "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_alg / scan_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (bytes_alg / scan_s / 1e9) / peaks["hbm_gbs"], "traffic": None}
+    roof["kernel"] = "scan_fp32_kernel" if best == "fp32" else "scan_tc_kernel"
+    roof["peak_source"] = peaks["source"] if bound_c != "alu" or roof["bound"] == "hbm" else \
+        f"152 SMs x 128 FFMA x 2 at {sm_mhz:.0f} MHz"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        ox, Qs, rows = oracle_sample(cfg, X, Q, P, assign, args, R["nprobe"], kp, args.cpu_sample)
+        t_cpu = time_oracle(ox, Qs, args, R["nprobe"], kp)
+        cpu = {"value": len(Qs) / t_cpu, "unit": "queries/s", "cores": min(oracle.num_threads(), len(Qs)),
+               "kind": "oracle", "sample": f"{len(Qs)} queries, nprobe {R['nprobe']}, {len(rows)} rows encoded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": R["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[best], "data": "synthetic",
+            "config": {"workload": args.workload, "N": len(X), "D": cfg["d"], "nlist": cfg["nlist"], "B": args.B,
+                       "nq": len(Q), "k": args.k, "rerank_k": kp, "nprobe": R["nprobe"], "precision": best,
+                       "recall@10": R["recall"], "l2": "inputs larger than L2 (codes > 129 MB)"},
+            "gcodes_per_s": R["work"]["pairs"] / (R["ms"] / 1e3) / 1e9,
+            "arms": {k: {"qps": v["qps"], "nprobe": v["nprobe"], "recall@10": v["recall"], "ms": v["ms"],
+                         "phases_ms": v["phases"], "pairs": v["work"]["pairs"]} for k, v in results.items()},
+            "recall_sweep": sweep,
+            "roofline": roof,
+            "e2e": {"value": len(Q) * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+                    "d2h_bytes_per_step": int(len(Q) * args.k * 12)},
+            "gpu_launches": R["launches"],
+            "clocks": R["clocks"],
+            "cpu_baseline": cpu,
+            "build_s": t_build, "data_s": t_data,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

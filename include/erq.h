@@ -1,0 +1,222 @@
+/*
+ * erq.h -- C ABI of the GB300 extended-RaBitQ search library (liberq.so).
+ *
+ * Extended RaBitQ (Gao et al., arXiv 2409.09913) quantizes each data vector
+ * o_r, after local centring o_r - c and a random orthogonal rotation
+ * o' = P^{-1}(o_r - c), to a B-bit-per-coordinate code ybar_u (Section 3.1,
+ * Algorithm 1) and estimates squared distances to a query q_r from the code,
+ * two per-vector floats and the rotated query (Eq. 3.3 with
+ * Eq. (eq:dis to ip)).  Combined with an IVF index (Section 4.1) this gives
+ * approximate nearest-neighbour search; the library adds exact re-ranking of
+ * the estimated top-k' and the gradient of the estimated scores with respect
+ * to the query.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are caller-owned CUDA device pointers unless the name
+ *    ends in _host.  The library never frees caller memory.
+ *  - Matrices are row-major and contiguous: X[N][D], P[D][D], Q[nq][D].
+ *  - D must be a multiple of 64 (the paper pads to a multiple of 64,
+ *    Section 5.1) and at most 4096; B is 1..8; N < 2^31.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Host-side validation errors return before any work is
+ *    queued.  Device-side errors (a wait that ran out, a bound that failed) are
+ *    recorded in a status word held by the index and returned by the next call
+ *    on that index or by erq_index_status().
+ *  - Every function returns an erq_status; on failure erq_last_error() gives a
+ *    thread-local message.
+ *  - A single erq_index may be used by one host thread at a time (it owns one
+ *    search workspace).
+ */
+#ifndef ERQ_H
+#define ERQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ERQ_OK = 0,
+    ERQ_EINVAL = 1,          /* bad argument (shape, range, null pointer)      */
+    ERQ_ENOMEM = 2,          /* device or host allocation failed               */
+    ERQ_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed    */
+    ERQ_ETIMEOUT = 4,        /* a bounded device-side wait ran out             */
+    ERQ_EUNSUPPORTED = 5,    /* valid request this build or GPU cannot serve   */
+    ERQ_EIO = 6              /* file error in save/load                        */
+} erq_status;
+
+/* Arithmetic of the code-by-query contraction in erq_search. */
+typedef enum {
+    ERQ_PREC_FP32 = 0,       /* CUDA-core FP32 FFMA scan (reference GPU path)           */
+    ERQ_PREC_FP16 = 1,       /* tcgen05 kind::f16: codes exact, rotated query in FP16,
+                                FP32 accumulation in tensor memory                       */
+    ERQ_PREC_FP8 = 2,        /* tcgen05 kind::f8f6f4: e4m3 query (per-query scale,
+                                hi+lo split), e4m3 codes, FP32 accumulation              */
+    ERQ_PREC_INT8 = 3        /* int8 tensor MMA: unavailable on sm_103a (ptxas rejects
+                                tcgen05 kind::i8) -> ERQ_EUNSUPPORTED                    */
+} erq_precision;
+
+typedef struct erq_index erq_index;   /* opaque; owns all of its device memory */
+
+/* Index construction parameters (Section 3.3 workflow, Section 4.1 IVF). */
+typedef struct {
+    int32_t B;                /* bits per coordinate, 1..8                               */
+    int32_t nlist;            /* IVF clusters; 1 = no IVF (one cluster, c = mean of X)   */
+    const float* P;           /* device [D][D] orthogonal matrix (the method's random
+                                 draw, Section 3.1 Eq. equ:rotation); required            */
+    const int32_t* assign;    /* device [N] cluster of each row, or NULL: the library runs
+                                 k-means (Lloyd) on the GPU to make one                   */
+    int32_t kmeans_iters;     /* Lloyd iterations when assign == NULL (default 10)        */
+    int32_t kmeans_sample;    /* rows sampled for k-means training, 0 = all              */
+    uint64_t seed;            /* k-means initialisation seed                             */
+    int32_t keep_raw;         /* keep the FP32 rows in the index (exact re-rank needs it)*/
+    int32_t reserved;
+} erq_build_params;
+
+/* Search parameters. */
+typedef struct {
+    int32_t k;                /* neighbours returned per query (>= 1)                    */
+    int32_t rerank_k;         /* k' >= k candidates (by estimate) re-ranked with exact
+                                 distances; 0 = return the estimated top-k (no re-rank)  */
+    int32_t nprobe;           /* clusters probed per query (1..nlist) when
+                                 nprobe_per_query is NULL                                */
+    int32_t precision;        /* erq_precision                                           */
+    const int32_t* nprobe_per_query; /* optional device [nq], each 1..nlist               */
+    const int32_t* probe;     /* optional device [nq][probe_stride] explicit probe lists
+                                 (distinct cluster ids; replaces the centroid search)    */
+    int32_t probe_stride;     /* row stride of `probe` (>= max nprobe)                   */
+    int32_t flags;            /* ERQ_SEARCH_TIMING: record per-phase CUDA events         */
+    int64_t* cand_ids;        /* optional device out [nq][kc], kc = max(k, rerank_k):
+                                 ids of the estimated top-kc, ascending by estimate      */
+    float* cand_est;          /* optional device out [nq][kc]: their estimates            */
+} erq_search_params;
+
+/* erq_search_params.flags */
+#define ERQ_SEARCH_TIMING 1
+
+/* Read-only description of an index. */
+typedef struct {
+    int64_t N;
+    int32_t D, B, nlist, keep_raw;
+    int64_t max_list;         /* rows in the largest cluster                             */
+    int64_t device_bytes;     /* device memory held by the index                         */
+} erq_index_info;
+
+/* Fields copied out by erq_index_export (cluster-major order unless noted). */
+typedef enum {
+    ERQ_FIELD_CENTROIDS = 0,      /* float  [nlist][D]  c_j (means of their rows)          */
+    ERQ_FIELD_ROT_CENTROIDS = 1,  /* float  [nlist][D]  c'_j = P^T c_j (FP64 accumulated)  */
+    ERQ_FIELD_LIST_OFFSETS = 2,   /* int64  [nlist+1]   first stored row of each cluster   */
+    ERQ_FIELD_LIST_IDS = 3,       /* int64  [N]         original row id of each stored row */
+    ERQ_FIELD_CODES = 4,          /* uint8  [N][D]      ybar_u, one byte per coordinate    */
+    ERQ_FIELD_F_ADD = 5,          /* float  [N]         ||o'||^2                           */
+    ERQ_FIELD_F_RES = 6,          /* float  [N]         -2 ||o'||^2 / <ybar, |o'|>          */
+    ERQ_FIELD_P = 7,              /* float  [D][D]                                         */
+    ERQ_FIELD_RAW = 8             /* float  [N][D] original order (keep_raw only)          */
+} erq_field;
+
+const char* erq_version(void);
+/* Message of the last failed call on this host thread ("" if none). */
+const char* erq_last_error(void);
+
+/* Build an IVF + extended-RaBitQ index from X (device [N][D]) -- Section 3.3
+ * workflow and Section 4.1:
+ *   c_j  = mean of the rows of cluster j (FP64 sum in ascending row id, rounded
+ *          once to FP32; Section 5.1 local centring),
+ *   o'   = fl32(P^T fl32(o_r - c)) accumulated in FP64 in ascending index,
+ *   code = Algorithm 1 on o' (FP64 comparisons; bit-identical to a sequential
+ *          FP64 implementation),
+ *   plus the per-vector factors (Section 5.1 metrics paragraph).
+ * X and P are read during the call only.  *out receives a new index owned by the
+ * caller (free with erq_free_index).  The call synchronises `stream` before it
+ * returns.  Errors: EINVAL (shape/B/nlist/assign range), ENOMEM, ECUDA. */
+erq_status erq_build_index(const float* X, int64_t N, int32_t D, const erq_build_params* params,
+                           void* stream, erq_index** out);
+
+void erq_free_index(erq_index* index);
+erq_status erq_index_info_get(const erq_index* index, erq_index_info* info);
+/* Synchronise `stream` and return (then clear) the device status word. */
+erq_status erq_index_status(erq_index* index, void* stream);
+
+/* out[n][D] = X[n][D] * P, i.e. each row becomes P^T x = P^{-1} x (Section 2.2,
+ * Eq. sec 2 qprime; Section 3.3 workflow).  accurate != 0: FP64 accumulation in
+ * ascending index, one rounding to FP32 (index time); accurate == 0: FP32
+ * accumulation (query time).  Errors: EINVAL, ECUDA. */
+erq_status erq_rotate(const float* X, int64_t n, int32_t D, const float* P, float* out, int32_t accurate,
+                      void* stream);
+
+/* Algorithm 1 (Section 3.1) on each row of Rrot (device [n][D], rotated
+ * residuals o', any scale).  Writes codes[n][D] (ybar_u, one byte per
+ * coordinate), f_add[n] = fl32(||o'||^2), f_res[n] = fl32(-2 ||o'||^2 / ip*) with
+ * ip* = <ybar, |o'|> at the optimum (0 for o' = 0), and optionally stats[n][2] =
+ * (ip*, ||ybar||^2) in FP64.  Critical values are visited in ascending exact
+ * rational order, ties by coordinate; <y_cur,o'> accumulates in FP64 in that
+ * order; the first state of maximal <y/||y||, o'> wins.
+ * Errors: EINVAL (B, D), ECUDA. */
+erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add,
+                      float* f_res, double* stats, void* stream);
+
+/* Batched IVF search (Section 4.1) for Q (device [nq][D]):
+ *   q' = P^T q_r (once per query), probe the nprobe nearest centroids (ties by
+ *   lower id), estimate every candidate of the probed clusters with Eq. 3.3 +
+ *   Eq. (eq:dis to ip), keep the k' = max(k, rerank_k) smallest estimates (ties by
+ *   lower id), and -- when rerank_k > 0 -- re-rank them by exact squared distance.
+ * ids[nq][k] (int64, -1 where fewer than k candidates exist) and dists[nq][k]
+ * (FP32: exact squared distances after re-rank, estimates otherwise).
+ * Errors: EINVAL (k, nprobe, probe ids, rerank without raw rows), EUNSUPPORTED
+ * (precision), ENOMEM (workspace), ECUDA, ETIMEOUT (device status). */
+erq_status erq_search(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params,
+                      int64_t* ids, float* dists, void* stream);
+
+/* The same search from HOST buffers: Q_host[nq][D] is copied to the device,
+ * searched, and ids_host/dists_host are copied back before the call returns.
+ * Pinned (page-locked) host memory gives asynchronous copies. */
+erq_status erq_search_host(erq_index* index, const float* Q_host, int64_t nq, const erq_search_params* params,
+                           int64_t* ids_host, float* dists_host, void* stream);
+
+/* Estimated squared distance (Eq. 3.3 + Eq. eq:dis to ip, FP32 path) of query i
+ * to each original id in ids[i][0..nc-1]; ids < 0 give NaN.  Q device [nq][D],
+ * ids device [nq][nc], est device [nq][nc].  Errors: EINVAL, ECUDA. */
+erq_status erq_estimate(erq_index* index, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                        float* est, void* stream);
+
+/* Gradient of sum_j grad_scores[i][j] * est(q_i, ids[i][j]) with respect to the
+ * raw query q_i, codes and ids fixed.  From Eq. (eq:dis to ip) and Eq. 3.3:
+ *   d est / d q_r = 2 (q_r - c) + f_res * P ybar,  ybar = ybar_u - (2^B-1)/2,
+ * evaluated as grad_Q = 2 (G q_r - sum_j g_j c_j) + (sum_j g_j f_res,j ybar_j) P^T
+ * (a gather over the codes, then one GEMM with P).  grad_Q device [nq][D] is
+ * overwritten.  ids < 0 contribute nothing.  Errors: EINVAL, ENOMEM, ECUDA. */
+erq_status erq_search_backward(erq_index* index, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                               const float* grad_scores, float* grad_Q, void* stream);
+
+/* Copy one field of the index to host memory (dst_host must hold dst_bytes).
+ * Errors: EINVAL (field, size), ECUDA. */
+erq_status erq_index_export(const erq_index* index, int32_t field, void* dst_host, int64_t dst_bytes);
+
+/* Versioned flat file holding every field; load rebuilds the device index. */
+erq_status erq_index_save(const erq_index* index, const char* path);
+erq_status erq_index_load(const char* path, void* stream, erq_index** out);
+
+/* Diagnostics.
+ * erq_search_timing: device time in milliseconds of the phases of the last
+ * erq_search on this index that ran with ERQ_SEARCH_TIMING, measured with CUDA
+ * events on the search stream: ms[0] query rotation, ms[1] centroid probe,
+ * ms[2] planning (probe inversion, pair scalars, one host read-back),
+ * ms[3] code scan (estimator + per-item top-k'), ms[4] merge, ms[5] re-rank.
+ * Synchronises those events.  n must be >= 6.  Errors: EINVAL (no timed search).
+ * erq_kernel_launches: number of kernels this library has launched in the
+ * process so far (all entry points, all threads).
+ * erq_search_stats: work of the last erq_search on this index: out[0] estimated
+ * (query, candidate) pairs, out[1] rows of the distinct probed clusters (codes
+ * that had to be read at least once), out[2] work items, out[3] per-(query,
+ * item) candidate lists.  n must be >= 4. */
+erq_status erq_search_timing(const erq_index* index, float* ms, int32_t n);
+uint64_t erq_kernel_launches(void);
+erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ERQ_H */

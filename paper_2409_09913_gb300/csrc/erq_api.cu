@@ -1,0 +1,758 @@
+// C ABI of liberq.so: argument validation, index lifecycle, and the order of
+// kernel launches for build / encode / search / estimate / backward.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "erq_kernels.cuh"
+#include "erq_search.cuh"
+
+namespace erq {
+
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_err = msg; }
+erq_status fail(erq_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+erq_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ERQ_ENOMEM : ERQ_ECUDA;
+}
+
+// k-means helpers (k_linalg.cu)
+cudaError_t launch_row_argmin(const float* V, int64_t rows, int ncols, int32_t* out, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* X, const int64_t* idx, int64_t n, int D, float* out, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+cudaError_t launch_strided_ids(int64_t* out, int64_t n, int64_t N, uint64_t seed, cudaStream_t s);
+// k_scan_tc.cu
+erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s);
+bool tc_available(int precision, int D, int kp);
+cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
+
+namespace {
+
+template <typename T>
+erq_status dalloc(T** p, size_t count, int64_t* tally = nullptr) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if (tally) *tally += (int64_t)(count * sizeof(T));
+    return ERQ_OK;
+}
+
+void free_index_arrays(erq_index* ix) {
+    void* ptrs[] = {ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
+                    ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
+                    ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (ix->pinned) cudaFreeHost(ix->pinned);
+    for (cudaEvent_t& e : ix->ev)
+        if (e) cudaEventDestroy(e);
+    delete ix->host_list_off;
+}
+
+// Bump allocator over a device workspace.
+struct Carver {
+    char* base;
+    size_t off = 0, cap;
+    Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) / 256 * 256;
+        T* p = (T*)(base ? base + off : nullptr);
+        off += std::max<size_t>(count, 1) * sizeof(T);
+        return p;
+    }
+};
+
+erq_status ensure_ws(void** ws, size_t* have, size_t need) {
+    if (*have >= need) return ERQ_OK;
+    if (*ws) cudaFree(*ws);
+    *ws = nullptr;
+    *have = 0;
+    const size_t bytes = need + need / 8 + (1 << 20);
+    cudaError_t e = cudaMalloc(ws, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace cudaMalloc");
+    *have = bytes;
+    return ERQ_OK;
+}
+
+erq_status check_status(erq_index* ix, cudaStream_t s) {
+    uint32_t st = 0;
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(&st, ix->status, 4, cudaMemcpyDeviceToHost, s));
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        ERQ_CHECK_CUDA(cudaMemsetAsync(ix->status, 0, 4, s));
+        ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (st & kStatusTimeout) return fail(ERQ_ETIMEOUT, "a device-side wait ran out of iterations");
+        if (st & kStatusRange)
+            return fail(ERQ_EUNSUPPORTED, "a rotated residual has a non-zero coordinate below 2^-118 of its largest");
+        return fail(ERQ_EINVAL, "a device-side bound check failed (cluster id, probe id, nprobe or row id out of range)");
+    }
+    return ERQ_OK;
+}
+
+bool valid_d(int32_t D) { return D >= 64 && D <= 4096 && D % 64 == 0; }
+
+}  // namespace
+}  // namespace erq
+
+using namespace erq;
+
+extern "C" const char* erq_version(void) { return "erq 0.1 (sm_103a)"; }
+extern "C" const char* erq_last_error(void) { return g_err.c_str(); }
+
+extern "C" void erq_free_index(erq_index* index) {
+    if (!index) return;
+    free_index_arrays(index);
+    delete index;
+}
+
+extern "C" erq_status erq_index_info_get(const erq_index* ix, erq_index_info* info) {
+    if (!ix || !info) return fail(ERQ_EINVAL, "null argument");
+    info->N = ix->N;
+    info->D = ix->D;
+    info->B = ix->B;
+    info->nlist = ix->nlist;
+    info->keep_raw = ix->keep_raw;
+    info->max_list = ix->max_list;
+    info->device_bytes = ix->device_bytes;
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_index_status(erq_index* ix, void* stream) {
+    if (!ix) return fail(ERQ_EINVAL, "null index");
+    return check_status(ix, (cudaStream_t)stream);
+}
+
+extern "C" erq_status erq_rotate(const float* X, int64_t n, int32_t D, const float* P, float* out, int32_t accurate,
+                      void* stream) {
+    if (n < 0 || !valid_d(D)) return fail(ERQ_EINVAL, "erq_rotate: D must be a multiple of 64 in [64, 4096], n >= 0");
+    if (n == 0) return ERQ_OK;
+    if (!X || !P || !out) return fail(ERQ_EINVAL, "erq_rotate: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = accurate ? launch_rotate_fp64(X, nullptr, nullptr, nullptr, P, out, n, D, s)
+                             : launch_sgemm(false, X, P, out, n, D, D, 1.f, nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "erq_rotate launch");
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add, float* f_res,
+                      double* stats, void* stream) {
+    if (n < 0 || !valid_d(D)) return fail(ERQ_EINVAL, "erq_encode: D must be a multiple of 64 in [64, 4096], n >= 0");
+    if (B < 1 || B > 8) return fail(ERQ_EINVAL, "erq_encode: B must be in [1, 8]");
+    if (n == 0) return ERQ_OK;
+    if (!Rrot || !codes || !f_add || !f_res) return fail(ERQ_EINVAL, "erq_encode: null pointer");
+    uint32_t* status = nullptr;
+    ERQ_CHECK_CUDA(cudaMalloc(&status, 4));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(status, 0, 4, s);
+    cudaError_t e = launch_encode(Rrot, n, D, B, codes, f_add, f_res, stats, status, s);
+    if (e != cudaSuccess) {
+        cudaFree(status);
+        return cuda_fail(e, "erq_encode launch");
+    }
+    uint32_t st = 0;
+    cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    cudaFree(status);
+    if (e != cudaSuccess) return cuda_fail(e, "erq_encode");
+    if (st & kStatusRange)
+        return fail(ERQ_EUNSUPPORTED, "erq_encode: a row has a non-zero coordinate below 2^-118 of its largest");
+    if (st) return fail(ERQ_EINVAL, "erq_encode: window bound violated (non-finite input?)");
+    return ERQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Build
+// ---------------------------------------------------------------------------
+static erq_status build_kmeans(const float* X, int64_t N, int D, int nlist, const erq_build_params* p, int32_t* assign,
+                               erq_index* ix, cudaStream_t s) {
+    const int iters = p->kmeans_iters > 0 ? p->kmeans_iters : 10;
+    int64_t S = p->kmeans_sample > 0 ? std::min<int64_t>(p->kmeans_sample, N) : N;
+    if (S < nlist) S = std::min<int64_t>(N, nlist);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(512ll << 20) / (4ll * nlist)));
+    // workspace: sample rows, their norms, ids, assignment, distance chunk, grouping
+    size_t need = 0;
+    {
+        Carver cv(nullptr, 0);
+        cv.take<float>((size_t)S * D);
+        cv.take<float>(S);
+        cv.take<int64_t>(S);
+        cv.take<int32_t>(S);
+        cv.take<float>((size_t)chunk * nlist);
+        cv.take<int64_t>(nlist + 1);
+        cv.take<int64_t>(S);
+        cv.take<char>(group_scratch_bytes(S, nlist));
+        cv.take<float>(N);
+        need = cv.off;
+    }
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, need));
+    Carver cv(ix->ws, ix->ws_bytes);
+    float* Xs = cv.take<float>((size_t)S * D);
+    float* xn = cv.take<float>(S);
+    int64_t* sid = cv.take<int64_t>(S);
+    int32_t* sa = cv.take<int32_t>(S);
+    float* dist = cv.take<float>((size_t)chunk * nlist);
+    int64_t* soff = cv.take<int64_t>(nlist + 1);
+    int64_t* sids = cv.take<int64_t>(S);
+    const size_t gbytes = group_scratch_bytes(S, nlist);
+    void* gscr = cv.take<char>(gbytes);
+    float* xall = cv.take<float>(N);
+    cudaError_t e;
+    if ((e = launch_strided_ids(sid, S, N, p->seed, s)) != cudaSuccess) return cuda_fail(e, "kmeans ids");
+    if ((e = launch_gather_rows(X, sid, S, D, Xs, s)) != cudaSuccess) return cuda_fail(e, "kmeans gather");
+    if ((e = launch_row_sqnorm(Xs, S, D, xn, s)) != cudaSuccess) return cuda_fail(e, "kmeans norms");
+    // initial centroids: nlist evenly spaced sample rows
+    std::vector<int64_t> init(nlist);
+    for (int j = 0; j < nlist; ++j) init[j] = (int64_t)((double)j * (double)S / nlist);
+    int64_t* init_d = sids;  // temporarily
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(init_d, init.data(), sizeof(int64_t) * nlist, cudaMemcpyHostToDevice, s));
+    if ((e = launch_gather_rows(Xs, init_d, nlist, D, ix->C, s)) != cudaSuccess) return cuda_fail(e, "kmeans init");
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (int it = 0; it < iters; ++it) {
+        if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return cuda_fail(e, "kmeans cn");
+        for (int64_t r0 = 0; r0 < S; r0 += chunk) {
+            const int64_t m = std::min(chunk, S - r0);
+            if ((e = launch_sqdist(Xs + r0 * D, xn + r0, ix->C, ix->cnorm2, dist, m, nlist, D, s)) != cudaSuccess)
+                return cuda_fail(e, "kmeans dist");
+            if ((e = launch_row_argmin(dist, m, nlist, sa + r0, s)) != cudaSuccess) return cuda_fail(e, "kmeans argmin");
+        }
+        if ((e = launch_group(sa, S, nlist, soff, sids, nullptr, nullptr, gscr, gbytes, ix->status, s)) != cudaSuccess)
+            return cuda_fail(e, "kmeans group");
+        if ((e = launch_centroids(Xs, soff, sids, nlist, D, ix->C, 1, s)) != cudaSuccess)
+            return cuda_fail(e, "kmeans centroids");
+    }
+    // final assignment of every row
+    if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return cuda_fail(e, "kmeans cn");
+    if ((e = launch_row_sqnorm(X, N, D, xall, s)) != cudaSuccess) return cuda_fail(e, "kmeans xn");
+    for (int64_t r0 = 0; r0 < N; r0 += chunk) {
+        const int64_t m = std::min(chunk, N - r0);
+        if ((e = launch_sqdist(X + r0 * D, xall + r0, ix->C, ix->cnorm2, dist, m, nlist, D, s)) != cudaSuccess)
+            return cuda_fail(e, "kmeans dist");
+        if ((e = launch_row_argmin(dist, m, nlist, assign + r0, s)) != cudaSuccess) return cuda_fail(e, "kmeans argmin");
+    }
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, const erq_build_params* p, void* stream,
+                                      erq_index** out) {
+    if (!out) return fail(ERQ_EINVAL, "erq_build_index: out is null");
+    *out = nullptr;
+    if (!p || !X || !p->P) return fail(ERQ_EINVAL, "erq_build_index: X, params and params->P are required");
+    if (N < 1 || N >= (1ll << 31)) return fail(ERQ_EINVAL, "erq_build_index: N must be in [1, 2^31)");
+    if (!valid_d(D)) return fail(ERQ_EINVAL, "erq_build_index: D must be a multiple of 64 in [64, 4096]");
+    if (p->B < 1 || p->B > 8) return fail(ERQ_EINVAL, "erq_build_index: B must be in [1, 8]");
+    if (p->nlist < 1 || p->nlist > 65536 || p->nlist > N)
+        return fail(ERQ_EINVAL, "erq_build_index: nlist must be in [1, min(N, 65536)]");
+    cudaStream_t s = (cudaStream_t)stream;
+    erq_index* ix = new erq_index();
+    ix->N = N;
+    ix->D = D;
+    ix->B = p->B;
+    ix->nlist = p->nlist;
+    ix->keep_raw = p->keep_raw ? 1 : 0;
+    ix->host_list_off = new std::vector<int64_t>();
+    auto bail = [&](erq_status st) {
+        cudaStreamSynchronize(s);
+        erq_free_index(ix);
+        return st;
+    };
+    const int nlist = p->nlist;
+    erq_status st;
+#define ALLOC(ptr, cnt)                                         \
+    if ((st = dalloc(&ix->ptr, (cnt), &ix->device_bytes)) != ERQ_OK) return bail(st);
+    ALLOC(P, (size_t)D * D);
+    ALLOC(C, (size_t)nlist * D);
+    ALLOC(Cp, (size_t)nlist * D);
+    ALLOC(cnorm2, nlist);
+    ALLOC(list_off, nlist + 1);
+    ALLOC(list_ids, N);
+    ALLOC(row_of, N);
+    ALLOC(cl_of_row, N);
+    ALLOC(codes, (size_t)N * D);
+    ALLOC(f_add, N);
+    ALLOC(f_res, N);
+    ALLOC(g_const, N);
+    ALLOC(status, 1);
+    if (ix->keep_raw) ALLOC(X, (size_t)N * D);
+#undef ALLOC
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ix->status, 0, 4, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemcpyAsync(ix->P, p->P, sizeof(float) * D * D, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy P"));
+    if (ix->keep_raw &&
+        (e = cudaMemcpyAsync(ix->X, X, sizeof(float) * (size_t)N * D, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy X"));
+    // --- assignment
+    int32_t* assign = nullptr;
+    if ((st = dalloc(&assign, N)) != ERQ_OK) return bail(st);
+    auto bail2 = [&](erq_status st2) {
+        cudaStreamSynchronize(s);
+        cudaFree(assign);
+        return bail(st2);
+    };
+    if (nlist == 1) {
+        if ((e = launch_fill_i32(assign, N, 0, s)) != cudaSuccess) return bail2(cuda_fail(e, "fill"));
+    } else if (p->assign) {
+        if ((e = cudaMemcpyAsync(assign, p->assign, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return bail2(cuda_fail(e, "copy assign"));
+    } else {
+        if ((st = build_kmeans(X, N, D, nlist, p, assign, ix, s)) != ERQ_OK) return bail2(st);
+    }
+    // --- group rows by cluster, centroids, rotated centroids
+    {
+        const size_t gbytes = group_scratch_bytes(N, nlist);
+        if ((st = ensure_ws(&ix->ws, &ix->ws_bytes, gbytes)) != ERQ_OK) return bail2(st);
+        if ((e = launch_group(assign, N, nlist, ix->list_off, ix->list_ids, ix->row_of, ix->cl_of_row, ix->ws,
+                              ix->ws_bytes, ix->status, s)) != cudaSuccess)
+            return bail2(cuda_fail(e, "group"));
+        if ((st = check_status(ix, s)) != ERQ_OK)
+            return bail2(fail(ERQ_EINVAL, "erq_build_index: assign holds a cluster id outside [0, nlist)"));
+    }
+    if ((e = launch_centroids(X, ix->list_off, ix->list_ids, nlist, D, ix->C, 0, s)) != cudaSuccess)
+        return bail2(cuda_fail(e, "centroids"));
+    if ((e = launch_rotate_fp64(ix->C, nullptr, nullptr, nullptr, ix->P, ix->Cp, nlist, D, s)) != cudaSuccess)
+        return bail2(cuda_fail(e, "rotate centroids"));
+    if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return bail2(cuda_fail(e, "cnorm"));
+    // --- rotate residuals and encode, in chunks of rows
+    {
+        const int64_t chunk = std::min<int64_t>(N, std::max<int64_t>(4096, (int64_t)(1ll << 30) / (4ll * D)));
+        if ((st = ensure_ws(&ix->ws, &ix->ws_bytes, (size_t)chunk * D * 4)) != ERQ_OK) return bail2(st);
+        float* R = (float*)ix->ws;
+        for (int64_t r0 = 0; r0 < N; r0 += chunk) {
+            const int64_t m = std::min(chunk, N - r0);
+            if ((e = launch_rotate_fp64(X, ix->list_ids + r0, ix->C, ix->cl_of_row + r0, ix->P, R, m, D, s)) !=
+                cudaSuccess)
+                return bail2(cuda_fail(e, "rotate residuals"));
+            if ((e = launch_encode(R, m, D, ix->B, ix->codes + r0 * D, ix->f_add + r0, ix->f_res + r0, nullptr,
+                                   ix->status, s)) != cudaSuccess)
+                return bail2(cuda_fail(e, "encode"));
+        }
+    }
+    if ((e = launch_gconst(ix->codes, ix->f_add, ix->f_res, ix->Cp, ix->cl_of_row, N, D, ix->B, ix->g_const, s)) !=
+        cudaSuccess)
+        return bail2(cuda_fail(e, "gconst"));
+    ix->host_list_off->resize(nlist + 1);
+    if ((e = cudaMemcpyAsync(ix->host_list_off->data(), ix->list_off, sizeof(int64_t) * (nlist + 1),
+                             cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return bail2(cuda_fail(e, "list_off"));
+    if ((st = check_status(ix, s)) != ERQ_OK) return bail2(st);
+    cudaFree(assign);
+    int64_t mx = 0;
+    for (int j = 0; j < nlist; ++j) mx = std::max(mx, (*ix->host_list_off)[j + 1] - (*ix->host_list_off)[j]);
+    ix->max_list = mx;
+    *out = ix;
+    return ERQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Search
+// ---------------------------------------------------------------------------
+static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p, int64_t* ids,
+                              float* dists, cudaStream_t s) {
+    const int D = ix->D, nlist = ix->nlist;
+    const int k = p->k;
+    const int kp = std::max(p->k, p->rerank_k);
+    const bool do_rerank = p->rerank_k > 0;
+    int maxp = p->probe ? p->nprobe : (nlist == 1 ? 1 : p->nprobe);
+    const bool explicit_probe = p->probe != nullptr;
+    const int prec = p->precision;
+    // ---- phase A workspace (sizes known on the host)
+    const int QT = prec == ERQ_PREC_FP32 ? 64 : 128;   // queries per work item of the scan kernel
+    int RR = 4096;
+    Carver plan(nullptr, 0);
+    auto layout = [&](Carver& cv, bool carve, void** slots) {
+        int i = 0;
+        auto T = [&](auto* dummy, size_t n) {
+            using TT = std::remove_pointer_t<decltype(dummy)>;
+            void* ptr = cv.take<TT>(n);
+            if (carve) slots[i] = ptr;
+            ++i;
+        };
+        T((float*)nullptr, (size_t)nq * D);                              // 0 Qrot
+        T((float*)nullptr, nq);                                          // 1 qn
+        T((float*)nullptr, (!explicit_probe && nlist > 1) ? (size_t)nq * nlist : 1);  // 2 sqd
+        T((int32_t*)nullptr, (size_t)nq * maxp);                         // 3 probe (computed)
+        T((int32_t*)nullptr, nq);                                        // 4 npr
+        T((float*)nullptr, (size_t)nq * maxp);                           // 5 dqc
+        T((int32_t*)nullptr, (size_t)nq * maxp);                         // 6 probe_c
+        T((int32_t*)nullptr, (size_t)nq * maxp);                         // 7 slot_nr
+        T((int32_t*)nullptr, (size_t)nq * maxp);                         // 8 slot_off
+        T((int64_t*)nullptr, nq);                                        // 9 qtot
+        T((int64_t*)nullptr, nq + 1);                                    // 10 qbase
+        T((int32_t*)nullptr, nlist);                                     // 11 cnt_c
+        T((int32_t*)nullptr, nlist);                                     // 12 pos_c
+        T((int64_t*)nullptr, nlist);                                     // 13 cnt64
+        T((int64_t*)nullptr, nlist);                                     // 14 items_c
+        T((int64_t*)nullptr, nlist + 1);                                 // 15 qoff
+        T((int64_t*)nullptr, nlist + 1);                                 // 16 item_off
+        T((int64_t*)nullptr, (size_t)nq * maxp);                         // 17 qlist
+        T((uint64_t*)nullptr, (size_t)nq * kp);                          // 18 cand
+        T((uint64_t*)nullptr, 2);                                        // 19 stats
+        T((__half*)nullptr, prec == ERQ_PREC_FP32 ? 1 : (size_t)nq * D); // 20 Qh
+    };
+    void* sl[21];
+    layout(plan, false, sl);
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
+    Carver cv(ix->ws, ix->ws_bytes);
+    layout(cv, true, sl);
+    float* Qrot = (float*)sl[0];
+    float* qn = (float*)sl[1];
+    float* sqd = (float*)sl[2];
+    int32_t* probe = (int32_t*)sl[3];
+    int32_t* npr = (int32_t*)sl[4];
+    float* dqc = (float*)sl[5];
+    PlanArgs pa;
+    pa.probe_c = (int32_t*)sl[6];
+    pa.slot_nr = (int32_t*)sl[7];
+    pa.slot_off = (int32_t*)sl[8];
+    pa.qtot = (int64_t*)sl[9];
+    pa.qbase = (int64_t*)sl[10];
+    pa.cnt_c = (int32_t*)sl[11];
+    pa.pos_c = (int32_t*)sl[12];
+    pa.cnt64 = (int64_t*)sl[13];
+    pa.items_c = (int64_t*)sl[14];
+    pa.qoff = (int64_t*)sl[15];
+    pa.item_off = (int64_t*)sl[16];
+    pa.qlist = (int64_t*)sl[17];
+    uint64_t* cand = (uint64_t*)sl[18];
+    pa.stats = (unsigned long long*)sl[19];
+    cudaError_t e;
+    const bool timed = (p->flags & ERQ_SEARCH_TIMING) != 0;
+    ix->timed = 0;
+    if (timed && !ix->ev[0])
+        for (cudaEvent_t& ev : ix->ev) ERQ_CHECK_CUDA(cudaEventCreate(&ev));
+    auto mark = [&](int i) -> erq_status {
+        if (timed) ERQ_CHECK_CUDA(cudaEventRecord(ix->ev[i], s));
+        return ERQ_OK;
+    };
+    ERQ_TRY(mark(0));
+    // ---- q' = P^T q_r
+    if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, D, D, 1.f, nullptr, s)) != cudaSuccess)
+        return cuda_fail(e, "query rotation");
+    if (prec != ERQ_PREC_FP32 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
+        return cuda_fail(e, "query half");
+    ERQ_TRY(mark(1));
+    // ---- probe
+    const int32_t* probe_use = probe;
+    int64_t probe_stride = maxp;
+    if (explicit_probe) {
+        probe_use = p->probe;
+        probe_stride = p->probe_stride;
+    } else if (nlist == 1) {
+        if ((e = launch_fill_i32(probe, nq, 0, s)) != cudaSuccess) return cuda_fail(e, "probe fill");
+    } else {
+        if ((e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
+        if ((e = launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s)) != cudaSuccess)
+            return cuda_fail(e, "centroid distances");
+        if ((e = launch_row_topk(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s)) != cudaSuccess)
+            return cuda_fail(e, "probe select");
+    }
+    ERQ_TRY(mark(2));
+    // ---- plan
+    pa.probe = probe_use;
+    pa.probe_stride = probe_stride;
+    pa.npr_in = p->nprobe_per_query;
+    pa.npr_uniform = maxp;
+    pa.nq = nq;
+    pa.maxp = maxp;
+    pa.nlist = nlist;
+    pa.QT = QT;
+    pa.RR = RR;
+    pa.list_off = ix->list_off;
+    pa.npr = npr;
+    pa.status = ix->status;
+    if ((e = launch_plan(pa, s)) != cudaSuccess) return cuda_fail(e, "plan");
+    // dqc needs the validated probe ids
+    if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
+    int64_t tot[2] = {0, 0};
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[0], pa.qbase + nq, 8, cudaMemcpyDeviceToHost, s));
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + nlist, 8, cudaMemcpyDeviceToHost, s));
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->last_stats, pa.stats, 16, cudaMemcpyDeviceToHost, s));
+    ERQ_TRY(check_status(ix, s));
+    const int64_t Ltot = tot[0], nitems = tot[1];
+    ix->last_stats[2] = nitems;
+    ix->last_stats[3] = Ltot;
+    // ---- phase B workspace
+    Carver pb(nullptr, 0);
+    pb.take<int4>(nitems);
+    pb.take<uint64_t>((size_t)Ltot * kp);
+    pb.take<int32_t>(Ltot);
+    pb.take<int64_t>(1);
+    ERQ_TRY(ensure_ws(&ix->ws_b, &ix->ws_b_bytes, pb.off));
+    Carver cb(ix->ws_b, ix->ws_b_bytes);
+    int4* items = cb.take<int4>(nitems);
+    uint64_t* inter = cb.take<uint64_t>((size_t)Ltot * kp);
+    int32_t* inter_cnt = cb.take<int32_t>(Ltot);
+    int64_t* n_items_d = cb.take<int64_t>(1);
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + nlist, 8, cudaMemcpyDeviceToDevice, s));
+    if (Ltot > 0) ERQ_CHECK_CUDA(cudaMemsetAsync(inter_cnt, 0, sizeof(int32_t) * Ltot, s));
+    if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
+    ERQ_TRY(mark(3));
+    // ---- scan
+    ScanLaunch L;
+    L.Qrot = Qrot; L.Qh = sl[20]; L.status = ix->status; L.N = ix->N; L.codes = ix->codes; L.g_const = ix->g_const; L.f_res = ix->f_res; L.list_off = ix->list_off;
+    L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
+    L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
+    L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    L.grid = (int)std::min<int64_t>(nitems, (int64_t)sms * (prec == ERQ_PREC_FP32 ? 2 : 1));
+    if (prec == ERQ_PREC_FP32) {
+        if ((e = launch_scan_fp32(L, s)) != cudaSuccess) return cuda_fail(e, "scan fp32");
+    } else {
+        ERQ_TRY(scan_tc(L, prec, s));
+    }
+    ERQ_TRY(mark(4));
+    // ---- merge, re-rank
+    if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, cand, s)) != cudaSuccess) return cuda_fail(e, "merge");
+    ERQ_TRY(mark(5));
+    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ids, dists, p->cand_ids, p->cand_est,
+                           s)) != cudaSuccess)
+        return cuda_fail(e, "rerank");
+    ERQ_TRY(mark(6));
+    if (timed) ix->timed = 1;
+    return ERQ_OK;
+}
+
+static erq_status validate_search(const erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p,
+                                  const void* ids, const void* dists) {
+    if (!ix || !p) return fail(ERQ_EINVAL, "erq_search: null index or params");
+    if (nq < 0) return fail(ERQ_EINVAL, "erq_search: nq < 0");
+    if (nq > 0 && (!Q || !ids || !dists)) return fail(ERQ_EINVAL, "erq_search: null Q/ids/dists");
+    if (p->k < 1) return fail(ERQ_EINVAL, "erq_search: k must be >= 1");
+    if (p->rerank_k != 0 && p->rerank_k < p->k) return fail(ERQ_EINVAL, "erq_search: rerank_k must be 0 or >= k");
+    const int kp = std::max(p->k, p->rerank_k);
+    if (kp > 1024) return fail(ERQ_EUNSUPPORTED, "erq_search: max(k, rerank_k) > 1024");
+    if (p->rerank_k > 0 && !ix->keep_raw) return fail(ERQ_EINVAL, "erq_search: re-ranking needs keep_raw");
+    if (p->probe) {
+        if (p->nprobe < 1 || p->probe_stride < p->nprobe)
+            return fail(ERQ_EINVAL, "erq_search: explicit probe needs nprobe >= 1 and probe_stride >= nprobe");
+        if (p->nprobe > ix->nlist) return fail(ERQ_EINVAL, "erq_search: nprobe > nlist");
+    } else if (ix->nlist > 1 && (p->nprobe < 1 || p->nprobe > ix->nlist)) {
+        return fail(ERQ_EINVAL, "erq_search: nprobe must be in [1, nlist]");
+    }
+    if (p->precision == ERQ_PREC_INT8)
+        return fail(ERQ_EUNSUPPORTED, "erq_search: int8 tensor MMA (tcgen05 kind::i8) is not available on sm_103a");
+    if (p->precision < 0 || p->precision > ERQ_PREC_INT8) return fail(ERQ_EINVAL, "erq_search: unknown precision");
+    if (p->precision != ERQ_PREC_FP32 && !tc_available(p->precision, ix->D, kp))
+        return fail(ERQ_EUNSUPPORTED, "erq_search: tensor-core path unavailable for this D / k'");
+    if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
+        return fail(ERQ_EUNSUPPORTED, "erq_search: k' too large for the FP32 scan");
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_search(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p, int64_t* ids,
+                                 float* dists, void* stream) {
+    ERQ_TRY(validate_search(ix, Q, nq, p, ids, dists));
+    if (nq == 0) return ERQ_OK;
+    return search_impl(ix, Q, nq, p, ids, dists, (cudaStream_t)stream);
+}
+
+extern "C" erq_status erq_search_host(erq_index* ix, const float* Q_host, int64_t nq, const erq_search_params* p,
+                                      int64_t* ids_host, float* dists_host, void* stream) {
+    ERQ_TRY(validate_search(ix, Q_host, nq, p, ids_host, dists_host));
+    if (nq == 0) return ERQ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t qb = (size_t)nq * ix->D * 4, ib = (size_t)nq * p->k * 8, db = (size_t)nq * p->k * 4;
+    ERQ_TRY(ensure_ws(&ix->io, &ix->io_bytes, qb + ib + db + 1024));
+    char* base = (char*)ix->io;
+    float* Qd = (float*)base;
+    int64_t* idd = (int64_t*)(base + (qb + 255) / 256 * 256);
+    float* dd = (float*)((char*)idd + (ib + 255) / 256 * 256);
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(Qd, Q_host, qb, cudaMemcpyHostToDevice, s));
+    ERQ_TRY(search_impl(ix, Qd, nq, p, idd, dd, s));
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(ids_host, idd, ib, cudaMemcpyDeviceToHost, s));
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(dists_host, dd, db, cudaMemcpyDeviceToHost, s));
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_estimate(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                   float* est, void* stream) {
+    if (!ix || nq < 0 || nc < 0) return fail(ERQ_EINVAL, "erq_estimate: bad arguments");
+    if (nq == 0 || nc == 0) return ERQ_OK;
+    if (!Q || !ids || !est) return fail(ERQ_EINVAL, "erq_estimate: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, (size_t)nq * ix->D * 4));
+    float* Qrot = (float*)ix->ws;
+    cudaError_t e;
+    if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, ix->D, ix->D, 1.f, nullptr, s)) != cudaSuccess)
+        return cuda_fail(e, "estimate rotation");
+    if ((e = launch_estimate(Q, Qrot, ids, nq, nc, ix, est, s)) != cudaSuccess) return cuda_fail(e, "estimate");
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                          const float* grad_scores, float* grad_Q, void* stream) {
+    if (!ix || nq < 0 || nc < 0) return fail(ERQ_EINVAL, "erq_search_backward: bad arguments");
+    if (nq == 0) return ERQ_OK;
+    if (!Q || !grad_Q || (nc > 0 && (!ids || !grad_scores))) return fail(ERQ_EINVAL, "erq_search_backward: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t mat = (size_t)nq * ix->D;
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, 2 * mat * 4 + 512));
+    float* V = (float*)ix->ws;
+    float* Wv = V + (mat + 63) / 64 * 64;
+    cudaError_t e;
+    if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, V, Wv, s)) != cudaSuccess)
+        return cuda_fail(e, "backward gather");
+    // grad_Q = V P^T + Wv  (NT: B = P read as [n][k])
+    if ((e = launch_sgemm(true, V, ix->P, grad_Q, nq, ix->D, ix->D, 1.f, Wv, s)) != cudaSuccess)
+        return cuda_fail(e, "backward gemm");
+    return ERQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Export / save / load
+// ---------------------------------------------------------------------------
+struct FieldDesc {
+    const void* ptr;
+    size_t bytes;
+};
+
+static FieldDesc field_of(const erq_index* ix, int f) {
+    const size_t N = ix->N, D = ix->D, nl = ix->nlist;
+    switch (f) {
+        case ERQ_FIELD_CENTROIDS: return {ix->C, nl * D * 4};
+        case ERQ_FIELD_ROT_CENTROIDS: return {ix->Cp, nl * D * 4};
+        case ERQ_FIELD_LIST_OFFSETS: return {ix->list_off, (nl + 1) * 8};
+        case ERQ_FIELD_LIST_IDS: return {ix->list_ids, N * 8};
+        case ERQ_FIELD_CODES: return {ix->codes, N * D};
+        case ERQ_FIELD_F_ADD: return {ix->f_add, N * 4};
+        case ERQ_FIELD_F_RES: return {ix->f_res, N * 4};
+        case ERQ_FIELD_P: return {ix->P, D * D * 4};
+        case ERQ_FIELD_RAW: return {ix->keep_raw ? ix->X : nullptr, ix->keep_raw ? N * D * 4 : 0};
+        default: return {nullptr, 0};
+    }
+}
+
+extern "C" erq_status erq_index_export(const erq_index* ix, int32_t field, void* dst_host, int64_t dst_bytes) {
+    if (!ix || !dst_host) return fail(ERQ_EINVAL, "erq_index_export: null argument");
+    const FieldDesc fd = field_of(ix, field);
+    if (!fd.ptr) return fail(ERQ_EINVAL, "erq_index_export: unknown or absent field");
+    if ((size_t)dst_bytes < fd.bytes) return fail(ERQ_EINVAL, "erq_index_export: destination too small");
+    ERQ_CHECK_CUDA(cudaMemcpy(dst_host, fd.ptr, fd.bytes, cudaMemcpyDeviceToHost));
+    return ERQ_OK;
+}
+
+static const char kMagic[8] = {'E', 'R', 'Q', 'I', 'D', 'X', '0', '1'};
+
+extern "C" erq_status erq_index_save(const erq_index* ix, const char* path) {
+    if (!ix || !path) return fail(ERQ_EINVAL, "erq_index_save: null argument");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(ERQ_EIO, std::string("erq_index_save: cannot open ") + path);
+    int64_t hdr[6] = {ix->N, ix->D, ix->B, ix->nlist, ix->keep_raw, ix->max_list};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 8, 6, f) == 6;
+    const void* arrays[] = {ix->P, ix->C, ix->Cp, ix->cnorm2, ix->list_off, ix->list_ids, ix->row_of,
+                            ix->cl_of_row, ix->codes, ix->f_add, ix->f_res, ix->g_const, ix->X};
+    const size_t N = ix->N, D = ix->D, nl = ix->nlist;
+    const size_t sizes[] = {D * D * 4, nl * D * 4, nl * D * 4, nl * 4, (nl + 1) * 8, N * 8, N * 8,
+                            N * 4, N * D, N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
+    std::vector<char> host;
+    for (int i = 0; i < 13 && ok; ++i) {
+        if (!sizes[i]) continue;
+        host.resize(sizes[i]);
+        if (cudaMemcpy(host.data(), arrays[i], sizes[i], cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            return fail(ERQ_ECUDA, "erq_index_save: device copy failed");
+        }
+        ok = fwrite(host.data(), 1, sizes[i], f) == sizes[i];
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? ERQ_OK : fail(ERQ_EIO, "erq_index_save: write failed");
+}
+
+extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index** out) {
+    if (!path || !out) return fail(ERQ_EINVAL, "erq_index_load: null argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(ERQ_EIO, std::string("erq_index_load: cannot open ") + path);
+    char magic[8];
+    int64_t hdr[6];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 8, 6, f) != 6) {
+        fclose(f);
+        return fail(ERQ_EIO, "erq_index_load: not an index file (bad magic or header)");
+    }
+    erq_index* ix = new erq_index();
+    ix->N = hdr[0];
+    ix->D = (int32_t)hdr[1];
+    ix->B = (int32_t)hdr[2];
+    ix->nlist = (int32_t)hdr[3];
+    ix->keep_raw = (int32_t)hdr[4];
+    ix->max_list = hdr[5];
+    ix->host_list_off = new std::vector<int64_t>(ix->nlist + 1);
+    if (ix->N < 1 || !valid_d(ix->D) || ix->B < 1 || ix->B > 8 || ix->nlist < 1) {
+        fclose(f);
+        erq_free_index(ix);
+        return fail(ERQ_EIO, "erq_index_load: corrupt header");
+    }
+    const size_t N = ix->N, D = ix->D, nl = ix->nlist;
+    erq_status st = ERQ_OK;
+    void** dst[] = {(void**)&ix->P, (void**)&ix->C, (void**)&ix->Cp, (void**)&ix->cnorm2, (void**)&ix->list_off,
+                    (void**)&ix->list_ids, (void**)&ix->row_of, (void**)&ix->cl_of_row, (void**)&ix->codes,
+                    (void**)&ix->f_add, (void**)&ix->f_res, (void**)&ix->g_const, (void**)&ix->X};
+    const size_t sizes[] = {D * D * 4, nl * D * 4, nl * D * 4, nl * 4, (nl + 1) * 8, N * 8, N * 8,
+                            N * 4, N * D, N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
+    std::vector<char> host;
+    for (int i = 0; i < 13 && st == ERQ_OK; ++i) {
+        if (!sizes[i]) continue;
+        if (cudaMalloc(dst[i], sizes[i]) != cudaSuccess) {
+            st = fail(ERQ_ENOMEM, "erq_index_load: cudaMalloc");
+            break;
+        }
+        ix->device_bytes += sizes[i];
+        host.resize(sizes[i]);
+        if (fread(host.data(), 1, sizes[i], f) != sizes[i]) {
+            st = fail(ERQ_EIO, "erq_index_load: truncated file");
+            break;
+        }
+        if (cudaMemcpy(*dst[i], host.data(), sizes[i], cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(ERQ_ECUDA, "erq_index_load: upload");
+        if (i == 4) memcpy(ix->host_list_off->data(), host.data(), sizes[i]);
+    }
+    fclose(f);
+    if (st == ERQ_OK && cudaMalloc(&ix->status, 4) != cudaSuccess) st = fail(ERQ_ENOMEM, "erq_index_load: status");
+    if (st == ERQ_OK && cudaMemset(ix->status, 0, 4) != cudaSuccess) st = fail(ERQ_ECUDA, "erq_index_load: status");
+    if (st != ERQ_OK) {
+        erq_free_index(ix);
+        return st;
+    }
+    (void)stream;
+    *out = ix;
+    return ERQ_OK;
+}
+
+
+extern "C" erq_status erq_search_timing(const erq_index* ix, float* ms, int32_t n) {
+    if (!ix || !ms || n < 6) return fail(ERQ_EINVAL, "erq_search_timing: bad arguments");
+    if (!ix->timed) return fail(ERQ_EINVAL, "erq_search_timing: no search ran with ERQ_SEARCH_TIMING");
+    ERQ_CHECK_CUDA(cudaEventSynchronize(ix->ev[6]));
+    for (int i = 0; i < 6; ++i) ERQ_CHECK_CUDA(cudaEventElapsedTime(&ms[i], ix->ev[i], ix->ev[i + 1]));
+    return ERQ_OK;
+}
+
+extern "C" uint64_t erq_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" erq_status erq_search_stats(const erq_index* ix, int64_t* out, int32_t n) {
+    if (!ix || !out || n < 4) return fail(ERQ_EINVAL, "erq_search_stats: bad arguments");
+    for (int i = 0; i < 4; ++i) out[i] = ix->last_stats[i];
+    return ERQ_OK;
+}

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of liberq.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/erq.h"
+
+namespace erq {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+erq_status fail(erq_status st, const std::string& msg);
+erq_status cuda_fail(cudaError_t e, const char* what);
+
+#define ERQ_CHECK_CUDA(expr)                                          \
+    do {                                                              \
+        cudaError_t _e = (expr);                                      \
+        if (_e != cudaSuccess) return ::erq::cuda_fail(_e, #expr);    \
+    } while (0)
+
+#define ERQ_CHECK_LAUNCH(name)                                        \
+    do {                                                              \
+        cudaError_t _e = cudaGetLastError();                          \
+        if (_e != cudaSuccess) return ::erq::cuda_fail(_e, name);     \
+    } while (0)
+
+#define ERQ_TRY(expr)                                                 \
+    do {                                                              \
+        erq_status _s = (expr);                                       \
+        if (_s != ERQ_OK) return _s;                                  \
+    } while (0)
+
+// Device status word bits (written by kernels, read by erq_index_status).
+enum : uint32_t { kStatusTimeout = 1u, kStatusBounds = 2u, kStatusRange = 4u };
+
+// ---------------------------------------------------------------- keys
+// Order-preserving map of an FP32 value to uint32 (NaN sorts last).
+__host__ __device__ inline uint32_t float_to_ordered(float f) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float ordered_to_float(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+// Candidate key: (estimate, original id) in lexicographic order.
+__host__ __device__ inline uint64_t make_key(float est, uint32_t id) {
+    return ((uint64_t)float_to_ordered(est) << 32) | (uint64_t)id;
+}
+__host__ __device__ inline float key_value(uint64_t k) { return ordered_to_float((uint32_t)(k >> 32)); }
+__host__ __device__ inline uint32_t key_id(uint64_t k) { return (uint32_t)(k & 0xffffffffu); }
+constexpr uint64_t kEmptyKey = ~0ull;
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Process-wide count of kernel launches issued by the library.
+void count_launch();
+
+// ---------------------------------------------------------------- index
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace erq
+
+// The index object.  All pointers are device memory owned by the index.
+struct erq_index {
+    int64_t N = 0;
+    int32_t D = 0, B = 0, nlist = 0, keep_raw = 0;
+    int64_t max_list = 0;
+    float* P = nullptr;          // [D][D]
+    float* C = nullptr;          // [nlist][D] centroids
+    float* Cp = nullptr;         // [nlist][D] rotated centroids P^T c
+    float* cnorm2 = nullptr;     // [nlist] ||c||^2 (FP32, for the probe)
+    int64_t* list_off = nullptr; // [nlist+1]
+    int64_t* list_ids = nullptr; // [N] original id of stored row
+    int64_t* row_of = nullptr;   // [N] stored row of original id
+    int32_t* cl_of_row = nullptr;// [N] cluster of stored row
+    uint8_t* codes = nullptr;    // [N][D] ybar_u
+    float* f_add = nullptr;      // [N]
+    float* f_res = nullptr;      // [N]
+    float* g_const = nullptr;    // [N] f_add - f_res * <ybar, c'>
+    float* X = nullptr;          // [N][D] raw rows, original order (keep_raw)
+    uint32_t* status = nullptr;  // device status word
+    std::vector<int64_t>* host_list_off = nullptr;  // host copy of list_off
+    // search workspace (grown on demand)
+    void* ws = nullptr;          // phase-A / build workspace
+    size_t ws_bytes = 0;
+    void* ws_b = nullptr;        // phase-B workspace (data-dependent sizes)
+    size_t ws_b_bytes = 0;
+    void* io = nullptr;          // device staging of erq_search_host
+    size_t io_bytes = 0;
+    void* pinned = nullptr;      // pinned host staging for erq_search_host
+    cudaEvent_t ev[7] = {};      // phase boundaries of the last timed search
+    int timed = 0;               // 1 when ev[] holds a timed search
+    int64_t last_stats[4] = {};  // pairs, distinct rows, work items, lists of the last search
+    size_t pinned_bytes = 0;
+    int64_t device_bytes = 0;
+};

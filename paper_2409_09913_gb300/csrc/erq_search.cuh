@@ -1,0 +1,77 @@
+// Launch descriptors of the search kernels (k_search.cu, k_scan_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "erq_internal.cuh"
+
+namespace erq {
+
+// Inputs/outputs of the planning kernels (probe lists -> work items).
+struct PlanArgs {
+    const int32_t* probe;       // [nq][probe_stride]
+    int64_t probe_stride;
+    const int32_t* npr_in;      // optional [nq]
+    int npr_uniform;
+    int64_t nq;
+    int maxp, nlist, QT, RR;
+    const int64_t* list_off;
+    int32_t* npr;               // [nq] effective nprobe
+    int32_t* probe_c;           // [nq][maxp] validated cluster or -1
+    int32_t* cnt_c;             // [nlist]
+    int32_t* pos_c;             // [nlist]
+    int32_t* slot_nr;           // [nq][maxp] ranges of the slot's cluster
+    int32_t* slot_off;          // [nq][maxp]
+    int64_t* qtot;              // [nq]
+    int64_t* qbase;             // [nq+1]
+    int64_t* cnt64;             // [nlist]
+    int64_t* items_c;           // [nlist]
+    int64_t* qoff;              // [nlist+1]
+    int64_t* item_off;          // [nlist+1]
+    int64_t* qlist;             // [nq*maxp]
+    uint32_t* status;
+    unsigned long long* stats;  // [2]: (query, candidate) pairs, rows of distinct probed clusters
+};
+
+struct ScanLaunch {
+    const float* Qrot;
+    const void* Qh;             // FP16 rotated queries (tensor-core path)
+    uint32_t* status;
+    int64_t N;
+    const uint8_t* codes;
+    const float* g_const;
+    const float* f_res;
+    const int64_t* list_off;
+    const int64_t* list_ids;
+    const int64_t* qlist;
+    const int64_t* qoff;
+    const int4* items;
+    const int64_t* n_items;
+    const float* dqc;
+    const int32_t* slot_off;
+    const int64_t* qbase;
+    uint64_t* inter;
+    int32_t* inter_cnt;
+    int maxp, D, B, kp, RR;
+    int grid;
+};
+
+cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
+                       int D, float* dqc, cudaStream_t s);
+cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s);
+cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
+cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
+size_t scan_fp32_smem(int kp);
+int merge_sortn(int kp);
+cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
+                         uint64_t* cand, cudaStream_t s);
+cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
+                          int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
+                          cudaStream_t s);
+cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
+                            const erq_index* ix, float* est, cudaStream_t s);
+cudaError_t launch_backward_gather(const float* Q, const int64_t* ids, const float* gs, int64_t nq, int nc,
+                                   const erq_index* ix, float* V, float* Wv, cudaStream_t s);
+
+}  // namespace erq

@@ -1,0 +1,653 @@
+// Search path kernels (Section 4.1 IVF search with the Section 3.2 estimator):
+//   dqc      ||q_r - c||^2 for every probed (query, cluster) pair
+//   plan     invert probe lists into per-cluster query lists and work items
+//   scan     estimate every (query, candidate) pair of an item and keep the
+//            item's top-k' per query (FP32 CUDA-core path)
+//   merge    per query, the k' smallest estimates over all of its items
+//   rerank   exact squared distances of the k' candidates, top-k
+//   estimate estimates of explicit (query, id) pairs
+//   backward gather of sum_j g_j f_res,j ybar_j and sum_j g_j c_j per query
+//
+// Estimator used by every GPU path (algebraically Eq. 3.3 + Eq. eq:dis to ip):
+//   est = ||q_r - c||^2 + g + (f_res / 2) * <2 ybar, q'>,
+//   q'  = P^T q_r (rotated once per query),  2 ybar = 2 ybar_u - (2^B - 1),
+//   g   = f_add - f_res <ybar, c'>  (per row, index time),
+// because P^T (q_r - c) = q' - c' and <ybar_u, x> - (2^B-1)/2 sum x = <ybar, x>.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "erq_kernels.cuh"
+#include "erq_search.cuh"
+
+namespace erq {
+
+// ---------------------------------------------------------------------------
+// ||q_r - c||^2 per probed pair, FP32, one warp per pair.
+// ---------------------------------------------------------------------------
+__global__ void dqc_kernel(const float* __restrict__ Q, const float* __restrict__ C,
+                           const int32_t* __restrict__ probe, const int32_t* __restrict__ npr, int64_t nq,
+                           int maxp, int D, float* __restrict__ dqc) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nq * maxp) return;
+    const int64_t q = w / maxp;
+    const int slot = (int)(w % maxp);
+    if (slot >= npr[q]) return;
+    const int c = probe[w];
+    if (c < 0) return;  // invalid probe id (reported through the status word)
+    const float* x = Q + q * D;
+    const float* y = C + (int64_t)c * D;
+    float s = 0.f;
+    for (int k = lane * 4; k < D; k += 128) {
+        const float4 a = *reinterpret_cast<const float4*>(x + k);
+        const float4 b = *reinterpret_cast<const float4*>(y + k);
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        s = fmaf(d0, d0, s);
+        s = fmaf(d1, d1, s);
+        s = fmaf(d2, d2, s);
+        s = fmaf(d3, d3, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) dqc[w] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Planning.  Effective nprobe per query, validation, pair counts per cluster.
+// ---------------------------------------------------------------------------
+__global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t probe_stride,
+                                  const int32_t* __restrict__ npr_in, int npr_uniform, int64_t nq, int maxp,
+                                  int nlist, const int64_t* __restrict__ list_off, int RR,
+                                  int32_t* __restrict__ npr, int32_t* __restrict__ probe_c,
+                                  int32_t* __restrict__ cnt_c, int32_t* __restrict__ slot_nr,
+                                  uint32_t* __restrict__ status, unsigned long long* __restrict__ stats) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq * maxp) return;
+    const int64_t q = t / maxp;
+    const int slot = (int)(t % maxp);
+    int np = npr_in ? npr_in[q] : npr_uniform;
+    if (np < 1 || np > maxp) {
+        if (slot == 0) atomicOr(status, kStatusBounds);
+        np = np < 1 ? 0 : maxp;
+    }
+    if (slot == 0) npr[q] = np;
+    int nr = 0;
+    int c = -1;
+    if (slot < np) {
+        c = probe[q * probe_stride + slot];
+        if (c < 0 || c >= nlist) {
+            atomicOr(status, kStatusBounds);
+            c = -1;
+        } else {
+            const int64_t size = list_off[c + 1] - list_off[c];
+            nr = (int)((size + RR - 1) / RR);
+            if (atomicAdd(&cnt_c[c], 1) == 0) atomicAdd(&stats[1], (unsigned long long)size);
+            atomicAdd(&stats[0], (unsigned long long)size);
+        }
+    }
+    probe_c[t] = c;
+    slot_nr[t] = nr;
+}
+
+// per query: offsets of its (slot, range) lists, and their total
+__global__ void plan_query_kernel(const int32_t* __restrict__ slot_nr, int64_t nq, int maxp,
+                                  int32_t* __restrict__ slot_off, int64_t* __restrict__ qtot) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    int run = 0;
+    for (int s = 0; s < maxp; ++s) {
+        slot_off[q * maxp + s] = run;
+        run += slot_nr[q * maxp + s];
+    }
+    qtot[q] = run;
+}
+
+// generic exclusive scan of n int64 (single block); out has n+1 entries
+__global__ void excl_scan_i64_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t a = t * per, b = min(n, a + per);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += in[i];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int64_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        out[n] = run;
+    }
+    __syncthreads();
+    s = part[t];
+    for (int64_t i = a; i < b; ++i) {
+        out[i] = s;
+        s += in[i];
+    }
+}
+
+// per cluster: pair count (int64) and item count
+__global__ void plan_cluster_kernel(const int32_t* __restrict__ cnt_c, const int64_t* __restrict__ list_off,
+                                    int nlist, int QT, int RR, int64_t* __restrict__ cnt64,
+                                    int64_t* __restrict__ items_c) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nlist) return;
+    const int64_t size = list_off[c + 1] - list_off[c];
+    const int64_t n = cnt_c[c];
+    cnt64[c] = n;
+    items_c[c] = (n > 0 && size > 0) ? ((n + QT - 1) / QT) * ((size + RR - 1) / RR) : 0;
+}
+
+__global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t nq, int maxp,
+                                    const int64_t* __restrict__ qoff, int32_t* __restrict__ pos_c,
+                                    int64_t* __restrict__ qlist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq * maxp) return;
+    const int c = probe_c[t];
+    if (c < 0) return;
+    const int p = atomicAdd(&pos_c[c], 1);
+    qlist[qoff[c] + p] = t;  // t = q * maxp + slot
+}
+
+__global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64_t* __restrict__ list_off,
+                                  const int64_t* __restrict__ item_off, int nlist, int QT, int RR,
+                                  int4* __restrict__ items) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nlist) return;
+    const int64_t b = item_off[c], e = item_off[c + 1];
+    if (b == e) return;
+    const int64_t size = list_off[c + 1] - list_off[c];
+    const int nranges = (int)((size + RR - 1) / RR);
+    int64_t w = b;
+    const int nchunks = (int)((cnt64[c] + QT - 1) / QT);
+    for (int r = 0; r < nranges; ++r)
+        for (int ch = 0; ch < nchunks; ++ch) items[w++] = make_int4(c, ch, r, 0);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CUDA-core scan.
+// Item = (cluster c, query chunk, row range).  Tile: 64 queries x 64 rows,
+// 256 threads with 4x4 outputs each, K step 32.  After a tile's dot products
+// the estimates go to shared memory and 64 threads (one per query) push them
+// through their query's max-heap of the k' best (estimate, id) keys.
+// ---------------------------------------------------------------------------
+constexpr int SC_QT = 64, SC_RB = 64, SC_BK = 32;
+
+struct ScanArgs {
+    const float* Qrot;          // [nq][D]
+    const uint8_t* codes;       // [N][D]
+    const float* g_const;       // [N]
+    const float* f_res;         // [N]
+    const int64_t* list_off;    // [nlist+1]
+    const int64_t* list_ids;    // [N]
+    const int64_t* qlist;       // per-cluster (q*maxp+slot) entries
+    const int64_t* qoff;        // [nlist+1]
+    const int4* items;
+    const int64_t* n_items;     // device scalar
+    const float* dqc;           // [nq][maxp]
+    const int32_t* slot_off;    // [nq][maxp]
+    const int64_t* qbase;       // [nq+1]
+    uint64_t* inter;            // [L][kp]
+    int32_t* inter_cnt;         // [L]
+    int maxp, D, B, kp, RR;
+};
+
+__global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float (*qs)[SC_QT + 4] = reinterpret_cast<float (*)[SC_QT + 4]>(smem);                         // [BK][QT+4]
+    float (*cs)[SC_RB + 4] = reinterpret_cast<float (*)[SC_RB + 4]>(smem + SC_BK * (SC_QT + 4) * 4); // [BK][RB+4]
+    float (*E)[SC_RB + 1] = reinterpret_cast<float (*)[SC_RB + 1]>(smem + SC_BK * (SC_QT + 4) * 4 +
+                                                                   SC_BK * (SC_RB + 4) * 4);        // [QT][RB+1]
+    uint64_t* heap = reinterpret_cast<uint64_t*>(smem + SC_BK * (SC_QT + 4) * 4 + SC_BK * (SC_RB + 4) * 4 +
+                                                 SC_QT * (SC_RB + 1) * 4 + 16);                     // [kp][QT]
+    __shared__ int64_t s_q[SC_QT];
+    __shared__ int64_t s_list[SC_QT];
+    __shared__ float s_dqc[SC_QT];
+    __shared__ int s_hsize[SC_QT];
+    __shared__ float s_g[SC_RB], s_fh[SC_RB];
+    __shared__ uint32_t s_id[SC_RB];
+
+    const int tid = threadIdx.x;
+    const int tq = tid % 16, tr = tid / 16;
+    const int D = a.D;
+    const float off = (float)((1 << a.B) - 1);
+    const int64_t nitems = *a.n_items;
+
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 item = a.items[it];
+        const int c = item.x;
+        const int64_t qb = a.qoff[c] + (int64_t)item.y * SC_QT;
+        const int nqi = (int)imin64(SC_QT, a.qoff[c + 1] - qb);
+        const int64_t rb0 = a.list_off[c] + (int64_t)item.z * a.RR;
+        const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
+        if (tid < SC_QT) {
+            if (tid < nqi) {
+                const int64_t e = a.qlist[qb + tid];
+                const int64_t q = e / a.maxp;
+                s_q[tid] = q;
+                s_dqc[tid] = a.dqc[e];
+                s_list[tid] = a.qbase[q] + a.slot_off[e] + item.z;
+            } else {
+                s_q[tid] = -1;
+            }
+            s_hsize[tid] = 0;
+        }
+        __syncthreads();
+        for (int64_t r0 = rb0; r0 < rb1; r0 += SC_RB) {
+            const int nr = (int)imin64(SC_RB, rb1 - r0);
+            if (tid < SC_RB) {
+                if (tid < nr) {
+                    s_g[tid] = a.g_const[r0 + tid];
+                    s_fh[tid] = 0.5f * a.f_res[r0 + tid];
+                    s_id[tid] = (uint32_t)a.list_ids[r0 + tid];
+                }
+            }
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int k0 = 0; k0 < D; k0 += SC_BK) {
+                // queries: 64 x 32 floats, 8 per thread
+                {
+                    const int qi = tid / 4, kk = (tid % 4) * 8;
+                    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                    if (qi < nqi) {
+                        const float* src = a.Qrot + s_q[qi] * D + k0 + kk;
+                        v0 = *reinterpret_cast<const float4*>(src);
+                        v1 = *reinterpret_cast<const float4*>(src + 4);
+                    }
+                    qs[kk + 0][qi] = v0.x; qs[kk + 1][qi] = v0.y; qs[kk + 2][qi] = v0.z; qs[kk + 3][qi] = v0.w;
+                    qs[kk + 4][qi] = v1.x; qs[kk + 5][qi] = v1.y; qs[kk + 6][qi] = v1.z; qs[kk + 7][qi] = v1.w;
+                }
+                // codes: 64 rows x 32 bytes, 8 per thread, centred 2*ybar
+                {
+                    const int ri = tid / 4, kk = (tid % 4) * 8;
+                    uint2 u = make_uint2(0u, 0u);
+                    if (ri < nr) u = *reinterpret_cast<const uint2*>(a.codes + (r0 + ri) * D + k0 + kk);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        cs[kk + b][ri] = 2.f * (float)((u.x >> (8 * b)) & 0xffu) - off;
+                        cs[kk + 4 + b][ri] = 2.f * (float)((u.y >> (8 * b)) & 0xffu) - off;
+                    }
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int kk = 0; kk < SC_BK; ++kk) {
+                    const float4 qv = *reinterpret_cast<const float4*>(&qs[kk][tq * 4]);
+                    const float4 cv = *reinterpret_cast<const float4*>(&cs[kk][tr * 4]);
+                    const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+                    const float ca[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                }
+                __syncthreads();
+            }
+            // estimates to shared memory
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int qi = tq * 4 + i, ri = tr * 4 + j;
+                    float e = INFINITY;
+                    if (qi < nqi && ri < nr) e = s_dqc[qi] + s_g[ri] + s_fh[ri] * acc[i][j];
+                    E[qi][ri] = e;
+                }
+            __syncthreads();
+            // heap update, one thread per query
+            if (tid < nqi) {
+                const int q = tid;
+                int hs = s_hsize[q];
+                const int kp = a.kp;
+                for (int r = 0; r < nr; ++r) {
+                    const uint64_t key = make_key(E[q][r], s_id[r]);
+                    if (hs < kp) {  // sift up into a max-heap
+                        int j = hs++;
+                        while (j > 0) {
+                            const int p = (j - 1) >> 1;
+                            const uint64_t pk = heap[p * SC_QT + q];
+                            if (pk >= key) break;
+                            heap[j * SC_QT + q] = pk;
+                            j = p;
+                        }
+                        heap[j * SC_QT + q] = key;
+                    } else if (key < heap[q]) {  // replace the root, sift down
+                        int j = 0;
+                        for (;;) {
+                            const int l = 2 * j + 1;
+                            if (l >= kp) break;
+                            int m = l;
+                            uint64_t mk = heap[l * SC_QT + q];
+                            if (l + 1 < kp) {
+                                const uint64_t rk = heap[(l + 1) * SC_QT + q];
+                                if (rk > mk) { m = l + 1; mk = rk; }
+                            }
+                            if (mk <= key) break;
+                            heap[j * SC_QT + q] = mk;
+                            j = m;
+                        }
+                        heap[j * SC_QT + q] = key;
+                    }
+                }
+                s_hsize[q] = hs;
+            }
+            __syncthreads();
+        }
+        // write the item's lists
+        if (tid < nqi) {
+            const int hs = s_hsize[tid];
+            const int64_t L = s_list[tid];
+            uint64_t* dst = a.inter + L * a.kp;
+            for (int j = 0; j < hs; ++j) dst[j] = heap[j * SC_QT + tid];
+            a.inter_cnt[L] = hs;
+        }
+        __syncthreads();
+    }
+}
+
+size_t scan_fp32_smem(int kp) {
+    return (size_t)SC_BK * (SC_QT + 4) * 4 + (size_t)SC_BK * (SC_RB + 4) * 4 + (size_t)SC_QT * (SC_RB + 1) * 4 + 16 +
+           (size_t)kp * SC_QT * 8;
+}
+
+// ---------------------------------------------------------------------------
+// Merge: per query the k' smallest keys over its lists, ascending.
+// Block of 256 threads; running best k' + a chunk, block bitonic sort.
+// ---------------------------------------------------------------------------
+__device__ void block_bitonic_u64(uint64_t* v, int n) {
+    for (int size = 2; size <= n; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t x = v[lo], y = v[hi];
+                if ((x > y) == up) { v[lo] = y; v[hi] = x; }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__ inter,
+                                                    const int32_t* __restrict__ inter_cnt,
+                                                    const int64_t* __restrict__ qbase, int kp, int sortn,
+                                                    uint64_t* __restrict__ cand) {
+    extern __shared__ uint64_t buf[];  // [sortn]
+    __shared__ int s_fill;
+    __shared__ uint64_t s_tau;         // entries >= s_tau cannot enter the top k'
+    const int64_t q = blockIdx.x;
+    const int64_t L0 = qbase[q], L1 = qbase[q + 1];
+    for (int i = threadIdx.x; i < sortn; i += blockDim.x) buf[i] = kEmptyKey;
+    if (threadIdx.x == 0) { s_fill = kp; s_tau = kEmptyKey; }
+    __syncthreads();
+    for (int64_t L = L0; L < L1; ++L) {
+        const int n = inter_cnt[L];
+        if (s_fill + n > sortn) {          // uniform: s_fill is shared
+            block_bitonic_u64(buf, sortn);
+            for (int i = kp + threadIdx.x; i < sortn; i += blockDim.x) buf[i] = kEmptyKey;
+            __syncthreads();
+            if (threadIdx.x == 0) { s_fill = kp; s_tau = buf[kp - 1]; }
+            __syncthreads();
+        }
+        const uint64_t tau = s_tau;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const uint64_t key = inter[L * kp + j];
+            if (key < tau) buf[atomicAdd(&s_fill, 1)] = key;
+        }
+        __syncthreads();
+    }
+    block_bitonic_u64(buf, sortn);
+    for (int j = threadIdx.x; j < kp; j += blockDim.x) cand[q * kp + j] = buf[j];
+}
+
+// ---------------------------------------------------------------------------
+// Re-rank: exact squared distances of the k' candidates (FP32), top-k.
+// Also writes cand_ids / cand_est when requested.  One block per query.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict__ cand, int kp, const float* __restrict__ X,
+                                                     const float* __restrict__ Q, int D, int k, int do_rerank,
+                                                     int sortn, int64_t* __restrict__ ids, float* __restrict__ dists,
+                                                     int64_t* __restrict__ cand_ids, float* __restrict__ cand_est) {
+    extern __shared__ uint64_t keys[];  // [sortn]
+    const int64_t q = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t* cq = cand + q * kp;
+    if (cand_ids)
+        for (int j = threadIdx.x; j < kp; j += blockDim.x) {
+            const uint64_t kk = cq[j];
+            cand_ids[q * kp + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
+            cand_est[q * kp + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+        }
+    if (!do_rerank) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+            const uint64_t kk = j < kp ? cq[j] : kEmptyKey;
+            ids[q * k + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
+            dists[q * k + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < sortn; i += blockDim.x) keys[i] = kEmptyKey;
+    __syncthreads();
+    const float* qr = Q + q * D;
+    for (int j = warp; j < kp; j += blockDim.x / 32) {
+        const uint64_t kk = cq[j];
+        if (kk == kEmptyKey) continue;
+        const uint32_t id = key_id(kk);
+        const float* x = X + (int64_t)id * D;
+        float s = 0.f;
+        for (int t = lane * 4; t < D; t += 128) {
+            const float4 a = *reinterpret_cast<const float4*>(x + t);
+            const float4 b = *reinterpret_cast<const float4*>(qr + t);
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            s = fmaf(d0, d0, s);
+            s = fmaf(d1, d1, s);
+            s = fmaf(d2, d2, s);
+            s = fmaf(d3, d3, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) keys[j] = make_key(s, id);
+    }
+    __syncthreads();
+    block_bitonic_u64(keys, sortn);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const uint64_t kk = keys[j];
+        ids[q * k + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
+        dists[q * k + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Estimates of explicit pairs, one warp per pair (FP32).
+// ---------------------------------------------------------------------------
+__global__ void estimate_kernel(const float* __restrict__ Q, const float* __restrict__ Qrot,
+                                const int64_t* __restrict__ ids, int64_t nq, int nc, int64_t N,
+                                const int64_t* __restrict__ row_of, const int32_t* __restrict__ cl_of_row,
+                                const float* __restrict__ C, const uint8_t* __restrict__ codes,
+                                const float* __restrict__ g_const, const float* __restrict__ f_res, int D, int B,
+                                float* __restrict__ est, uint32_t* __restrict__ status) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nq * nc) return;
+    const int64_t q = w / nc;
+    const int64_t id = ids[w];
+    if (id < 0 || id >= N) {
+        if (lane == 0) {
+            est[w] = NAN;
+            if (id >= N) atomicOr(status, kStatusBounds);
+        }
+        return;
+    }
+    const int64_t row = row_of[id];
+    const float* c = C + (int64_t)cl_of_row[row] * D;
+    const float* x = Q + q * D;
+    const float* xr = Qrot + q * D;
+    const uint8_t* code = codes + row * D;
+    const float off = (float)((1 << B) - 1);
+    float dq = 0.f, ip = 0.f;
+    for (int k = lane; k < D; k += 32) {
+        const float d = x[k] - c[k];
+        dq = fmaf(d, d, dq);
+        ip = fmaf(2.f * (float)code[k] - off, xr[k], ip);
+    }
+    dq = warp_sum(dq);
+    ip = warp_sum(ip);
+    if (lane == 0) est[w] = dq + g_const[row] + 0.5f * f_res[row] * ip;
+}
+
+// ---------------------------------------------------------------------------
+// Backward gather: per query
+//   V[q]  = sum_j g_j f_res,j ybar_j          (rotated space)
+//   Wv[q] = 2 (G q_r - sum_j g_j c_j),  G = sum_j g_j
+// then grad_Q = V P^T + Wv (one SGEMM).  One block per query, coordinates
+// strided over threads, candidates in order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) backward_gather_kernel(const float* __restrict__ Q,
+                                                              const int64_t* __restrict__ ids,
+                                                              const float* __restrict__ gs, int nc, int64_t N,
+                                                              const int64_t* __restrict__ row_of,
+                                                              const int32_t* __restrict__ cl_of_row,
+                                                              const float* __restrict__ C,
+                                                              const uint8_t* __restrict__ codes,
+                                                              const float* __restrict__ f_res, int D, int B,
+                                                              float* __restrict__ V, float* __restrict__ Wv,
+                                                              uint32_t* __restrict__ status) {
+    const int64_t q = blockIdx.x;
+    const float off = 0.5f * (float)((1 << B) - 1);
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+        float v = 0.f, wc = 0.f, G = 0.f;
+        for (int j = 0; j < nc; ++j) {
+            const int64_t id = ids[q * nc + j];
+            if (id < 0) continue;
+            if (id >= N) {
+                if (k == 0) atomicOr(status, kStatusBounds);
+                continue;
+            }
+            const float g = gs[q * nc + j];
+            const int64_t row = row_of[id];
+            const float yb = (float)codes[row * D + k] - off;
+            v = fmaf(g * f_res[row], yb, v);
+            wc = fmaf(g, C[(int64_t)cl_of_row[row] * D + k], wc);
+            G += g;
+        }
+        V[q * D + k] = v;
+        Wv[q * D + k] = 2.f * (G * Q[q * D + k] - wc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers
+// ---------------------------------------------------------------------------
+cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
+                       int D, float* dqc, cudaStream_t s) {
+    const int64_t warps = nq * maxp;
+    if (warps <= 0) return cudaSuccess;
+    count_launch();
+    dqc_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
+    const int64_t pairs = p.nq * p.maxp;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.cnt_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.pos_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.stats, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    count_launch();
+    plan_count_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(
+        p.probe, p.probe_stride, p.npr_in, p.npr_uniform, p.nq, p.maxp, p.nlist, p.list_off, p.RR, p.npr, p.probe_c,
+        p.cnt_c, p.slot_nr, p.status, p.stats);
+    count_launch();
+    plan_query_kernel<<<(unsigned)ceil_div(p.nq, 256), 256, 0, s>>>(p.slot_nr, p.nq, p.maxp, p.slot_off, p.qtot);
+    count_launch();
+    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.qtot, p.nq, p.qbase);
+    count_launch();
+    plan_cluster_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.nlist, p.QT, p.RR,
+                                                                          p.cnt64, p.items_c);
+    count_launch();
+    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.cnt64, p.nlist, p.qoff);
+    count_launch();
+    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.items_c, p.nlist, p.item_off);
+    count_launch();
+    plan_scatter_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(p.probe_c, p.nq, p.maxp, p.qoff, p.pos_c,
+                                                                       p.qlist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s) {
+    count_launch();
+    plan_items_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off, p.nlist, p.QT,
+                                                                       p.RR, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
+    ScanArgs a;
+    a.Qrot = L.Qrot; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;
+    a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
+    a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
+    a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR;
+    const size_t smem = scan_fp32_smem(L.kp);
+    cudaError_t e = cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (L.grid <= 0) return cudaSuccess;
+    count_launch();
+    scan_fp32_kernel<<<L.grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int merge_sortn(int kp) {
+    int sortn = 1024;
+    while (sortn < 4 * kp) sortn <<= 1;
+    return sortn;
+}
+
+cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
+                         uint64_t* cand, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    const int sortn = merge_sortn(kp);
+    cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    merge_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(inter, inter_cnt, qbase, kp, sortn, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
+                          int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
+                          cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    int sortn = 32;
+    while (sortn < kp) sortn <<= 1;
+    cudaError_t e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    rerank_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(cand, kp, X, Q, D, k, do_rerank, sortn, ids, dists, cand_ids,
+                                                       cand_est);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
+                            const erq_index* ix, float* est, cudaStream_t s) {
+    const int64_t w = nq * nc;
+    if (w <= 0) return cudaSuccess;
+    count_launch();
+    estimate_kernel<<<(unsigned)ceil_div(w * 32, 256), 256, 0, s>>>(Q, Qrot, ids, nq, nc, ix->N, ix->row_of,
+                                                                    ix->cl_of_row, ix->C, ix->codes, ix->g_const,
+                                                                    ix->f_res, ix->D, ix->B, est, ix->status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_gather(const float* Q, const int64_t* ids, const float* gs, int64_t nq, int nc,
+                                   const erq_index* ix, float* V, float* Wv, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    count_launch();
+    backward_gather_kernel<<<(unsigned)nq, 256, 0, s>>>(Q, ids, gs, nc, ix->N, ix->row_of, ix->cl_of_row, ix->C,
+                                                        ix->codes, ix->f_res, ix->D, ix->B, V, Wv, ix->status);
+    return cudaGetLastError();
+}
+
+}  // namespace erq

@@ -1,0 +1,284 @@
+"""Thin Python binding of liberq.so (include/erq.h) -- argument marshalling only.
+
+Every step of the search path runs in the library's CUDA kernels; this module
+only checks tensor shapes/dtypes, passes device pointers and the current CUDA
+stream, and turns error codes into exceptions.  It has no CPU fallback: if the
+shared library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liberq.so")
+
+ERQ_OK, ERQ_EINVAL, ERQ_ENOMEM, ERQ_ECUDA, ERQ_ETIMEOUT, ERQ_EUNSUPPORTED, ERQ_EIO = range(7)
+PREC = {"fp32": 0, "fp16": 1, "fp8": 2, "int8": 3}
+FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, "codes": 4, "f_add": 5,
+          "f_res": 6, "P": 7, "raw": 8}
+
+# names of every entry point declared in include/erq.h
+EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index", "erq_index_info_get",
+           "erq_index_status", "erq_rotate", "erq_encode", "erq_search", "erq_search_host", "erq_estimate",
+           "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
+           "erq_kernel_launches", "erq_search_stats"]
+
+
+class ErqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"erq error {code}: {msg}")
+        self.code = code
+
+
+class BuildParams(ct.Structure):
+    _fields_ = [("B", ct.c_int32), ("nlist", ct.c_int32), ("P", ct.c_void_p), ("assign", ct.c_void_p),
+                ("kmeans_iters", ct.c_int32), ("kmeans_sample", ct.c_int32), ("seed", ct.c_uint64),
+                ("keep_raw", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class SearchParams(ct.Structure):
+    _fields_ = [("k", ct.c_int32), ("rerank_k", ct.c_int32), ("nprobe", ct.c_int32), ("precision", ct.c_int32),
+                ("nprobe_per_query", ct.c_void_p), ("probe", ct.c_void_p), ("probe_stride", ct.c_int32),
+                ("flags", ct.c_int32), ("cand_ids", ct.c_void_p), ("cand_est", ct.c_void_p)]
+
+
+class IndexInfo(ct.Structure):
+    _fields_ = [("N", ct.c_int64), ("D", ct.c_int32), ("B", ct.c_int32), ("nlist", ct.c_int32),
+                ("keep_raw", ct.c_int32), ("max_list", ct.c_int64), ("device_bytes", ct.c_int64)]
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load liberq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"liberq.so not found at {p}: run __graft_entry__.build() (or "
+                           f"python -m paper_2409_09913_gb300.build) first; there is no CPU fallback")
+    L = ct.CDLL(p)
+    vp, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int32
+    L.erq_version.restype = ct.c_char_p
+    L.erq_last_error.restype = ct.c_char_p
+    L.erq_build_index.argtypes = [vp, i64, i32, ct.POINTER(BuildParams), vp, ct.POINTER(vp)]
+    L.erq_free_index.argtypes = [vp]
+    L.erq_free_index.restype = None
+    L.erq_index_info_get.argtypes = [vp, ct.POINTER(IndexInfo)]
+    L.erq_index_status.argtypes = [vp, vp]
+    L.erq_rotate.argtypes = [vp, i64, i32, vp, vp, i32, vp]
+    L.erq_encode.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp]
+    L.erq_search.argtypes = [vp, vp, i64, ct.POINTER(SearchParams), vp, vp, vp]
+    L.erq_search_host.argtypes = [vp, vp, i64, ct.POINTER(SearchParams), vp, vp, vp]
+    L.erq_estimate.argtypes = [vp, vp, i64, i32, vp, vp, vp]
+    L.erq_search_backward.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+    L.erq_index_export.argtypes = [vp, i32, vp, i64]
+    L.erq_index_save.argtypes = [vp, ct.c_char_p]
+    L.erq_index_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
+    L.erq_search_timing.argtypes = [vp, ct.POINTER(ct.c_float), i32]
+    L.erq_kernel_launches.argtypes = []
+    L.erq_kernel_launches.restype = ct.c_uint64
+    L.erq_search_stats.argtypes = [vp, ct.POINTER(ct.c_int64), i32]
+    for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
+                 "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
+                 "erq_index_save", "erq_index_load", "erq_search_timing",
+                 "erq_search_stats"):
+        getattr(L, name).restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != ERQ_OK:
+        raise ErqError(code, lib().erq_last_error().decode())
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ct.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _dev(t, dtype, name, ndim=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims")
+    return t.contiguous()
+
+
+def kernel_launches() -> int:
+    return int(lib().erq_kernel_launches())
+
+
+def version() -> str:
+    return lib().erq_version().decode()
+
+
+def rotate(X, P, accurate=False, out=None):
+    """out = X P (rows become P^T x); FP64 accumulation when accurate."""
+    X = _dev(X, torch.float32, "X", 2)
+    P = _dev(P, torch.float32, "P", 2)
+    out = torch.empty_like(X) if out is None else out
+    _check(lib().erq_rotate(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(out), int(bool(accurate)), _stream()))
+    return out
+
+
+def encode(R, B, with_stats=False):
+    """Algorithm 1 on each row of R (rotated residuals) -> (codes, f_add, f_res[, stats])."""
+    R = _dev(R, torch.float32, "R", 2)
+    n, d = R.shape
+    codes = torch.empty((n, d), dtype=torch.uint8, device=R.device)
+    f_add = torch.empty(n, dtype=torch.float32, device=R.device)
+    f_res = torch.empty(n, dtype=torch.float32, device=R.device)
+    stats = torch.empty((n, 2), dtype=torch.float64, device=R.device) if with_stats else None
+    _check(lib().erq_encode(_ptr(R), n, d, int(B), _ptr(codes), _ptr(f_add), _ptr(f_res), _ptr(stats), _stream()))
+    return (codes, f_add, f_res, stats) if with_stats else (codes, f_add, f_res)
+
+
+class Index:
+    """Owner of an erq_index (device memory freed with the object)."""
+
+    def __init__(self, handle):
+        self._h = ct.c_void_p(handle)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.erq_free_index(h)
+            self._h = ct.c_void_p(0)
+
+    def free(self):
+        self.__del__()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = IndexInfo()
+        _check(lib().erq_index_info_get(self._h, ct.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
+
+    def status(self):
+        _check(lib().erq_index_status(self._h, _stream()))
+
+    def search(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp32", probe=None, nprobe_per_query=None,
+               return_candidates=False, timing=False):
+        Q = _dev(Q, torch.float32, "Q", 2)
+        nq = Q.shape[0]
+        sp = SearchParams()
+        sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        sp.flags = 1 if timing else 0
+        keep = []
+        if nprobe_per_query is not None:
+            nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
+            keep.append(nprobe_per_query)
+            sp.nprobe_per_query = nprobe_per_query.data_ptr()
+        if probe is not None:
+            probe = _dev(probe, torch.int32, "probe", 2)
+            keep.append(probe)
+            sp.probe = probe.data_ptr()
+            sp.probe_stride = probe.shape[1]
+        kc = max(int(k), int(rerank_k))
+        cand_ids = cand_est = None
+        if return_candidates:
+            cand_ids = torch.empty((nq, kc), dtype=torch.int64, device=Q.device)
+            cand_est = torch.empty((nq, kc), dtype=torch.float32, device=Q.device)
+            sp.cand_ids, sp.cand_est = cand_ids.data_ptr(), cand_est.data_ptr()
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        _check(lib().erq_search(self._h, _ptr(Q), nq, ct.byref(sp), _ptr(ids), _ptr(dists), _stream()))
+        if return_candidates:
+            return ids, dists, cand_ids, cand_est
+        return ids, dists
+
+    def timing(self):
+        """Per-phase device ms of the last timed search: rotate, probe, plan, scan, merge, rerank."""
+        ms = (ct.c_float * 6)()
+        _check(lib().erq_search_timing(self._h, ms, 6))
+        return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms)))
+
+    def stats(self):
+        """Work of the last search: pairs, distinct rows, items, lists."""
+        out = (ct.c_int64 * 4)()
+        _check(lib().erq_search_stats(self._h, out, 4))
+        return dict(zip(("pairs", "rows", "items", "lists"), list(out)))
+
+    def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32"):
+        """Search from host memory (pinned for asynchronous copies); returns host tensors."""
+        if Q_host.is_cuda or Q_host.dtype != torch.float32:
+            raise TypeError("Q_host must be a CPU float32 tensor")
+        Q_host = Q_host.contiguous()
+        nq = Q_host.shape[0]
+        sp = SearchParams()
+        sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        pin = Q_host.is_pinned()
+        ids = torch.empty((nq, k), dtype=torch.int64, pin_memory=pin)
+        dists = torch.empty((nq, k), dtype=torch.float32, pin_memory=pin)
+        _check(lib().erq_search_host(self._h, _ptr(Q_host), nq, ct.byref(sp), _ptr(ids), _ptr(dists), _stream()))
+        return ids, dists
+
+    def estimate(self, Q, ids):
+        Q = _dev(Q, torch.float32, "Q", 2)
+        ids = _dev(ids, torch.int64, "ids", 2)
+        est = torch.empty(ids.shape, dtype=torch.float32, device=Q.device)
+        _check(lib().erq_estimate(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(est), _stream()))
+        return est
+
+    def search_backward(self, Q, ids, grad_scores):
+        Q = _dev(Q, torch.float32, "Q", 2)
+        ids = _dev(ids, torch.int64, "ids", 2)
+        g = _dev(grad_scores, torch.float32, "grad_scores", 2)
+        out = torch.empty_like(Q)
+        _check(lib().erq_search_backward(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
+                                         _ptr(out), _stream()))
+        return out
+
+    def export(self, field):
+        inf = self.info()
+        N, D, nl = inf["N"], inf["D"], inf["nlist"]
+        shapes = {"centroids": ((nl, D), torch.float32), "rot_centroids": ((nl, D), torch.float32),
+                  "list_offsets": ((nl + 1,), torch.int64), "list_ids": ((N,), torch.int64),
+                  "codes": ((N, D), torch.uint8), "f_add": ((N,), torch.float32), "f_res": ((N,), torch.float32),
+                  "P": ((D, D), torch.float32), "raw": ((N, D), torch.float32)}
+        shape, dt = shapes[field]
+        out = torch.empty(shape, dtype=dt)
+        torch.cuda.current_stream().synchronize()
+        _check(lib().erq_index_export(self._h, FIELDS[field], _ptr(out), out.numel() * out.element_size()))
+        return out
+
+    def save(self, path):
+        torch.cuda.current_stream().synchronize()
+        _check(lib().erq_index_save(self._h, str(path).encode()))
+
+    @staticmethod
+    def load(path):
+        h = ct.c_void_p()
+        _check(lib().erq_index_load(str(path).encode(), _stream(), ct.byref(h)))
+        return Index(h.value)
+
+
+def build_index(X, P, B, nlist=1, *, assign=None, keep_raw=True, kmeans_iters=10, kmeans_sample=0, seed=0):
+    """Build an IVF + extended-RaBitQ index from device rows X [N, D]."""
+    X = _dev(X, torch.float32, "X", 2)
+    P = _dev(P, torch.float32, "P", 2)
+    bp = BuildParams()
+    bp.B, bp.nlist, bp.P = int(B), int(nlist), P.data_ptr()
+    if assign is not None:
+        assign = _dev(assign, torch.int32, "assign", 1)
+        bp.assign = assign.data_ptr()
+    bp.kmeans_iters, bp.kmeans_sample, bp.seed, bp.keep_raw = int(kmeans_iters), int(kmeans_sample), int(seed), \
+        int(bool(keep_raw))
+    h = ct.c_void_p()
+    _check(lib().erq_build_index(_ptr(X), X.shape[0], X.shape[1], ct.byref(bp), _stream(), ct.byref(h)))
+    return Index(h.value)

@@ -35,6 +35,7 @@ __all__ = [
     "uniform_ints",
     "normal",
     "kmeans_assign",
+    "kmeans_assign_torch",
     "WORKLOADS",
 ]
 
@@ -174,6 +175,47 @@ def kmeans_assign(X: np.ndarray, nlist: int, iters: int, seed: int, sample: int 
         blk = X64[s0:s0 + (1 << 14)]
         d2 = (blk ** 2).sum(1)[:, None] - 2 * blk @ C.T + (C ** 2).sum(1)[None, :]
         out[s0:s0 + len(blk)] = d2.argmin(1)
+    return out
+
+
+def kmeans_assign_torch(X, nlist: int, iters: int, seed: int, sample: int | None = None, device=None,
+                        chunk: int = 32768):
+    """Lloyd k-means with plain torch ops (runs on ``device``, GPU if given),
+    returning the cluster of every row (int32 numpy).  An input generator for
+    the IVF partition at million scale, where the numpy version is too slow;
+    it is not part of the method and not part of the library under test."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cpu")
+    g = rng(seed)
+    n = len(X)
+    idx = np.sort(g.choice(n, size=sample, replace=False)) if sample and sample < n else np.arange(n)
+    Xs = torch.from_numpy(np.ascontiguousarray(X[idx])).to(dev)
+    C = Xs[torch.from_numpy(g.choice(len(idx), size=nlist, replace=False)).to(dev)].clone()
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+
+    def assign(rows):
+        out = torch.empty(len(rows), dtype=torch.int64, device=dev)
+        cn = (C * C).sum(1)
+        for s0 in range(0, len(rows), chunk):
+            b = rows[s0:s0 + chunk]
+            d = cn[None, :] - 2.0 * (b @ C.T)
+            out[s0:s0 + len(b)] = d.argmin(1)
+        return out
+
+    try:
+        for _ in range(iters):
+            a = assign(Xs)
+            sums = torch.zeros_like(C).index_add_(0, a, Xs)
+            cnt = torch.bincount(a, minlength=nlist).to(C.dtype)
+            nz = cnt > 0
+            C[nz] = sums[nz] / cnt[nz, None]
+        out = np.empty(n, dtype=np.int32)
+        for s0 in range(0, n, 1 << 18):
+            blk = torch.from_numpy(np.ascontiguousarray(X[s0:s0 + (1 << 18)])).to(dev)
+            out[s0:s0 + len(blk)] = assign(blk).cpu().numpy()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
     return out
 
 

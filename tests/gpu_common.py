@@ -1,0 +1,66 @@
+"""Helpers shared by the GPU parity tests (comparison rules written once)."""
+import numpy as np
+import pytest
+import torch
+
+# Tolerance of the FP32 GPU path against the FP64 oracle (relative, with an
+# absolute floor proportional to the typical magnitude of the row).
+FP32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="session")
+def erq():
+    from paper_2409_09913_gb300 import build, erq as _erq
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return _erq
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def assert_close_rel(got, ref, rtol=FP32_RTOL, what="values"):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    fin = np.isfinite(ref)
+    assert (np.isfinite(got) == fin).all(), f"{what}: finiteness differs"
+    scale = np.abs(ref[fin]) + 1e-3 * np.median(np.abs(ref[fin])) if fin.any() else 1.0
+    err = np.abs(got[fin] - ref[fin]) / scale
+    assert err.max(initial=0.0) <= rtol, f"{what}: max rel err {err.max():.3e} > {rtol}"
+    return err.max(initial=0.0)
+
+
+def compare_topk_ids(got_ids, ref_ids, ref_vals, tol, what="ids", max_excluded=0.02):
+    """Ids must match bit-exactly wherever the oracle's ranking is not decided
+    by a near-tie.  ``ref_ids``/``ref_vals`` may carry one extra column (the
+    oracle's (k+1)-th entry) so that ties across the cut are detected.  Slot j
+    of query i is compared unless the oracle's value j lies within
+    2*tol*|value| of value j-1 or j+1.  Returns the fraction of excluded
+    slots, which must stay small."""
+    got_ids = np.asarray(got_ids)
+    ref_ids = np.asarray(ref_ids)
+    v = np.asarray(ref_vals, np.float64)
+    nq, k = got_ids.shape
+    excluded = 0
+    for i in range(nq):
+        vi = v[i]
+        fin = np.isfinite(vi)
+        for j in range(k):
+            if not fin[j]:
+                assert got_ids[i, j] == -1, f"{what}: query {i} slot {j} should be empty"
+                continue
+            t = 2 * tol * (abs(vi[j]) + 1e-30)
+            near = (j > 0 and abs(vi[j] - vi[j - 1]) <= t) or \
+                   (j + 1 < len(vi) and fin[j + 1] and abs(vi[j + 1] - vi[j]) <= t)
+            if near:
+                excluded += 1
+                continue
+            assert got_ids[i, j] == ref_ids[i, j], f"{what}: query {i} slot {j}: {got_ids[i, j]} != {ref_ids[i, j]}"
+    frac = excluded / max(1, nq * k)
+    assert frac <= max_excluded, f"{what}: too many near-tie exclusions ({frac:.3f})"
+    return frac

@@ -1,0 +1,86 @@
+"""Tensor-core (tcgen05 kind::f16) scan against the FP64 oracle.
+
+The FP16 path is exact in the codes (2*ybar is an odd integer <= 255) and
+rounds only the rotated query q' to FP16, so every estimate must lie within a
+per-result bound derived from that rounding:
+    |est_gpu - est| <= |f_res|/2 * 2^-11 * sum_i |2 ybar_i| |q'_i|  (+ FP32 slack).
+Ids are compared bit-exactly outside near-ties of that size, and the
+re-ranked top-k must match the oracle's exact re-rank."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as S
+from gpu_common import assert_close_rel, compare_topk_ids, erq, to_dev  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _index(erq, N, D, B, nlist, seed):
+    X, lab = S.mixture(N, D, 16, seed, scale="aniso")
+    assign = S.kmeans_assign(X, nlist, 4, seed + 7)
+    P = S.random_orthogonal(D, seed + 1)
+    return X, P, erq.build_index(to_dev(X), to_dev(P), B, nlist, assign=to_dev(assign)), \
+        oracle.build_index(X, P, assign, nlist, B)
+
+
+def _bound(ox, Q, ids):
+    """Per-result bound of the FP16 query rounding (FP64)."""
+    B = ox["B"]
+    qp = Q.astype(np.float64) @ ox["P"].astype(np.float64)          # q' = P^T q_r (rows)
+    _, f_res = oracle.stored_factors(ox["stats"])
+    rows = ox["row_of"][np.maximum(ids, 0)]
+    y2 = 2.0 * ox["codes"][rows].astype(np.float64) - (2 ** B - 1)   # [nq, k, D]
+    s = np.einsum("qkd,qd->qk", np.abs(y2), np.abs(qp))
+    return 0.5 * np.abs(f_res[rows]).astype(np.float64) * s * 2.0 ** -11
+
+
+@pytest.mark.parametrize("D,B,nq", [(128, 5, 1500), (64, 3, 400), (960, 7, 300)])
+def test_tc_scan_within_fp16_bound(erq, D, B, nq):
+    X, P, gx, ox = _index(erq, 20000, D, B, 64, 3000 + D + B)
+    Q, _ = S.mixture(nq, D, 16, 3100 + D, comp_seed=3000 + D + B, scale="aniso")
+    probe = S.random_probe_lists(nq, 64, 8, 3200 + D)
+    k, kp = 10, 40
+    ids, dists, cids, cest = gx.search(to_dev(Q), k, rerank_k=kp, probe=to_dev(probe), nprobe=8,
+                                       precision="fp16", return_candidates=True)
+    torch.cuda.synchronize()
+    gid = cids.cpu().numpy()
+    ge = cest.cpu().numpy().astype(np.float64)
+    assert (gid >= 0).all()
+    oest = oracle.estimate_rows(ox, Q, gid)
+    bound = _bound(ox, Q, gid) + 2e-5 * (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))
+    viol = np.abs(ge - oest) > bound
+    assert not viol.any(), f"{viol.sum()} estimates outside the FP16 bound"
+    # ids: exact outside near-ties of twice the largest observed relative error
+    err = (np.abs(ge - oest) / (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))).max()
+    ref = oracle.search(ox, Q, k, kprime=kp + 1, probe=probe)
+    compare_topk_ids(gid, ref["cand_ids"], ref["cand_est"], 1.5 * max(err, 1e-7), "fp16 candidates",
+                     max_excluded=0.15)
+    # exact re-rank of the same candidate sets gives the oracle's top-k
+    refr = oracle.search(ox, Q, k, kprime=kp, probe=probe)
+    same = (np.sort(gid, 1) == np.sort(ref["cand_ids"][:, :kp], 1)).all(1)
+    assert same.mean() > 0.5
+    gi = ids.cpu().numpy()
+    derr = assert_close_rel(dists.cpu().numpy()[same], refr["dists"][same], 1e-5, "re-ranked distances")
+    compare_topk_ids(gi[same], refr["ids"][same], refr["dists"][same], 1.5 * max(derr, 1e-7), "re-ranked ids",
+                     max_excluded=0.05)
+
+
+def test_tc_matches_fp32_recall(erq):
+    X, P, gx, ox = _index(erq, 30000, 128, 4, 32, 3300)
+    Q, _ = S.mixture(500, 128, 16, 3301, comp_seed=3300, scale="aniso")
+    a_ids, _ = gx.search(to_dev(Q), 10, rerank_k=32, nprobe=6, precision="fp32")
+    b_ids, _ = gx.search(to_dev(Q), 10, rerank_k=32, nprobe=6, precision="fp16")
+    gt, _ = oracle.exact_knn(X, Q, 10)
+    rec = lambda ids: np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy(), gt)])
+    ra, rb = rec(a_ids), rec(b_ids)
+    assert rb >= ra - 0.005, (ra, rb)
+    assert (a_ids == b_ids).float().mean().item() > 0.97
+
+
+def test_tc_rejects_large_k(erq):
+    X, P, gx, ox = _index(erq, 3000, 64, 4, 8, 3400)
+    Q = to_dev(S.mixture(4, 64, 16, 3401, comp_seed=3400, scale="aniso")[0])
+    with pytest.raises(erq.ErqError, match="tensor-core"):
+        gx.search(Q, 10, rerank_k=100, nprobe=2, precision="fp16")
