@@ -49,15 +49,20 @@ def parse():
     ap.add_argument("--recall", type=float, default=0.95)
     ap.add_argument("--cpu-sample", type=int, default=16, help="queries in the timed oracle sample")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of N and nq (smoke runs only)")
+    ap.add_argument("--n", type=int, default=0, help="override N (profiling cases)")
+    ap.add_argument("--nq", type=int, default=0, help="override the query count")
+    ap.add_argument("--nlist", type=int, default=0, help="override the IVF cluster count")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------------------- data
 def make_workload(args, rank=0):
-    cfg = S.WORKLOADS[args.workload]
-    n = int(cfg["n"] * args.scale)
-    nq = int(cfg["nq"] * args.scale)
+    cfg = dict(S.WORKLOADS[args.workload])
+    if args.nlist:
+        cfg["nlist"] = args.nlist
+    n = args.n or int(cfg["n"] * args.scale)
+    nq = args.nq or int(cfg["nq"] * args.scale)
     d = cfg["d"]
     X, _ = S.mixture(n, d, cfg["n_comp"], cfg["data_seed"], scale=cfg.get("scale", "unit"),
                      normalize=cfg.get("normalize", False))

@@ -94,7 +94,9 @@ typedef struct {
 } erq_search_params;
 
 /* erq_search_params.flags */
-#define ERQ_SEARCH_TIMING 1
+#define ERQ_SEARCH_TIMING 1      /* record per-phase CUDA events (erq_search_timing)        */
+#define ERQ_SEARCH_SIMT_GEMM 2   /* run the query rotation and centroid distances on the
+                                    CUDA-core SGEMM instead of the tensor-core FP32 GEMM    */
 
 /* Read-only description of an index. */
 typedef struct {

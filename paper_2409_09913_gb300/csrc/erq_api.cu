@@ -55,7 +55,8 @@ erq_status dalloc(T** p, size_t count, int64_t* tally = nullptr) {
 }
 
 void free_index_arrays(erq_index* ix) {
-    void* ptrs[] = {ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
+    void* ptrs[] = {ix->PT,    ix->eP,    ix->ePT,     ix->eC,
+                    ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io};
     for (void* p : ptrs)
@@ -108,6 +109,22 @@ erq_status check_status(erq_index* ix, cudaStream_t s) {
 }
 
 bool valid_d(int32_t D) { return D >= 64 && D <= 4096 && D % 64 == 0; }
+
+// P^T and the row exponents used by the tensor-core GEMM (from P and C).
+erq_status derive_gemm_arrays(erq_index* ix, cudaStream_t s) {
+    const int D = ix->D;
+    if (!ix->PT && cudaMalloc(&ix->PT, sizeof(float) * D * D) != cudaSuccess) return fail(ERQ_ENOMEM, "cudaMalloc P^T");
+    if (!ix->eP && cudaMalloc(&ix->eP, sizeof(int32_t) * D) != cudaSuccess) return fail(ERQ_ENOMEM, "cudaMalloc");
+    if (!ix->ePT && cudaMalloc(&ix->ePT, sizeof(int32_t) * D) != cudaSuccess) return fail(ERQ_ENOMEM, "cudaMalloc");
+    if (!ix->eC && cudaMalloc(&ix->eC, sizeof(int32_t) * ix->nlist) != cudaSuccess) return fail(ERQ_ENOMEM, "cudaMalloc");
+    ix->device_bytes += (int64_t)D * D * 4 + 8 * D + 4 * ix->nlist;
+    cudaError_t e;
+    if ((e = launch_transpose(ix->P, D, D, ix->PT, s)) != cudaSuccess) return cuda_fail(e, "transpose P");
+    if ((e = launch_row_exp(ix->P, D, D, ix->eP, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    if ((e = launch_row_exp(ix->PT, D, D, ix->ePT, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    if ((e = launch_row_exp(ix->C, ix->nlist, D, ix->eC, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    return ERQ_OK;
+}
 
 }  // namespace
 }  // namespace erq
@@ -331,6 +348,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     if ((e = launch_rotate_fp64(ix->C, nullptr, nullptr, nullptr, ix->P, ix->Cp, nlist, D, s)) != cudaSuccess)
         return bail2(cuda_fail(e, "rotate centroids"));
     if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return bail2(cuda_fail(e, "cnorm"));
+    if ((st = derive_gemm_arrays(ix, s)) != ERQ_OK) return bail2(st);
     // --- rotate residuals and encode, in chunks of rows
     {
         const int64_t chunk = std::min<int64_t>(N, std::max<int64_t>(4096, (int64_t)(1ll << 30) / (4ll * D)));
@@ -407,8 +425,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((uint64_t*)nullptr, (size_t)nq * kp);                          // 18 cand
         T((uint64_t*)nullptr, 2);                                        // 19 stats
         T((__half*)nullptr, prec == ERQ_PREC_FP32 ? 1 : (size_t)nq * D); // 20 Qh
+        T((int32_t*)nullptr, nq);                                        // 21 eQ
     };
-    void* sl[21];
+    void* sl[22];
     layout(plan, false, sl);
     ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
     Carver cv(ix->ws, ix->ws_bytes);
@@ -445,8 +464,17 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     };
     ERQ_TRY(mark(0));
     // ---- q' = P^T q_r
-    if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, D, D, 1.f, nullptr, s)) != cudaSuccess)
-        return cuda_fail(e, "query rotation");
+    const bool simt = (p->flags & ERQ_SEARCH_SIMT_GEMM) != 0;
+    int32_t* eQ = (int32_t*)sl[21];
+    if (simt) {
+        if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, D, D, 1.f, nullptr, s)) != cudaSuccess)
+            return cuda_fail(e, "query rotation");
+    } else {
+        if ((e = launch_row_exp(Q, nq, D, eQ, s)) != cudaSuccess) return cuda_fail(e, "query exponents");
+        if ((e = launch_gemm_tc(Q, eQ, nq, ix->PT, ix->ePT, D, D, Qrot, D, 0, nullptr, nullptr, nullptr, ix->status,
+                                s)) != cudaSuccess)
+            return cuda_fail(e, "query rotation");
+    }
     if (prec != ERQ_PREC_FP32 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
         return cuda_fail(e, "query half");
     ERQ_TRY(mark(1));
@@ -460,9 +488,11 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         if ((e = launch_fill_i32(probe, nq, 0, s)) != cudaSuccess) return cuda_fail(e, "probe fill");
     } else {
         if ((e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
-        if ((e = launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s)) != cudaSuccess)
-            return cuda_fail(e, "centroid distances");
-        if ((e = launch_row_topk(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s)) != cudaSuccess)
+        e = simt ? launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s)
+                 : launch_gemm_tc(Q, eQ, nq, ix->C, ix->eC, nlist, D, sqd, nlist, 1, nullptr, qn, ix->cnorm2,
+                                  ix->status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "centroid distances");
+        if ((e = launch_row_topk_fast(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s)) != cudaSuccess)
             return cuda_fail(e, "probe select");
     }
     ERQ_TRY(mark(2));
@@ -608,14 +638,17 @@ extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t
     if (!Q || !grad_Q || (nc > 0 && (!ids || !grad_scores))) return fail(ERQ_EINVAL, "erq_search_backward: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t mat = (size_t)nq * ix->D;
-    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, 2 * mat * 4 + 512));
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, 2 * mat * 4 + (size_t)nq * 4 + 1024));
     float* V = (float*)ix->ws;
     float* Wv = V + (mat + 63) / 64 * 64;
+    int32_t* eV = (int32_t*)(Wv + (mat + 63) / 64 * 64);
     cudaError_t e;
     if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, V, Wv, s)) != cudaSuccess)
         return cuda_fail(e, "backward gather");
-    // grad_Q = V P^T + Wv  (NT: B = P read as [n][k])
-    if ((e = launch_sgemm(true, V, ix->P, grad_Q, nq, ix->D, ix->D, 1.f, Wv, s)) != cudaSuccess)
+    // grad_Q = V P^T + Wv  (B = P read as [n][k])
+    if ((e = launch_row_exp(V, nq, ix->D, eV, s)) != cudaSuccess) return cuda_fail(e, "backward exponents");
+    if ((e = launch_gemm_tc(V, eV, nq, ix->P, ix->eP, ix->D, ix->D, grad_Q, ix->D, 0, Wv, nullptr, nullptr, ix->status,
+                            s)) != cudaSuccess)
         return cuda_fail(e, "backward gemm");
     return ERQ_OK;
 }
@@ -731,11 +764,13 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
     fclose(f);
     if (st == ERQ_OK && cudaMalloc(&ix->status, 4) != cudaSuccess) st = fail(ERQ_ENOMEM, "erq_index_load: status");
     if (st == ERQ_OK && cudaMemset(ix->status, 0, 4) != cudaSuccess) st = fail(ERQ_ECUDA, "erq_index_load: status");
+    if (st == ERQ_OK) st = derive_gemm_arrays(ix, (cudaStream_t)stream);
+    if (st == ERQ_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        st = fail(ERQ_ECUDA, "erq_index_load: derive");
     if (st != ERQ_OK) {
         erq_free_index(ix);
         return st;
     }
-    (void)stream;
     *out = ix;
     return ERQ_OK;
 }

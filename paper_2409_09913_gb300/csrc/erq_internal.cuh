@@ -86,6 +86,10 @@ struct erq_index {
     int32_t D = 0, B = 0, nlist = 0, keep_raw = 0;
     int64_t max_list = 0;
     float* P = nullptr;          // [D][D]
+    float* PT = nullptr;         // [D][D] transpose of P (B operand of q' = P^T q)
+    int32_t* eP = nullptr;       // [D] row exponents of P (tensor-core GEMM scaling)
+    int32_t* ePT = nullptr;      // [D] row exponents of P^T
+    int32_t* eC = nullptr;       // [nlist] row exponents of the centroids
     float* C = nullptr;          // [nlist][D] centroids
     float* Cp = nullptr;         // [nlist][D] rotated centroids P^T c
     float* cnorm2 = nullptr;     // [nlist] ||c||^2 (FP32, for the probe)

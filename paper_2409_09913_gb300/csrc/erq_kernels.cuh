@@ -60,6 +60,15 @@ cudaError_t launch_group(const int32_t* assign, int64_t n, int nlist, int64_t* l
 size_t group_scratch_bytes(int64_t n, int nlist);
 cudaError_t launch_row_topk(const float* V, int64_t rows, int ncols, int64_t ld, int p, int32_t* out_idx,
                             float* out_val, int64_t ld_out, cudaStream_t s);
+cudaError_t launch_row_topk_fast(const float* V, int64_t rows, int ncols, int64_t ld, int p, int32_t* out_idx,
+                                 float* out_val, int64_t ld_out, cudaStream_t s);
+
+// ---- k_gemm_tc.cu
+cudaError_t launch_row_exp(const float* X, int64_t n, int K, int32_t* e, cudaStream_t s);
+cudaError_t launch_gemm_tc(const float* A, const int32_t* eA, int64_t M, const float* B, const int32_t* eB, int N,
+                           int K, float* C, int64_t ldc, int epi, const float* addend, const float* rown,
+                           const float* coln, uint32_t* status, cudaStream_t s);
+cudaError_t launch_transpose(const float* X, int rows, int cols, float* out, cudaStream_t s);
 
 // ---- k_encode.cu
 cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* codes, float* f_add, float* f_res,

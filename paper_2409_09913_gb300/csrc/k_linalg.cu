@@ -601,3 +601,156 @@ cudaError_t launch_strided_ids(int64_t* out, int64_t n, int64_t N, uint64_t seed
 }
 
 }  // namespace erq
+
+namespace erq {
+
+// ---------------------------------------------------------------------------
+// Per-row selection by radix select (probe lists): the p smallest (value,
+// column) pairs of each row, ascending, ties by lower column.  One block of 256
+// threads per row; the row's order-preserving keys stay in shared memory
+// (ncols <= 16384).  Three histogram passes over 11 + 11 + 10 key bits find the
+// p-th smallest key T; the entries below T and the lowest-column entries equal
+// to T are gathered and sorted with a small bitonic network.
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+
+__global__ void __launch_bounds__(RS_THREADS) row_topk_radix_kernel(const float* __restrict__ V, int ncols,
+                                                                    int64_t ld, int p, int sortn,
+                                                                    int32_t* __restrict__ out_idx,
+                                                                    float* __restrict__ out_val, int64_t ld_out) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    // [ncols] keys | [2048] histogram | [sortn] selected (the u64 array must be
+    // 8-byte aligned for any ncols, so the key region is padded to 16 bytes)
+    const size_t keys_bytes = ((size_t)ncols * 4 + 15) / 16 * 16;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(rs_smem);
+    int* hist = reinterpret_cast<int*>(rs_smem + keys_bytes);
+    uint64_t* sel = reinterpret_cast<uint64_t*>(rs_smem + keys_bytes + 2048 * 4);
+    __shared__ int s_bin, s_below, s_nsel;
+    const int64_t row = blockIdx.x;
+    const float* v = V + row * ld;
+    for (int i = threadIdx.x; i < ncols; i += RS_THREADS) keys[i] = float_to_ordered(v[i]);
+    uint32_t prefix = 0, pmask = 0;
+    int need = p;                       // rank (1-based) of the wanted key among the candidates
+    const int shifts[3] = {21, 10, 0};
+    const int widths[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; ++pass) {
+        const int nb = 1 << widths[pass];
+        for (int i = threadIdx.x; i < nb; i += RS_THREADS) hist[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncols; i += RS_THREADS) {
+            const uint32_t k = keys[i];
+            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {           // first bin whose running count reaches `need`
+            const int per = nb / 32, lane = threadIdx.x;
+            int mine = 0;
+            for (int b = lane * per; b < (lane + 1) * per; ++b) mine += hist[b];
+            int incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = incl - mine;
+            const unsigned hit = __ballot_sync(0xffffffffu, incl >= need && excl < need);
+            if (lane == __ffs(hit) - 1) {
+                int run = excl, b = lane * per;
+                for (; b < (lane + 1) * per - 1; ++b) {
+                    if (run + hist[b] >= need) break;
+                    run += hist[b];
+                }
+                s_bin = b;
+                s_below = run;
+            }
+        }
+        __syncthreads();
+        need -= s_below;
+        prefix |= (uint32_t)s_bin << shifts[pass];
+        pmask |= (uint32_t)(nb - 1) << shifts[pass];
+        __syncthreads();
+    }
+    // T = prefix: `need` entries equal to T are wanted, all smaller ones are in
+    const uint32_t T = prefix;
+    if (threadIdx.x == 0) s_nsel = 0;
+    for (int i = threadIdx.x; i < sortn; i += RS_THREADS) sel[i] = kEmptyKey;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncols; i += RS_THREADS) {
+        const uint32_t k = keys[i];
+        if (k < T) sel[atomicAdd(&s_nsel, 1)] = ((uint64_t)k << 32) | (uint32_t)i;
+    }
+    __syncthreads();
+    // entries equal to T: the `need` lowest columns, found by scanning in column order
+    if (threadIdx.x < 32) {
+        const int base = s_nsel;
+        int taken = 0;
+        for (int c0 = 0; c0 < ncols && taken < need; c0 += 32) {
+            const int i = c0 + threadIdx.x;
+            const bool eq = i < ncols && keys[i] == T;
+            const unsigned m = __ballot_sync(0xffffffffu, eq);
+            const int rank = __popc(m & ((1u << threadIdx.x) - 1u));
+            if (eq && taken + rank < need) sel[base + taken + rank] = ((uint64_t)T << 32) | (uint32_t)i;
+            taken += __popc(m);
+        }
+    }
+    __syncthreads();
+    // sort the p selected keys
+    for (int size = 2; size <= sortn; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < sortn / 2; i += RS_THREADS) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t x = sel[lo], y = sel[hi];
+                if ((x > y) == up) { sel[lo] = y; sel[hi] = x; }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < p; i += RS_THREADS) {
+        const uint64_t k = sel[i];
+        out_idx[row * ld_out + i] = k == kEmptyKey ? -1 : (int32_t)(k & 0xffffffffu);
+        if (out_val) out_val[row * ld_out + i] = k == kEmptyKey ? INFINITY : ordered_to_float((uint32_t)(k >> 32));
+    }
+}
+
+cudaError_t launch_row_topk_fast(const float* V, int64_t rows, int ncols, int64_t ld, int p, int32_t* out_idx,
+                                 float* out_val, int64_t ld_out, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    if (ncols > 16384 || p > 2048) return launch_row_topk(V, rows, ncols, ld, p, out_idx, out_val, ld_out, s);
+    int sortn = 32;
+    while (sortn < p) sortn <<= 1;
+    const size_t smem = ((size_t)ncols * 4 + 15) / 16 * 16 + 2048 * 4 + (size_t)sortn * 8;
+    cudaError_t e = cudaFuncSetAttribute(row_topk_radix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    row_topk_radix_kernel<<<(unsigned)rows, RS_THREADS, smem, s>>>(V, ncols, ld, p, sortn, out_idx, out_val, ld_out);
+    return cudaGetLastError();
+}
+
+}  // namespace erq
+
+namespace erq {
+
+// out[c][r] = X[r][c] (32x32 tiles through shared memory).
+__global__ void transpose_kernel(const float* __restrict__ X, int rows, int cols, float* __restrict__ out) {
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = X[(int64_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(int64_t)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose(const float* X, int rows, int cols, float* out, cudaStream_t s) {
+    count_launch();
+    transpose_kernel<<<dim3((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32)), dim3(32, 8), 0, s>>>(X, rows,
+                                                                                                         cols, out);
+    return cudaGetLastError();
+}
+
+}  // namespace erq

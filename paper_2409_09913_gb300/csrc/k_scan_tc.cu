@@ -23,12 +23,15 @@
 // the MMAs of the next.  Every mbarrier wait is bounded: on expiry the kernel
 // records ERQ_ETIMEOUT in the status word, stops issuing work, waits (bounded)
 // for its MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "erq_kernels.cuh"
 #include "erq_search.cuh"
+#include "tc_common.cuh"
 
 namespace erq {
 
@@ -38,105 +41,31 @@ constexpr int QT = 128;          // queries per item (MMA M)
 constexpr int NB = 128;          // rows per MMA block (MMA N)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
 constexpr int STAGES = 4;
-constexpr int KCAP = 64;         // max k' of the in-shared-memory heaps
+constexpr int LOOK = STAGES - 1; // producer lookahead (stages in flight ahead of conversion)
+constexpr int KCAP = 48;         // max k' of the in-shared-memory heaps
 constexpr int THREADS = 288;
 constexpr int STAGE_A = QT * KB * 2;   // 16 KB
 constexpr int STAGE_B = NB * KB * 2;   // 16 KB
-constexpr uint64_t kWaitNs = 2000000000ull;   // a bounded wait gives up after 2 s
+constexpr int STAGE_RAW = NB * KB;     // 8 KB of u8 codes (TMA staging)
 
 struct Smem {
     // offsets in bytes from a 1024-aligned base
     static constexpr int a = 0;
     static constexpr int b = a + STAGES * STAGE_A;
-    static constexpr int heap = b + STAGES * STAGE_B;              // [KCAP][QT] u64
+    static constexpr int raw = b + STAGES * STAGE_B;               // TMA staging of raw codes
+    static constexpr int heap = raw + STAGES * STAGE_RAW;          // [KCAP][QT] u64
     static constexpr int bars = heap + KCAP * QT * 8;               // mbarriers (8 B each)
-    static constexpr int nbars = 2 * STAGES + 4 + 1;
+    static constexpr int nbars = 3 * STAGES + 4 + 1;
     static constexpr int tmem_slot = bars + nbars * 8;
     static constexpr int abort_flag = tmem_slot + 4;
     static constexpr int total = abort_flag + 4 + 1024;             // + alignment slack
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t now_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait; returns false (and raises the abort flag) when 2 s pass or
-// another role has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_test(bar, parity)) return true;
-    const uint64_t t0 = now_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (*abort_flag) return false;
-            if (now_ns() - t0 > kWaitNs) {
-                *abort_flag = 1;
-                return false;
-            }
-        }
-    }
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3fff);        // start address
-    d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;              // SBO
-    d |= (uint64_t)1 << 46;                        // version
-    d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, N, M.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-#define ERQ_TMEM_LD32(taddr, r)                                                                                   \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                         \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),          \
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
-                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),   \
-                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),   \
-                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                           \
-                 : "r"(taddr))
-
-// 16 u8 codes -> 16 FP16 values 2u - off, exact (1024 + u is exact in FP16).
-__device__ __forceinline__ void expand16(uint4 u, __half2 m2, __half2 off2, uint4& lo, uint4& hi) {
+// 16 u8 codes -> 16 FP16 values 2u - off, exact: 1024 + u is exact in FP16
+// (byte u as mantissa of 0x6400), fma(1024 + u, 2, -2048) = 2u is exact, and
+// 2u - off is an odd integer of magnitude <= 255 (exact).  off = 2^B - 1 is
+// applied separately because -(2048 + off) itself is not representable.
+__device__ __forceinline__ void expand16(uint4 u, __half2 two, __half2 m2048, __half2 off2, uint4& lo, uint4& hi) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
     uint32_t o[8];
 #pragma unroll
@@ -145,8 +74,8 @@ __device__ __forceinline__ void expand16(uint4 u, __half2 m2, __half2 off2, uint
         const uint32_t p1 = __byte_perm(w[i], 0x6464u, 0x4342u);   // {b2, 0x64, b3, 0x64}
         __half2 h0 = *reinterpret_cast<const __half2*>(&p0);
         __half2 h1 = *reinterpret_cast<const __half2*>(&p1);
-        h0 = __hfma2(h0, m2, off2);
-        h1 = __hfma2(h1, m2, off2);
+        h0 = __hsub2(__hfma2(h0, two, m2048), off2);
+        h1 = __hsub2(__hfma2(h1, two, m2048), off2);
         o[2 * i] = *reinterpret_cast<uint32_t*>(&h0);
         o[2 * i + 1] = *reinterpret_cast<uint32_t*>(&h1);
     }
@@ -179,7 +108,7 @@ struct Args {
 
 using namespace tc;
 
-__global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
+__global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* heap = reinterpret_cast<uint64_t*>(sm + Smem::heap);
@@ -189,6 +118,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
     const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
     const uint32_t done_bar = smem_u32(&bars[2 * STAGES + 4]);
+    const uint32_t tma0 = smem_u32(&bars[2 * STAGES + 5]);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, nkb = D / KB;
@@ -204,6 +134,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
             mbar_init(tempty0 + 8 * b, 128);
         }
         mbar_init(done_bar, 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(tma0 + 8 * s, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -218,11 +149,20 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
 
     if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------ producers
-        const int pt = tid - 128;                      // 0..127
-        const __half2 m2 = __floats2half2_rn(2.f, 2.f);
-        const float offv = -(2048.f + (float)((1 << a.B) - 1));
+        // Step t of an item = (128-row block, 64-wide K block).  issue(t): wait
+        // until the stage is free, then one thread starts a TMA load of the raw u8
+        // codes (128 rows x 64 bytes) into the stage's staging buffer and every
+        // thread cp.asyncs its 8 16-byte chunks of FP16 query rows straight into the
+        // swizzled A tile (zeros for absent queries).  convert(t), LOOK steps later:
+        // wait for the thread's own cp.asyncs and the TMA, expand the codes into the
+        // swizzled FP16 B tile, fence the async proxy, and arrive on full[stage].
+        const int pt = tid - 128;
+        const __half2 two = __floats2half2_rn(2.f, 2.f);
+        const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
+        const float offv = (float)((1 << a.B) - 1);
         const __half2 off2 = __floats2half2_rn(offv, offv);
-        uint32_t it = 0;                               // global stage iteration counter
+        const int achunk = pt & 7, bgrp = pt & 3;
+        uint32_t it = 0;                               // global stage counter at the item start
         bool ok = true;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int4 w = a.items[item];
@@ -231,60 +171,74 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
             const int nqi = (int)imin64(QT, a.qoff[c + 1] - qb);
             const int64_t rb0 = a.list_off[c] + (int64_t)w.z * a.RR;
             const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
-            // the 8 A rows this thread copies: rows pt/8 + 16*i, chunk pt%8
-            const int achunk = pt & 7;
-            int64_t qrow[8];
+            const int nblk = (int)((rb1 - rb0 + NB - 1) / NB);
+            const int nsteps = nblk * nkb;
+            const __half* qsrc[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = (pt >> 3) + 16 * i;
-                qrow[i] = r < nqi ? a.qlist[qb + r] / a.maxp : -1;
+                qsrc[i] = r < nqi ? a.Qh + (a.qlist[qb + r] / a.maxp) * D + achunk * 8 : nullptr;
             }
-            for (int64_t r0 = rb0; r0 < rb1 && ok; r0 += NB) {
-                const int nr = (int)imin64(NB, rb1 - r0);
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    if (!mbar_wait(empty0 + 8 * s, ((it / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    unsigned char* sa = sm + Smem::a + s * STAGE_A;
-                    unsigned char* sb = sm + Smem::b + s * STAGE_B;
-                    const int k0 = kb * KB;
-                    // A: 128 rows x 8 chunks of 16 B
-                    uint4 av[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        av[i] = qrow[i] >= 0
-                                    ? *reinterpret_cast<const uint4*>(a.Qh + qrow[i] * D + k0 + achunk * 8)
-                                    : make_uint4(0u, 0u, 0u, 0u);
-                    // B: 128 rows x 4 groups of 16 codes; this thread: rows pt/4 + 32*i, group pt%4
-                    const int bgrp = pt & 3;
-                    uint4 bv[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = (pt >> 2) + 32 * i;
-                        bv[i] = r < nr ? *reinterpret_cast<const uint4*>(a.codes + (r0 + r) * D + k0 + bgrp * 16)
-                                       : make_uint4(0u, 0u, 0u, 0u);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = (pt >> 3) + 16 * i;
-                        *reinterpret_cast<uint4*>(sa + r * 128 + ((achunk ^ (r & 7)) << 4)) = av[i];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = (pt >> 2) + 32 * i;
-                        uint4 lo, hi;
-                        if (r < nr) {
-                            expand16(bv[i], m2, off2, lo, hi);
-                        } else {
-                            lo = hi = make_uint4(0u, 0u, 0u, 0u);
-                        }
-                        *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp) ^ (r & 7)) << 4)) = lo;
-                        *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp + 1) ^ (r & 7)) << 4)) = hi;
-                    }
-                    fence_proxy_async();
-                    mbar_arrive(full0 + 8 * s);
+            auto issue = [&](int t) -> bool {
+                const uint32_t g = it + t;
+                const int s = g % STAGES;
+                if (!mbar_wait(empty0 + 8 * s, ((g / STAGES) & 1) ^ 1, abort_flag)) return false;
+                const int k0 = (t % nkb) * KB;
+                const int64_t r0 = rb0 + (int64_t)(t / nkb) * NB;
+                if (pt == 0) {
+                    mbar_arrive_expect_tx(tma0 + 8 * s, STAGE_RAW);
+                    tma_load_2d(smem_u32(sm + Smem::raw + s * STAGE_RAW), &codes_map, k0, (int)r0, tma0 + 8 * s);
                 }
+                const uint32_t sa = smem_u32(sm + Smem::a + s * STAGE_A);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = (pt >> 3) + 16 * i;
+                    const uint32_t dst = sa + r * 128 + ((achunk ^ (r & 7)) << 4);
+                    cp_async16(dst, qsrc[i] ? (const void*)(qsrc[i] + k0) : (const void*)a.Qh, qsrc[i] ? 16u : 0u);
+                }
+                cp_async_commit();
+                return true;
+            };
+            auto convert = [&](int t, int pending) -> bool {
+                const uint32_t g = it + t;
+                const int s = g % STAGES;
+                // own cp.asyncs of step t done: at most `pending` newer groups may remain
+                if (pending >= 3) cp_async_wait<3>();
+                else if (pending == 2) cp_async_wait<2>();
+                else if (pending == 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+                if (!mbar_wait(tma0 + 8 * s, (g / STAGES) & 1, abort_flag)) return false;
+                const int nr = (int)imin64(NB, rb1 - (rb0 + (int64_t)(t / nkb) * NB));
+                const unsigned char* raw = sm + Smem::raw + s * STAGE_RAW;
+                unsigned char* sb = sm + Smem::b + s * STAGE_B;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = (pt >> 2) + 32 * i;
+                    uint4 lo, hi;
+                    if (r < nr) {
+                        const uint4 u = *reinterpret_cast<const uint4*>(raw + r * KB + bgrp * 16);
+                        expand16(u, two, m2048, off2, lo, hi);
+                    } else {
+                        lo = hi = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                    *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp) ^ (r & 7)) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp + 1) ^ (r & 7)) << 4)) = hi;
+                }
+                fence_proxy_async();
+                mbar_arrive(full0 + 8 * s);
+                return true;
+            };
+            const int pre = nsteps < LOOK ? nsteps : LOOK;
+            for (int t = 0; t < pre && ok; ++t) ok = issue(t);
+            for (int t = 0; t < nsteps && ok; ++t) {
+                if (t + LOOK < nsteps) ok = issue(t + LOOK);
+                if (!ok) break;
+                const int issued = (t + LOOK < nsteps) ? t + LOOK + 1 : nsteps;
+                ok = convert(t, issued - t - 1);
             }
+            it += nsteps;
         }
+        cp_async_wait<0>();
     } else if (warp == 8) {
         // ------------------------------------------------------------ MMA issuer
         uint32_t it = 0, acc = 0;
@@ -297,12 +251,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
             const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
             for (int64_t r0 = rb0; r0 < rb1 && ok; r0 += NB, ++acc) {
                 const int buf = acc & 1;
-                if (!mbar_wait(tempty0 + 8 * buf, ((acc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait_warp(tempty0 + 8 * buf, ((acc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dt = tmem + buf * NB;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % STAGES;
-                    if (!mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait_warp(full0 + 8 * s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
                     tc_fence_after();
                     if (lane == 0) {
                         const uint32_t sa = smem_u32(sm + Smem::a + s * STAGE_A);
@@ -320,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
         // all issued MMAs complete before TMEM is released
         if (lane == 0) mma_commit(done_bar);
         __syncwarp();
-        mbar_wait(done_bar, 0, abort_flag);
+        mbar_wait_warp(done_bar, 0, abort_flag);
     } else {
         // ------------------------------------------------------------ epilogue
         const int q = tid;                             // TMEM lane = query slot
@@ -349,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(tc::Args a) {
             for (int64_t r0 = rb0; r0 < rb1; r0 += NB, ++acc) {
                 const int nr = (int)imin64(NB, rb1 - r0);
                 const int buf = acc & 1;
-                if (!mbar_wait(tfull0 + 8 * buf, (acc >> 1) & 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait_warp(tfull0 + 8 * buf, (acc >> 1) & 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
                 for (int cc = 0; cc < NB; cc += 32) {
@@ -430,6 +384,26 @@ bool tc_available(int precision, int D, int kp) {
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
 
+static bool make_codes_map(CUtensorMap* map, const uint8_t* codes, int64_t N, int D) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)D};          // bytes between rows
+    const cuuint32_t box[2] = {(cuuint32_t)KB, (cuuint32_t)NB};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)codes, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!tc_available(precision, L.D, L.kp))
         return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 64");
@@ -443,8 +417,11 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
+    CUtensorMap map;
+    if (((uintptr_t)L.codes & 15) != 0 || (L.D % 16) != 0 || !make_codes_map(&map, L.codes, L.N, L.D))
+        return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     count_launch();
-    scan_tc_kernel<<<L.grid, THREADS, smem, s>>>(a);
+    scan_tc_kernel<<<L.grid, THREADS, smem, s>>>(map, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc launch");
     return ERQ_OK;

@@ -173,12 +173,12 @@ class Index:
         _check(lib().erq_index_status(self._h, _stream()))
 
     def search(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp32", probe=None, nprobe_per_query=None,
-               return_candidates=False, timing=False):
+               return_candidates=False, timing=False, simt_gemm=False):
         Q = _dev(Q, torch.float32, "Q", 2)
         nq = Q.shape[0]
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
-        sp.flags = 1 if timing else 0
+        sp.flags = (1 if timing else 0) | (2 if simt_gemm else 0)
         keep = []
         if nprobe_per_query is not None:
             nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)

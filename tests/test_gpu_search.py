@@ -195,3 +195,37 @@ def test_kmeans_build_runs_and_partitions(erq):
     gt, _ = oracle.exact_knn(X, Q.cpu().numpy(), 10)
     recall = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(res.cpu().numpy(), gt)])
     assert recall > 0.8
+
+
+def test_tensor_core_gemm_matches_simt(erq):
+    """The FP32-accurate tensor-core GEMM (hi/lo FP16 split) used for the query
+    rotation and centroid distances agrees with the CUDA-core SGEMM to FP32
+    precision, so estimates and probe lists agree."""
+    X, P, assign, gx, ox = _build_pair(erq, 8000, 256, 5, 32, 1500, scale="aniso")
+    Q, _ = S.mixture(300, 256, 32, 1501, comp_seed=1500, scale="aniso")
+    a = gx.search(to_dev(Q), 10, rerank_k=30, nprobe=5, return_candidates=True)
+    b = gx.search(to_dev(Q), 10, rerank_k=30, nprobe=5, return_candidates=True, simt_gemm=True)
+    ok = (a[2] == b[2]).all(1).cpu().numpy()
+    assert ok.mean() > 0.95
+    assert_close_rel(a[3].cpu().numpy()[ok], b[3].cpu().numpy()[ok], 2e-6, "tc vs simt estimates")
+    oest = oracle.estimate_rows(ox, Q, a[2].cpu().numpy())
+    assert_close_rel(a[3].cpu().numpy(), oest, FP32_RTOL, "tc-gemm estimates vs oracle")
+
+
+def test_probe_ties_take_lower_cluster(erq):
+    """Identical centroids (a cluster duplicated) tie exactly; the probe keeps
+    the lower cluster id, as the oracle does."""
+    X, lab = S.mixture(2000, 64, 6, 1600)
+    assign = S.kmeans_assign(X, 6, 4, 1601)
+    X2 = np.concatenate([X, X])
+    a2 = np.concatenate([assign, assign + 6]).astype(np.int32)
+    P = S.random_orthogonal(64, 1602)
+    gx = erq.build_index(to_dev(X2), to_dev(P), 4, 12, assign=to_dev(a2))
+    ox = oracle.build_index(X2, P, a2, 12, 4)
+    Q, _ = S.mixture(40, 64, 6, 1603, comp_seed=1600)
+    for nprobe in (1, 3, 5):
+        ids, _, cids, cest = gx.search(to_dev(Q), 5, rerank_k=0, nprobe=nprobe, return_candidates=True)
+        ref = oracle.search(ox, Q, 5, kprime=6, nprobe=nprobe)
+        # every candidate comes from the first copy (ids < 2000): the lower cluster ids win the ties
+        assert (cids.cpu().numpy() < 2000).all()
+        assert (ref["cand_ids"][:, :5] < 2000).all()
