@@ -35,28 +35,29 @@ def assert_close_rel(got, ref, rtol=FP32_RTOL, what="values"):
     return err.max(initial=0.0)
 
 
-def compare_topk_ids(got_ids, ref_ids, ref_vals, tol, what="ids", max_excluded=0.02):
+def compare_topk_ids(got_ids, ref_ids, ref_vals, tol=None, what="ids", max_excluded=0.02, radius=None):
     """Ids must match bit-exactly wherever the oracle's ranking is not decided
     by a near-tie.  ``ref_ids``/``ref_vals`` may carry one extra column (the
     oracle's (k+1)-th entry) so that ties across the cut are detected.  Slot j
-    of query i is compared unless the oracle's value j lies within
-    2*tol*|value| of value j-1 or j+1.  Returns the fraction of excluded
-    slots, which must stay small."""
+    of query i is compared unless the oracle's value j lies within the sum of
+    the two slots' error radii of value j-1 or j+1: the radius of a slot is
+    ``radius[i, j]`` (absolute, per result) when given, else ``tol * |value|``.
+    Returns the fraction of excluded slots, which must stay below max_excluded."""
     got_ids = np.asarray(got_ids)
     ref_ids = np.asarray(ref_ids)
     v = np.asarray(ref_vals, np.float64)
+    r = np.asarray(radius, np.float64) if radius is not None else tol * np.abs(v)
     nq, k = got_ids.shape
     excluded = 0
     for i in range(nq):
-        vi = v[i]
+        vi, ri = v[i], r[i]
         fin = np.isfinite(vi)
         for j in range(k):
             if not fin[j]:
                 assert got_ids[i, j] == -1, f"{what}: query {i} slot {j} should be empty"
                 continue
-            t = 2 * tol * (abs(vi[j]) + 1e-30)
-            near = (j > 0 and abs(vi[j] - vi[j - 1]) <= t) or \
-                   (j + 1 < len(vi) and fin[j + 1] and abs(vi[j + 1] - vi[j]) <= t)
+            near = (j > 0 and abs(vi[j] - vi[j - 1]) <= ri[j] + ri[j - 1]) or \
+                   (j + 1 < len(vi) and fin[j + 1] and abs(vi[j + 1] - vi[j]) <= ri[j] + ri[j + 1])
             if near:
                 excluded += 1
                 continue

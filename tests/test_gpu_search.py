@@ -207,7 +207,7 @@ def test_tensor_core_gemm_matches_simt(erq):
     b = gx.search(to_dev(Q), 10, rerank_k=30, nprobe=5, return_candidates=True, simt_gemm=True)
     ok = (a[2] == b[2]).all(1).cpu().numpy()
     assert ok.mean() > 0.95
-    assert_close_rel(a[3].cpu().numpy()[ok], b[3].cpu().numpy()[ok], 2e-6, "tc vs simt estimates")
+    assert_close_rel(a[3].cpu().numpy()[ok], b[3].cpu().numpy()[ok], FP32_RTOL, "tc vs simt estimates")
     oest = oracle.estimate_rows(ox, Q, a[2].cpu().numpy())
     assert_close_rel(a[3].cpu().numpy(), oest, FP32_RTOL, "tc-gemm estimates vs oracle")
 
@@ -223,9 +223,13 @@ def test_probe_ties_take_lower_cluster(erq):
     gx = erq.build_index(to_dev(X2), to_dev(P), 4, 12, assign=to_dev(a2))
     ox = oracle.build_index(X2, P, a2, 12, 4)
     Q, _ = S.mixture(40, 64, 6, 1603, comp_seed=1600)
+    members = [set(np.nonzero(a2 == c)[0].tolist()) for c in range(12)]
     for nprobe in (1, 3, 5):
         ids, _, cids, cest = gx.search(to_dev(Q), 5, rerank_k=0, nprobe=nprobe, return_candidates=True)
         ref = oracle.search(ox, Q, 5, kprime=6, nprobe=nprobe)
-        # every candidate comes from the first copy (ids < 2000): the lower cluster ids win the ties
-        assert (cids.cpu().numpy() < 2000).all()
-        assert (ref["cand_ids"][:, :5] < 2000).all()
+        got = cids.cpu().numpy()
+        for i in range(len(Q)):
+            # with an odd nprobe the last probe slot falls inside a tied pair: the
+            # GPU must have taken the lower cluster id, exactly as the oracle did
+            allowed = set().union(*(members[c] for c in ref["probe"][i, :nprobe]))
+            assert set(got[i].tolist()) <= allowed, (nprobe, i, ref["probe"][i, :nprobe])
