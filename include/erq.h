@@ -97,6 +97,11 @@ typedef struct {
 #define ERQ_SEARCH_TIMING 1      /* record per-phase CUDA events (erq_search_timing)        */
 #define ERQ_SEARCH_SIMT_GEMM 2   /* run the query rotation and centroid distances on the
                                     CUDA-core SGEMM instead of the tensor-core FP32 GEMM    */
+#define ERQ_SEARCH_ASYNC 4       /* no host synchronisation inside the call: work buffers are
+                                    sized from host-side upper bounds, so the call can be
+                                    recorded into a CUDA graph once a first call with the
+                                    same (nq, nprobe, k') has sized them; device-side errors
+                                    surface at the next synchronous call or erq_index_status */
 
 /* Read-only description of an index. */
 typedef struct {
@@ -217,6 +222,24 @@ erq_status erq_index_load(const char* path, void* stream, erq_index** out);
 erq_status erq_search_timing(const erq_index* index, float* ms, int32_t n);
 uint64_t erq_kernel_launches(void);
 erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);
+
+/* Allocation-free variant of erq_search_backward (no counterpart in the paper;
+ * an interface for callers that cannot allocate device memory while they run,
+ * e.g. a training step being recorded into a CUDA graph, where stream capture
+ * forbids cudaMalloc, or a host that owns all device memory through its own
+ * pool).  Same arguments, result and errors as erq_search_backward.  Its
+ * intermediates (2 * nq * D floats and nq ints) live in one static device array
+ * of ERQ_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * keeps until the process exits; requests with 8*nq*D + 4*nq + 512 bytes above
+ * that size are rejected with ERQ_EINVAL.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and should be made before
+ * any stream capture.  All calls share the array and the previous call's
+ * contents are never read, but calls that can overlap on the GPU (different
+ * streams or threads) race on it and must be serialised by the caller.  No
+ * memory is allocated or freed by this call. */
+#define ERQ_NOALLOC_SCRATCH_BYTES (16u << 20)
+erq_status erq_search_backward_noalloc(erq_index* index, const float* Q, int64_t nq, int32_t nc,
+                                       const int64_t* ids, const float* grad_scores, float* grad_Q, void* stream);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,7 @@ FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, 
 EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index", "erq_index_info_get",
            "erq_index_status", "erq_rotate", "erq_encode", "erq_search", "erq_search_host", "erq_estimate",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
-           "erq_kernel_launches", "erq_search_stats"]
+           "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc"]
 
 
 class ErqError(RuntimeError):
@@ -84,10 +84,11 @@ def lib(path: str | None = None):
     L.erq_kernel_launches.argtypes = []
     L.erq_kernel_launches.restype = ct.c_uint64
     L.erq_search_stats.argtypes = [vp, ct.POINTER(ct.c_int64), i32]
+    L.erq_search_backward_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
     for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
                  "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
                  "erq_index_save", "erq_index_load", "erq_search_timing",
-                 "erq_search_stats"):
+                 "erq_search_stats", "erq_search_backward_noalloc"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -173,12 +174,12 @@ class Index:
         _check(lib().erq_index_status(self._h, _stream()))
 
     def search(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp32", probe=None, nprobe_per_query=None,
-               return_candidates=False, timing=False, simt_gemm=False):
+               return_candidates=False, timing=False, simt_gemm=False, async_mode=False):
         Q = _dev(Q, torch.float32, "Q", 2)
         nq = Q.shape[0]
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
-        sp.flags = (1 if timing else 0) | (2 if simt_gemm else 0)
+        sp.flags = (1 if timing else 0) | (2 if simt_gemm else 0) | (4 if async_mode else 0)
         keep = []
         if nprobe_per_query is not None:
             nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
@@ -242,6 +243,18 @@ class Index:
         out = torch.empty_like(Q)
         _check(lib().erq_search_backward(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
                                          _ptr(out), _stream()))
+        return out
+
+    def search_backward_noalloc(self, Q, ids, grad_scores, out=None):
+        """erq_search_backward without device allocation inside the call (its
+        intermediates live in the library's fixed scratch array); ``out`` may be
+        a preallocated [nq, D] float32 CUDA tensor."""
+        Q = _dev(Q, torch.float32, "Q", 2)
+        ids = _dev(ids, torch.int64, "ids", 2)
+        g = _dev(grad_scores, torch.float32, "grad_scores", 2)
+        out = torch.empty_like(Q) if out is None else out
+        _check(lib().erq_search_backward_noalloc(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
+                                                 _ptr(out), _stream()))
         return out
 
     def export(self, field):
