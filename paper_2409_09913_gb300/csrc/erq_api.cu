@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -55,7 +56,7 @@ erq_status dalloc(T** p, size_t count, int64_t* tally = nullptr) {
 }
 
 void free_index_arrays(erq_index* ix) {
-    void* ptrs[] = {ix->PT,    ix->eP,    ix->ePT,     ix->eC,
+    void* ptrs[] = {ix->PT,    ix->eP,    ix->ePT,     ix->eC,   ix->corder,
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io};
@@ -123,6 +124,16 @@ erq_status derive_gemm_arrays(erq_index* ix, cudaStream_t s) {
     if ((e = launch_row_exp(ix->P, D, D, ix->eP, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->PT, D, D, ix->ePT, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->C, ix->nlist, D, ix->eC, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    // clusters by decreasing size: work items of the largest clusters are scheduled first
+    std::vector<int32_t> order(ix->nlist);
+    for (int j = 0; j < ix->nlist; ++j) order[j] = j;
+    const std::vector<int64_t>& off = *ix->host_list_off;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return off[x + 1] - off[x] > off[y + 1] - off[y]; });
+    if (!ix->corder && cudaMalloc(&ix->corder, sizeof(int32_t) * ix->nlist) != cudaSuccess)
+        return fail(ERQ_ENOMEM, "cudaMalloc");
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->corder, order.data(), sizeof(int32_t) * ix->nlist, cudaMemcpyHostToDevice, s));
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
     return ERQ_OK;
 }
 
@@ -348,7 +359,6 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     if ((e = launch_rotate_fp64(ix->C, nullptr, nullptr, nullptr, ix->P, ix->Cp, nlist, D, s)) != cudaSuccess)
         return bail2(cuda_fail(e, "rotate centroids"));
     if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return bail2(cuda_fail(e, "cnorm"));
-    if ((st = derive_gemm_arrays(ix, s)) != ERQ_OK) return bail2(st);
     // --- rotate residuals and encode, in chunks of rows
     {
         const int64_t chunk = std::min<int64_t>(N, std::max<int64_t>(4096, (int64_t)(1ll << 30) / (4ll * D)));
@@ -372,6 +382,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return bail2(cuda_fail(e, "list_off"));
     if ((st = check_status(ix, s)) != ERQ_OK) return bail2(st);
+    if ((st = derive_gemm_arrays(ix, s)) != ERQ_OK) return bail2(st);
     cudaFree(assign);
     int64_t mx = 0;
     for (int j = 0; j < nlist; ++j) mx = std::max(mx, (*ix->host_list_off)[j + 1] - (*ix->host_list_off)[j]);
@@ -507,33 +518,59 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.QT = QT;
     pa.RR = RR;
     pa.list_off = ix->list_off;
+    pa.corder = ix->corder;
     pa.npr = npr;
     pa.status = ix->status;
     if ((e = launch_plan(pa, s)) != cudaSuccess) return cuda_fail(e, "plan");
     // dqc needs the validated probe ids
     if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
-    int64_t tot[2] = {0, 0};
-    ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[0], pa.qbase + nq, 8, cudaMemcpyDeviceToHost, s));
-    ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + nlist, 8, cudaMemcpyDeviceToHost, s));
-    ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->last_stats, pa.stats, 16, cudaMemcpyDeviceToHost, s));
-    ERQ_TRY(check_status(ix, s));
-    const int64_t Ltot = tot[0], nitems = tot[1];
-    ix->last_stats[2] = nitems;
-    ix->last_stats[3] = Ltot;
+    int64_t Ltot = 0, nitems = 0;
+    const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0;
+    if (async) {
+        // upper bounds from the cluster sizes (no read-back):
+        //   items <= maxR * ceil(nq * maxp / QT) + sum_c nr_c,  lists <= nq * (sum of the maxp largest nr_c)
+        const std::vector<int64_t>& off = *ix->host_list_off;
+        std::vector<int64_t> nr(nlist);
+        int64_t maxR = 0, sumR = 0;
+        for (int c = 0; c < nlist; ++c) {
+            nr[c] = (off[c + 1] - off[c] + RR - 1) / RR;
+            maxR = std::max(maxR, nr[c]);
+            sumR += nr[c];
+        }
+        std::partial_sort(nr.begin(), nr.begin() + std::min(maxp, nlist), nr.end(), std::greater<int64_t>());
+        int64_t topR = 0;
+        for (int i = 0; i < std::min(maxp, nlist); ++i) topR += nr[i];
+        nitems = maxR * ceil_div(nq * (int64_t)maxp, QT) + sumR;
+        Ltot = nq * topR;
+    } else {
+        int64_t tot[2] = {0, 0};
+        ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[0], pa.qbase + nq, 8, cudaMemcpyDeviceToHost, s));
+        ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + nlist, 8, cudaMemcpyDeviceToHost, s));
+        ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->last_stats, pa.stats, 16, cudaMemcpyDeviceToHost, s));
+        ERQ_TRY(check_status(ix, s));
+        Ltot = tot[0];
+        nitems = tot[1];
+        ix->last_stats[2] = nitems;
+        ix->last_stats[3] = Ltot;
+    }
     // ---- phase B workspace
     Carver pb(nullptr, 0);
     pb.take<int4>(nitems);
-    pb.take<uint64_t>((size_t)Ltot * kp);
+    const int lstride = scan_list_stride(prec, kp);
+    pb.take<uint64_t>((size_t)Ltot * lstride);
     pb.take<int32_t>(Ltot);
     pb.take<int64_t>(1);
+    if (async && ix->ws_b_bytes < pb.off)
+        ERQ_CHECK_CUDA(cudaStreamSynchronize(s));   // growing the buffer frees the old one
     ERQ_TRY(ensure_ws(&ix->ws_b, &ix->ws_b_bytes, pb.off));
     Carver cb(ix->ws_b, ix->ws_b_bytes);
     int4* items = cb.take<int4>(nitems);
-    uint64_t* inter = cb.take<uint64_t>((size_t)Ltot * kp);
+    uint64_t* inter = cb.take<uint64_t>((size_t)Ltot * lstride);
     int32_t* inter_cnt = cb.take<int32_t>(Ltot);
     int64_t* n_items_d = cb.take<int64_t>(1);
     ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + nlist, 8, cudaMemcpyDeviceToDevice, s));
     if (Ltot > 0) ERQ_CHECK_CUDA(cudaMemsetAsync(inter_cnt, 0, sizeof(int32_t) * Ltot, s));
+
     if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
     ERQ_TRY(mark(3));
     // ---- scan
@@ -553,7 +590,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     }
     ERQ_TRY(mark(4));
     // ---- merge, re-rank
-    if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, cand, s)) != cudaSuccess) return cuda_fail(e, "merge");
+    if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, lstride, cand, s)) != cudaSuccess)
+        return cuda_fail(e, "merge");
     ERQ_TRY(mark(5));
     if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ids, dists, p->cand_ids, p->cand_est,
                            s)) != cudaSuccess)

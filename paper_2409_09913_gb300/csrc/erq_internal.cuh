@@ -104,6 +104,7 @@ struct erq_index {
     float* X = nullptr;          // [N][D] raw rows, original order (keep_raw)
     uint32_t* status = nullptr;  // device status word
     std::vector<int64_t>* host_list_off = nullptr;  // host copy of list_off
+    int32_t* corder = nullptr;   // [nlist] cluster ids by decreasing size (work-item order)
     // search workspace (grown on demand)
     void* ws = nullptr;          // phase-A / build workspace
     size_t ws_bytes = 0;

@@ -17,6 +17,7 @@ struct PlanArgs {
     int64_t nq;
     int maxp, nlist, QT, RR;
     const int64_t* list_off;
+    const int32_t* corder;      // [nlist] clusters by decreasing size
     int32_t* npr;               // [nq] effective nprobe
     int32_t* probe_c;           // [nq][maxp] validated cluster or -1
     int32_t* cnt_c;             // [nlist]
@@ -63,9 +64,10 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s);
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
 size_t scan_fp32_smem(int kp);
-int merge_sortn(int kp);
+int merge_sortn(int kp, int lstride);
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
-                         uint64_t* cand, cudaStream_t s);
+                         int lstride, uint64_t* cand, cudaStream_t s);
+int scan_list_stride(int precision, int kp);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           cudaStream_t s);

@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(gemm::THREADS, 1) gemm_tc_kernel(gemm::Args a)
                             *reinterpret_cast<float4*>(crow + j) = o;
                         }
                     } else {
-                        for (int j = 0; j < 32 && nb + j < a.N; ++j) crow[j] = out[j] + (arow ? arow[j] : 0.f);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (nb + j < a.N) crow[j] = out[j] + (arow ? arow[j] : 0.f);
                     }
                 }
             }

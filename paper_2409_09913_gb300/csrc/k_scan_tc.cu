@@ -12,13 +12,15 @@
 // with ||q_r - c||^2 from FP32 and g, f_res the stored per-row factors.
 //
 // Warp roles (288 threads, one CTA per SM, persistent over work items):
-//   warps 0-3  epilogue: TMEM lane = query; tcgen05.ld of the accumulator row,
-//              estimator, and a per-query max-heap of the k' best (estimate, id)
-//              keys in shared memory (k' <= 64);
+//   warps 0-3  epilogue: tcgen05.ld of 32 accumulator columns per step, an
+//              in-register warp transpose so that each query's estimates lie
+//              across the warp, warp-wide admission filtering against a per-query
+//              threshold and per-query candidate lists in shared memory, compacted
+//              by a warp bitonic sort (k' <= 32);
 //   warps 4-7  producers: gather FP16 query rows and expand u8 codes into the
 //              128B-swizzled K-major layout of a pipeline stage;
 //   warp 8     MMA issuer (one elected thread) and TMEM owner.
-// Pipeline: 4 stages of (A 16 KB, B 16 KB) per 64-wide K block; two TMEM
+// Pipeline: 3 stages of (A 16 KB, B 16 KB, raw codes 8 KB) per 64-wide K block; two TMEM
 // accumulators of 128 columns so the epilogue of one 128-row block overlaps
 // the MMAs of the next.  Every mbarrier wait is bounded: on expiry the kernel
 // records ERQ_ETIMEOUT in the status word, stops issuing work, waits (bounded)
@@ -40,9 +42,10 @@ namespace tc {
 constexpr int QT = 128;          // queries per item (MMA M)
 constexpr int NB = 128;          // rows per MMA block (MMA N)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int LOOK = STAGES - 1; // producer lookahead (stages in flight ahead of conversion)
-constexpr int KCAP = 48;         // max k' of the in-shared-memory heaps
+constexpr int KCAP = 32;         // max k' of the tensor-core path
+constexpr int KC = 64;           // per-query candidate list capacity (list stride of the output)
 constexpr int THREADS = 288;
 constexpr int STAGE_A = QT * KB * 2;   // 16 KB
 constexpr int STAGE_B = NB * KB * 2;   // 16 KB
@@ -53,8 +56,12 @@ struct Smem {
     static constexpr int a = 0;
     static constexpr int b = a + STAGES * STAGE_A;
     static constexpr int raw = b + STAGES * STAGE_B;               // TMA staging of raw codes
-    static constexpr int heap = raw + STAGES * STAGE_RAW;          // [KCAP][QT] u64
-    static constexpr int bars = heap + KCAP * QT * 8;               // mbarriers (8 B each)
+    static constexpr int lists = raw + STAGES * STAGE_RAW;         // [QT][KC] u64 candidate keys
+    static constexpr int cnt = lists + QT * KC * 8;                 // [QT] int   list fill
+    static constexpr int tau = cnt + QT * 4;                        // [QT] u64   admission threshold
+    static constexpr int dqc = tau + QT * 8;                        // [QT] float ||q_r - c||^2
+    static constexpr int lidx = dqc + QT * 4;                       // [QT] int64 output list index
+    static constexpr int bars = lidx + QT * 8;                      // mbarriers (8 B each)
     static constexpr int nbars = 3 * STAGES + 4 + 1;
     static constexpr int tmem_slot = bars + nbars * 8;
     static constexpr int abort_flag = tmem_slot + 4;
@@ -108,10 +115,87 @@ struct Args {
 
 using namespace tc;
 
+// 32x32 transpose of a warp's registers (5 butterfly stages, static indices):
+// on entry lane t holds row t in v[0..31]; on exit lane l holds column l, i.e.
+// v[i] = (old row i)[l].
+__device__ __forceinline__ void warp_transpose32(uint32_t (&v)[32], int lane) {
+#pragma unroll
+    for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool upper = (lane & sft) != 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i & sft) continue;
+            const uint32_t send = upper ? v[i] : v[i ^ sft];
+            const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, sft);
+            if (upper) v[i] = recv;
+            else v[i ^ sft] = recv;
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t x, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)x, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(x >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Ascending warp bitonic sort of 64 keys held as element e = i*32 + lane in v[i].
+__device__ __forceinline__ void warp_sort64(uint64_t (&v)[2], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int e = i * 32 + lane;
+                const bool asc = (e & size) == 0 || size == 64;
+                if (d == 32) {                     // partner in the other register of this lane
+                    if (i == 0) {
+                        const uint64_t a = v[0], b = v[1];
+                        const bool a_lo = asc;     // e < e ^ 32 here
+                        v[0] = (a < b) == a_lo ? a : b;
+                        v[1] = (a < b) == a_lo ? b : a;
+                    }
+                } else {
+                    const uint64_t p = shfl_xor_u64(v[i], d);
+                    const bool lower = (e & d) == 0;
+                    const bool keep_min = lower == asc;
+                    v[i] = keep_min ? (p < v[i] ? p : v[i]) : (p > v[i] ? p : v[i]);
+                }
+            }
+        }
+    }
+}
+
+// Keep the kp smallest keys of one query's list (cnt <= KC entries) in its
+// first kp slots, sorted; returns the new admission threshold (the kp-th key).
+__device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, int lane) {
+    uint64_t v[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int e = i * 32 + lane;
+        v[i] = e < cnt ? list[e] : kEmptyKey;
+    }
+    warp_sort64(v, lane);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int e = i * 32 + lane;
+        if (e < kp) list[e] = v[i];
+    }
+    const int t = kp - 1;
+    const uint64_t th = shfl_u64(t >= 32 ? v[1] : v[0], t & 31);
+    __syncwarp();
+    return th;
+}
+
 __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* heap = reinterpret_cast<uint64_t*>(sm + Smem::heap);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Smem::tmem_slot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + Smem::abort_flag);
@@ -173,11 +257,14 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
             const int nblk = (int)((rb1 - rb0 + NB - 1) / NB);
             const int nsteps = nblk * nkb;
+            // query i of the item sits in A row (slot) (i % 4) * 32 + i / 4, so that
+            // the active queries spread over all four epilogue warps
             const __half* qsrc[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = (pt >> 3) + 16 * i;
-                qsrc[i] = r < nqi ? a.Qh + (a.qlist[qb + r] / a.maxp) * D + achunk * 8 : nullptr;
+                const int qi = (r & 31) * 4 + (r >> 5);
+                qsrc[i] = qi < nqi ? a.Qh + (a.qlist[qb + qi] / a.maxp) * D + achunk * 8 : nullptr;
             }
             auto issue = [&](int t) -> bool {
                 const uint32_t g = it + t;
@@ -277,8 +364,21 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         mbar_wait_warp(done_bar, 0, abort_flag);
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = tid;                             // TMEM lane = query slot
+        // Warp w owns TMEM lanes (query slots) 32w..32w+31.  Per 32-column chunk
+        // the accumulator rows are transposed in registers, so lane l holds column
+        // l of all 32 slots: the estimates of one query then sit across the warp,
+        // are filtered against that query's admission threshold with one ballot,
+        // and the survivors are appended to its list; a list that fills is
+        // compacted by a warp bitonic sort to its kp smallest keys, which also
+        // tightens the threshold.  Each list is a superset of the item's top-kp.
+        uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
+        int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
+        uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
+        float* s_dqc = reinterpret_cast<float*>(sm + Smem::dqc);
+        int64_t* s_lidx = reinterpret_cast<int64_t*>(sm + Smem::lidx);
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const uint32_t below = (1u << lane) - 1u;
+        const int kp = a.kp;
         uint32_t acc = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -288,18 +388,18 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int nqi = (int)imin64(QT, a.qoff[c + 1] - qb);
             const int64_t rb0 = a.list_off[c] + (int64_t)w.z * a.RR;
             const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
-            const bool active = q < nqi;
-            float dqc = 0.f;
-            int64_t list = 0;
-            if (active) {
-                const int64_t e = a.qlist[qb + q];
-                const int64_t qq = e / a.maxp;
-                dqc = a.dqc[e];
-                list = a.qbase[qq] + a.slot_off[e] + w.z;
+            {   // slot setup: slot = warp*32 + lane holds query lane*4 + warp
+                const int slot = warp * 32 + lane, qi = lane * 4 + warp;
+                s_cnt[slot] = 0;
+                s_tau[slot] = kEmptyKey;
+                if (qi < nqi) {
+                    const int64_t e = a.qlist[qb + qi];
+                    s_dqc[slot] = a.dqc[e];
+                    s_lidx[slot] = a.qbase[e / a.maxp] + a.slot_off[e] + w.z;
+                }
             }
-            int hs = 0;
-            uint64_t root = kEmptyKey;                  // heap maximum once full
-            const int kp = a.kp;
+            __syncwarp();
+            const int nact = nqi > warp ? (nqi - warp + 3) / 4 : 0;   // active slots of this warp
             for (int64_t r0 = rb0; r0 < rb1; r0 += NB, ++acc) {
                 const int nr = (int)imin64(NB, rb1 - r0);
                 const int buf = acc & 1;
@@ -307,66 +407,56 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 tc_fence_after();
 #pragma unroll 1
                 for (int cc = 0; cc < NB; cc += 32) {
-                    uint32_t r[32];
-                    ERQ_TMEM_LD32(tmem + lane_base + buf * NB + cc, r);
-                    // row factors of columns cc..cc+31: one coalesced load, then shuffles
-                    const int mc = cc + lane;
+                    uint32_t v[32];
+                    ERQ_TMEM_LD32(tmem + lane_base + buf * NB + cc, v);
+                    const int col = cc + lane;
+                    const bool valid = col < nr;
                     float mg = 0.f, mf = 0.f;
                     uint32_t mid = 0;
-                    if (mc < nr) {
-                        mg = a.g_const[r0 + mc];
-                        mf = 0.5f * a.f_res[r0 + mc];
-                        mid = (uint32_t)a.list_ids[r0 + mc];
+                    if (valid) {
+                        mg = a.g_const[r0 + col];
+                        mf = 0.5f * a.f_res[r0 + col];
+                        mid = (uint32_t)a.list_ids[r0 + col];
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    const int ncol = nr - cc < 32 ? nr - cc : 32;
-#pragma unroll 4
-                    for (int j = 0; j < 32; ++j) {
-                        const float gj = __shfl_sync(0xffffffffu, mg, j);
-                        const float fj = __shfl_sync(0xffffffffu, mf, j);
-                        const uint32_t idj = __shfl_sync(0xffffffffu, mid, j);
-                        if (!active || j >= ncol) continue;
-                        const float est = dqc + gj + fj * __uint_as_float(r[j]);
-                        const uint64_t key = make_key(est, idj);
-                        if (hs < kp) {
-                            int h = hs++;
-                            while (h > 0) {
-                                const int p = (h - 1) >> 1;
-                                const uint64_t pk = heap[p * QT + q];
-                                if (pk >= key) break;
-                                heap[h * QT + q] = pk;
-                                h = p;
-                            }
-                            heap[h * QT + q] = key;
-                            if (hs == kp) root = heap[q];
-                        } else if (key < root) {
-                            int h = 0;
-                            for (;;) {
-                                const int l = 2 * h + 1;
-                                if (l >= kp) break;
-                                int m = l;
-                                uint64_t mk = heap[l * QT + q];
-                                if (l + 1 < kp) {
-                                    const uint64_t rk = heap[(l + 1) * QT + q];
-                                    if (rk > mk) { m = l + 1; mk = rk; }
-                                }
-                                if (mk <= key) break;
-                                heap[h * QT + q] = mk;
-                                h = m;
-                            }
-                            heap[h * QT + q] = key;
-                            root = heap[q];
+                    if (nact == 0 || cc >= nr) continue;
+                    warp_transpose32(v, lane);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i >= nact) break;                       // warp-uniform
+                        const int slot = warp * 32 + i;
+                        const float est = s_dqc[slot] + mg + mf * __uint_as_float(v[i]);
+                        const uint64_t key = make_key(est, mid);
+                        const bool pass = valid && key < s_tau[slot];
+                        const uint32_t m = __ballot_sync(0xffffffffu, pass);
+                        if (m == 0u) continue;
+                        int cnt = s_cnt[slot];
+                        if (pass) lists[slot * KC + cnt + __popc(m & below)] = key;
+                        cnt += __popc(m);
+                        __syncwarp();
+                        if (cnt > KC - 32) {
+                            const uint64_t th = compact_list(lists + slot * KC, cnt, kp, lane);
+                            cnt = kp;
+                            if (lane == 0) s_tau[slot] = th;
                         }
+                        if (lane == 0) s_cnt[slot] = cnt;
+                        __syncwarp();
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(tempty0 + 8 * buf);
             }
-            if (active && ok) {
-                uint64_t* dst = a.inter + list * kp;
-                for (int j = 0; j < hs; ++j) dst[j] = heap[j * QT + q];
-                a.inter_cnt[list] = hs;
+            if (ok) {
+                for (int i = 0; i < nact; ++i) {                     // write this warp's lists
+                    const int slot = warp * 32 + i;
+                    const int cnt = s_cnt[slot];
+                    const int64_t L = s_lidx[slot];
+                    uint64_t* dst = a.inter + L * KC;
+                    for (int e = lane; e < cnt; e += 32) dst[e] = lists[slot * KC + e];
+                    if (lane == 0) a.inter_cnt[L] = cnt;
+                }
             }
+            __syncwarp();
         }
     }
     tc_fence_before();
@@ -381,6 +471,9 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
 bool tc_available(int precision, int D, int kp) {
     return precision == ERQ_PREC_FP16 && D % KB == 0 && kp <= KCAP;
 }
+
+// Capacity (stride) of the per-(query, item) candidate lists written by the scan.
+int scan_list_stride(int precision, int kp) { return precision == ERQ_PREC_FP32 ? kp : KC; }
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
 
@@ -406,7 +499,7 @@ static bool make_codes_map(CUtensorMap* map, const uint8_t* codes, int64_t N, in
 
 erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!tc_available(precision, L.D, L.kp))
-        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 64");
+        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 32");
     if (!L.Qh) return fail(ERQ_EINVAL, "tensor-core scan: FP16 queries missing");
     tc::Args a;
     a.Qh = (const __half*)L.Qh; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;

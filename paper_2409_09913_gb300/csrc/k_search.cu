@@ -129,15 +129,18 @@ __global__ void excl_scan_i64_kernel(const int64_t* __restrict__ in, int64_t n, 
 }
 
 // per cluster: pair count (int64) and item count
+// per cluster: pair count (int64) and, at the cluster's rank in `corder`
+// (decreasing size), its number of work items
 __global__ void plan_cluster_kernel(const int32_t* __restrict__ cnt_c, const int64_t* __restrict__ list_off,
-                                    int nlist, int QT, int RR, int64_t* __restrict__ cnt64,
-                                    int64_t* __restrict__ items_c) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nlist) return;
+                                    const int32_t* __restrict__ corder, int nlist, int QT, int RR,
+                                    int64_t* __restrict__ cnt64, int64_t* __restrict__ items_r) {
+    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rk >= nlist) return;
+    const int c = corder ? corder[rk] : rk;
     const int64_t size = list_off[c + 1] - list_off[c];
     const int64_t n = cnt_c[c];
     cnt64[c] = n;
-    items_c[c] = (n > 0 && size > 0) ? ((n + QT - 1) / QT) * ((size + RR - 1) / RR) : 0;
+    items_r[rk] = (n > 0 && size > 0) ? ((n + QT - 1) / QT) * ((size + RR - 1) / RR) : 0;
 }
 
 __global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t nq, int maxp,
@@ -152,11 +155,12 @@ __global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t
 }
 
 __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64_t* __restrict__ list_off,
-                                  const int64_t* __restrict__ item_off, int nlist, int QT, int RR,
-                                  int4* __restrict__ items) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nlist) return;
-    const int64_t b = item_off[c], e = item_off[c + 1];
+                                  const int64_t* __restrict__ item_off, const int32_t* __restrict__ corder,
+                                  int nlist, int QT, int RR, int4* __restrict__ items) {
+    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rk >= nlist) return;
+    const int c = corder ? corder[rk] : rk;
+    const int64_t b = item_off[rk], e = item_off[rk + 1];
     if (b == e) return;
     const int64_t size = list_off[c + 1] - list_off[c];
     const int nranges = (int)((size + RR - 1) / RR);
@@ -374,8 +378,8 @@ __device__ void block_bitonic_u64(uint64_t* v, int n) {
 
 __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__ inter,
                                                     const int32_t* __restrict__ inter_cnt,
-                                                    const int64_t* __restrict__ qbase, int kp, int sortn,
-                                                    uint64_t* __restrict__ cand) {
+                                                    const int64_t* __restrict__ qbase, int kp, int lstride,
+                                                    int sortn, uint64_t* __restrict__ cand) {
     extern __shared__ uint64_t buf[];  // [sortn]
     __shared__ int s_fill;
     __shared__ uint64_t s_tau;         // entries >= s_tau cannot enter the top k'
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__
         }
         const uint64_t tau = s_tau;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const uint64_t key = inter[L * kp + j];
+            const uint64_t key = inter[L * lstride + j];
             if (key < tau) buf[atomicAdd(&s_fill, 1)] = key;
         }
         __syncthreads();
@@ -565,8 +569,8 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     count_launch();
     excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.qtot, p.nq, p.qbase);
     count_launch();
-    plan_cluster_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.nlist, p.QT, p.RR,
-                                                                          p.cnt64, p.items_c);
+    plan_cluster_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.corder, p.nlist,
+                                                                          p.QT, p.RR, p.cnt64, p.items_c);
     count_launch();
     excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.cnt64, p.nlist, p.qoff);
     count_launch();
@@ -579,8 +583,8 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
 
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s) {
     count_launch();
-    plan_items_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off, p.nlist, p.QT,
-                                                                       p.RR, items);
+    plan_items_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off, p.corder,
+                                                                       p.nlist, p.QT, p.RR, items);
     return cudaGetLastError();
 }
 
@@ -599,20 +603,20 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int merge_sortn(int kp) {
-    int sortn = 1024;
-    while (sortn < 4 * kp) sortn <<= 1;
+int merge_sortn(int kp, int lstride) {
+    int sortn = 128;
+    while (sortn < 4 * kp || sortn < kp + lstride + 32) sortn <<= 1;
     return sortn;
 }
 
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
-                         uint64_t* cand, cudaStream_t s) {
+                         int lstride, uint64_t* cand, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
-    const int sortn = merge_sortn(kp);
+    const int sortn = merge_sortn(kp, lstride);
     cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
     if (e != cudaSuccess) return e;
     count_launch();
-    merge_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(inter, inter_cnt, qbase, kp, sortn, cand);
+    merge_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(inter, inter_cnt, qbase, kp, lstride, sortn, cand);
     return cudaGetLastError();
 }
 

@@ -233,3 +233,33 @@ def test_probe_ties_take_lower_cluster(erq):
             # GPU must have taken the lower cluster id, exactly as the oracle did
             allowed = set().union(*(members[c] for c in ref["probe"][i, :nprobe]))
             assert set(got[i].tolist()) <= allowed, (nprobe, i, ref["probe"][i, :nprobe])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_async_mode_and_cuda_graph(erq, precision):
+    """ERQ_SEARCH_ASYNC sizes its buffers from host-side bounds (no read-back),
+    returns the same results as the synchronous call, and can be recorded into
+    a CUDA graph whose replay searches new queries."""
+    X, P, assign, gx, ox = _build_pair(erq, 12000, 128, 5, 48, 1700, scale="aniso")
+    Q1, _ = S.mixture(400, 128, 48, 1701, comp_seed=1700, scale="aniso")
+    Q2, _ = S.mixture(400, 128, 48, 1702, comp_seed=1700, scale="aniso")
+    kw = dict(rerank_k=20, nprobe=6, precision=precision)
+    ref1 = gx.search(to_dev(Q1), 10, **kw)
+    ref2 = gx.search(to_dev(Q2), 10, **kw)
+    a1 = gx.search(to_dev(Q1), 10, async_mode=True, **kw)       # also sizes the buffers
+    torch.cuda.synchronize()
+    assert torch.equal(a1[0], ref1[0]) and torch.equal(a1[1], ref1[1])
+    static_q = to_dev(Q1).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        gx.search(static_q, 10, async_mode=True, **kw)          # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        out_ids, out_d = gx.search(static_q, 10, async_mode=True, **kw)
+    static_q.copy_(to_dev(Q2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out_ids, ref2[0]) and torch.equal(out_d, ref2[1])
+    gx.status()                                                 # no device-side error was recorded
