@@ -218,7 +218,10 @@ erq_status erq_index_load(const char* path, void* stream, erq_index** out);
  * erq_search_stats: work of the last erq_search on this index: out[0] estimated
  * (query, candidate) pairs, out[1] rows of the distinct probed clusters (codes
  * that had to be read at least once), out[2] work items, out[3] per-(query,
- * item) candidate lists.  n must be >= 4. */
+ * item) candidate lists, and for the tensor-core scan out[4] 128-row blocks
+ * streamed through the tensor cores and out[5] the sum over those blocks of the
+ * item's query count padded to the MMA width (0 for the FP32 path).  Fills
+ * min(n, 6) entries; n must be >= 4.  Synchronises the device. */
 erq_status erq_search_timing(const erq_index* index, float* ms, int32_t n);
 uint64_t erq_kernel_launches(void);
 erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);

@@ -59,7 +59,8 @@ void free_index_arrays(erq_index* ix) {
     void* ptrs[] = {ix->PT,    ix->eP,    ix->ePT,     ix->eC,   ix->corder,
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
-                    ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io};
+                    ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_t,
+                    ix->dstats};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
@@ -124,6 +125,26 @@ erq_status derive_gemm_arrays(erq_index* ix, cudaStream_t s) {
     if ((e = launch_row_exp(ix->P, D, D, ix->eP, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->PT, D, D, ix->ePT, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->C, ix->nlist, D, ix->eC, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    // tiled, padded copy of the codes and per-row factors for the tensor-core scan
+    {
+        const std::vector<int64_t>& lo = *ix->host_list_off;
+        std::vector<int64_t> po(ix->nlist + 1, 0);
+        for (int c = 0; c < ix->nlist; ++c) po[c + 1] = po[c] + (lo[c + 1] - lo[c] + 31) / 32 * 32;
+        ix->Np = po[ix->nlist];
+        if (!ix->poff && cudaMalloc(&ix->poff, sizeof(int64_t) * (ix->nlist + 1)) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc padded offsets");
+        ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->poff, po.data(), sizeof(int64_t) * (ix->nlist + 1), cudaMemcpyHostToDevice, s));
+        const size_t np = (size_t)std::max<int64_t>(ix->Np, 32);
+        if (!ix->codes_t && cudaMalloc(&ix->codes_t, np * D) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc tiled codes");
+        if (!ix->rowmeta && cudaMalloc(&ix->rowmeta, sizeof(float4) * np) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc row factors");
+        ix->device_bytes += (int64_t)(np * D + 16 * np + 8 * (ix->nlist + 1));
+        if ((e = launch_scan_layout(ix->codes, ix->g_const, ix->f_res, ix->list_ids, ix->list_off, ix->poff, ix->nlist,
+                                    ix->Np, D, ix->codes_t, ix->rowmeta, s)) != cudaSuccess)
+            return cuda_fail(e, "scan layout");
+        ERQ_CHECK_CUDA(cudaStreamSynchronize(s));   // po (host) goes out of scope
+    }
     // clusters by decreasing size: work items of the largest clusters are scheduled first
     std::vector<int32_t> order(ix->nlist);
     for (int j = 0; j < ix->nlist; ++j) order[j] = j;
@@ -404,7 +425,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     const bool explicit_probe = p->probe != nullptr;
     const int prec = p->precision;
     // ---- phase A workspace (sizes known on the host)
-    const int QT = prec == ERQ_PREC_FP32 ? 64 : 128;   // queries per work item of the scan kernel
+    const int QT = 64;                                  // queries per work item of the scan kernels
     int RR = 4096;
     Carver plan(nullptr, 0);
     auto layout = [&](Carver& cv, bool carve, void** slots) {
@@ -434,11 +455,12 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((int64_t*)nullptr, nlist + 1);                                 // 16 item_off
         T((int64_t*)nullptr, (size_t)nq * maxp);                         // 17 qlist
         T((uint64_t*)nullptr, (size_t)nq * kp);                          // 18 cand
-        T((uint64_t*)nullptr, 2);                                        // 19 stats
+        T((uint64_t*)nullptr, 1);                                        // 19 (unused)
         T((__half*)nullptr, prec == ERQ_PREC_FP32 ? 1 : (size_t)nq * D); // 20 Qh
         T((int32_t*)nullptr, nq);                                        // 21 eQ
+        T((uint64_t*)nullptr, prec == ERQ_PREC_FP32 ? 1 : nq);           // 22 query-wide thresholds
     };
-    void* sl[22];
+    void* sl[23];
     layout(plan, false, sl);
     ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
     Carver cv(ix->ws, ix->ws_bytes);
@@ -463,7 +485,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.item_off = (int64_t*)sl[16];
     pa.qlist = (int64_t*)sl[17];
     uint64_t* cand = (uint64_t*)sl[18];
-    pa.stats = (unsigned long long*)sl[19];
+    if (!ix->dstats && cudaMalloc(&ix->dstats, 4 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(ERQ_ENOMEM, "cudaMalloc search counters");
+    pa.stats = ix->dstats;
     cudaError_t e;
     const bool timed = (p->flags & ERQ_SEARCH_TIMING) != 0;
     ix->timed = 0;
@@ -546,7 +570,6 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         int64_t tot[2] = {0, 0};
         ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[0], pa.qbase + nq, 8, cudaMemcpyDeviceToHost, s));
         ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + nlist, 8, cudaMemcpyDeviceToHost, s));
-        ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->last_stats, pa.stats, 16, cudaMemcpyDeviceToHost, s));
         ERQ_TRY(check_status(ix, s));
         Ltot = tot[0];
         nitems = tot[1];
@@ -560,6 +583,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pb.take<uint64_t>((size_t)Ltot * lstride);
     pb.take<int32_t>(Ltot);
     pb.take<int64_t>(1);
+    const bool tcp = prec != ERQ_PREC_FP32;
+    pb.take<int4>(tcp ? nitems : 0);
+    pb.take<int4>(tcp ? nitems * QT : 0);
     if (async && ix->ws_b_bytes < pb.off)
         ERQ_CHECK_CUDA(cudaStreamSynchronize(s));   // growing the buffer frees the old one
     ERQ_TRY(ensure_ws(&ix->ws_b, &ix->ws_b_bytes, pb.off));
@@ -568,10 +594,15 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     uint64_t* inter = cb.take<uint64_t>((size_t)Ltot * lstride);
     int32_t* inter_cnt = cb.take<int32_t>(Ltot);
     int64_t* n_items_d = cb.take<int64_t>(1);
+    int4* itemd = cb.take<int4>(tcp ? nitems : 0);
+    int4* itemq = cb.take<int4>(tcp ? nitems * QT : 0);
     ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + nlist, 8, cudaMemcpyDeviceToDevice, s));
     if (Ltot > 0) ERQ_CHECK_CUDA(cudaMemsetAsync(inter_cnt, 0, sizeof(int32_t) * Ltot, s));
 
     if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
+    if (tcp && (e = launch_item_tables(items, n_items_d, nitems, ix->list_off, ix->poff, pa.qoff, pa.qlist, dqc,
+                                       pa.qbase, pa.slot_off, maxp, RR, itemd, itemq, pa.stats, s)) != cudaSuccess)
+        return cuda_fail(e, "item tables");
     ERQ_TRY(mark(3));
     // ---- scan
     ScanLaunch L;
@@ -579,6 +610,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
     L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
     L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR;
+    L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_t = ix->codes_t; L.Np = ix->Np;
+    L.tq = (unsigned long long*)sl[22];
+    if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -826,6 +860,13 @@ extern "C" uint64_t erq_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" erq_status erq_search_stats(const erq_index* ix, int64_t* out, int32_t n) {
     if (!ix || !out || n < 4) return fail(ERQ_EINVAL, "erq_search_stats: bad arguments");
-    for (int i = 0; i < 4; ++i) out[i] = ix->last_stats[i];
+    unsigned long long d[4] = {0, 0, 0, 0};
+    if (ix->dstats) {
+        ERQ_CHECK_CUDA(cudaDeviceSynchronize());
+        ERQ_CHECK_CUDA(cudaMemcpy(d, ix->dstats, sizeof(d), cudaMemcpyDeviceToHost));
+    }
+    const int64_t v[6] = {(int64_t)d[0], (int64_t)d[1], ix->last_stats[2], ix->last_stats[3], (int64_t)d[2],
+                          (int64_t)d[3]};
+    for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
     return ERQ_OK;
 }

@@ -101,6 +101,12 @@ struct erq_index {
     float* f_add = nullptr;      // [N]
     float* f_res = nullptr;      // [N]
     float* g_const = nullptr;    // [N] f_add - f_res * <ybar, c'>
+    // tensor-core scan layout: every list padded to a multiple of 32 rows; codes
+    // tiled as [Np/32 tiles][D/64 K blocks][32 rows][64 bytes]
+    int64_t Np = 0;              // padded rows
+    int64_t* poff = nullptr;     // [nlist+1] padded list offsets
+    uint8_t* codes_t = nullptr;  // [Np * D] tiled codes
+    float4* rowmeta = nullptr;   // [Np] {g, f_res/2, id, 0} per padded row (zeros for padding)
     float* X = nullptr;          // [N][D] raw rows, original order (keep_raw)
     uint32_t* status = nullptr;  // device status word
     std::vector<int64_t>* host_list_off = nullptr;  // host copy of list_off
@@ -116,6 +122,8 @@ struct erq_index {
     cudaEvent_t ev[7] = {};      // phase boundaries of the last timed search
     int timed = 0;               // 1 when ev[] holds a timed search
     int64_t last_stats[4] = {};  // pairs, distinct rows, work items, lists of the last search
+    unsigned long long* dstats = nullptr;  // [4] device counters of the last search: pairs, distinct rows,
+                                           //     tensor-core row blocks, row blocks x padded queries
     size_t pinned_bytes = 0;
     int64_t device_bytes = 0;
 };

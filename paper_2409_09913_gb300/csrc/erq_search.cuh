@@ -32,7 +32,8 @@ struct PlanArgs {
     int64_t* item_off;          // [nlist+1]
     int64_t* qlist;             // [nq*maxp]
     uint32_t* status;
-    unsigned long long* stats;  // [2]: (query, candidate) pairs, rows of distinct probed clusters
+    unsigned long long* stats;  // [4]: (query, candidate) pairs, rows of distinct probed clusters,
+                                //      tensor-core row blocks, row blocks x padded queries (item tables)
 };
 
 struct ScanLaunch {
@@ -54,6 +55,12 @@ struct ScanLaunch {
     const int64_t* qbase;
     uint64_t* inter;
     int32_t* inter_cnt;
+    const int4* itemd;          // tensor-core path: per-item {rb0 lo, rb0 hi, rows, queries}
+    const int4* itemq;          // tensor-core path: per-item query slots
+    const float4* rowmeta;      // tensor-core path: per padded row {g, f_res/2, id, 0}
+    const uint8_t* codes_t;     // tensor-core path: tiled, padded codes
+    int64_t Np;                 // tensor-core path: padded rows
+    unsigned long long* tq;     // tensor-core path: [nq] query-wide thresholds (all ones at the start)
     int maxp, D, B, kp, RR;
     int grid;
 };
@@ -68,6 +75,13 @@ int merge_sortn(int kp, int lstride);
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
                          int lstride, uint64_t* cand, cudaStream_t s);
 int scan_list_stride(int precision, int kp);
+cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
+                               const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int4* itemd,
+                               int4* itemq, unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
+                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
+                               uint8_t* codes_t, float4* rowmeta, cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           cudaStream_t s);

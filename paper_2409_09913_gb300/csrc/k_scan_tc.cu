@@ -2,29 +2,49 @@
 // <2 ybar, q'> for every (query, candidate) pair of a work item, on the
 // 5th-generation tensor cores with FP32 accumulation in tensor memory.
 //
-// Operands of one MMA (kind::f16, M = 128, N = 128, K = 16):
-//   A = 128 queries of the item (rotated queries q' in FP16), K-major;
-//   B = 128 stored rows of the cluster, codes expanded to 2*ybar_u - (2^B-1),
-//       which are odd integers in [-255, 255] and therefore exact in FP16.
-// The product is exact up to the FP16 rounding of q' (relative 2^-11 per
-// element); accumulation is FP32.  The estimate is then
-//   est = ||q_r - c||^2 + g + (f_res / 2) * acc,
-// with ||q_r - c||^2 from FP32 and g, f_res the stored per-row factors.
+// A work item is (cluster, up to 64 of the queries that probe it, up to RR
+// stored rows).  Operands of one MMA (kind::f16, M = 128, N = npad, K = 16):
+//   A = 128 stored rows of the cluster, codes expanded to 2*ybar_u - (2^B-1),
+//       odd integers in [-255, 255] and therefore exact in FP16, K-major;
+//   B = the item's queries (rotated q' in FP16), npad = the query count rounded
+//       up to a multiple of 16, K-major.
+// Codes are read from a scan-specific copy: every inverted list padded to a
+// multiple of 32 rows and stored as [tiles of 32 rows][K blocks of 64][32][64]
+// bytes, so the 128 rows x 64 bytes of one stage are four contiguous 2 KB pieces
+// fetched by one 4-D TMA load.
+// The accumulator holds row r in TMEM lane r and query j in column j; the
+// estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
+// stored per-row factors.  The product is exact up to the FP16 rounding of q'
+// (relative 2^-11 per element); accumulation is FP32.
 //
-// Warp roles (288 threads, one CTA per SM, persistent over work items):
-//   warps 0-3  epilogue: tcgen05.ld of 32 accumulator columns per step, an
-//              in-register warp transpose so that each query's estimates lie
-//              across the warp, warp-wide admission filtering against a per-query
-//              threshold and per-query candidate lists in shared memory, compacted
-//              by a warp bitonic sort (k' <= 32);
-//   warps 4-7  producers: gather FP16 query rows and expand u8 codes into the
-//              128B-swizzled K-major layout of a pipeline stage;
-//   warp 8     MMA issuer (one elected thread) and TMEM owner.
-// Pipeline: 3 stages of (A 16 KB, B 16 KB, raw codes 8 KB) per 64-wide K block; two TMEM
-// accumulators of 128 columns so the epilogue of one 128-row block overlaps
-// the MMAs of the next.  Every mbarrier wait is bounded: on expiry the kernel
-// records ERQ_ETIMEOUT in the status word, stops issuing work, waits (bounded)
-// for its MMAs, frees TMEM and returns.
+// Warp roles (320 + 32 NG threads, one CTA per SM, persistent over work items):
+//   warp 9     loader: per stage (128-row block, 64-wide K block) one TMA load
+//              of the raw u8 codes (L2 evict-first); per row block a bulk copy
+//              of the rows' factors and ids; per item the queries'
+//              ||q_r - c||^2 and output slots.  It runs up to LS stages ahead
+//              of the tensor cores;
+//   warps 10.. gatherers (NG warps): per stage, cp.async of the item's FP16 query rows
+//              (L2 evict-last) into the 128B-swizzled B tile, completion
+//              tracked on the stage's query barrier;
+//   warps 4-7  converters: expand the raw codes of a stage into the swizzled
+//              FP16 A tile;
+//   warp 8     MMA issuer (one elected thread) and TMEM owner;
+//   warps 0-3  epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32 rows for
+//              all queries), stores g + (f_res/2)*acc into a query-major tile
+//              in shared memory, and after a named barrier filters the rows of
+//              the queries it owns (q = w mod 4) against per-query thresholds
+//              into per-query candidate lists (warp ballots, compaction by a
+//              warp bitonic sort; k' <= 32).  A query's threshold starts at the
+//              smallest k'-th key published by its items finished so far (every
+//              item publishes its own k'-th key with atomicMin), which is never
+//              below the query's final k'-th key, so each list stays a superset
+//              of what the item contributes to the query's top-k'.
+// Two TMEM accumulators of 64 columns let the epilogue of one row block overlap
+// the MMAs of the next; two estimate tiles let one epilogue warp start a block
+// while the others still filter the previous one.  Every mbarrier wait is bounded: on expiry the kernel
+// records ERQ_ETIMEOUT in the status word, stops issuing work, drains the copies
+// and MMAs it issued (bounded), frees TMEM and returns; the epilogue warps take
+// every early exit together through a reducing named barrier.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -39,34 +59,42 @@ namespace erq {
 
 namespace tc {
 
-constexpr int QT = 128;          // queries per item (MMA M)
-constexpr int NB = 128;          // rows per MMA block (MMA N)
+constexpr int MR = 128;          // stored rows per MMA block (MMA M)
+constexpr int QN = 64;           // queries per item (MMA N <= QN)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int STAGES = 3;
-constexpr int LOOK = STAGES - 1; // producer lookahead (stages in flight ahead of conversion)
+constexpr int SA = 3;            // expanded code tiles
+constexpr int LS = 4;            // load stages (raw codes + query tile) in flight
+constexpr int MS = 4;            // row-factor buffers (one per row block)
 constexpr int KCAP = 32;         // max k' of the tensor-core path
 constexpr int KC = 64;           // per-query candidate list capacity (list stride of the output)
-constexpr int THREADS = 288;
-constexpr int STAGE_A = QT * KB * 2;   // 16 KB
-constexpr int STAGE_B = NB * KB * 2;   // 16 KB
-constexpr int STAGE_RAW = NB * KB;     // 8 KB of u8 codes (TMA staging)
+constexpr int NG = 2;            // query-gather warps
+constexpr int THREADS = 320 + 32 * NG;
+constexpr int TILE_A = MR * KB * 2;    // 16 KB
+constexpr int TILE_Q = QN * KB * 2;    // 8 KB
+constexpr int TILE_RAW = MR * KB;      // 8 KB of u8 codes (TMA staging)
+constexpr int TMEM_COLS = 2 * QN;
 
 struct Smem {
     // offsets in bytes from a 1024-aligned base
-    static constexpr int a = 0;
-    static constexpr int b = a + STAGES * STAGE_A;
-    static constexpr int raw = b + STAGES * STAGE_B;               // TMA staging of raw codes
-    static constexpr int lists = raw + STAGES * STAGE_RAW;         // [QT][KC] u64 candidate keys
-    static constexpr int cnt = lists + QT * KC * 8;                 // [QT] int   list fill
-    static constexpr int tau = cnt + QT * 4;                        // [QT] u64   admission threshold
-    static constexpr int dqc = tau + QT * 8;                        // [QT] float ||q_r - c||^2
-    static constexpr int lidx = dqc + QT * 4;                       // [QT] int64 output list index
-    static constexpr int bars = lidx + QT * 8;                      // mbarriers (8 B each)
-    static constexpr int nbars = 3 * STAGES + 4 + 1;
+    static constexpr int a = 0;                                    // SA  x [128 rows][64] FP16, swizzled
+    static constexpr int q = a + SA * TILE_A;                      // LS  x [64 queries][64] FP16, swizzled
+    static constexpr int raw = q + LS * TILE_Q;                    // LS  x [128 rows][64] u8
+    static constexpr int est = raw + LS * TILE_RAW;                // 2 x [QN][MR] f32  g + (f_res/2) acc
+    static constexpr int lists = est + 2 * QN * MR * 4;            // [QN][KC] u64 candidate keys
+    static constexpr int meta = lists + QN * KC * 8;               // MS x [MR] float4 {g, f_res/2, id, 0}
+    static constexpr int iq = meta + MS * MR * 16;                 // 2 x [QN] int4 {query row, dqc, slot lo, hi}
+    static constexpr int idesc = iq + 2 * QN * 16;                 // 2 x int4 {rb0 lo, rb0 hi, rows, queries}
+    static constexpr int ids = idesc + 2 * 16;                     // 2 x [MR] u32 ids of the row block
+    static constexpr int cnt = ids + 2 * MR * 4;                   // [QN] int   list fill
+    static constexpr int tau = cnt + QN * 4;                       // [QN] u64   admission threshold
+    static constexpr int tq = tau + QN * 8;                        // 2 x [QN] u64 query-wide threshold at item start
+    static constexpr int bars = tq + 2 * QN * 8;                   // mbarriers (8 B each)
+    static constexpr int nbars = 3 * LS + 2 * SA + 4 + 2 * MS + 4 + 1;
     static constexpr int tmem_slot = bars + nbars * 8;
     static constexpr int abort_flag = tmem_slot + 4;
-    static constexpr int total = abort_flag + 4 + 1024;             // + alignment slack
+    static constexpr int total = abort_flag + 4 + 1024;            // + alignment slack
 };
+static_assert(Smem::total <= 227 * 1024, "scan_tc shared memory");
 
 // 16 u8 codes -> 16 FP16 values 2u - off, exact: 1024 + u is exact in FP16
 // (byte u as mantissa of 0x6400), fma(1024 + u, 2, -2048) = 2u is exact, and
@@ -92,46 +120,23 @@ __device__ __forceinline__ void expand16(uint4 u, __half2 two, __half2 m2048, __
 
 struct Args {
     const __half* Qh;             // [nq][D] FP16 rotated queries
-    const uint8_t* codes;         // [N][D]
-    const float* g_const;
-    const float* f_res;
-    const int64_t* list_off;
-    const int64_t* list_ids;
-    const int64_t* qlist;
-    const int64_t* qoff;
-    const int4* items;
+    const int4* itemd;            // [items] {rb0 lo, rb0 hi, rows, queries}
+    const int4* itemq;            // [items][QN] {query row or -1, dqc bits, output list index lo, hi}
+    const float4* rowmeta;        // [N] {g, f_res / 2, id bits, 0} in stored-row order
     const int64_t* n_items;
-    const float* dqc;
-    const int32_t* slot_off;
-    const int64_t* qbase;
     uint64_t* inter;
     int32_t* inter_cnt;
+    unsigned long long* tq;       // [nq] query-wide admission threshold (k'-th key of a finished item)
     uint32_t* status;
-    int64_t N;
-    int maxp, D, B, kp, RR;
+    int D, B, kp;
 };
+
+__device__ __forceinline__ int npad_of(int nqi) { return nqi <= 16 ? 16 : (nqi + 15) & ~15; }
+__device__ __forceinline__ int64_t rb0_of(int4 d) { return (int64_t)(uint32_t)d.x | ((int64_t)d.y << 32); }
 
 }  // namespace tc
 
 using namespace tc;
-
-// 32x32 transpose of a warp's registers (5 butterfly stages, static indices):
-// on entry lane t holds row t in v[0..31]; on exit lane l holds column l, i.e.
-// v[i] = (old row i)[l].
-__device__ __forceinline__ void warp_transpose32(uint32_t (&v)[32], int lane) {
-#pragma unroll
-    for (int sft = 16; sft >= 1; sft >>= 1) {
-        const bool upper = (lane & sft) != 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if (i & sft) continue;
-            const uint32_t send = upper ? v[i] : v[i ^ sft];
-            const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, sft);
-            if (upper) v[i] = recv;
-            else v[i ^ sft] = recv;
-        }
-    }
-}
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m) {
     const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
@@ -199,31 +204,51 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Smem::tmem_slot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + Smem::abort_flag);
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
-    const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
-    const uint32_t done_bar = smem_u32(&bars[2 * STAGES + 4]);
-    const uint32_t tma0 = smem_u32(&bars[2 * STAGES + 5]);
+    int4* s_iq = reinterpret_cast<int4*>(sm + Smem::iq);
+    int4* s_idesc = reinterpret_cast<int4*>(sm + Smem::idesc);
+    const float4* s_meta = reinterpret_cast<const float4*>(sm + Smem::meta);
+    // barrier addresses
+    const uint32_t full_load0 = smem_u32(&bars[0]), empty_load0 = smem_u32(&bars[LS]);
+    const uint32_t full_q0 = smem_u32(&bars[2 * LS]);
+    const uint32_t full_a0 = smem_u32(&bars[3 * LS]), empty_a0 = smem_u32(&bars[3 * LS + SA]);
+    const uint32_t tfull0 = smem_u32(&bars[3 * LS + 2 * SA]), tempty0 = smem_u32(&bars[3 * LS + 2 * SA + 2]);
+    const uint32_t full_meta0 = smem_u32(&bars[3 * LS + 2 * SA + 4]);
+    const uint32_t empty_meta0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + MS]);
+    const uint32_t full_item0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS]);
+    const uint32_t empty_item0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS + 2]);
+    const uint32_t done_bar = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS + 4]);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, nkb = D / KB;
     const int64_t nitems = *a.n_items;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 128);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < LS; ++s) {
+            mbar_init(full_load0 + 8 * s, 1);      // the TMA expect_tx arrival
+            mbar_init(empty_load0 + 8 * s, 1);
+            mbar_init(full_q0 + 8 * s, 32 * NG);   // one cp.async arrival per gatherer lane
+        }
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(full_a0 + 8 * s, 128);
+            mbar_init(empty_a0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull0 + 8 * b, 1);
             mbar_init(tempty0 + 8 * b, 128);
+            mbar_init(full_item0 + 8 * b, 32);
+            mbar_init(empty_item0 + 8 * b, 128);
+        }
+        for (int m = 0; m < MS; ++m) {
+            mbar_init(full_meta0 + 8 * m, 1);
+            mbar_init(empty_meta0 + 8 * m, 128);
         }
         mbar_init(done_bar, 1);
-        for (int s = 0; s < STAGES; ++s) mbar_init(tma0 + 8 * s, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 8) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -231,127 +256,183 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 4 && warp < 8) {
-        // ------------------------------------------------------------ producers
-        // Step t of an item = (128-row block, 64-wide K block).  issue(t): wait
-        // until the stage is free, then one thread starts a TMA load of the raw u8
-        // codes (128 rows x 64 bytes) into the stage's staging buffer and every
-        // thread cp.asyncs its 8 16-byte chunks of FP16 query rows straight into the
-        // swizzled A tile (zeros for absent queries).  convert(t), LOOK steps later:
-        // wait for the thread's own cp.asyncs and the TMA, expand the codes into the
-        // swizzled FP16 B tile, fence the async proxy, and arrive on full[stage].
+    if (warp == 9) {
+        // ------------------------------------------------------------ loader
+        uint32_t g = 0, rbg = 0, li = 0;
+        bool ok = true;
+        int64_t item = blockIdx.x;
+        int4 dcur = make_int4(0, 0, 0, 0), q0 = dcur, q1 = dcur;
+        if (item < nitems) {
+            dcur = a.itemd[item];
+            q0 = a.itemq[item * QN + lane];
+            q1 = a.itemq[item * QN + 32 + lane];
+        }
+        const uint64_t pol_codes = l2_evict_first();
+        for (; item < nitems && ok; item += gridDim.x, ++li) {
+            // next item's descriptors are fetched while this one streams
+            const int64_t nxt = item + gridDim.x;
+            int4 dn = make_int4(0, 0, 0, 0), n0 = dn, n1 = dn;
+            if (nxt < nitems) {
+                dn = a.itemd[nxt];
+                n0 = a.itemq[nxt * QN + lane];
+                n1 = a.itemq[nxt * QN + 32 + lane];
+            }
+            const int ib = li & 1;
+            if (!mbar_wait_warp(empty_item0 + 8 * ib, ((li >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+            int4* iq = s_iq + ib * QN;
+            iq[lane] = q0;
+            iq[32 + lane] = q1;
+            unsigned long long* tqs = reinterpret_cast<unsigned long long*>(sm + Smem::tq) + ib * QN;
+            tqs[lane] = q0.x >= 0 ? __ldcg(a.tq + q0.x) : kEmptyKey;
+            tqs[32 + lane] = q1.x >= 0 ? __ldcg(a.tq + q1.x) : kEmptyKey;
+            if (lane == 0) s_idesc[ib] = dcur;
+            mbar_arrive(full_item0 + 8 * ib);
+            __syncwarp();
+            const int64_t rb0 = rb0_of(dcur);                 // first padded row (multiple of 32)
+            const int nrows = dcur.z;
+            for (int r = 0; r < nrows && ok; r += MR, ++rbg) {
+                const int nr = min(MR, nrows - r);
+                const int64_t r0 = rb0 + r;
+                const int m = rbg % MS;
+                if (!mbar_wait_warp(empty_meta0 + 8 * m, ((rbg / MS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(full_meta0 + 8 * m, (uint32_t)nr * 16u);
+                    bulk_load(smem_u32(sm + Smem::meta + m * MR * 16), a.rowmeta + r0, (uint32_t)nr * 16u,
+                              full_meta0 + 8 * m);
+                }
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % LS;
+                    if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(full_load0 + 8 * s, TILE_RAW);
+                        tma_load_4d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW), &codes_map, 0, 0, kb,
+                                         (int)(r0 >> 5), full_load0 + 8 * s, pol_codes);
+                    }
+                    __syncwarp();
+                }
+            }
+            dcur = dn;
+            q0 = n0;
+            q1 = n1;
+        }
+        // drain: every copy this warp issued has landed before the CTA exits
+        for (uint32_t k = 0; k < LS && k < g; ++k) {
+            const uint32_t gg = g - 1 - k;
+            mbar_wait_drain(full_load0 + 8 * (gg % LS), (gg / LS) & 1);
+        }
+        for (uint32_t k = 0; k < MS && k < rbg; ++k) {
+            const uint32_t gg = rbg - 1 - k;
+            mbar_wait_drain(full_meta0 + 8 * (gg % MS), (gg / MS) & 1);
+        }
+        __syncwarp();
+    } else if (warp >= 10) {
+        // ------------------------------------------------------------ gatherers
+        const uint64_t pol_q = l2_evict_last();
+        const int ch = lane & 7, gi = warp - 10;
+        uint32_t g = 0, li = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int4* iq = s_iq + ib * QN;
+            const int4 d = s_idesc[ib];
+            const int nq4 = npad_of(d.w) / 4;
+            const int nsteps = ((d.z + MR - 1) / MR) * nkb;
+            // this lane gathers 16-byte chunk ch of query rows (lane >> 3) + 4 (gi + NG i)
+            const __half* qp[QN / 4 / NG];
+#pragma unroll
+            for (int i = 0; i < QN / 4 / NG; ++i) {
+                const int qrow = iq[(lane >> 3) + 4 * (gi + NG * i)].x;
+                qp[i] = qrow >= 0 ? a.Qh + (int64_t)qrow * D + ch * 8 : nullptr;
+            }
+            for (int t = 0; t < nsteps; ++t, ++g) {
+                const int s = g % LS, kb = t % nkb;
+                if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                const uint32_t qs = smem_u32(sm + Smem::q + s * TILE_Q);
+#pragma unroll
+                for (int i = 0; i < QN / 4 / NG; ++i) {
+                    if (gi + NG * i < nq4) {
+                        const int qq = (lane >> 3) + 4 * (gi + NG * i);
+                        const uint32_t dst = qs + qq * 128 + ((ch ^ (qq & 7)) << 4);
+                        cp_async16_hint(dst, qp[i] ? (const void*)(qp[i] + kb * KB) : (const void*)a.Qh,
+                                        qp[i] ? 16u : 0u, pol_q);
+                    }
+                }
+                cp_async_mbar_arrive(full_q0 + 8 * s);
+            }
+        }
+        cp_async_wait<0>();
+        for (uint32_t k = 0; k < LS && k < g; ++k) {
+            const uint32_t gg = g - 1 - k;
+            mbar_wait_drain(full_q0 + 8 * (gg % LS), (gg / LS) & 1);
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------------ converters
         const int pt = tid - 128;
         const __half2 two = __floats2half2_rn(2.f, 2.f);
         const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
         const float offv = (float)((1 << a.B) - 1);
         const __half2 off2 = __floats2half2_rn(offv, offv);
-        const int achunk = pt & 7, bgrp = pt & 3;
-        uint32_t it = 0;                               // global stage counter at the item start
+        const int bgrp = pt & 3;
+        uint32_t g = 0, li = 0;
         bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int4 w = a.items[item];
-            const int c = w.x;
-            const int64_t qb = a.qoff[c] + (int64_t)w.y * QT;
-            const int nqi = (int)imin64(QT, a.qoff[c + 1] - qb);
-            const int64_t rb0 = a.list_off[c] + (int64_t)w.z * a.RR;
-            const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
-            const int nblk = (int)((rb1 - rb0 + NB - 1) / NB);
-            const int nsteps = nblk * nkb;
-            // query i of the item sits in A row (slot) (i % 4) * 32 + i / 4, so that
-            // the active queries spread over all four epilogue warps
-            const __half* qsrc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = (pt >> 3) + 16 * i;
-                const int qi = (r & 31) * 4 + (r >> 5);
-                qsrc[i] = qi < nqi ? a.Qh + (a.qlist[qb + qi] / a.maxp) * D + achunk * 8 : nullptr;
-            }
-            auto issue = [&](int t) -> bool {
-                const uint32_t g = it + t;
-                const int s = g % STAGES;
-                if (!mbar_wait(empty0 + 8 * s, ((g / STAGES) & 1) ^ 1, abort_flag)) return false;
-                const int k0 = (t % nkb) * KB;
-                const int64_t r0 = rb0 + (int64_t)(t / nkb) * NB;
-                if (pt == 0) {
-                    mbar_arrive_expect_tx(tma0 + 8 * s, STAGE_RAW);
-                    tma_load_2d(smem_u32(sm + Smem::raw + s * STAGE_RAW), &codes_map, k0, (int)r0, tma0 + 8 * s);
-                }
-                const uint32_t sa = smem_u32(sm + Smem::a + s * STAGE_A);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = (pt >> 3) + 16 * i;
-                    const uint32_t dst = sa + r * 128 + ((achunk ^ (r & 7)) << 4);
-                    cp_async16(dst, qsrc[i] ? (const void*)(qsrc[i] + k0) : (const void*)a.Qh, qsrc[i] ? 16u : 0u);
-                }
-                cp_async_commit();
-                return true;
-            };
-            auto convert = [&](int t, int pending) -> bool {
-                const uint32_t g = it + t;
-                const int s = g % STAGES;
-                // own cp.asyncs of step t done: at most `pending` newer groups may remain
-                if (pending >= 3) cp_async_wait<3>();
-                else if (pending == 2) cp_async_wait<2>();
-                else if (pending == 1) cp_async_wait<1>();
-                else cp_async_wait<0>();
-                if (!mbar_wait(tma0 + 8 * s, (g / STAGES) & 1, abort_flag)) return false;
-                const int nr = (int)imin64(NB, rb1 - (rb0 + (int64_t)(t / nkb) * NB));
-                const unsigned char* raw = sm + Smem::raw + s * STAGE_RAW;
-                unsigned char* sb = sm + Smem::b + s * STAGE_B;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int nrows = s_idesc[ib].z;
+            const int nsteps = ((nrows + MR - 1) / MR) * nkb;
+            for (int t = 0; t < nsteps; ++t, ++g) {
+                const int s = g % LS, sa = g % SA;
+                if (!mbar_wait_warp(full_load0 + 8 * s, (g / LS) & 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait_warp(empty_a0 + 8 * sa, ((g / SA) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                const unsigned char* raw = sm + Smem::raw + s * TILE_RAW;
+                unsigned char* ta = sm + Smem::a + sa * TILE_A;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int r = (pt >> 2) + 32 * i;
                     uint4 lo, hi;
-                    if (r < nr) {
-                        const uint4 u = *reinterpret_cast<const uint4*>(raw + r * KB + bgrp * 16);
-                        expand16(u, two, m2048, off2, lo, hi);
-                    } else {
-                        lo = hi = make_uint4(0u, 0u, 0u, 0u);
-                    }
-                    *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp) ^ (r & 7)) << 4)) = lo;
-                    *reinterpret_cast<uint4*>(sb + r * 128 + (((2 * bgrp + 1) ^ (r & 7)) << 4)) = hi;
+                    const uint4 u = *reinterpret_cast<const uint4*>(raw + r * KB + bgrp * 16);
+                    expand16(u, two, m2048, off2, lo, hi);
+                    *reinterpret_cast<uint4*>(ta + r * 128 + (((2 * bgrp) ^ (r & 7)) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(ta + r * 128 + (((2 * bgrp + 1) ^ (r & 7)) << 4)) = hi;
                 }
                 fence_proxy_async();
-                mbar_arrive(full0 + 8 * s);
-                return true;
-            };
-            const int pre = nsteps < LOOK ? nsteps : LOOK;
-            for (int t = 0; t < pre && ok; ++t) ok = issue(t);
-            for (int t = 0; t < nsteps && ok; ++t) {
-                if (t + LOOK < nsteps) ok = issue(t + LOOK);
-                if (!ok) break;
-                const int issued = (t + LOOK < nsteps) ? t + LOOK + 1 : nsteps;
-                ok = convert(t, issued - t - 1);
+                mbar_arrive(full_a0 + 8 * sa);
             }
-            it += nsteps;
         }
-        cp_async_wait<0>();
     } else if (warp == 8) {
         // ------------------------------------------------------------ MMA issuer
-        uint32_t it = 0, acc = 0;
+        uint32_t g = 0, acc = 0, li = 0;
         bool ok = true;
-        const uint32_t idesc = idesc_f16(QT, NB);
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int4 w = a.items[item];
-            const int c = w.x;
-            const int64_t rb0 = a.list_off[c] + (int64_t)w.z * a.RR;
-            const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
-            for (int64_t r0 = rb0; r0 < rb1 && ok; r0 += NB, ++acc) {
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int4 d = s_idesc[ib];
+            const uint32_t idesc = idesc_f16(MR, npad_of(d.w));
+            const int nblk = (d.z + MR - 1) / MR;
+            for (int b = 0; b < nblk && ok; ++b, ++acc) {
                 const int buf = acc & 1;
                 if (!mbar_wait_warp(tempty0 + 8 * buf, ((acc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t dt = tmem + buf * NB;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    if (!mbar_wait_warp(full0 + 8 * s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+                const uint32_t dt = tmem + buf * QN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % LS, sa = g % SA;
+                    if (!mbar_wait_warp(full_a0 + 8 * sa, (g / SA) & 1, abort_flag) ||
+                        !mbar_wait_warp(full_q0 + 8 * s, (g / LS) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();       // query tile written by cp.async (generic proxy)
                     tc_fence_after();
                     if (lane == 0) {
-                        const uint32_t sa = smem_u32(sm + Smem::a + s * STAGE_A);
-                        const uint32_t sb = smem_u32(sm + Smem::b + s * STAGE_B);
+                        const uint32_t ta = smem_u32(sm + Smem::a + sa * TILE_A);
+                        const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
 #pragma unroll
                         for (int k = 0; k < KB / 16; ++k)
-                            mma_f16(dt, sdesc(sa + k * 32), sdesc(sb + k * 32), idesc, (kb | k) != 0);
-                        mma_commit(empty0 + 8 * s);            // stage free when these MMAs finish
+                            mma_f16(dt, sdesc(ta + k * 32), sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                        mma_commit(empty_a0 + 8 * sa);
+                        mma_commit(empty_load0 + 8 * s);
                         if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
                     }
                     __syncwarp();
@@ -361,102 +442,113 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         // all issued MMAs complete before TMEM is released
         if (lane == 0) mma_commit(done_bar);
         __syncwarp();
-        mbar_wait_warp(done_bar, 0, abort_flag);
+        mbar_wait_drain(done_bar, 0);
+        __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        // Warp w owns TMEM lanes (query slots) 32w..32w+31.  Per 32-column chunk
-        // the accumulator rows are transposed in registers, so lane l holds column
-        // l of all 32 slots: the estimates of one query then sit across the warp,
-        // are filtered against that query's admission threshold with one ballot,
-        // and the survivors are appended to its list; a list that fills is
-        // compacted by a warp bitonic sort to its kp smallest keys, which also
-        // tightens the threshold.  Each list is a superset of the item's top-kp.
+        float* s_est = reinterpret_cast<float*>(sm + Smem::est);
         uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
+        uint32_t* s_ids = reinterpret_cast<uint32_t*>(sm + Smem::ids);
         int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
         uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
-        float* s_dqc = reinterpret_cast<float*>(sm + Smem::dqc);
-        int64_t* s_lidx = reinterpret_cast<int64_t*>(sm + Smem::lidx);
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
-        uint32_t acc = 0;
-        bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int4 w = a.items[item];
-            const int c = w.x;
-            const int64_t qb = a.qoff[c] + (int64_t)w.y * QT;
-            const int nqi = (int)imin64(QT, a.qoff[c + 1] - qb);
-            const int64_t rb0 = a.list_off[c] + (int64_t)w.z * a.RR;
-            const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
-            {   // slot setup: slot = warp*32 + lane holds query lane*4 + warp
-                const int slot = warp * 32 + lane, qi = lane * 4 + warp;
-                s_cnt[slot] = 0;
-                s_tau[slot] = kEmptyKey;
-                if (qi < nqi) {
-                    const int64_t e = a.qlist[qb + qi];
-                    s_dqc[slot] = a.dqc[e];
-                    s_lidx[slot] = a.qbase[e / a.maxp] + a.slot_off[e] + w.z;
+        const int row = warp * 32 + lane;
+        uint32_t acc = 0, rbg = 0, li = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+            const int ib = li & 1;
+            const bool got = mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag);
+            if (bar_or(1, 128, !got || *abort_flag != 0)) break;
+            const int4 d = s_idesc[ib];
+            const int nrows = d.z, nqi = d.w, npad = npad_of(nqi);
+            const int4* iq = s_iq + ib * QN;
+            if (lane < 16) {                                   // owned queries q = warp + 4 * lane
+                const int q = warp + 4 * lane;
+                if (q < nqi) {
+                    s_cnt[q] = 0;
+                    s_tau[q] = reinterpret_cast<const unsigned long long*>(sm + Smem::tq)[ib * QN + q];
                 }
             }
             __syncwarp();
-            const int nact = nqi > warp ? (nqi - warp + 3) / 4 : 0;   // active slots of this warp
-            for (int64_t r0 = rb0; r0 < rb1; r0 += NB, ++acc) {
-                const int nr = (int)imin64(NB, rb1 - r0);
-                const int buf = acc & 1;
-                if (!mbar_wait_warp(tfull0 + 8 * buf, (acc >> 1) & 1, abort_flag)) { ok = false; break; }
-                tc_fence_after();
+            bool stop = false;
+            for (int r = 0; r < nrows; r += MR, ++acc, ++rbg) {
+                const int nr = min(MR, nrows - r);
+                const int buf = acc & 1, m = rbg % MS;
+                bool okw = mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag);
+                okw = okw && mbar_wait_warp(tfull0 + 8 * buf, (acc >> 1) & 1, abort_flag);
+                float* est_t = s_est + (acc & 1) * (QN * MR);   // tiles alternate between row blocks
+                uint32_t* ids_t = s_ids + (acc & 1) * MR;
+                if (okw) {
+                    // phase 1: own 32 rows x all queries -> query-major tile
+                    tc_fence_after();
+                    const float4 mt = s_meta[m * MR + row];
+                    ids_t[row] = __float_as_uint(mt.z);
 #pragma unroll 1
-                for (int cc = 0; cc < NB; cc += 32) {
-                    uint32_t v[32];
-                    ERQ_TMEM_LD32(tmem + lane_base + buf * NB + cc, v);
-                    const int col = cc + lane;
-                    const bool valid = col < nr;
-                    float mg = 0.f, mf = 0.f;
-                    uint32_t mid = 0;
-                    if (valid) {
-                        mg = a.g_const[r0 + col];
-                        mf = 0.5f * a.f_res[r0 + col];
-                        mid = (uint32_t)a.list_ids[r0 + col];
-                    }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (nact == 0 || cc >= nr) continue;
-                    warp_transpose32(v, lane);
+                    for (int cc = 0; cc < npad; cc += 32) {
+                        uint32_t v[32];
+                        ERQ_TMEM_LD32(tmem + lane_base + buf * QN + cc, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i >= nact) break;                       // warp-uniform
-                        const int slot = warp * 32 + i;
-                        const float est = s_dqc[slot] + mg + mf * __uint_as_float(v[i]);
-                        const uint64_t key = make_key(est, mid);
-                        const bool pass = valid && key < s_tau[slot];
-                        const uint32_t m = __ballot_sync(0xffffffffu, pass);
-                        if (m == 0u) continue;
-                        int cnt = s_cnt[slot];
-                        if (pass) lists[slot * KC + cnt + __popc(m & below)] = key;
-                        cnt += __popc(m);
+                        for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+                    }
+                    tc_fence_before();
+                }
+                mbar_arrive(tempty0 + 8 * buf);
+                mbar_arrive(empty_meta0 + 8 * m);
+                if (bar_or(1, 128, !okw || *abort_flag != 0)) { stop = true; break; }
+                // phase 2: the 128 rows of each owned query; the four 32-row
+                // groups' estimates are loaded together, compared as floats
+                // against the threshold's estimate (a superset of the key
+                // test), and only groups with a candidate form exact keys
+                for (int q = warp; q < nqi; q += 4) {
+                    const float dq = __int_as_float(iq[q].y);
+                    uint64_t tau = s_tau[q];
+                    float tf = tau == kEmptyKey ? INFINITY : key_value(tau);
+                    int cnt = s_cnt[q];
+                    float e[MR / 32];
+#pragma unroll
+                    for (int j = 0; j < MR / 32; ++j) e[j] = dq + est_t[q * MR + j * 32 + lane];
+#pragma unroll
+                    for (int j = 0; j < MR / 32; ++j) {
+                        const int rr = j * 32 + lane;
+                        const bool pre = rr < nr && e[j] <= tf;
+                        if (!__any_sync(0xffffffffu, pre)) continue;
+                        const uint64_t key = make_key(e[j], ids_t[rr]);
+                        const bool pass = pre && key < tau;
+                        const uint32_t msk = __ballot_sync(0xffffffffu, pass);
+                        if (msk == 0u) continue;
+                        if (pass) lists[q * KC + cnt + __popc(msk & below)] = key;
+                        cnt += __popc(msk);
                         __syncwarp();
                         if (cnt > KC - 32) {
-                            const uint64_t th = compact_list(lists + slot * KC, cnt, kp, lane);
+                            tau = compact_list(lists + q * KC, cnt, kp, lane);
+                            tf = key_value(tau);
                             cnt = kp;
-                            if (lane == 0) s_tau[slot] = th;
                         }
-                        if (lane == 0) s_cnt[slot] = cnt;
-                        __syncwarp();
                     }
+                    if (lane == 0) {
+                        s_cnt[q] = cnt;
+                        s_tau[q] = tau;
+                    }
+                    __syncwarp();
                 }
-                tc_fence_before();
-                mbar_arrive(tempty0 + 8 * buf);
             }
-            if (ok) {
-                for (int i = 0; i < nact; ++i) {                     // write this warp's lists
-                    const int slot = warp * 32 + i;
-                    const int cnt = s_cnt[slot];
-                    const int64_t L = s_lidx[slot];
-                    uint64_t* dst = a.inter + L * KC;
-                    for (int e = lane; e < cnt; e += 32) dst[e] = lists[slot * KC + e];
-                    if (lane == 0) a.inter_cnt[L] = cnt;
+            if (stop) break;
+            for (int q = warp; q < nqi; q += 4) {               // write this warp's lists
+                int cnt = s_cnt[q];
+                if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
+                    const uint64_t th = compact_list(lists + q * KC, cnt, kp, lane);
+                    cnt = kp;
+                    if (lane == 0) atomicMin(a.tq + iq[q].x, (unsigned long long)th);
                 }
+                const int64_t L = (int64_t)(uint32_t)iq[q].z | ((int64_t)iq[q].w << 32);
+                uint64_t* dst = a.inter + L * KC;
+                for (int e = lane; e < cnt; e += 32) dst[e] = lists[q * KC + e];
+                if (lane == 0) a.inter_cnt[L] = cnt;
             }
             __syncwarp();
+            mbar_arrive(empty_item0 + 8 * ib);
         }
     }
     tc_fence_before();
@@ -464,7 +556,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     if (*abort_flag && tid == 0) atomicOr(a.status, kStatusTimeout);
     if (warp == 8) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
     }
 }
 
@@ -477,7 +569,99 @@ int scan_list_stride(int precision, int kp) { return precision == ERQ_PREC_FP32 
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
 
-static bool make_codes_map(CUtensorMap* map, const uint8_t* codes, int64_t N, int D) {
+
+// Per work item: {first padded row (lo, hi), rows, queries} and, per query slot,
+// {query row or -1, ||q_r - c||^2 bits, output list index (lo, hi)}.  One warp per item.
+__global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t* __restrict__ n_items,
+                                   const int64_t* __restrict__ list_off, const int64_t* __restrict__ poff,
+                                   const int64_t* __restrict__ qoff, const int64_t* __restrict__ qlist,
+                                   const float* __restrict__ dqc, const int64_t* __restrict__ qbase,
+                                   const int32_t* __restrict__ slot_off, int maxp, int RR, int4* __restrict__ itemd,
+                                   int4* __restrict__ itemq, unsigned long long* __restrict__ stats) {
+    const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (it >= *n_items) return;
+    const int4 w = items[it];
+    const int c = w.x;
+    const int64_t qb = qoff[c] + (int64_t)w.y * QN;
+    const int nqi = (int)imin64(QN, qoff[c + 1] - qb);
+    const int64_t size = list_off[c + 1] - list_off[c];
+    const int64_t r0 = (int64_t)w.z * RR;
+    const int64_t rb0 = poff[c] + r0;
+    const int nrows = (int)(imin64(size, r0 + RR) - r0);
+    if (lane == 0) {
+        itemd[it] = make_int4((int)(uint32_t)rb0, (int)(rb0 >> 32), nrows, nqi);
+        const unsigned long long nblk = (unsigned long long)((nrows + MR - 1) / MR);
+        atomicAdd(&stats[2], nblk);
+        atomicAdd(&stats[3], nblk * (unsigned long long)(nqi <= 16 ? 16 : (nqi + 15) & ~15));
+    }
+    for (int q = lane; q < QN; q += 32) {
+        int4 v = make_int4(-1, 0, 0, 0);
+        if (q < nqi) {
+            const int64_t e = qlist[qb + q];
+            const int64_t qr = e / maxp;
+            const int64_t L = qbase[qr] + slot_off[e] + w.z;
+            v = make_int4((int)qr, __float_as_int(dqc[e]), (int)(uint32_t)L, (int)(L >> 32));
+        }
+        itemq[it * QN + q] = v;
+    }
+}
+
+cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
+                               const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int4* itemd,
+                               int4* itemq, unsigned long long* stats, cudaStream_t s) {
+    if (items_bound <= 0) return cudaSuccess;
+    count_launch();
+    item_tables_kernel<<<(unsigned)ceil_div(items_bound, 8), 256, 0, s>>>(
+        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, itemd, itemq, stats);
+    return cudaGetLastError();
+}
+
+// Scan layout of the index (one warp per padded row p): the row's codes into
+// the tiled array and {g, f_res / 2, id, 0} into rowmeta; padding rows get zeros.
+__global__ void scan_layout_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ g,
+                                   const float* __restrict__ f_res, const int64_t* __restrict__ ids,
+                                   const int64_t* __restrict__ list_off, const int64_t* __restrict__ poff, int nlist,
+                                   int64_t Np, int D, uint8_t* __restrict__ codes_t, float4* __restrict__ rowmeta) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= Np) return;
+    int lo = 0, hi = nlist;                      // cluster with poff[lo] <= p < poff[lo + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (poff[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    const int64_t j = p - poff[lo];
+    const bool valid = j < list_off[lo + 1] - list_off[lo];
+    const int64_t src = list_off[lo] + j;
+    const int nkb = D / 64;
+    const int64_t t = p >> 5;
+    const int r = (int)(p & 31);
+    for (int x = lane; x < D / 16; x += 32) {
+        const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + src * D)[x] : make_uint4(0u, 0u, 0u, 0u);
+        const int kb = x >> 2, w = x & 3;
+        reinterpret_cast<uint4*>(codes_t + ((t * nkb + kb) * 32 + r) * 64)[w] = v;
+    }
+    if (lane == 0)
+        rowmeta[p] = valid ? make_float4(g[src], 0.5f * f_res[src], __uint_as_float((uint32_t)ids[src]), 0.f)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
+                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
+                               uint8_t* codes_t, float4* rowmeta, cudaStream_t s) {
+    if (Np <= 0) return cudaSuccess;
+    count_launch();
+    scan_layout_kernel<<<(unsigned)ceil_div(Np, 8), 256, 0, s>>>(codes, g, f_res, ids, list_off, poff, nlist, Np, D,
+                                                                 codes_t, rowmeta);
+    return cudaGetLastError();
+}
+
+// 4-D view of the tiled codes: (64 bytes, 32 rows, K block, tile); a box of
+// (64, 32, 1, 4) is the 128 x 64-byte tile of one stage, rows in order.
+static bool make_codes_map(CUtensorMap* map, const uint8_t* codes_t, int64_t Np, int D) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -488,12 +672,13 @@ static bool make_codes_map(CUtensorMap* map, const uint8_t* codes, int64_t N, in
             return false;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)N};
-    const cuuint64_t strides[1] = {(cuuint64_t)D};          // bytes between rows
-    const cuuint32_t box[2] = {(cuuint32_t)KB, (cuuint32_t)NB};
-    const cuuint32_t estr[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)codes, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    const int nkb = D / KB;
+    const cuuint64_t dims[4] = {(cuuint64_t)KB, 32, (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
+    const cuuint64_t strides[3] = {(cuuint64_t)KB, (cuuint64_t)KB * 32, (cuuint64_t)KB * 32 * nkb};
+    const cuuint32_t box[4] = {(cuuint32_t)KB, 32, 1, MR / 32};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, (void*)codes_t, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -501,17 +686,18 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!tc_available(precision, L.D, L.kp))
         return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 32");
     if (!L.Qh) return fail(ERQ_EINVAL, "tensor-core scan: FP16 queries missing");
+    if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
     tc::Args a;
-    a.Qh = (const __half*)L.Qh; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;
-    a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
-    a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
-    a.status = L.status; a.N = L.N; a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR;
+    a.Qh = (const __half*)L.Qh; a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
+    a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
+    a.tq = L.tq;
     const int smem = Smem::total;
     cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
     CUtensorMap map;
-    if (((uintptr_t)L.codes & 15) != 0 || (L.D % 16) != 0 || !make_codes_map(&map, L.codes, L.N, L.D))
+    if (!L.codes_t || ((uintptr_t)L.codes_t & 15) != 0 || (L.D % KB) != 0 ||
+        !make_codes_map(&map, L.codes_t, L.Np, L.D))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     count_launch();
     scan_tc_kernel<<<L.grid, THREADS, smem, s>>>(map, a);

@@ -559,7 +559,7 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(p.cnt_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.pos_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p.stats, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     count_launch();
     plan_count_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(
         p.probe, p.probe_stride, p.npr_in, p.npr_uniform, p.nq, p.maxp, p.nlist, p.list_off, p.RR, p.npr, p.probe_c,

@@ -210,10 +210,11 @@ class Index:
         return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms)))
 
     def stats(self):
-        """Work of the last search: pairs, distinct rows, items, lists."""
-        out = (ct.c_int64 * 4)()
-        _check(lib().erq_search_stats(self._h, out, 4))
-        return dict(zip(("pairs", "rows", "items", "lists"), list(out)))
+        """Work of the last search: pairs, distinct rows, items, lists, tensor-core
+        row blocks and row blocks x padded query count (the last two 0 for FP32)."""
+        out = (ct.c_int64 * 6)()
+        _check(lib().erq_search_stats(self._h, out, 6))
+        return dict(zip(("pairs", "rows", "items", "lists", "blocks", "slot_blocks"), list(out)))
 
     def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32"):
         """Search from host memory (pinned for asynchronous copies); returns host tensors."""
