@@ -5,13 +5,16 @@
 // A work item is (cluster, up to 64 of the queries that probe it, up to RR
 // stored rows).  Operands of one MMA (kind::f16, M = 128, N = npad, K = 16):
 //   A = 128 stored rows of the cluster, codes expanded to 2*ybar_u - (2^B-1),
-//       odd integers in [-255, 255] and therefore exact in FP16, K-major;
+//       odd integers in [-255, 255] and therefore exact in FP16, held in
+//       tensor memory (row = lane, two FP16 values per column);
 //   B = the item's queries (rotated q' in FP16), npad = the query count rounded
 //       up to a multiple of 16, K-major.
 // Codes are read from a scan-specific copy: every inverted list padded to a
 // multiple of 32 rows and stored as [tiles of 32 rows][K blocks of 64][32][64]
 // bytes, so the 128 rows x 64 bytes of one stage are four contiguous 2 KB pieces
-// fetched by one 4-D TMA load.
+// fetched by one 4-D TMA load.  Tensor memory: columns [0, 256) hold two
+// buffers of RP accumulators (64 columns each), columns [256, 448) the three
+// expanded-code stages of RP x 32 columns.
 // The accumulator holds row r in TMEM lane r and query j in column j; the
 // estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
 // stored per-row factors.  The product is exact up to the FP16 rounding of q'
@@ -26,8 +29,9 @@
 //   warps 10.. gatherers (NG warps): per stage, cp.async of the item's FP16 query rows
 //              (L2 evict-last) into the 128B-swizzled B tile, completion
 //              tracked on the stage's query barrier;
-//   warps 4-7  converters: expand the raw codes of a stage into the swizzled
-//              FP16 A tile;
+//   warps 4-7  converters: one thread per row expands the row's 64 raw codes
+//              of a stage (64B-swizzled by the TMA, so reads are conflict-free)
+//              in registers and stores them into the stage's TMEM columns;
 //   warp 8     MMA issuer (one elected thread) and TMEM owner;
 //   warps 0-3  epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32 rows for
 //              all queries), stores g + (f_res/2)*acc into a query-major tile
@@ -39,9 +43,12 @@
 //              item publishes its own k'-th key with atomicMin), which is never
 //              below the query's final k'-th key, so each list stays a superset
 //              of what the item contributes to the query's top-k'.
-// Two TMEM accumulators of 64 columns let the epilogue of one row block overlap
-// the MMAs of the next; two estimate tiles let one epilogue warp start a block
-// while the others still filter the previous one.  Every mbarrier wait is bounded: on expiry the kernel
+// A stage covers up to RP = 2 row blocks that share the stage's query tile and
+// accumulate into separate TMEM accumulators, so two MMA dependency chains are
+// in flight and the query gather is amortised over 256 rows.  Accumulators are
+// double-buffered per stage group, so the epilogue of one group overlaps the
+// MMAs of the next; two estimate tiles let one epilogue warp start a block while
+// the others still filter the previous one.  Every mbarrier wait is bounded: on expiry the kernel
 // records ERQ_ETIMEOUT in the status word, stops issuing work, drains the copies
 // and MMAs it issued (bounded), frees TMEM and returns; the epilogue warps take
 // every early exit together through a reducing named barrier.
@@ -62,23 +69,24 @@ namespace tc {
 constexpr int MR = 128;          // stored rows per MMA block (MMA M)
 constexpr int QN = 64;           // queries per item (MMA N <= QN)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int SA = 3;            // expanded code tiles
+constexpr int RP = 2;            // 128-row blocks per stage (independent accumulators, shared query tile)
+constexpr int SA = 3;            // expanded code stages (tensor memory, RP x 32 columns each)
 constexpr int LS = 4;            // load stages (raw codes + query tile) in flight
 constexpr int MS = 4;            // row-factor buffers (one per row block)
 constexpr int KCAP = 32;         // max k' of the tensor-core path
 constexpr int KC = 64;           // per-query candidate list capacity (list stride of the output)
 constexpr int NG = 2;            // query-gather warps
 constexpr int THREADS = 320 + 32 * NG;
-constexpr int TILE_A = MR * KB * 2;    // 16 KB
 constexpr int TILE_Q = QN * KB * 2;    // 8 KB
-constexpr int TILE_RAW = MR * KB;      // 8 KB of u8 codes (TMA staging)
-constexpr int TMEM_COLS = 2 * QN;
+constexpr int TILE_RAW = RP * MR * KB; // 16 KB of u8 codes (TMA staging)
+constexpr int ACOL = 2 * RP * QN;  // first TMEM column of the expanded-code stages
+constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + SA x RP x 32 columns of codes
+static_assert(ACOL + SA * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
 
 struct Smem {
     // offsets in bytes from a 1024-aligned base
-    static constexpr int a = 0;                                    // SA  x [128 rows][64] FP16, swizzled
-    static constexpr int q = a + SA * TILE_A;                      // LS  x [64 queries][64] FP16, swizzled
-    static constexpr int raw = q + LS * TILE_Q;                    // LS  x [128 rows][64] u8
+    static constexpr int q = 0;                                    // LS  x [64 queries][64] FP16, swizzled
+    static constexpr int raw = q + LS * TILE_Q;                    // LS  x RP x [128 rows][64] u8, 64B-swizzled
     static constexpr int est = raw + LS * TILE_RAW;                // 2 x [QN][MR] f32  g + (f_res/2) acc
     static constexpr int lists = est + 2 * QN * MR * 4;            // [QN][KC] u64 candidate keys
     static constexpr int meta = lists + QN * KC * 8;               // MS x [MR] float4 {g, f_res/2, id, 0}
@@ -290,23 +298,26 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             __syncwarp();
             const int64_t rb0 = rb0_of(dcur);                 // first padded row (multiple of 32)
             const int nrows = dcur.z;
-            for (int r = 0; r < nrows && ok; r += MR, ++rbg) {
-                const int nr = min(MR, nrows - r);
-                const int64_t r0 = rb0 + r;
-                const int m = rbg % MS;
-                if (!mbar_wait_warp(empty_meta0 + 8 * m, ((rbg / MS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(full_meta0 + 8 * m, (uint32_t)nr * 16u);
-                    bulk_load(smem_u32(sm + Smem::meta + m * MR * 16), a.rowmeta + r0, (uint32_t)nr * 16u,
-                              full_meta0 + 8 * m);
+            for (int r = 0; r < nrows && ok; r += RP * MR) {
+                const int nb = min(RP, (nrows - r + MR - 1) / MR);     // 128-row blocks in this stage group
+                for (int bb = 0; bb < nb && ok; ++bb, ++rbg) {
+                    const int nr = min(MR, nrows - r - bb * MR);
+                    const int m = rbg % MS;
+                    if (!mbar_wait_warp(empty_meta0 + 8 * m, ((rbg / MS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(full_meta0 + 8 * m, (uint32_t)nr * 16u);
+                        bulk_load(smem_u32(sm + Smem::meta + m * MR * 16), a.rowmeta + rb0 + r + bb * MR,
+                                  (uint32_t)nr * 16u, full_meta0 + 8 * m);
+                    }
                 }
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
                     const int s = g % LS;
                     if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(full_load0 + 8 * s, TILE_RAW);
-                        tma_load_4d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW), &codes_map, 0, 0, kb,
-                                         (int)(r0 >> 5), full_load0 + 8 * s, pol_codes);
+                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)(nb * MR * KB));
+                        for (int bb = 0; bb < nb; ++bb)
+                            tma_load_4d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB), &codes_map, 0, 0,
+                                             kb, (int)((rb0 + r + bb * MR) >> 5), full_load0 + 8 * s, pol_codes);
                     }
                     __syncwarp();
                 }
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int4* iq = s_iq + ib * QN;
             const int4 d = s_idesc[ib];
             const int nq4 = npad_of(d.w) / 4;
-            const int nsteps = ((d.z + MR - 1) / MR) * nkb;
+            const int nsteps = ((d.z + RP * MR - 1) / (RP * MR)) * nkb;
             // this lane gathers 16-byte chunk ch of query rows (lane >> 3) + 4 (gi + NG i)
             const __half* qp[QN / 4 / NG];
 #pragma unroll
@@ -369,35 +380,43 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         __syncwarp();
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------ converters
-        const int pt = tid - 128;
+        // converter thread = one row of the stage (TMEM lane); warp w writes lanes 32 (w - 4)..
+        const int r = tid - 128;
+        const uint32_t lane_addr = (uint32_t)((warp - 4) * 32) << 16;
         const __half2 two = __floats2half2_rn(2.f, 2.f);
         const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
         const float offv = (float)((1 << a.B) - 1);
         const __half2 off2 = __floats2half2_rn(offv, offv);
-        const int bgrp = pt & 3;
+        const int swz = (r >> 1) & 3;                          // 64-byte TMA swizzle of row r
         uint32_t g = 0, li = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
             const int ib = li & 1;
             if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
             const int nrows = s_idesc[ib].z;
-            const int nsteps = ((nrows + MR - 1) / MR) * nkb;
+            const int nsteps = ((nrows + RP * MR - 1) / (RP * MR)) * nkb;
             for (int t = 0; t < nsteps; ++t, ++g) {
                 const int s = g % LS, sa = g % SA;
+                const int r0 = (t / nkb) * (RP * MR);
+                const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
                 if (!mbar_wait_warp(full_load0 + 8 * s, (g / LS) & 1, abort_flag)) { ok = false; break; }
                 if (!mbar_wait_warp(empty_a0 + 8 * sa, ((g / SA) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                const unsigned char* raw = sm + Smem::raw + s * TILE_RAW;
-                unsigned char* ta = sm + Smem::a + sa * TILE_A;
+                tc_fence_after();
+                for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
+                    const unsigned char* rp = sm + Smem::raw + s * TILE_RAW + bb * MR * KB + r * KB;
+                    uint32_t w[32];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = (pt >> 2) + 32 * i;
-                    uint4 lo, hi;
-                    const uint4 u = *reinterpret_cast<const uint4*>(raw + r * KB + bgrp * 16);
-                    expand16(u, two, m2048, off2, lo, hi);
-                    *reinterpret_cast<uint4*>(ta + r * 128 + (((2 * bgrp) ^ (r & 7)) << 4)) = lo;
-                    *reinterpret_cast<uint4*>(ta + r * 128 + (((2 * bgrp + 1) ^ (r & 7)) << 4)) = hi;
+                    for (int c = 0; c < 4; ++c) {                  // 16 codes -> 8 columns of FP16 pairs
+                        const uint4 u = *reinterpret_cast<const uint4*>(rp + ((c ^ swz) << 4));
+                        uint4 lo, hi;
+                        expand16(u, two, m2048, off2, lo, hi);
+                        w[8 * c + 0] = lo.x; w[8 * c + 1] = lo.y; w[8 * c + 2] = lo.z; w[8 * c + 3] = lo.w;
+                        w[8 * c + 4] = hi.x; w[8 * c + 5] = hi.y; w[8 * c + 6] = hi.z; w[8 * c + 7] = hi.w;
+                    }
+                    ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (sa * RP + bb) * (KB / 2), w);
                 }
-                fence_proxy_async();
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
                 mbar_arrive(full_a0 + 8 * sa);
             }
         }
@@ -410,12 +429,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
             const int4 d = s_idesc[ib];
             const uint32_t idesc = idesc_f16(MR, npad_of(d.w));
-            const int nblk = (d.z + MR - 1) / MR;
-            for (int b = 0; b < nblk && ok; ++b, ++acc) {
+            for (int r0 = 0; r0 < d.z && ok; r0 += RP * MR, ++acc) {   // acc counts stage groups
+                const int nb = min(RP, (d.z - r0 + MR - 1) / MR);
                 const int buf = acc & 1;
                 if (!mbar_wait_warp(tempty0 + 8 * buf, ((acc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t dt = tmem + buf * QN;
+                const uint32_t dt = tmem + buf * (RP * QN);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = g % LS, sa = g % SA;
                     if (!mbar_wait_warp(full_a0 + 8 * sa, (g / SA) & 1, abort_flag) ||
@@ -426,11 +445,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     fence_proxy_async();       // query tile written by cp.async (generic proxy)
                     tc_fence_after();
                     if (lane == 0) {
-                        const uint32_t ta = smem_u32(sm + Smem::a + sa * TILE_A);
+                        const uint32_t ta = tmem + ACOL + sa * RP * (KB / 2);
                         const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
+                        // the RP blocks' accumulation chains interleave, so one MMA's latency
+                        // overlaps the next block's MMA
 #pragma unroll
                         for (int k = 0; k < KB / 16; ++k)
-                            mma_f16(dt, sdesc(ta + k * 32), sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                            for (int bb = 0; bb < nb; ++bb)
+                                mma_f16_ta(dt + bb * QN, ta + bb * (KB / 2) + k * 8, sdesc(tq + k * 32), idesc,
+                                           (kb | k) != 0);
                         mma_commit(empty_a0 + 8 * sa);
                         mma_commit(empty_load0 + 8 * s);
                         if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
@@ -455,7 +478,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
         const int row = warp * 32 + lane;
-        uint32_t acc = 0, rbg = 0, li = 0;
+        uint32_t blk = 0, pc = 0, rbg = 0, li = 0;     // row blocks, stage groups, meta slots, items
+        bool okp = true;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
             const int ib = li & 1;
             const bool got = mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag);
@@ -472,13 +496,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             }
             __syncwarp();
             bool stop = false;
-            for (int r = 0; r < nrows; r += MR, ++acc, ++rbg) {
+            for (int r = 0; r < nrows; r += MR, ++blk, ++rbg) {
+                const int bb = (r / MR) % RP;                   // block within its stage group
+                const int nb = min(RP, (nrows - (r - bb * MR) + MR - 1) / MR);
                 const int nr = min(MR, nrows - r);
-                const int buf = acc & 1, m = rbg % MS;
+                const int buf = pc & 1, m = rbg % MS;
                 bool okw = mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag);
-                okw = okw && mbar_wait_warp(tfull0 + 8 * buf, (acc >> 1) & 1, abort_flag);
-                float* est_t = s_est + (acc & 1) * (QN * MR);   // tiles alternate between row blocks
-                uint32_t* ids_t = s_ids + (acc & 1) * MR;
+                if (bb == 0) okp = mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag);
+                okw = okw && okp;
+                float* est_t = s_est + (blk & 1) * (QN * MR);   // tiles alternate between row blocks
+                uint32_t* ids_t = s_ids + (blk & 1) * MR;
                 if (okw) {
                     // phase 1: own 32 rows x all queries -> query-major tile
                     tc_fence_after();
@@ -487,14 +514,17 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
 #pragma unroll 1
                     for (int cc = 0; cc < npad; cc += 32) {
                         uint32_t v[32];
-                        ERQ_TMEM_LD32(tmem + lane_base + buf * QN + cc, v);
+                        ERQ_TMEM_LD32(tmem + lane_base + buf * (RP * QN) + bb * QN + cc, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                         for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
                     }
                     tc_fence_before();
                 }
-                mbar_arrive(tempty0 + 8 * buf);
+                if (bb == nb - 1) {                             // the group's accumulators are free
+                    mbar_arrive(tempty0 + 8 * buf);
+                    ++pc;
+                }
                 mbar_arrive(empty_meta0 + 8 * m);
                 if (bar_or(1, 128, !okw || *abort_flag != 0)) { stop = true; break; }
                 // phase 2: the 128 rows of each owned query; the four 32-row
@@ -678,7 +708,7 @@ static bool make_codes_map(CUtensorMap* map, const uint8_t* codes_t, int64_t Np,
     const cuuint32_t box[4] = {(cuuint32_t)KB, 32, 1, MR / 32};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, (void*)codes_t, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
