@@ -60,7 +60,7 @@ void free_index_arrays(erq_index* ix) {
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_t,
-                    ix->dstats};
+                    ix->dstats, ix->PT_hi, ix->C_hi};   // PT_lo / C_lo live inside those blocks
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
@@ -125,6 +125,21 @@ erq_status derive_gemm_arrays(erq_index* ix, cudaStream_t s) {
     if ((e = launch_row_exp(ix->P, D, D, ix->eP, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->PT, D, D, ix->ePT, s)) != cudaSuccess) return cuda_fail(e, "row exp");
     if ((e = launch_row_exp(ix->C, ix->nlist, D, ix->eC, s)) != cudaSuccess) return cuda_fail(e, "row exp");
+    // FP16 hi / lo splits of P^T and the centroids for the query-time GEMMs
+    {
+        const size_t pd = (size_t)D * D, cd = (size_t)ix->nlist * D;
+        if (!ix->PT_hi && cudaMalloc(&ix->PT_hi, 2 * pd * sizeof(__half)) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc P^T split");
+        if (!ix->C_hi && cudaMalloc(&ix->C_hi, 2 * cd * sizeof(__half)) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc centroid split");
+        ix->PT_lo = ix->PT_hi + pd;
+        ix->C_lo = ix->C_hi + cd;
+        ix->device_bytes += (int64_t)(4 * (pd + cd));
+        if ((e = launch_split_hilo(ix->PT, ix->ePT, D, D, ix->PT_hi, ix->PT_lo, s)) != cudaSuccess)
+            return cuda_fail(e, "split P^T");
+        if ((e = launch_split_hilo(ix->C, ix->eC, ix->nlist, D, ix->C_hi, ix->C_lo, s)) != cudaSuccess)
+            return cuda_fail(e, "split centroids");
+    }
     // tiled, padded copy of the codes and per-row factors for the tensor-core scan
     {
         const std::vector<int64_t>& lo = *ix->host_list_off;
@@ -459,8 +474,11 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((__half*)nullptr, prec == ERQ_PREC_FP32 ? 1 : (size_t)nq * D); // 20 Qh
         T((int32_t*)nullptr, nq);                                        // 21 eQ
         T((uint64_t*)nullptr, prec == ERQ_PREC_FP32 ? 1 : nq);           // 22 query-wide thresholds
+        T((__half*)nullptr, (size_t)nq * D);                              // 23 Q hi
+        T((__half*)nullptr, (size_t)nq * D);                              // 24 Q lo
+        T((float*)nullptr, (!explicit_probe && nlist > 1) ? (size_t)nq * ((nlist + 31) / 32) : 1);  // 25 group minima
     };
-    void* sl[23];
+    void* sl[26];
     layout(plan, false, sl);
     ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
     Carver cv(ix->ws, ix->ws_bytes);
@@ -506,8 +524,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
             return cuda_fail(e, "query rotation");
     } else {
         if ((e = launch_row_exp(Q, nq, D, eQ, s)) != cudaSuccess) return cuda_fail(e, "query exponents");
-        if ((e = launch_gemm_tc(Q, eQ, nq, ix->PT, ix->ePT, D, D, Qrot, D, 0, nullptr, nullptr, nullptr, ix->status,
-                                s)) != cudaSuccess)
+        if ((e = launch_split_hilo(Q, eQ, nq, D, (__half*)sl[23], (__half*)sl[24], s)) != cudaSuccess)
+            return cuda_fail(e, "query split");
+        if ((e = launch_gemm_tma((__half*)sl[23], (__half*)sl[24], eQ, nq, ix->PT_hi, ix->PT_lo, ix->ePT, D, D, Qrot,
+                                 D, 0, nullptr, nullptr, nullptr, ix->status, s)) != cudaSuccess)
             return cuda_fail(e, "query rotation");
     }
     if (prec != ERQ_PREC_FP32 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
@@ -524,11 +544,13 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     } else {
         if ((e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
         e = simt ? launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s)
-                 : launch_gemm_tc(Q, eQ, nq, ix->C, ix->eC, nlist, D, sqd, nlist, 1, nullptr, qn, ix->cnorm2,
-                                  ix->status, s);
+                 : launch_gemm_tma((__half*)sl[23], (__half*)sl[24], eQ, nq, ix->C_hi, ix->C_lo, ix->eC, nlist, D, sqd,
+                                   nlist, 1, qn, ix->cnorm2, (!simt && maxp <= 32) ? (float*)sl[25] : nullptr,
+                                   ix->status, s);
         if (e != cudaSuccess) return cuda_fail(e, "centroid distances");
-        if ((e = launch_row_topk_fast(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s)) != cudaSuccess)
-            return cuda_fail(e, "probe select");
+        e = (!simt && maxp <= 32) ? launch_row_topk_groups(sqd, (float*)sl[25], nq, nlist, nlist, maxp, probe, maxp, s)
+                                  : launch_row_topk_fast(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "probe select");
     }
     ERQ_TRY(mark(2));
     // ---- plan

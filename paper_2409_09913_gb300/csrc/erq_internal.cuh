@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of liberq.so.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -90,6 +91,10 @@ struct erq_index {
     int32_t* eP = nullptr;       // [D] row exponents of P (tensor-core GEMM scaling)
     int32_t* ePT = nullptr;      // [D] row exponents of P^T
     int32_t* eC = nullptr;       // [nlist] row exponents of the centroids
+    __half* PT_hi = nullptr;     // [D][D] P^T scaled by 2^-ePT, split into FP16 hi / lo parts
+    __half* PT_lo = nullptr;
+    __half* C_hi = nullptr;      // [nlist][D] centroids scaled by 2^-eC, FP16 hi / lo parts
+    __half* C_lo = nullptr;
     float* C = nullptr;          // [nlist][D] centroids
     float* Cp = nullptr;         // [nlist][D] rotated centroids P^T c
     float* cnorm2 = nullptr;     // [nlist] ||c||^2 (FP32, for the probe)

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "erq_kernels.cuh"
+#include "warp_sort.cuh"
 
 namespace erq {
 
@@ -713,9 +714,125 @@ __global__ void __launch_bounds__(RS_THREADS) row_topk_radix_kernel(const float*
     }
 }
 
+// Smallest p <= 32 entries of each row (keys (value, column), so ties take the
+// lower column), one warp per row.  A first pass takes the p-th smallest of the
+// 32 lanes' minima over their columns: at least p entries lie at or below it,
+// so it is a valid admission bound, and a tight one.  The second pass keeps the
+// current p best in a sorted 32-entry list across the lanes; a 32-column chunk
+// with an entry below the bound and the list's p-th key is sorted and merged in.
+__global__ void __launch_bounds__(256) row_topk_warp_kernel(const float* __restrict__ V, int64_t rows, int ncols,
+                                                            int64_t ld, int p, int32_t* __restrict__ out_idx,
+                                                            float* __restrict__ out_val, int64_t ld_out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const float* v = V + row * ld;
+    constexpr int PF = 8;                        // chunks loaded ahead
+    uint32_t lmin = 0xffffffffu;                 // this lane's smallest ordered value
+    for (int c0 = 0; c0 < ncols; c0 += 32 * PF) {
+        uint32_t o[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int c = c0 + 32 * u + lane;
+            o[u] = c < ncols ? float_to_ordered(v[c]) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) lmin = o[u] < lmin ? o[u] : lmin;
+    }
+    // p-th smallest lane minimum (lanes that saw no column contribute the maximum)
+    const uint32_t bound = (uint32_t)(ws_shfl(ws_sort32(((uint64_t)lmin << 32) | (uint32_t)lane, lane), p - 1) >> 32);
+    uint64_t list = kEmptyKey, th = kEmptyKey;
+    for (int c0 = 0; c0 < ncols; c0 += 32 * PF) {
+        uint32_t o[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int c = c0 + 32 * u + lane;
+            o[u] = c < ncols ? float_to_ordered(v[c]) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int c = c0 + 32 * u + lane;
+            const uint64_t key = ((uint64_t)o[u] << 32) | (uint32_t)c;
+            const bool pass = c < ncols && o[u] <= bound && key < th;
+            if (!__any_sync(0xffffffffu, pass)) continue;
+            list = ws_merge32(list, ws_sort32(pass ? key : kEmptyKey, lane), lane);
+            th = ws_shfl(list, p - 1);
+        }
+    }
+    if (lane < p) {
+        out_idx[row * ld_out + lane] = list == kEmptyKey ? -1 : (int32_t)(list & 0xffffffffu);
+        if (out_val) out_val[row * ld_out + lane] = list == kEmptyKey ? INFINITY : ordered_to_float((uint32_t)(list >> 32));
+    }
+}
+
+// Smallest p <= 32 entries of each row (keys (value, column), ties to the lower
+// column) given the minimum of every 32-column group, one warp per row: the
+// p-th smallest group minimum bounds the p-th smallest entry (p groups hold an
+// entry at or below it), so only groups whose minimum is at or below it can
+// hold an answer; those are read and merged into a sorted 32-entry warp list.
+__global__ void __launch_bounds__(256) row_topk_groups_kernel(const float* __restrict__ V,
+                                                              const float* __restrict__ gmin, int64_t rows, int ncols,
+                                                              int64_t ld, int p, int32_t* __restrict__ out_idx,
+                                                              int64_t ld_out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const int ng = (ncols + 31) / 32;
+    const float* gm = gmin + row * ng;
+    // bound: p-th smallest group minimum (groups visited 32 at a time)
+    uint64_t best = kEmptyKey;
+    for (int g0 = 0; g0 < ng; g0 += 32) {
+        const int gi = g0 + lane;
+        const uint64_t key = gi < ng ? ((uint64_t)float_to_ordered(gm[gi]) << 32) | (uint32_t)gi : kEmptyKey;
+        best = ws_merge32(best, ws_sort32(key, lane), lane);
+    }
+    const uint32_t bound = (uint32_t)(ws_shfl(best, p - 1) >> 32);
+    const float* v = V + row * ld;
+    uint64_t list = kEmptyKey, th = kEmptyKey;
+    for (int g0 = 0; g0 < ng; g0 += 32) {
+        const int gi = g0 + lane;
+        uint32_t cand = __ballot_sync(0xffffffffu, gi < ng && float_to_ordered(gm[gi]) <= bound);
+        while (cand) {                                   // candidate groups, up to 4 loaded together
+            int gsel[4];
+            uint32_t o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                gsel[u] = cand ? g0 + __ffs(cand) - 1 : -1;
+                if (cand) cand &= cand - 1;
+                const int c = gsel[u] * 32 + lane;
+                o[u] = (gsel[u] >= 0 && c < ncols) ? float_to_ordered(v[c]) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (gsel[u] < 0) break;                      // warp-uniform
+                const int c = gsel[u] * 32 + lane;
+                const uint64_t key = ((uint64_t)o[u] << 32) | (uint32_t)c;
+                const bool pass = c < ncols && o[u] <= bound && key < th;
+                ws_insert_each(list, th, key, pass, p, lane);
+            }
+        }
+    }
+    if (lane < p) out_idx[row * ld_out + lane] = list == kEmptyKey ? -1 : (int32_t)(list & 0xffffffffu);
+}
+
+cudaError_t launch_row_topk_groups(const float* V, const float* gmin, int64_t rows, int ncols, int64_t ld, int p,
+                                   int32_t* out_idx, int64_t ld_out, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    count_launch();
+    row_topk_groups_kernel<<<(unsigned)ceil_div(rows * 32, 256), 256, 0, s>>>(V, gmin, rows, ncols, ld, p, out_idx,
+                                                                            ld_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_row_topk_fast(const float* V, int64_t rows, int ncols, int64_t ld, int p, int32_t* out_idx,
                                  float* out_val, int64_t ld_out, cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
+    if (p <= 32) {
+        count_launch();
+        row_topk_warp_kernel<<<(unsigned)ceil_div(rows * 32, 256), 256, 0, s>>>(V, rows, ncols, ld, p, out_idx, out_val,
+                                                                               ld_out);
+        return cudaGetLastError();
+    }
     if (ncols > 16384 || p > 2048) return launch_row_topk(V, rows, ncols, ld, p, out_idx, out_val, ld_out, s);
     int sortn = 32;
     while (sortn < p) sortn <<= 1;

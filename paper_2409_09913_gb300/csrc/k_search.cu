@@ -18,37 +18,42 @@
 
 #include "erq_kernels.cuh"
 #include "erq_search.cuh"
+#include "warp_sort.cuh"
 
 namespace erq {
 
 // ---------------------------------------------------------------------------
 // ||q_r - c||^2 per probed pair, FP32, one warp per pair.
 // ---------------------------------------------------------------------------
+// ||q_r - c||^2 for every probed (query, cluster): one block per query, the
+// query row in shared memory, one warp per probed cluster.
 __global__ void dqc_kernel(const float* __restrict__ Q, const float* __restrict__ C,
                            const int32_t* __restrict__ probe, const int32_t* __restrict__ npr, int64_t nq,
                            int maxp, int D, float* __restrict__ dqc) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= nq * maxp) return;
-    const int64_t q = w / maxp;
-    const int slot = (int)(w % maxp);
-    if (slot >= npr[q]) return;
-    const int c = probe[w];
-    if (c < 0) return;  // invalid probe id (reported through the status word)
-    const float* x = Q + q * D;
-    const float* y = C + (int64_t)c * D;
-    float s = 0.f;
-    for (int k = lane * 4; k < D; k += 128) {
-        const float4 a = *reinterpret_cast<const float4*>(x + k);
-        const float4 b = *reinterpret_cast<const float4*>(y + k);
-        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
-        s = fmaf(d0, d0, s);
-        s = fmaf(d1, d1, s);
-        s = fmaf(d2, d2, s);
-        s = fmaf(d3, d3, s);
+    extern __shared__ float qs[];
+    const int64_t q = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x * 4; k < D; k += blockDim.x * 4)
+        *reinterpret_cast<float4*>(qs + k) = *reinterpret_cast<const float4*>(Q + q * D + k);
+    __syncthreads();
+    const int np = npr[q];
+    for (int slot = warp; slot < np; slot += blockDim.x >> 5) {
+        const int c = probe[q * maxp + slot];
+        if (c < 0) continue;  // invalid probe id (reported through the status word)
+        const float* y = C + (int64_t)c * D;
+        float s = 0.f;
+        for (int k = lane * 4; k < D; k += 128) {
+            const float4 a = *reinterpret_cast<const float4*>(qs + k);
+            const float4 b = *reinterpret_cast<const float4*>(y + k);
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            s = fmaf(d0, d0, s);
+            s = fmaf(d1, d1, s);
+            s = fmaf(d2, d2, s);
+            s = fmaf(d3, d3, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) dqc[q * maxp + slot] = s;
     }
-    s = warp_sum(s);
-    if (lane == 0) dqc[w] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -61,31 +66,43 @@ __global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t pro
                                   int32_t* __restrict__ cnt_c, int32_t* __restrict__ slot_nr,
                                   uint32_t* __restrict__ status, unsigned long long* __restrict__ stats) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nq * maxp) return;
-    const int64_t q = t / maxp;
-    const int slot = (int)(t % maxp);
-    int np = npr_in ? npr_in[q] : npr_uniform;
-    if (np < 1 || np > maxp) {
-        if (slot == 0) atomicOr(status, kStatusBounds);
-        np = np < 1 ? 0 : maxp;
-    }
-    if (slot == 0) npr[q] = np;
-    int nr = 0;
-    int c = -1;
-    if (slot < np) {
-        c = probe[q * probe_stride + slot];
-        if (c < 0 || c >= nlist) {
-            atomicOr(status, kStatusBounds);
-            c = -1;
-        } else {
-            const int64_t size = list_off[c + 1] - list_off[c];
-            nr = (int)((size + RR - 1) / RR);
-            if (atomicAdd(&cnt_c[c], 1) == 0) atomicAdd(&stats[1], (unsigned long long)size);
-            atomicAdd(&stats[0], (unsigned long long)size);
+    unsigned long long add_pairs = 0, add_rows = 0;
+    if (t < nq * maxp) {
+        const int64_t q = t / maxp;
+        const int slot = (int)(t % maxp);
+        int np = npr_in ? npr_in[q] : npr_uniform;
+        if (np < 1 || np > maxp) {
+            if (slot == 0) atomicOr(status, kStatusBounds);
+            np = np < 1 ? 0 : maxp;
         }
+        if (slot == 0) npr[q] = np;
+        int nr = 0;
+        int c = -1;
+        if (slot < np) {
+            c = probe[q * probe_stride + slot];
+            if (c < 0 || c >= nlist) {
+                atomicOr(status, kStatusBounds);
+                c = -1;
+            } else {
+                const int64_t size = list_off[c + 1] - list_off[c];
+                nr = (int)((size + RR - 1) / RR);
+                if (atomicAdd(&cnt_c[c], 1) == 0) add_rows = (unsigned long long)size;
+                add_pairs = (unsigned long long)size;
+            }
+        }
+        probe_c[t] = c;
+        slot_nr[t] = nr;
     }
-    probe_c[t] = c;
-    slot_nr[t] = nr;
+    // one atomic per warp for the work counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        add_pairs += __shfl_xor_sync(0xffffffffu, add_pairs, o);
+        add_rows += __shfl_xor_sync(0xffffffffu, add_rows, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (add_pairs) atomicAdd(&stats[0], add_pairs);
+        if (add_rows) atomicAdd(&stats[1], add_rows);
+    }
 }
 
 // per query: offsets of its (slot, range) lists, and their total
@@ -408,6 +425,36 @@ __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__
     for (int j = threadIdx.x; j < kp; j += blockDim.x) cand[q * kp + j] = buf[j];
 }
 
+// Merge for k' <= 32: one warp per query keeps the k' smallest keys in a
+// sorted 32-entry list across the lanes; each list is read in 32-key chunks,
+// and a chunk with a key below the current k'-th is sorted and merged in.
+__global__ void __launch_bounds__(256) merge_warp_kernel(const uint64_t* __restrict__ inter,
+                                                         const int32_t* __restrict__ inter_cnt,
+                                                         const int64_t* __restrict__ qbase, int64_t nq, int kp,
+                                                         int lstride, uint64_t* __restrict__ cand) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    const int64_t L0 = qbase[q], L1 = qbase[q + 1];
+    uint64_t list = kEmptyKey, th = kEmptyKey;
+    for (int64_t Lb = L0; Lb < L1; Lb += 32) {
+        const int nl = (int)imin64(32, L1 - Lb);
+        const int myn = lane < nl ? inter_cnt[Lb + lane] : 0;     // counts of up to 32 lists at once
+        for (int i = 0; i < nl; ++i) {
+            const int n = __shfl_sync(0xffffffffu, myn, i);
+            const uint64_t* src = inter + (Lb + i) * lstride;
+            for (int c0 = 0; c0 < n; c0 += 32) {
+                const uint64_t key = c0 + lane < n ? src[c0 + lane] : kEmptyKey;
+                const bool pass = key < th;
+                if (!__any_sync(0xffffffffu, pass)) continue;
+                list = ws_merge32(list, ws_sort32(pass ? key : kEmptyKey, lane), lane);
+                th = ws_shfl(list, kp - 1);
+            }
+        }
+    }
+    if (lane < kp) cand[q * kp + lane] = list;
+}
+
 // ---------------------------------------------------------------------------
 // Re-rank: exact squared distances of the k' candidates (FP32), top-k.
 // Also writes cand_ids / cand_est when requested.  One block per query.
@@ -443,14 +490,27 @@ __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict_
         const uint32_t id = key_id(kk);
         const float* x = X + (int64_t)id * D;
         float s = 0.f;
-        for (int t = lane * 4; t < D; t += 128) {
-            const float4 a = *reinterpret_cast<const float4*>(x + t);
-            const float4 b = *reinterpret_cast<const float4*>(qr + t);
-            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
-            s = fmaf(d0, d0, s);
-            s = fmaf(d1, d1, s);
-            s = fmaf(d2, d2, s);
-            s = fmaf(d3, d3, s);
+        constexpr int RU = 8;                 // float4 loads per lane in flight
+        for (int t0 = 0; t0 < D; t0 += 128 * RU) {
+            float4 a[RU], b[RU];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int t = t0 + 128 * u + lane * 4;
+                if (t < D) {
+                    a[u] = *reinterpret_cast<const float4*>(x + t);
+                    b[u] = *reinterpret_cast<const float4*>(qr + t);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                if (t0 + 128 * u + lane * 4 < D) {
+                    const float d0 = a[u].x - b[u].x, d1 = a[u].y - b[u].y, d2 = a[u].z - b[u].z, d3 = a[u].w - b[u].w;
+                    s = fmaf(d0, d0, s);
+                    s = fmaf(d1, d1, s);
+                    s = fmaf(d2, d2, s);
+                    s = fmaf(d3, d3, s);
+                }
+            }
         }
         s = warp_sum(s);
         if (lane == 0) keys[j] = make_key(s, id);
@@ -547,10 +607,12 @@ __global__ void __launch_bounds__(256) backward_gather_kernel(const float* __res
 // ---------------------------------------------------------------------------
 cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
                        int D, float* dqc, cudaStream_t s) {
-    const int64_t warps = nq * maxp;
-    if (warps <= 0) return cudaSuccess;
+    if (nq <= 0 || maxp <= 0) return cudaSuccess;
+    const size_t smem = (size_t)D * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(dqc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     count_launch();
-    dqc_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
+    dqc_kernel<<<(unsigned)nq, 128, smem, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
     return cudaGetLastError();
 }
 
@@ -612,6 +674,12 @@ int merge_sortn(int kp, int lstride) {
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
                          int lstride, uint64_t* cand, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
+    if (kp <= 32) {
+        count_launch();
+        merge_warp_kernel<<<(unsigned)ceil_div(nq * 32, 256), 256, 0, s>>>(inter, inter_cnt, qbase, nq, kp, lstride,
+                                                                          cand);
+        return cudaGetLastError();
+    }
     const int sortn = merge_sortn(kp, lstride);
     cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
     if (e != cudaSuccess) return e;
@@ -620,10 +688,80 @@ cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const 
     return cudaGetLastError();
 }
 
+// Re-rank for k' <= 32: one block of k' warps per query, one candidate per warp
+// (the query row staged in shared memory, the candidate's raw row read with all
+// of its loads in flight); warp 0 sorts the k' exact distances.
+__global__ void __launch_bounds__(1024) rerank32_kernel(const uint64_t* __restrict__ cand, int kp,
+                                                        const float* __restrict__ X, const float* __restrict__ Q,
+                                                        int D, int k, int64_t* __restrict__ ids,
+                                                        float* __restrict__ dists, int64_t* __restrict__ cand_ids,
+                                                        float* __restrict__ cand_est) {
+    extern __shared__ float qrow[];           // [D]
+    __shared__ uint64_t keys[32];
+    const int64_t q = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t* cq = cand + q * kp;
+    for (int t = threadIdx.x * 4; t < D; t += blockDim.x * 4)
+        *reinterpret_cast<float4*>(qrow + t) = *reinterpret_cast<const float4*>(Q + q * D + t);
+    if (cand_ids && threadIdx.x < kp) {
+        const uint64_t kk = cq[threadIdx.x];
+        cand_ids[q * kp + threadIdx.x] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
+        cand_est[q * kp + threadIdx.x] = kk == kEmptyKey ? INFINITY : key_value(kk);
+    }
+    __syncthreads();
+    const uint64_t kk = cq[warp];
+    uint64_t key = kEmptyKey;
+    if (kk != kEmptyKey) {
+        const uint32_t id = key_id(kk);
+        const float* x = X + (int64_t)id * D;
+        float s = 0.f;
+        constexpr int RU = 8;
+        for (int t0 = 0; t0 < D; t0 += 128 * RU) {
+            float4 a[RU];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int t = t0 + 128 * u + lane * 4;
+                if (t < D) a[u] = *reinterpret_cast<const float4*>(x + t);
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int t = t0 + 128 * u + lane * 4;
+                if (t < D) {
+                    const float4 b = *reinterpret_cast<const float4*>(qrow + t);
+                    const float d0 = a[u].x - b.x, d1 = a[u].y - b.y, d2 = a[u].z - b.z, d3 = a[u].w - b.w;
+                    s = fmaf(d0, d0, s);
+                    s = fmaf(d1, d1, s);
+                    s = fmaf(d2, d2, s);
+                    s = fmaf(d3, d3, s);
+                }
+            }
+        }
+        s = warp_sum(s);
+        key = make_key(s, id);
+    }
+    if (lane == 0) keys[warp] = key;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t v = ws_sort32(lane < kp ? keys[lane] : kEmptyKey, lane);
+        if (lane < k) {
+            ids[q * k + lane] = v == kEmptyKey ? -1 : (int64_t)key_id(v);
+            dists[q * k + lane] = v == kEmptyKey ? INFINITY : key_value(v);
+        }
+    }
+}
+
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
+    if (do_rerank && kp <= 32) {
+        const size_t smem = (size_t)D * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(rerank32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        rerank32_kernel<<<(unsigned)nq, 32 * kp, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est);
+        return cudaGetLastError();
+    }
     int sortn = 32;
     while (sortn < kp) sortn <<= 1;
     cudaError_t e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
