@@ -37,7 +37,7 @@ METRIC = "QPS at recall@10>=0.95 (batched IVF search, 1 GB300)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="erq", choices=["erq", "reference"])
     ap.add_argument("--workload", default="ivf_n1m_d960_nlist4096")
@@ -146,6 +146,36 @@ def measured_peaks():
 def ffma_peak_tflops(sm_mhz):
     """FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops per cycle at the clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def scan_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_scan_tc.cu", "tc_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2409_09913_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload, nprobe, precision):
+    """DRAM bytes per launch of the tensor-core scan from the committed ncu
+    capture (profiles/scan_tc_traffic_*.txt), only while the kernel source is
+    the one that was profiled; None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"scan_tc_traffic_{workload}.txt")
+    if precision == "fp32" or not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.lstrip().startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    try:
+        if kv.get("kernel_source_sha256") != scan_source_sha() or int(kv.get("nprobe", -1)) != nprobe:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # ----------------------------------------------------------------------------- oracle sample
@@ -279,12 +309,13 @@ def main():
     results = {}
     for prec, p in chosen.items():
         def step():
-            ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec)
+            ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        ix.timing_total()                  # reset the per-phase sums to the timed region
         launches0 = erq.kernel_launches()
         st = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,9 +333,10 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
             dist.barrier()
-        # phase split and work counters from one extra timed search
-        ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True)
-        phases = ix.timing()
+        # per-phase device time averaged over the timed searches (CUDA events on the
+        # search stream), and the work counters of the last one
+        tot, cnt = ix.timing_total()
+        phases = {kk: v / max(cnt, 1) for kk, v in tot.items()}
         work = ix.stats()
         results[prec] = dict(nprobe=p, ms=ms, qps=len(Q) * world / (ms / 1e3), recall=sweep[prec][p],
                              phases=phases, work=work, clocks=clk.summary(), launches=launches)
@@ -351,6 +383,8 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": bytes_alg / scan_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (bytes_alg / scan_s / 1e9) / peaks["hbm_gbs"], "traffic": None}
+    roof["traffic"] = profiled_traffic(args.workload, R["nprobe"], best)
+    roof["bytes_alg_per_launch"] = bytes_alg
     roof["kernel"] = "scan_fp32_kernel" if best == "fp32" else "scan_tc_kernel"
     roof["peak_source"] = peaks["source"] if bound_c != "alu" or roof["bound"] == "hbm" else \
         f"152 SMs x 128 FFMA x 2 at {sm_mhz:.0f} MHz"

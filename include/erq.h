@@ -223,6 +223,11 @@ erq_status erq_index_load(const char* path, void* stream, erq_index** out);
  * item's query count padded to the MMA width (0 for the FP32 path).  Fills
  * min(n, 6) entries; n must be >= 4.  Synchronises the device. */
 erq_status erq_search_timing(const erq_index* index, float* ms, int32_t n);
+/* erq_search_timing_total: per-phase device milliseconds summed over the timed
+ * searches since the previous call (at most the last 512 of them; *count says
+ * how many were summed), same phase order as erq_search_timing.  Synchronises
+ * on those searches' events.  Errors: EINVAL for null arguments or n < 6. */
+erq_status erq_search_timing_total(erq_index* index, float* ms, int32_t n, int64_t* count);
 uint64_t erq_kernel_launches(void);
 erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);
 

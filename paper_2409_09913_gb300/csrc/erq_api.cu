@@ -64,8 +64,11 @@ void free_index_arrays(erq_index* ix) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
-    for (cudaEvent_t& e : ix->ev)
-        if (e) cudaEventDestroy(e);
+    if (ix->ev_ring) {
+        for (int i = 0; i < erq_index::kTimingRing * 7; ++i)
+            if (ix->ev_ring[i]) cudaEventDestroy(ix->ev_ring[i]);
+        delete[] ix->ev_ring;
+    }
     delete ix->host_list_off;
 }
 
@@ -509,10 +512,13 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     cudaError_t e;
     const bool timed = (p->flags & ERQ_SEARCH_TIMING) != 0;
     ix->timed = 0;
-    if (timed && !ix->ev[0])
-        for (cudaEvent_t& ev : ix->ev) ERQ_CHECK_CUDA(cudaEventCreate(&ev));
+    if (timed && !ix->ev_ring) ix->ev_ring = new cudaEvent_t[erq_index::kTimingRing * 7]();
+    cudaEvent_t* ev = timed ? ix->ev_ring + (ix->timing_seq % erq_index::kTimingRing) * 7 : nullptr;
+    if (timed)
+        for (int i = 0; i < 7; ++i)
+            if (!ev[i]) ERQ_CHECK_CUDA(cudaEventCreate(&ev[i]));
     auto mark = [&](int i) -> erq_status {
-        if (timed) ERQ_CHECK_CUDA(cudaEventRecord(ix->ev[i], s));
+        if (timed) ERQ_CHECK_CUDA(cudaEventRecord(ev[i], s));
         return ERQ_OK;
     };
     ERQ_TRY(mark(0));
@@ -653,7 +659,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
                            s)) != cudaSuccess)
         return cuda_fail(e, "rerank");
     ERQ_TRY(mark(6));
-    if (timed) ix->timed = 1;
+    if (timed) {
+        ix->timed = 1;
+        ++ix->timing_seq;
+    }
     return ERQ_OK;
 }
 
@@ -873,8 +882,27 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
 extern "C" erq_status erq_search_timing(const erq_index* ix, float* ms, int32_t n) {
     if (!ix || !ms || n < 6) return fail(ERQ_EINVAL, "erq_search_timing: bad arguments");
     if (!ix->timed) return fail(ERQ_EINVAL, "erq_search_timing: no search ran with ERQ_SEARCH_TIMING");
-    ERQ_CHECK_CUDA(cudaEventSynchronize(ix->ev[6]));
-    for (int i = 0; i < 6; ++i) ERQ_CHECK_CUDA(cudaEventElapsedTime(&ms[i], ix->ev[i], ix->ev[i + 1]));
+    const cudaEvent_t* ev = ix->ev_ring + ((ix->timing_seq - 1) % erq_index::kTimingRing) * 7;
+    ERQ_CHECK_CUDA(cudaEventSynchronize(ev[6]));
+    for (int i = 0; i < 6; ++i) ERQ_CHECK_CUDA(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_search_timing_total(erq_index* ix, float* ms, int32_t n, int64_t* count) {
+    if (!ix || !ms || n < 6 || !count) return fail(ERQ_EINVAL, "erq_search_timing_total: bad arguments");
+    for (int i = 0; i < 6; ++i) ms[i] = 0.f;
+    const int64_t first = std::max(ix->timing_base, ix->timing_seq - erq_index::kTimingRing);
+    for (int64_t t = first; t < ix->timing_seq; ++t) {
+        const cudaEvent_t* ev = ix->ev_ring + (t % erq_index::kTimingRing) * 7;
+        ERQ_CHECK_CUDA(cudaEventSynchronize(ev[6]));
+        for (int i = 0; i < 6; ++i) {
+            float x = 0.f;
+            ERQ_CHECK_CUDA(cudaEventElapsedTime(&x, ev[i], ev[i + 1]));
+            ms[i] += x;
+        }
+    }
+    *count = ix->timing_seq - first;
+    ix->timing_base = ix->timing_seq;
     return ERQ_OK;
 }
 

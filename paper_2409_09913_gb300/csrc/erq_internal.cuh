@@ -124,8 +124,11 @@ struct erq_index {
     void* io = nullptr;          // device staging of erq_search_host
     size_t io_bytes = 0;
     void* pinned = nullptr;      // pinned host staging for erq_search_host
-    cudaEvent_t ev[7] = {};      // phase boundaries of the last timed search
-    int timed = 0;               // 1 when ev[] holds a timed search
+    static constexpr int kTimingRing = 512;   // timed searches whose phase events are kept
+    cudaEvent_t* ev_ring = nullptr;  // [kTimingRing][7] phase boundaries of timed searches
+    int64_t timing_seq = 0;      // timed searches so far
+    int64_t timing_base = 0;     // first timed search not yet summed by erq_search_timing_total
+    int timed = 0;               // 1 when the last search was timed
     int64_t last_stats[4] = {};  // pairs, distinct rows, work items, lists of the last search
     unsigned long long* dstats = nullptr;  // [4] device counters of the last search: pairs, distinct rows,
                                            //     tensor-core row blocks, row blocks x padded queries

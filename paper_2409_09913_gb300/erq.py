@@ -24,7 +24,7 @@ FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, 
 EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index", "erq_index_info_get",
            "erq_index_status", "erq_rotate", "erq_encode", "erq_search", "erq_search_host", "erq_estimate",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
-           "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc"]
+           "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total"]
 
 
 class ErqError(RuntimeError):
@@ -81,6 +81,7 @@ def lib(path: str | None = None):
     L.erq_index_save.argtypes = [vp, ct.c_char_p]
     L.erq_index_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
     L.erq_search_timing.argtypes = [vp, ct.POINTER(ct.c_float), i32]
+    L.erq_search_timing_total.argtypes = [vp, ct.POINTER(ct.c_float), i32, ct.POINTER(ct.c_int64)]
     L.erq_kernel_launches.argtypes = []
     L.erq_kernel_launches.restype = ct.c_uint64
     L.erq_search_stats.argtypes = [vp, ct.POINTER(ct.c_int64), i32]
@@ -88,7 +89,7 @@ def lib(path: str | None = None):
     for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
                  "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
                  "erq_index_save", "erq_index_load", "erq_search_timing",
-                 "erq_search_stats", "erq_search_backward_noalloc"):
+                 "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -208,6 +209,14 @@ class Index:
         ms = (ct.c_float * 6)()
         _check(lib().erq_search_timing(self._h, ms, 6))
         return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms)))
+
+    def timing_total(self):
+        """Per-phase device ms summed over the timed searches since the previous
+        call, and how many searches that covers."""
+        ms = (ct.c_float * 6)()
+        cnt = ct.c_int64()
+        _check(lib().erq_search_timing_total(self._h, ms, 6, ct.byref(cnt)))
+        return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms))), cnt.value
 
     def stats(self):
         """Work of the last search: pairs, distinct rows, items, lists, tensor-core
