@@ -20,7 +20,7 @@
 // stored per-row factors.  The product is exact up to the FP16 rounding of q'
 // (relative 2^-11 per element); accumulation is FP32.
 //
-// Warp roles (320 + 32 NG threads, one CTA per SM, persistent over work items):
+// Warp roles (320 + 32 (NG + NFX) threads, one CTA per SM, persistent over work items):
 //   warp 9     loader: per stage (128-row block, 64-wide K block) one TMA load
 //              of the raw u8 codes (L2 evict-first); per row block a bulk copy
 //              of the rows' factors and ids; per item the queries'
@@ -32,11 +32,13 @@
 //   warps 4-7  converters: one thread per row expands the row's 64 raw codes
 //              of a stage (64B-swizzled by the TMA, so reads are conflict-free)
 //              in registers and stores them into the stage's TMEM columns;
-//   warp 8     MMA issuer (one elected thread) and TMEM owner;
+//   warp 8     MMA issuer of row block 0 (one elected thread) and TMEM owner;
+//   last warp  MMA issuer of row block 1;
 //   warps 0-3  epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32 rows for
-//              all queries), stores g + (f_res/2)*acc into a query-major tile
-//              in shared memory, and after a named barrier filters the rows of
-//              the queries it owns (q = w mod 4) against per-query thresholds
+//              all queries) and stores g + (f_res/2)*acc into a query-major tile
+//              in shared memory; after a named barrier these four warps and the
+//              NFX filter-only warps each filter the rows of the queries they
+//              own (q = filter-warp index mod NFW) against per-query thresholds
 //              into per-query candidate lists (warp ballots, compaction by a
 //              warp bitonic sort; k' <= 32).  A query's threshold starts at the
 //              smallest k'-th key published by its items finished so far (every
@@ -75,8 +77,11 @@ constexpr int LS = 4;            // load stages (raw codes + query tile) in flig
 constexpr int MS = 4;            // row-factor buffers (one per row block)
 constexpr int KCAP = 32;         // max k' of the tensor-core path
 constexpr int KC = 64;           // per-query candidate list capacity (list stride of the output)
-constexpr int NG = 2;            // query-gather warps
-constexpr int THREADS = 320 + 32 * NG;
+constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
+constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
+constexpr int NFW = 4 + NFX;     // warps that filter candidates
+constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
+constexpr int THREADS = 32 * (MMA2 + 1);
 constexpr int TILE_Q = QN * KB * 2;    // 8 KB
 constexpr int TILE_RAW = RP * MR * KB; // 16 KB of u8 codes (TMA staging)
 constexpr int ACOL = 2 * RP * QN;  // first TMEM column of the expanded-code stages
@@ -233,24 +238,24 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < LS; ++s) {
             mbar_init(full_load0 + 8 * s, 1);      // the TMA expect_tx arrival
-            mbar_init(empty_load0 + 8 * s, 1);
+            mbar_init(empty_load0 + 8 * s, RP);    // one MMA commit per issuer
             mbar_init(full_q0 + 8 * s, 32 * NG);   // one cp.async arrival per gatherer lane
         }
         for (int s = 0; s < SA; ++s) {
             mbar_init(full_a0 + 8 * s, 128);
-            mbar_init(empty_a0 + 8 * s, 1);
+            mbar_init(empty_a0 + 8 * s, RP);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tfull0 + 8 * b, RP);
             mbar_init(tempty0 + 8 * b, 128);
             mbar_init(full_item0 + 8 * b, 32);
-            mbar_init(empty_item0 + 8 * b, 128);
+            mbar_init(empty_item0 + 8 * b, 32 * NFW);
         }
         for (int m = 0; m < MS; ++m) {
             mbar_init(full_meta0 + 8 * m, 1);
             mbar_init(empty_meta0 + 8 * m, 128);
         }
-        mbar_init(done_bar, 1);
+        mbar_init(done_bar, RP);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             mbar_wait_drain(full_meta0 + 8 * (gg % MS), (gg / MS) & 1);
         }
         __syncwarp();
-    } else if (warp >= 10) {
+    } else if (warp >= 10 && warp < 10 + NG) {
         // ------------------------------------------------------------ gatherers
         const uint64_t pol_q = l2_evict_last();
         const int ch = lane & 7, gi = warp - 10;
@@ -420,8 +425,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 mbar_arrive(full_a0 + 8 * sa);
             }
         }
-    } else if (warp == 8) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp == 8 || warp == MMA2) {
+        // ------------------------------------------------------------ MMA issuers
+        // Each issuer runs the accumulation chain of one row block of a stage
+        // group (tcgen05.mma issue stalls the issuing thread, so two issuers
+        // keep two chains in flight); both commit to the stage and tile barriers.
+        const int mrb = warp == 8 ? 0 : 1;
         uint32_t g = 0, acc = 0, li = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
@@ -445,15 +454,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     fence_proxy_async();       // query tile written by cp.async (generic proxy)
                     tc_fence_after();
                     if (lane == 0) {
-                        const uint32_t ta = tmem + ACOL + sa * RP * (KB / 2);
-                        const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
-                        // the RP blocks' accumulation chains interleave, so one MMA's latency
-                        // overlaps the next block's MMA
+                        if (mrb < nb) {
+                            const uint32_t ta = tmem + ACOL + (sa * RP + mrb) * (KB / 2);
+                            const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
 #pragma unroll
-                        for (int k = 0; k < KB / 16; ++k)
-                            for (int bb = 0; bb < nb; ++bb)
-                                mma_f16_ta(dt + bb * QN, ta + bb * (KB / 2) + k * 8, sdesc(tq + k * 32), idesc,
-                                           (kb | k) != 0);
+                            for (int k = 0; k < KB / 16; ++k)
+                                mma_f16_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                        }
                         mma_commit(empty_a0 + 8 * sa);
                         mma_commit(empty_load0 + 8 * s);
                         if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
@@ -474,21 +481,24 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         uint32_t* s_ids = reinterpret_cast<uint32_t*>(sm + Smem::ids);
         int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
         uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // warps 0-3 also move their TMEM lane quarter into the estimate tile
+        const bool tm = warp < 4;
+        const int fw = tm ? warp : warp - (10 + NG) + 4;     // filter warp index 0 .. NFW-1
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
-        const int row = warp * 32 + lane;
+        const int row = (warp & 3) * 32 + lane;
         uint32_t blk = 0, pc = 0, rbg = 0, li = 0;     // row blocks, stage groups, meta slots, items
         bool okp = true;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
             const int ib = li & 1;
             const bool got = mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag);
-            if (bar_or(1, 128, !got || *abort_flag != 0)) break;
+            if (bar_or(1, 32 * NFW, !got || *abort_flag != 0)) break;
             const int4 d = s_idesc[ib];
             const int nrows = d.z, nqi = d.w, npad = npad_of(nqi);
             const int4* iq = s_iq + ib * QN;
-            if (lane < 16) {                                   // owned queries q = warp + 4 * lane
-                const int q = warp + 4 * lane;
+            if (lane < QN / NFW) {                             // owned queries q = fw + NFW * lane
+                const int q = fw + NFW * lane;
                 if (q < nqi) {
                     s_cnt[q] = 0;
                     s_tau[q] = reinterpret_cast<const unsigned long long*>(sm + Smem::tq)[ib * QN + q];
@@ -501,12 +511,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 const int nb = min(RP, (nrows - (r - bb * MR) + MR - 1) / MR);
                 const int nr = min(MR, nrows - r);
                 const int buf = pc & 1, m = rbg % MS;
-                bool okw = mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag);
-                if (bb == 0) okp = mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag);
-                okw = okw && okp;
+                bool okw = true;
+                if (tm) {
+                    okw = mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag);
+                    if (bb == 0) okp = mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag);
+                    okw = okw && okp;
+                }
                 float* est_t = s_est + (blk & 1) * (QN * MR);   // tiles alternate between row blocks
                 uint32_t* ids_t = s_ids + (blk & 1) * MR;
-                if (okw) {
+                if (tm && okw) {
                     // phase 1: own 32 rows x all queries -> query-major tile
                     tc_fence_after();
                     const float4 mt = s_meta[m * MR + row];
@@ -522,16 +535,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     tc_fence_before();
                 }
                 if (bb == nb - 1) {                             // the group's accumulators are free
-                    mbar_arrive(tempty0 + 8 * buf);
+                    if (tm) mbar_arrive(tempty0 + 8 * buf);
                     ++pc;
                 }
-                mbar_arrive(empty_meta0 + 8 * m);
-                if (bar_or(1, 128, !okw || *abort_flag != 0)) { stop = true; break; }
+                if (tm) mbar_arrive(empty_meta0 + 8 * m);
+                if (bar_or(1, 32 * NFW, !okw || *abort_flag != 0)) { stop = true; break; }
                 // phase 2: the 128 rows of each owned query; the four 32-row
                 // groups' estimates are loaded together, compared as floats
                 // against the threshold's estimate (a superset of the key
                 // test), and only groups with a candidate form exact keys
-                for (int q = warp; q < nqi; q += 4) {
+                for (int q = fw; q < nqi; q += NFW) {
                     const float dq = __int_as_float(iq[q].y);
                     uint64_t tau = s_tau[q];
                     float tf = tau == kEmptyKey ? INFINITY : key_value(tau);
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 }
             }
             if (stop) break;
-            for (int q = warp; q < nqi; q += 4) {               // write this warp's lists
+            for (int q = fw; q < nqi; q += NFW) {               // write this warp's lists
                 int cnt = s_cnt[q];
                 if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
                     const uint64_t th = compact_list(lists + q * KC, cnt, kp, lane);
