@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--nq", type=int, default=0, help="override the query count")
     ap.add_argument("--nlist", type=int, default=0, help="override the IVF cluster count")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sync", action="store_true",
+                    help="size work buffers from a host read-back of the plan (default: host-side bounds, no "
+                         "synchronisation inside a search)")
     return ap.parse_args()
 
 
@@ -309,7 +312,8 @@ def main():
     results = {}
     for prec, p in chosen.items():
         def step():
-            ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True)
+            ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True,
+                      async_mode=not args.sync)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -352,11 +356,13 @@ def main():
     # end to end through the C ABI from pinned host buffers
     Qh = torch.from_numpy(Q).pin_memory()
     for _ in range(max(1, args.warmup)):
-        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best)
+        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
+                       async_mode=not args.sync)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(args.steps):
-        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best)
+        ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
+                       async_mode=not args.sync)
     e2e_s = (time.perf_counter() - te) / args.steps
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)

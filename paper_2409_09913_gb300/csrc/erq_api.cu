@@ -443,7 +443,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     const bool explicit_probe = p->probe != nullptr;
     const int prec = p->precision;
     // ---- phase A workspace (sizes known on the host)
-    const int QT = 64;                                  // queries per work item of the scan kernels
+    // queries per work item of the scan kernels
+    const int QT = prec == ERQ_PREC_FP32 ? 64 : scan_tc_queries_per_item(kp);
     int RR = 4096;
     Carver plan(nullptr, 0);
     auto layout = [&](Carver& cv, bool carve, void** slots) {
@@ -629,7 +630,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
 
     if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
     if (tcp && (e = launch_item_tables(items, n_items_d, nitems, ix->list_off, ix->poff, pa.qoff, pa.qlist, dqc,
-                                       pa.qbase, pa.slot_off, maxp, RR, itemd, itemq, pa.stats, s)) != cudaSuccess)
+                                       pa.qbase, pa.slot_off, maxp, RR, QT, itemd, itemq, pa.stats, s)) != cudaSuccess)
         return cuda_fail(e, "item tables");
     ERQ_TRY(mark(3));
     // ---- scan

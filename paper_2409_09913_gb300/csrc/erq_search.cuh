@@ -77,8 +77,9 @@ cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const 
 int scan_list_stride(int precision, int kp);
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
-                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int4* itemd,
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
                                int4* itemq, unsigned long long* stats, cudaStream_t s);
+int scan_tc_queries_per_item(int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
                                const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
                                uint8_t* codes_t, float4* rowmeta, cudaStream_t s);

@@ -69,45 +69,54 @@ namespace erq {
 namespace tc {
 
 constexpr int MR = 128;          // stored rows per MMA block (MMA M)
-constexpr int QN = 64;           // queries per item (MMA N <= QN)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
 constexpr int RP = 2;            // 128-row blocks per stage (independent accumulators, shared query tile)
 constexpr int SA = 3;            // expanded code stages (tensor memory, RP x 32 columns each)
 constexpr int LS = 4;            // load stages (raw codes + query tile) in flight
 constexpr int MS = 4;            // row-factor buffers (one per row block)
-constexpr int KCAP = 32;         // max k' of the tensor-core path
-constexpr int KC = 64;           // per-query candidate list capacity (list stride of the output)
+constexpr int KCAP = 128;        // max k' of the tensor-core path
 constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
 constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
 constexpr int NFW = 4 + NFX;     // warps that filter candidates
 constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
 constexpr int THREADS = 32 * (MMA2 + 1);
-constexpr int TILE_Q = QN * KB * 2;    // 8 KB
 constexpr int TILE_RAW = RP * MR * KB; // 16 KB of u8 codes (TMA staging)
-constexpr int ACOL = 2 * RP * QN;  // first TMEM column of the expanded-code stages
 constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + SA x RP x 32 columns of codes
-static_assert(ACOL + SA * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
 
-struct Smem {
-    // offsets in bytes from a 1024-aligned base
-    static constexpr int q = 0;                                    // LS  x [64 queries][64] FP16, swizzled
-    static constexpr int raw = q + LS * TILE_Q;                    // LS  x RP x [128 rows][64] u8, 64B-swizzled
-    static constexpr int est = raw + LS * TILE_RAW;                // 2 x [QN][MR] f32  g + (f_res/2) acc
-    static constexpr int lists = est + 2 * QN * MR * 4;            // [QN][KC] u64 candidate keys
-    static constexpr int meta = lists + QN * KC * 8;               // MS x [MR] float4 {g, f_res/2, id, 0}
-    static constexpr int iq = meta + MS * MR * 16;                 // 2 x [QN] int4 {query row, dqc, slot lo, hi}
-    static constexpr int idesc = iq + 2 * QN * 16;                 // 2 x int4 {rb0 lo, rb0 hi, rows, queries}
-    static constexpr int ids = idesc + 2 * 16;                     // 2 x [MR] u32 ids of the row block
-    static constexpr int cnt = ids + 2 * MR * 4;                   // [QN] int   list fill
-    static constexpr int tau = cnt + QN * 4;                       // [QN] u64   admission threshold
-    static constexpr int tq = tau + QN * 8;                        // 2 x [QN] u64 query-wide threshold at item start
-    static constexpr int bars = tq + 2 * QN * 8;                   // mbarriers (8 B each)
-    static constexpr int nbars = 3 * LS + 2 * SA + 4 + 2 * MS + 4 + 1;
-    static constexpr int tmem_slot = bars + nbars * 8;
-    static constexpr int abort_flag = tmem_slot + 4;
-    static constexpr int total = abort_flag + 4 + 1024;            // + alignment slack
+// Two configurations: up to 64 queries per item with 64-entry candidate lists
+// (k' <= 32), or up to 32 queries per item with 160-entry lists (k' <= 128).
+template <int QN_, int KC_>
+struct Cfg {
+    static constexpr int QN = QN_;                 // queries per item (MMA N <= QN)
+    static constexpr int KC = KC_;                 // per-query list capacity (list stride of the output)
+    static constexpr int KS = KC_ <= 64 ? 64 : 256;   // sort width of a list compaction
+    static constexpr int TILE_Q = QN * KB * 2;
+    static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
+    static_assert(ACOL + SA * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
+    static_assert(QN % (4 * NG) == 0 && QN % NFW == 0 && QN <= 64, "query tile split");
+    struct Smem {
+        // offsets in bytes from a 1024-aligned base
+        static constexpr int q = 0;                                // LS  x [QN queries][64] FP16, swizzled
+        static constexpr int raw = q + LS * TILE_Q;                // LS  x RP x [128 rows][64] u8, 64B-swizzled
+        static constexpr int est = raw + LS * TILE_RAW;            // 2 x [QN][MR] f32  g + (f_res/2) acc
+        static constexpr int lists = est + 2 * QN * MR * 4;        // [QN][KC] u64 candidate keys
+        static constexpr int meta = lists + QN * KC * 8;           // MS x [MR] float4 {g, f_res/2, id, 0}
+        static constexpr int iq = meta + MS * MR * 16;             // 2 x [QN] int4 {query row, dqc, slot lo, hi}
+        static constexpr int idesc = iq + 2 * QN * 16;             // 2 x int4 {rb0 lo, rb0 hi, rows, queries}
+        static constexpr int ids = idesc + 2 * 16;                 // 2 x [MR] u32 ids of the row block
+        static constexpr int cnt = ids + 2 * MR * 4;               // [QN] int   list fill
+        static constexpr int tau = cnt + QN * 4;                   // [QN] u64   admission threshold
+        static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
+        static constexpr int bars = tq + 2 * QN * 8;               // mbarriers (8 B each)
+        static constexpr int nbars = 3 * LS + 2 * SA + 4 + 2 * MS + 4 + 1;
+        static constexpr int tmem_slot = bars + nbars * 8;
+        static constexpr int abort_flag = tmem_slot + 4;
+        static constexpr int total = abort_flag + 4 + 1024;        // + alignment slack
+    };
+    static_assert(Smem::total <= 227 * 1024, "scan_tc shared memory");
 };
-static_assert(Smem::total <= 227 * 1024, "scan_tc shared memory");
+using CfgSmall = Cfg<64, 64>;     // k' <= 32
+using CfgLarge = Cfg<32, 160>;    // k' <= 128
 
 // 16 u8 codes -> 16 FP16 values 2u - off, exact: 1024 + u is exact in FP16
 // (byte u as mantissa of 0x6400), fma(1024 + u, 2, -2048) = 2u is exact, and
@@ -162,22 +171,24 @@ __device__ __forceinline__ uint64_t shfl_u64(uint64_t x, int src) {
     return ((uint64_t)hi << 32) | lo;
 }
 
-// Ascending warp bitonic sort of 64 keys held as element e = i*32 + lane in v[i].
-__device__ __forceinline__ void warp_sort64(uint64_t (&v)[2], int lane) {
+// Ascending warp bitonic sort of N (a power of two >= 64) keys held as element
+// e = i*32 + lane in v[i].
+template <int N>
+__device__ __forceinline__ void warp_sort(uint64_t (&v)[N / 32], int lane) {
 #pragma unroll
-    for (int size = 2; size <= 64; size <<= 1) {
+    for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
         for (int d = size >> 1; d > 0; d >>= 1) {
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < N / 32; ++i) {
                 const int e = i * 32 + lane;
-                const bool asc = (e & size) == 0 || size == 64;
-                if (d == 32) {                     // partner in the other register of this lane
-                    if (i == 0) {
-                        const uint64_t a = v[0], b = v[1];
-                        const bool a_lo = asc;     // e < e ^ 32 here
-                        v[0] = (a < b) == a_lo ? a : b;
-                        v[1] = (a < b) == a_lo ? b : a;
+                const bool asc = (e & size) == 0 || size == N;
+                if (d >= 32) {                     // partner in another register of this lane
+                    const int j = i ^ (d / 32);
+                    if (j > i) {
+                        const uint64_t x = v[i], y = v[j];
+                        v[i] = (x < y) == asc ? x : y;
+                        v[j] = (x < y) == asc ? y : x;
                     }
                 } else {
                     const uint64_t p = shfl_xor_u64(v[i], d);
@@ -190,28 +201,33 @@ __device__ __forceinline__ void warp_sort64(uint64_t (&v)[2], int lane) {
     }
 }
 
-// Keep the kp smallest keys of one query's list (cnt <= KC entries) in its
+// Keep the kp smallest keys of one query's list (cnt <= KS entries) in its
 // first kp slots, sorted; returns the new admission threshold (the kp-th key).
+template <int KS>
 __device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, int lane) {
-    uint64_t v[2];
+    uint64_t v[KS / 32];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < KS / 32; ++i) {
         const int e = i * 32 + lane;
         v[i] = e < cnt ? list[e] : kEmptyKey;
     }
-    warp_sort64(v, lane);
+    warp_sort<KS>(v, lane);
+    uint64_t th = kEmptyKey;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < KS / 32; ++i) {
         const int e = i * 32 + lane;
         if (e < kp) list[e] = v[i];
+        const uint64_t t = shfl_u64(v[i], (kp - 1) & 31);
+        if (i == (kp - 1) / 32) th = t;
     }
-    const int t = kp - 1;
-    const uint64_t th = shfl_u64(t >= 32 ? v[1] : v[0], t & 31);
     __syncwarp();
     return th;
 }
 
+template <class C>
 __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
+    constexpr int QN = C::QN, KC = C::KC, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
+    using Smem = typename C::Smem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars);
@@ -278,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         if (item < nitems) {
             dcur = a.itemd[item];
             q0 = a.itemq[item * QN + lane];
-            q1 = a.itemq[item * QN + 32 + lane];
+            if (QN > 32) q1 = a.itemq[item * QN + 32 + lane];
         }
         const uint64_t pol_codes = l2_evict_first();
         for (; item < nitems && ok; item += gridDim.x, ++li) {
@@ -288,16 +304,18 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             if (nxt < nitems) {
                 dn = a.itemd[nxt];
                 n0 = a.itemq[nxt * QN + lane];
-                n1 = a.itemq[nxt * QN + 32 + lane];
+                if (QN > 32) n1 = a.itemq[nxt * QN + 32 + lane];
             }
             const int ib = li & 1;
             if (!mbar_wait_warp(empty_item0 + 8 * ib, ((li >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
             int4* iq = s_iq + ib * QN;
-            iq[lane] = q0;
-            iq[32 + lane] = q1;
             unsigned long long* tqs = reinterpret_cast<unsigned long long*>(sm + Smem::tq) + ib * QN;
+            iq[lane] = q0;
             tqs[lane] = q0.x >= 0 ? __ldcg(a.tq + q0.x) : kEmptyKey;
-            tqs[32 + lane] = q1.x >= 0 ? __ldcg(a.tq + q1.x) : kEmptyKey;
+            if (QN > 32) {
+                iq[32 + lane] = q1;
+                tqs[32 + lane] = q1.x >= 0 ? __ldcg(a.tq + q1.x) : kEmptyKey;
+            }
             if (lane == 0) s_idesc[ib] = dcur;
             mbar_arrive(full_item0 + 8 * ib);
             __syncwarp();
@@ -565,7 +583,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                         cnt += __popc(msk);
                         __syncwarp();
                         if (cnt > KC - 32) {
-                            tau = compact_list(lists + q * KC, cnt, kp, lane);
+                            tau = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
                             tf = key_value(tau);
                             cnt = kp;
                         }
@@ -581,7 +599,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             for (int q = fw; q < nqi; q += NFW) {               // write this warp's lists
                 int cnt = s_cnt[q];
                 if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
-                    const uint64_t th = compact_list(lists + q * KC, cnt, kp, lane);
+                    const uint64_t th = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
                     cnt = kp;
                     if (lane == 0) atomicMin(a.tq + iq[q].x, (unsigned long long)th);
                 }
@@ -607,8 +625,13 @@ bool tc_available(int precision, int D, int kp) {
     return precision == ERQ_PREC_FP16 && D % KB == 0 && kp <= KCAP;
 }
 
+// Queries per work item of the tensor-core scan for this k'.
+int scan_tc_queries_per_item(int kp) { return kp <= 32 ? CfgSmall::QN : CfgLarge::QN; }
+
 // Capacity (stride) of the per-(query, item) candidate lists written by the scan.
-int scan_list_stride(int precision, int kp) { return precision == ERQ_PREC_FP32 ? kp : KC; }
+int scan_list_stride(int precision, int kp) {
+    return precision == ERQ_PREC_FP32 ? kp : (kp <= 32 ? CfgSmall::KC : CfgLarge::KC);
+}
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
 
@@ -619,8 +642,9 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
                                    const int64_t* __restrict__ list_off, const int64_t* __restrict__ poff,
                                    const int64_t* __restrict__ qoff, const int64_t* __restrict__ qlist,
                                    const float* __restrict__ dqc, const int64_t* __restrict__ qbase,
-                                   const int32_t* __restrict__ slot_off, int maxp, int RR, int4* __restrict__ itemd,
-                                   int4* __restrict__ itemq, unsigned long long* __restrict__ stats) {
+                                   const int32_t* __restrict__ slot_off, int maxp, int RR, int QN,
+                                   int4* __restrict__ itemd, int4* __restrict__ itemq,
+                                   unsigned long long* __restrict__ stats) {
     const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (it >= *n_items) return;
@@ -652,12 +676,12 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
 
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
-                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int4* itemd,
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
                                int4* itemq, unsigned long long* stats, cudaStream_t s) {
     if (items_bound <= 0) return cudaSuccess;
     count_launch();
     item_tables_kernel<<<(unsigned)ceil_div(items_bound, 8), 256, 0, s>>>(
-        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, itemd, itemq, stats);
+        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, qn, itemd, itemq, stats);
     return cudaGetLastError();
 }
 
@@ -725,17 +749,10 @@ static bool make_codes_map(CUtensorMap* map, const uint8_t* codes_t, int64_t Np,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
-    if (!tc_available(precision, L.D, L.kp))
-        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 32");
-    if (!L.Qh) return fail(ERQ_EINVAL, "tensor-core scan: FP16 queries missing");
-    if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
-    tc::Args a;
-    a.Qh = (const __half*)L.Qh; a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
-    a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
-    a.tq = L.tq;
-    const int smem = Smem::total;
-    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <class C>
+static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStream_t s) {
+    const int smem = C::Smem::total;
+    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
     CUtensorMap map;
@@ -743,10 +760,22 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
         !make_codes_map(&map, L.codes_t, L.Np, L.D))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     count_launch();
-    scan_tc_kernel<<<L.grid, THREADS, smem, s>>>(map, a);
+    scan_tc_kernel<C><<<L.grid, THREADS, smem, s>>>(map, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc launch");
     return ERQ_OK;
+}
+
+erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
+    if (!tc_available(precision, L.D, L.kp))
+        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 128");
+    if (!L.Qh) return fail(ERQ_EINVAL, "tensor-core scan: FP16 queries missing");
+    if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
+    tc::Args a;
+    a.Qh = (const __half*)L.Qh; a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
+    a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
+    a.tq = L.tq;
+    return L.kp <= 32 ? scan_tc_launch<CfgSmall>(L, a, s) : scan_tc_launch<CfgLarge>(L, a, s);
 }
 
 // FP32 -> FP16 (round to nearest) of the rotated queries.

@@ -225,7 +225,7 @@ class Index:
         _check(lib().erq_search_stats(self._h, out, 6))
         return dict(zip(("pairs", "rows", "items", "lists", "blocks", "slot_blocks"), list(out)))
 
-    def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32"):
+    def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32", async_mode=False):
         """Search from host memory (pinned for asynchronous copies); returns host tensors."""
         if Q_host.is_cuda or Q_host.dtype != torch.float32:
             raise TypeError("Q_host must be a CPU float32 tensor")
@@ -233,6 +233,7 @@ class Index:
         nq = Q_host.shape[0]
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        sp.flags = 4 if async_mode else 0
         pin = Q_host.is_pinned()
         ids = torch.empty((nq, k), dtype=torch.int64, pin_memory=pin)
         dists = torch.empty((nq, k), dtype=torch.float32, pin_memory=pin)

@@ -36,12 +36,15 @@ def _bound(ox, Q, ids):
     return 0.5 * np.abs(f_res[rows]).astype(np.float64) * s * 2.0 ** -11
 
 
-@pytest.mark.parametrize("D,B,nq", [(128, 5, 1500), (64, 3, 400), (960, 7, 300)])
-def test_tc_scan_within_fp16_bound(erq, D, B, nq):
+@pytest.mark.parametrize("D,B,nq,kp", [(128, 5, 1500, 32), (64, 3, 400, 32), (960, 7, 300, 32), (128, 5, 600, 100),
+                                       (64, 4, 300, 128)])
+def test_tc_scan_within_fp16_bound(erq, D, B, nq, kp):
+    """k' <= 32 runs the 64-query / 64-entry-list configuration of the scan,
+    larger k' the 32-query / 160-entry-list one."""
     X, P, gx, ox = _index(erq, 20000, D, B, 64, 3000 + D + B)
     Q, _ = S.mixture(nq, D, 16, 3100 + D, comp_seed=3000 + D + B, scale="aniso")
     probe = S.random_probe_lists(nq, 64, 8, 3200 + D)
-    k, kp = 10, 32
+    k = 10
     ids, dists, cids, cest = gx.search(to_dev(Q), k, rerank_k=kp, probe=to_dev(probe), nprobe=8,
                                        precision="fp16", return_candidates=True)
     torch.cuda.synchronize()
@@ -98,4 +101,4 @@ def test_tc_rejects_large_k(erq):
     X, P, gx, ox = _index(erq, 3000, 64, 4, 8, 3400)
     Q = to_dev(S.mixture(4, 64, 16, 3401, comp_seed=3400, scale="aniso")[0])
     with pytest.raises(erq.ErqError, match="tensor-core"):
-        gx.search(Q, 10, rerank_k=33, nprobe=2, precision="fp16")
+        gx.search(Q, 10, rerank_k=129, nprobe=2, precision="fp16")
