@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="erq", choices=["erq", "reference"])
     ap.add_argument("--workload", default="ivf_n1m_d960_nlist4096")
-    ap.add_argument("--B", type=int, default=5)
+    ap.add_argument("--B", type=int, default=0, help="bits per coordinate (0 = the workload's)")
     ap.add_argument("--precision", default="auto", help="fp32 | fp16 | fp8 | auto (best meeting recall)")
     ap.add_argument("--nprobe", type=int, default=0, help="0 = smallest meeting the recall target")
     ap.add_argument("--rerank-k", type=int, default=20)
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--nq", type=int, default=0, help="override the query count")
     ap.add_argument("--nlist", type=int, default=0, help="override the IVF cluster count")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic scan work-item shape")
     ap.add_argument("--sync", action="store_true",
                     help="size work buffers from a host read-back of the plan (default: host-side bounds, no "
                          "synchronisation inside a search)")
@@ -67,11 +68,13 @@ def make_workload(args, rank=0):
     n = args.n or int(cfg["n"] * args.scale)
     nq = args.nq or int(cfg["nq"] * args.scale)
     d = cfg["d"]
-    X, _ = S.mixture(n, d, cfg["n_comp"], cfg["data_seed"], scale=cfg.get("scale", "unit"),
-                     normalize=cfg.get("normalize", False))
+    w = S.zipf_weights(cfg["n_comp"], cfg["zipf_s"]) if "zipf_s" in cfg else None
+    X, labels = S.mixture(n, d, cfg["n_comp"], cfg["data_seed"], scale=cfg.get("scale", "unit"),
+                          normalize=cfg.get("normalize", False), weights=w)
     Q, _ = S.mixture(nq, d, cfg["n_comp"], cfg["query_seed"] + 1000 * rank, comp_seed=cfg["data_seed"],
-                     scale=cfg.get("scale", "unit"), normalize=cfg.get("normalize", False))
+                     scale=cfg.get("scale", "unit"), normalize=cfg.get("normalize", False), weights=w)
     P = S.random_orthogonal(d, cfg["p_seed"])
+    cfg["labels"] = labels
     return cfg, X, Q, P
 
 
@@ -79,6 +82,8 @@ def ivf_assign(cfg, X, args, device):
     nlist = cfg["nlist"]
     if nlist == 1:
         return np.zeros(len(X), np.int32)
+    if "zipf_s" in cfg and nlist == cfg["n_comp"]:
+        return cfg["labels"].astype(np.int32)          # IVF cluster = generating component
     sample = min(len(X), cfg.get("kmeans_sample", 262_144))
     return S.kmeans_assign_torch(X, nlist, cfg.get("kmeans_iters", 10), 17, sample=sample, device=device)
 
@@ -212,6 +217,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg, X, Q, P = make_workload(args)
+    args.B = args.B or cfg["B"]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     assign = ivf_assign(cfg, X, args, dev)
     nprobe = args.nprobe or 32
@@ -235,10 +241,81 @@ def run_reference(args):
     return 0
 
 
+def run_backward(args):
+    """Backward workload: gradient of the top-k' estimated scores of a query
+    batch with respect to the queries (erq_search_backward), one step = one
+    backward call for the whole batch."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2409_09913_gb300 import build as erq_build
+    erq_build.build()
+    from paper_2409_09913_gb300 import erq
+    cfg, X, Q, P = make_workload(args)
+    args.B = args.B or cfg["B"]
+    assign = ivf_assign(cfg, X, args, dev)
+    Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    ix = erq.build_index(Xd, torch.from_numpy(P).to(dev), args.B, cfg["nlist"],
+                         assign=torch.from_numpy(assign).to(dev))
+    kc = cfg["k"]
+    nprobe = args.nprobe or cfg["nprobe"]
+    ids, est = ix.search(Qd, kc, rerank_k=0, nprobe=nprobe, precision=args.precision if args.precision != "auto"
+                         else "fp16")
+    gs = torch.from_numpy(S.rng(cfg["grad_seed"]).standard_normal((len(Q), kc)).astype(np.float32)).to(dev)
+    out = torch.empty_like(Qd)
+
+    def step():
+        erq._check(erq.lib().erq_search_backward(ix.handle, erq._ptr(Qd), len(Q), kc, erq._ptr(ids), erq._ptr(gs),
+                                                 erq._ptr(out), erq._stream()))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = erq.kernel_launches()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = erq.kernel_launches() - launches0
+    ix.status()
+    # end to end: queries and upstream gradients from pinned host memory, gradient back
+    Qh, gh = torch.from_numpy(Q).pin_memory(), gs.cpu().pin_memory()
+    outh = torch.empty_like(Qh).pin_memory()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        Qd.copy_(Qh, non_blocking=True)
+        gs.copy_(gh, non_blocking=True)
+        step()
+        outh.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / args.steps
+    D = cfg["d"]
+    flops = 2.0 * len(Q) * D * D * 3 + 4.0 * len(Q) * kc * D      # GEMM (3 split-FP16 passes) + gather
+    line = {"metric": "backward queries/s (d top-k' estimated scores / d queries)", "value": len(Q) / (ms / 1e3),
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": len(X), "D": D, "B": args.B, "nlist": cfg["nlist"],
+                       "nq": len(Q), "k_scores": kc, "nprobe": nprobe},
+            "achieved_tflops": flops / (ms / 1e3) / 1e12,
+            "e2e": {"value": len(Q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes + gs.numel() * 4),
+                    "d2h_bytes_per_step": int(Q.nbytes)},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("backward"):
+        return run_backward(args)
     import torch
     import torch.distributed as dist
 
@@ -255,6 +332,7 @@ def main():
 
     t0 = time.perf_counter()
     cfg, X, Q, P = make_workload(args, rank)
+    args.B = args.B or cfg["B"]
     assign = ivf_assign(cfg, X, args, dev)
     t_data = time.perf_counter() - t0
     Xd = torch.from_numpy(X).to(dev)
@@ -269,27 +347,35 @@ def main():
     # exact ground truth (FP32 GEMM, measurement helper only)
     torch.backends.cuda.matmul.allow_tf32 = False
     xn = (Xd * Xd).sum(1)
-    gt = torch.empty((len(Q), args.k), dtype=torch.int64, device=dev)
+    RK = 10                                   # recall@10
+    gt = torch.empty((len(Q), RK), dtype=torch.int64, device=dev)
     for s0 in range(0, len(Q), 1024):
         q = Qd[s0:s0 + 1024]
         best_d = best_i = None
         for x0 in range(0, len(X), 1 << 18):
             d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
-            v, i = torch.topk(d, args.k, dim=1, largest=False)
+            v, i = torch.topk(d, RK, dim=1, largest=False)
             i = i + x0
             if best_d is None:
                 best_d, best_i = v, i
             else:
                 cat_d, cat_i = torch.cat([best_d, v], 1), torch.cat([best_i, i], 1)
-                best_d, j = torch.topk(cat_d, args.k, dim=1, largest=False)
+                best_d, j = torch.topk(cat_d, RK, dim=1, largest=False)
                 best_i = torch.gather(cat_i, 1, j)
         gt[s0:s0 + len(q)] = best_i
     gt_np = gt.cpu().numpy()
     del xn
 
     def recall(ids):
-        ids = ids.cpu().numpy()
-        return float(np.mean([len(set(a) & set(b)) / args.k for a, b in zip(ids, gt_np)]))
+        ids = ids[:, :RK].cpu().numpy()
+        return float(np.mean([len(set(a) & set(b)) / RK for a, b in zip(ids, gt_np)]))
+
+    # per-query nprobe (Zipf workload: uniform in [nprobe_lo, nprobe_hi], seeded)
+    npr_d = None
+    if "nprobe_lo" in cfg and not args.nprobe:
+        npr = S.rng(cfg["nprobe_seed"]).integers(cfg["nprobe_lo"], cfg["nprobe_hi"] + 1, size=len(Q))
+        npr_d = torch.from_numpy(npr.astype(np.int32)).to(dev)
+        cfg["nprobes"] = (cfg["nprobe_hi"],)
 
     kp = max(args.k, args.rerank_k)
     precisions = ["fp32", "fp16", "fp8"] if args.precision == "auto" else [args.precision]
@@ -298,7 +384,8 @@ def main():
     for prec in precisions:
         for p in ([args.nprobe] if args.nprobe else cfg.get("nprobes", (16, 32, 64, 128, 256))):
             try:
-                ids, _ = ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec)
+                ids, _ = ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
+                                   nprobe_per_query=npr_d)
             except erq.ErqError as e:
                 sweep[prec] = f"unavailable: {e}"
                 break
@@ -310,10 +397,14 @@ def main():
                 break
 
     results = {}
+    shapes = {}
     for prec, p in chosen.items():
+        if prec != "fp32" and not args.no_autotune:     # scan work-item shape, timed on this batch
+            shapes[prec] = ix.autotune(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
+                                       nprobe_per_query=npr_d, reps=3)
         def step():
             ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True,
-                      async_mode=not args.sync)
+                      async_mode=not args.sync, nprobe_per_query=npr_d)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -343,7 +434,8 @@ def main():
         phases = {kk: v / max(cnt, 1) for kk, v in tot.items()}
         work = ix.stats()
         results[prec] = dict(nprobe=p, ms=ms, qps=len(Q) * world / (ms / 1e3), recall=sweep[prec][p],
-                             phases=phases, work=work, clocks=clk.summary(), launches=launches)
+                             phases=phases, work=work, clocks=clk.summary(), launches=launches,
+                             shape=ix.scan_config(), tuned=prec in shapes)
 
     if not results:
         if rank == 0:
@@ -357,17 +449,72 @@ def main():
     Qh = torch.from_numpy(Q).pin_memory()
     for _ in range(max(1, args.warmup)):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                       async_mode=not args.sync)
+                       async_mode=not args.sync, nprobe_per_query=npr_d)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(args.steps):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                       async_mode=not args.sync)
+                       async_mode=not args.sync, nprobe_per_query=npr_d)
     e2e_s = (time.perf_counter() - te) / args.steps
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+
+    # the same search recorded once into a CUDA graph and replayed (queries in a
+    # static buffer; every replay runs the whole path without host work)
+    graph = None
+    try:
+        static_q = Qd.clone()
+        sg = torch.cuda.Stream()
+        sg.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(sg):
+            ix.search(static_q, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
+                      async_mode=True, nprobe_per_query=npr_d)
+        torch.cuda.current_stream().wait_stream(sg)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            g_ids, _ = ix.search(static_q, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
+                                 async_mode=True, nprobe_per_query=npr_d)
+        for _ in range(args.warmup):
+            cg.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            cg.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / args.steps
+        graph = {"value": len(Q) * world / (gms / 1e3), "unit": "queries/s", "ms_per_step": gms,
+                 "recall@10": recall(g_ids)}
+        del cg
+    except Exception as ex:                      # report, do not hide, a capture failure
+        graph = {"error": str(ex)[:200]}
+
+    # index-time kernels on a sample: exact rotation (FP64 accumulation) and the
+    # Algorithm 1 encoder, rows per second
+    idx = None
+    try:
+        ns = min(len(X), 262_144)
+        Xs = Xd[:ns].contiguous()
+        Pd = torch.from_numpy(P).to(dev)
+        Rs = erq.rotate(Xs, Pd, accurate=True)
+        erq.encode(Rs, args.B)
+        torch.cuda.synchronize()
+        t_r = time.perf_counter()
+        Rs = erq.rotate(Xs, Pd, accurate=True)
+        torch.cuda.synchronize()
+        t_e = time.perf_counter()
+        erq.encode(Rs, args.B)
+        torch.cuda.synchronize()
+        t_f = time.perf_counter()
+        idx = {"rows": ns, "rotate_rows_per_s": ns / (t_e - t_r), "encode_rows_per_s": ns / (t_f - t_e),
+               "encode_critical_values_per_s": ns * cfg["d"] * (2 ** (args.B - 1) - 1) / (t_f - t_e),
+               "build_index_s": t_build}
+        del Xs, Rs
+    except Exception as ex:
+        idx = {"error": str(ex)[:200]}
 
     # roofline of the dominant kernel (the code scan)
     peaks = measured_peaks()
@@ -409,16 +556,22 @@ def main():
             "warmup": args.warmup, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[best], "data": "synthetic",
             "config": {"workload": args.workload, "N": len(X), "D": cfg["d"], "nlist": cfg["nlist"], "B": args.B,
-                       "nq": len(Q), "k": args.k, "rerank_k": kp, "nprobe": R["nprobe"], "precision": best,
+                       "nq": len(Q), "k": args.k, "rerank_k": kp, "precision": best,
+                       "nprobe": ("per query U{%d..%d}" % (cfg["nprobe_lo"], cfg["nprobe_hi"])) if npr_d is not None
+                       else R["nprobe"],
                        "recall@10": R["recall"], "l2": "inputs larger than L2 (codes > 129 MB)"},
             "gcodes_per_s": R["work"]["pairs"] / (R["ms"] / 1e3) / 1e9,
             "arms": {k: {"qps": v["qps"], "nprobe": v["nprobe"], "recall@10": v["recall"], "ms": v["ms"],
-                         "phases_ms": v["phases"], "pairs": v["work"]["pairs"]} for k, v in results.items()},
+                         "phases_ms": v["phases"], "pairs": v["work"]["pairs"],
+                         "scan_shape": {"queries_per_item": v["shape"][0], "rows_per_item": v["shape"][1],
+                                        "autotuned": v["tuned"]}} for k, v in results.items()},
             "recall_sweep": sweep,
             "roofline": roof,
             "e2e": {"value": len(Q) * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
                     "d2h_bytes_per_step": int(len(Q) * args.k * 12)},
             "gpu_launches": R["launches"],
+            "graph": graph,
+            "index_path": idx,
             "clocks": R["clocks"],
             "cpu_baseline": cpu,
             "build_s": t_build, "data_s": t_data,

@@ -433,6 +433,29 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
 // ---------------------------------------------------------------------------
 // Search
 // ---------------------------------------------------------------------------
+// Work-item shape of the scan: queries per item (the tensor-core MMA's N
+// extent) and rows per item.  Heuristic: wide items when clusters are probed by
+// many queries on average (nq * nprobe / nlist > 96).
+static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq, int maxp, int* qn, int* rr) {
+    if (prec == ERQ_PREC_FP32) {
+        *qn = 64;
+        *rr = ix->force_rr > 0 ? ix->force_rr : 4096;
+        return;
+    }
+    const int cls = kp <= 32 ? 0 : 1;
+    const int64_t work = nq * (int64_t)maxp;
+    int q = cls == 0 ? ((double)work / ix->nlist > 96.0 ? 128 : 64) : 32, r = 4096;
+    const erq_index::ScanTune& t = ix->tune[cls];
+    if (t.valid && work <= 4 * t.work && 4 * work >= t.work) {
+        q = t.qn;
+        r = t.rr;
+    }
+    if (ix->force_qn > 0 && scan_tc_shape_ok(ix->force_qn, kp)) q = ix->force_qn;
+    if (ix->force_rr > 0) r = ix->force_rr;
+    *qn = q;
+    *rr = r;
+}
+
 static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p, int64_t* ids,
                               float* dists, cudaStream_t s) {
     const int D = ix->D, nlist = ix->nlist;
@@ -444,8 +467,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     const int prec = p->precision;
     // ---- phase A workspace (sizes known on the host)
     // queries per work item of the scan kernels
-    const int QT = prec == ERQ_PREC_FP32 ? 64 : scan_tc_queries_per_item(kp);
-    int RR = 4096;
+    int QT = 64, RR = 4096;
+    choose_scan_shape(ix, prec, kp, nq, maxp, &QT, &RR);
+    ix->last_qn = QT;
+    ix->last_rr = RR;
     Carver plan(nullptr, 0);
     auto layout = [&](Carver& cv, bool carve, void** slots) {
         int i = 0;
@@ -608,7 +633,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     // ---- phase B workspace
     Carver pb(nullptr, 0);
     pb.take<int4>(nitems);
-    const int lstride = scan_list_stride(prec, kp);
+    const int lstride = scan_list_stride(prec, kp, QT);
     pb.take<uint64_t>((size_t)Ltot * lstride);
     pb.take<int32_t>(Ltot);
     pb.take<int64_t>(1);
@@ -638,7 +663,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.Qrot = Qrot; L.Qh = sl[20]; L.status = ix->status; L.N = ix->N; L.codes = ix->codes; L.g_const = ix->g_const; L.f_res = ix->f_res; L.list_off = ix->list_off;
     L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
     L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
-    L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR;
+    L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
     L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_t = ix->codes_t; L.Np = ix->Np;
     L.tq = (unsigned long long*)sl[22];
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
@@ -905,6 +930,93 @@ extern "C" erq_status erq_search_timing_total(erq_index* ix, float* ms, int32_t 
     *count = ix->timing_seq - first;
     ix->timing_base = ix->timing_seq;
     return ERQ_OK;
+}
+
+extern "C" erq_status erq_set_scan_config(erq_index* ix, int32_t queries_per_item, int32_t rows_per_item) {
+    if (!ix) return fail(ERQ_EINVAL, "erq_set_scan_config: null index");
+    if (queries_per_item != 0 && queries_per_item != 32 && queries_per_item != 64 && queries_per_item != 128)
+        return fail(ERQ_EINVAL, "erq_set_scan_config: queries_per_item must be 0, 32, 64 or 128");
+    if (rows_per_item != 0 && (rows_per_item < 256 || rows_per_item % 256 != 0 || rows_per_item > (1 << 20)))
+        return fail(ERQ_EINVAL, "erq_set_scan_config: rows_per_item must be 0 or a multiple of 256 in [256, 2^20]");
+    ix->force_qn = queries_per_item;
+    ix->force_rr = rows_per_item;
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_scan_config(const erq_index* ix, int32_t* out, int32_t n) {
+    if (!ix || !out || n < 2) return fail(ERQ_EINVAL, "erq_scan_config: bad arguments");
+    out[0] = ix->last_qn;
+    out[1] = ix->last_rr;
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_autotune(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p,
+                                   int32_t reps, void* stream, int32_t* best_out) {
+    ERQ_TRY(validate_search(ix, Q, nq, p, p ? (const void*)p : nullptr, p ? (const void*)p : nullptr));
+    if (nq == 0 || reps < 1) return fail(ERQ_EINVAL, "erq_autotune: nq and reps must be positive");
+    if (p->precision == ERQ_PREC_FP32) return fail(ERQ_EUNSUPPORTED, "erq_autotune: tunes the tensor-core scan");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kp = std::max(p->k, p->rerank_k);
+    const int cls = kp <= 32 ? 0 : 1;
+    const int maxp = p->probe ? p->nprobe : (ix->nlist == 1 ? 1 : p->nprobe);
+    const int qns[3] = {32, 64, 128};
+    const int rrs[3] = {2048, 4096, 8192};
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    erq_status st = ERQ_OK;
+    if (cudaMalloc(&ids, sizeof(int64_t) * nq * p->k) != cudaSuccess ||
+        cudaMalloc(&dists, sizeof(float) * nq * p->k) != cudaSuccess)
+        st = fail(ERQ_ENOMEM, "erq_autotune: cudaMalloc");
+    if (st == ERQ_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(ERQ_ECUDA, "erq_autotune: cudaEventCreate");
+    const int keep_qn = ix->force_qn, keep_rr = ix->force_rr;
+    float best = -1.f;
+    int bq = 0, br = 0;
+    erq_search_params pp = *p;
+    pp.flags &= ~ERQ_SEARCH_TIMING;
+    pp.cand_ids = nullptr;
+    pp.cand_est = nullptr;
+    for (int qi = 0; qi < 3 && st == ERQ_OK; ++qi) {
+        if (!scan_tc_shape_ok(qns[qi], kp)) continue;
+        for (int ri = 0; ri < 3 && st == ERQ_OK; ++ri) {
+            ix->force_qn = qns[qi];
+            ix->force_rr = rrs[ri];
+            if ((st = search_impl(ix, Q, nq, &pp, ids, dists, s)) != ERQ_OK) break;   // warm-up, sizes buffers
+            if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(ERQ_ECUDA, "erq_autotune: event"); break; }
+            for (int r = 0; r < reps && st == ERQ_OK; ++r) st = search_impl(ix, Q, nq, &pp, ids, dists, s);
+            if (st != ERQ_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = fail(ERQ_ECUDA, "erq_autotune: timing");
+                break;
+            }
+            if (best < 0.f || ms < best) {
+                best = ms;
+                bq = qns[qi];
+                br = rrs[ri];
+            }
+        }
+    }
+    ix->force_qn = keep_qn;
+    ix->force_rr = keep_rr;
+    if (st == ERQ_OK) st = check_status(ix, s);
+    if (st == ERQ_OK && best >= 0.f) {
+        ix->tune[cls].valid = 1;
+        ix->tune[cls].work = nq * (int64_t)maxp;
+        ix->tune[cls].qn = bq;
+        ix->tune[cls].rr = br;
+        if (best_out) {
+            best_out[0] = bq;
+            best_out[1] = br;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ids) cudaFree(ids);
+    if (dists) cudaFree(dists);
+    return st;
 }
 
 extern "C" uint64_t erq_kernel_launches(void) { return g_launches.load(); }

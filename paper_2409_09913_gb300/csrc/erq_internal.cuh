@@ -130,6 +130,12 @@ struct erq_index {
     int64_t timing_base = 0;     // first timed search not yet summed by erq_search_timing_total
     int timed = 0;               // 1 when the last search was timed
     int64_t last_stats[4] = {};  // pairs, distinct rows, work items, lists of the last search
+    // scan work-item shape (queries per item qn, rows per item rr): forced by
+    // erq_set_scan_config, else the autotuned entry of the k' class when its
+    // queries x nprobe is within 4x of the search's, else a heuristic
+    int force_qn = 0, force_rr = 0;
+    struct ScanTune { int valid = 0; int64_t work = 0; int qn = 0, rr = 0; } tune[2];
+    int last_qn = 0, last_rr = 0;
     unsigned long long* dstats = nullptr;  // [4] device counters of the last search: pairs, distinct rows,
                                            //     tensor-core row blocks, row blocks x padded queries
     size_t pinned_bytes = 0;

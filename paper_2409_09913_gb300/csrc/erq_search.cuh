@@ -62,6 +62,7 @@ struct ScanLaunch {
     int64_t Np;                 // tensor-core path: padded rows
     unsigned long long* tq;     // tensor-core path: [nq] query-wide thresholds (all ones at the start)
     int maxp, D, B, kp, RR;
+    int qn;                     // tensor-core path: queries per work item (32, 64 or 128)
     int grid;
 };
 
@@ -74,12 +75,12 @@ size_t scan_fp32_smem(int kp);
 int merge_sortn(int kp, int lstride);
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
                          int lstride, uint64_t* cand, cudaStream_t s);
-int scan_list_stride(int precision, int kp);
+int scan_list_stride(int precision, int kp, int qn);
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
                                const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
                                int4* itemq, unsigned long long* stats, cudaStream_t s);
-int scan_tc_queries_per_item(int kp);
+bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
                                const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
                                uint8_t* codes_t, float4* rowmeta, cudaStream_t s);

@@ -70,41 +70,44 @@ namespace tc {
 
 constexpr int MR = 128;          // stored rows per MMA block (MMA M)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int RP = 2;            // 128-row blocks per stage (independent accumulators, shared query tile)
 constexpr int SA = 3;            // expanded code stages (tensor memory, RP x 32 columns each)
-constexpr int LS = 4;            // load stages (raw codes + query tile) in flight
 constexpr int MS = 4;            // row-factor buffers (one per row block)
+constexpr int NMMA = 2;          // MMA issuing warps
 constexpr int KCAP = 128;        // max k' of the tensor-core path
 constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
 constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
 constexpr int NFW = 4 + NFX;     // warps that filter candidates
 constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
 constexpr int THREADS = 32 * (MMA2 + 1);
-constexpr int TILE_RAW = RP * MR * KB; // 16 KB of u8 codes (TMA staging)
 constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + SA x RP x 32 columns of codes
 
-// Two configurations: up to 64 queries per item with 64-entry candidate lists
-// (k' <= 32), or up to 32 queries per item with 160-entry lists (k' <= 128).
-template <int QN_, int KC_>
+// Work-item shapes: QN queries per item (the MMA's N extent), KC-entry
+// candidate lists, RP row blocks per stage, LS load stages, EB estimate tiles.
+template <int QN_, int KC_, int RP_, int LS_, int EB_>
 struct Cfg {
     static constexpr int QN = QN_;                 // queries per item (MMA N <= QN)
     static constexpr int KC = KC_;                 // per-query list capacity (list stride of the output)
+    static constexpr int RP = RP_;                 // 128-row blocks per stage (independent accumulators)
+    static constexpr int LS = LS_;                 // load stages (raw codes + query tile) in flight
+    static constexpr int EB = EB_;                 // estimate tiles (2: filtering overlaps the next block)
     static constexpr int KS = KC_ <= 64 ? 64 : 256;   // sort width of a list compaction
     static constexpr int TILE_Q = QN * KB * 2;
+    static constexpr int TILE_RAW = RP * MR * KB;  // u8 codes of a stage (TMA staging)
     static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
     static_assert(ACOL + SA * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
-    static_assert(QN % (4 * NG) == 0 && QN % NFW == 0 && QN <= 64, "query tile split");
+    static_assert(QN % (4 * NG) == 0 && QN % NFW == 0 && QN % 32 == 0, "query tile split");
+    static_assert(RP >= 1 && RP <= NMMA && (EB == 1 || EB == 2), "stage shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
         static constexpr int q = 0;                                // LS  x [QN queries][64] FP16, swizzled
         static constexpr int raw = q + LS * TILE_Q;                // LS  x RP x [128 rows][64] u8, 64B-swizzled
-        static constexpr int est = raw + LS * TILE_RAW;            // 2 x [QN][MR] f32  g + (f_res/2) acc
-        static constexpr int lists = est + 2 * QN * MR * 4;        // [QN][KC] u64 candidate keys
+        static constexpr int est = raw + LS * TILE_RAW;            // EB x [QN][MR] f32  g + (f_res/2) acc
+        static constexpr int lists = est + EB * QN * MR * 4;       // [QN][KC] u64 candidate keys
         static constexpr int meta = lists + QN * KC * 8;           // MS x [MR] float4 {g, f_res/2, id, 0}
         static constexpr int iq = meta + MS * MR * 16;             // 2 x [QN] int4 {query row, dqc, slot lo, hi}
         static constexpr int idesc = iq + 2 * QN * 16;             // 2 x int4 {rb0 lo, rb0 hi, rows, queries}
-        static constexpr int ids = idesc + 2 * 16;                 // 2 x [MR] u32 ids of the row block
-        static constexpr int cnt = ids + 2 * MR * 4;               // [QN] int   list fill
+        static constexpr int ids = idesc + 2 * 16;                 // EB x [MR] u32 ids of the row block
+        static constexpr int cnt = ids + EB * MR * 4;              // [QN] int   list fill
         static constexpr int tau = cnt + QN * 4;                   // [QN] u64   admission threshold
         static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
         static constexpr int bars = tq + 2 * QN * 8;               // mbarriers (8 B each)
@@ -115,8 +118,9 @@ struct Cfg {
     };
     static_assert(Smem::total <= 227 * 1024, "scan_tc shared memory");
 };
-using CfgSmall = Cfg<64, 64>;     // k' <= 32
-using CfgLarge = Cfg<32, 160>;    // k' <= 128
+using CfgSmall = Cfg<64, 64, 2, 4, 2>;    // k' <= 32, up to 64 queries per item
+using CfgLarge = Cfg<32, 160, 2, 4, 2>;   // k' <= 128, up to 32 queries per item
+using CfgWide = Cfg<128, 64, 1, 3, 1>;    // k' <= 32, up to 128 queries per item (query-heavy lists)
 
 // 16 u8 codes -> 16 FP16 values 2u - off, exact: 1024 + u is exact in FP16
 // (byte u as mantissa of 0x6400), fma(1024 + u, 2, -2048) = 2u is exact, and
@@ -227,6 +231,7 @@ __device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, i
 template <class C>
 __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
     constexpr int QN = C::QN, KC = C::KC, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
+    constexpr int RP = C::RP, LS = C::LS, EB = C::EB, TILE_RAW = C::TILE_RAW;
     using Smem = typename C::Smem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -254,15 +259,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < LS; ++s) {
             mbar_init(full_load0 + 8 * s, 1);      // the TMA expect_tx arrival
-            mbar_init(empty_load0 + 8 * s, RP);    // one MMA commit per issuer
+            mbar_init(empty_load0 + 8 * s, NMMA);  // one MMA commit per issuer
             mbar_init(full_q0 + 8 * s, 32 * NG);   // one cp.async arrival per gatherer lane
         }
         for (int s = 0; s < SA; ++s) {
             mbar_init(full_a0 + 8 * s, 128);
-            mbar_init(empty_a0 + 8 * s, RP);
+            mbar_init(empty_a0 + 8 * s, NMMA);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(tfull0 + 8 * b, RP);
+            mbar_init(tfull0 + 8 * b, NMMA);
             mbar_init(tempty0 + 8 * b, 128);
             mbar_init(full_item0 + 8 * b, 32);
             mbar_init(empty_item0 + 8 * b, 32 * NFW);
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             mbar_init(full_meta0 + 8 * m, 1);
             mbar_init(empty_meta0 + 8 * m, 128);
         }
-        mbar_init(done_bar, RP);
+        mbar_init(done_bar, NMMA);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -290,31 +295,34 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         uint32_t g = 0, rbg = 0, li = 0;
         bool ok = true;
         int64_t item = blockIdx.x;
-        int4 dcur = make_int4(0, 0, 0, 0), q0 = dcur, q1 = dcur;
+        int4 dcur = make_int4(0, 0, 0, 0), qv[QN / 32];
+#pragma unroll
+        for (int j = 0; j < QN / 32; ++j) qv[j] = dcur;
         if (item < nitems) {
             dcur = a.itemd[item];
-            q0 = a.itemq[item * QN + lane];
-            if (QN > 32) q1 = a.itemq[item * QN + 32 + lane];
+#pragma unroll
+            for (int j = 0; j < QN / 32; ++j) qv[j] = a.itemq[item * QN + 32 * j + lane];
         }
         const uint64_t pol_codes = l2_evict_first();
         for (; item < nitems && ok; item += gridDim.x, ++li) {
             // next item's descriptors are fetched while this one streams
             const int64_t nxt = item + gridDim.x;
-            int4 dn = make_int4(0, 0, 0, 0), n0 = dn, n1 = dn;
+            int4 dn = make_int4(0, 0, 0, 0), nv[QN / 32];
+#pragma unroll
+            for (int j = 0; j < QN / 32; ++j) nv[j] = dn;
             if (nxt < nitems) {
                 dn = a.itemd[nxt];
-                n0 = a.itemq[nxt * QN + lane];
-                if (QN > 32) n1 = a.itemq[nxt * QN + 32 + lane];
+#pragma unroll
+                for (int j = 0; j < QN / 32; ++j) nv[j] = a.itemq[nxt * QN + 32 * j + lane];
             }
             const int ib = li & 1;
             if (!mbar_wait_warp(empty_item0 + 8 * ib, ((li >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
             int4* iq = s_iq + ib * QN;
             unsigned long long* tqs = reinterpret_cast<unsigned long long*>(sm + Smem::tq) + ib * QN;
-            iq[lane] = q0;
-            tqs[lane] = q0.x >= 0 ? __ldcg(a.tq + q0.x) : kEmptyKey;
-            if (QN > 32) {
-                iq[32 + lane] = q1;
-                tqs[32 + lane] = q1.x >= 0 ? __ldcg(a.tq + q1.x) : kEmptyKey;
+#pragma unroll
+            for (int j = 0; j < QN / 32; ++j) {
+                iq[32 * j + lane] = qv[j];
+                tqs[32 * j + lane] = qv[j].x >= 0 ? __ldcg(a.tq + qv[j].x) : kEmptyKey;
             }
             if (lane == 0) s_idesc[ib] = dcur;
             mbar_arrive(full_item0 + 8 * ib);
@@ -346,8 +354,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 }
             }
             dcur = dn;
-            q0 = n0;
-            q1 = n1;
+#pragma unroll
+            for (int j = 0; j < QN / 32; ++j) qv[j] = nv[j];
         }
         // drain: every copy this warp issued has landed before the CTA exits
         for (uint32_t k = 0; k < LS && k < g; ++k) {
@@ -535,8 +543,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     if (bb == 0) okp = mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag);
                     okw = okw && okp;
                 }
-                float* est_t = s_est + (blk & 1) * (QN * MR);   // tiles alternate between row blocks
-                uint32_t* ids_t = s_ids + (blk & 1) * MR;
+                float* est_t = s_est + (blk % EB) * (QN * MR);  // tiles alternate between row blocks
+                uint32_t* ids_t = s_ids + (blk % EB) * MR;
                 if (tm && okw) {
                     // phase 1: own 32 rows x all queries -> query-major tile
                     tc_fence_after();
@@ -594,6 +602,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     }
                     __syncwarp();
                 }
+                if (EB == 1) bar_sync(1, 32 * NFW);            // the single tile is free again
             }
             if (stop) break;
             for (int q = fw; q < nqi; q += NFW) {               // write this warp's lists
@@ -625,12 +634,15 @@ bool tc_available(int precision, int D, int kp) {
     return precision == ERQ_PREC_FP16 && D % KB == 0 && kp <= KCAP;
 }
 
-// Queries per work item of the tensor-core scan for this k'.
-int scan_tc_queries_per_item(int kp) { return kp <= 32 ? CfgSmall::QN : CfgLarge::QN; }
+// Work-item query counts the tensor-core scan is built for, given k'.
+bool scan_tc_shape_ok(int qn, int kp) {
+    return (qn == CfgSmall::QN && kp <= 32) || (qn == CfgWide::QN && kp <= 32) || (qn == CfgLarge::QN && kp <= KCAP);
+}
 
 // Capacity (stride) of the per-(query, item) candidate lists written by the scan.
-int scan_list_stride(int precision, int kp) {
-    return precision == ERQ_PREC_FP32 ? kp : (kp <= 32 ? CfgSmall::KC : CfgLarge::KC);
+int scan_list_stride(int precision, int kp, int qn) {
+    if (precision == ERQ_PREC_FP32) return kp;
+    return qn == CfgLarge::QN ? CfgLarge::KC : CfgSmall::KC;   // CfgWide shares CfgSmall's list capacity
 }
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
@@ -775,7 +787,10 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     a.Qh = (const __half*)L.Qh; a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
     a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
     a.tq = L.tq;
-    return L.kp <= 32 ? scan_tc_launch<CfgSmall>(L, a, s) : scan_tc_launch<CfgLarge>(L, a, s);
+    if (!scan_tc_shape_ok(L.qn, L.kp)) return fail(ERQ_EINVAL, "tensor-core scan: no kernel for this item shape");
+    if (L.qn == CfgWide::QN) return scan_tc_launch<CfgWide>(L, a, s);
+    if (L.qn == CfgSmall::QN) return scan_tc_launch<CfgSmall>(L, a, s);
+    return scan_tc_launch<CfgLarge>(L, a, s);
 }
 
 // FP32 -> FP16 (round to nearest) of the rotated queries.

@@ -24,7 +24,8 @@ FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, 
 EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index", "erq_index_info_get",
            "erq_index_status", "erq_rotate", "erq_encode", "erq_search", "erq_search_host", "erq_estimate",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
-           "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total"]
+           "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total",
+           "erq_autotune", "erq_set_scan_config", "erq_scan_config"]
 
 
 class ErqError(RuntimeError):
@@ -82,6 +83,9 @@ def lib(path: str | None = None):
     L.erq_index_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
     L.erq_search_timing.argtypes = [vp, ct.POINTER(ct.c_float), i32]
     L.erq_search_timing_total.argtypes = [vp, ct.POINTER(ct.c_float), i32, ct.POINTER(ct.c_int64)]
+    L.erq_autotune.argtypes = [vp, vp, i64, ct.POINTER(SearchParams), i32, vp, ct.POINTER(i32)]
+    L.erq_set_scan_config.argtypes = [vp, i32, i32]
+    L.erq_scan_config.argtypes = [vp, ct.POINTER(i32), i32]
     L.erq_kernel_launches.argtypes = []
     L.erq_kernel_launches.restype = ct.c_uint64
     L.erq_search_stats.argtypes = [vp, ct.POINTER(ct.c_int64), i32]
@@ -89,7 +93,8 @@ def lib(path: str | None = None):
     for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
                  "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
                  "erq_index_save", "erq_index_load", "erq_search_timing",
-                 "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total"):
+                 "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total", "erq_autotune",
+                 "erq_set_scan_config", "erq_scan_config"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -210,6 +215,29 @@ class Index:
         _check(lib().erq_search_timing(self._h, ms, 6))
         return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms)))
 
+    def autotune(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp16", nprobe_per_query=None, reps=3):
+        """Time every supported scan work-item shape on this query batch and keep
+        the fastest for later searches of this size; returns (queries per item,
+        rows per item)."""
+        Q = _dev(Q, torch.float32, "Q", 2)
+        sp = SearchParams()
+        sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        keep = None
+        if nprobe_per_query is not None:
+            keep = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
+            sp.nprobe_per_query = keep.data_ptr()
+        best = (ct.c_int32 * 2)()
+        _check(lib().erq_autotune(self._h, _ptr(Q), Q.shape[0], ct.byref(sp), int(reps), _stream(), best))
+        return int(best[0]), int(best[1])
+
+    def set_scan_config(self, queries_per_item=0, rows_per_item=0):
+        _check(lib().erq_set_scan_config(self._h, int(queries_per_item), int(rows_per_item)))
+
+    def scan_config(self):
+        out = (ct.c_int32 * 2)()
+        _check(lib().erq_scan_config(self._h, out, 2))
+        return int(out[0]), int(out[1])
+
     def timing_total(self):
         """Per-phase device ms summed over the timed searches since the previous
         call, and how many searches that covers."""
@@ -225,8 +253,10 @@ class Index:
         _check(lib().erq_search_stats(self._h, out, 6))
         return dict(zip(("pairs", "rows", "items", "lists", "blocks", "slot_blocks"), list(out)))
 
-    def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32", async_mode=False):
-        """Search from host memory (pinned for asynchronous copies); returns host tensors."""
+    def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32", async_mode=False,
+                    nprobe_per_query=None):
+        """Search from host memory (pinned for asynchronous copies); returns host tensors.
+        ``nprobe_per_query`` (optional) is a device int32 tensor [nq]."""
         if Q_host.is_cuda or Q_host.dtype != torch.float32:
             raise TypeError("Q_host must be a CPU float32 tensor")
         Q_host = Q_host.contiguous()
@@ -234,6 +264,9 @@ class Index:
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
         sp.flags = 4 if async_mode else 0
+        if nprobe_per_query is not None:
+            nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
+            sp.nprobe_per_query = nprobe_per_query.data_ptr()
         pin = Q_host.is_pinned()
         ids = torch.empty((nq, k), dtype=torch.int64, pin_memory=pin)
         dists = torch.empty((nq, k), dtype=torch.float32, pin_memory=pin)
