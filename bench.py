@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--nlist", type=int, default=0, help="override the IVF cluster count")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic scan work-item shape")
+    ap.add_argument("--scan-shape", default="", help="force the scan work-item shape QN,RR (e.g. 64,8192) instead "
+                                                       "of autotuning (profiling runs)")
     ap.add_argument("--sync", action="store_true",
                     help="size work buffers from a host read-back of the plan (default: host-side bounds, no "
                          "synchronisation inside a search)")
@@ -165,7 +167,7 @@ def scan_source_sha():
     return h.hexdigest()
 
 
-def profiled_traffic(workload, nprobe, precision):
+def profiled_traffic(workload, nprobe, precision, shape):
     """DRAM bytes per launch of the tensor-core scan from the committed ncu
     capture (profiles/scan_tc_traffic_*.txt), only while the kernel source is
     the one that was profiled; None otherwise."""
@@ -180,6 +182,8 @@ def profiled_traffic(workload, nprobe, precision):
                 kv[k.strip()] = v.strip()
     try:
         if kv.get("kernel_source_sha256") != scan_source_sha() or int(kv.get("nprobe", -1)) != nprobe:
+            return None
+        if (int(kv.get("queries_per_item", -1)), int(kv.get("rows_per_item", -1))) != tuple(shape):
             return None
         return float(kv["dram_bytes_per_launch"])
     except (KeyError, ValueError):
@@ -310,10 +314,42 @@ def run_backward(args):
     return 0
 
 
+def run_encoder_sweep(args):
+    """Algorithm 1 throughput at the paper's Table 4 shape (D = 3072, unit-norm
+    embedding-like rows), B = 1..8: one JSON line per B with rows/s on a
+    sample of rotated residuals (the same kernel erq_build_index runs) and the
+    implied time for 10^6 rows."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2409_09913_gb300 import build as erq_build
+    erq_build.build()
+    from paper_2409_09913_gb300 import erq
+    d = 3072
+    n = args.n or 65_536
+    X, _ = S.mixture(n, d, 64, 11, normalize=True)
+    P = torch.from_numpy(S.random_orthogonal(d, 12)).to(dev)
+    Xd = torch.from_numpy(X).to(dev)
+    R = erq.rotate(Xd - Xd.mean(0, keepdim=True), P, accurate=True)
+    for B in range(1, 9):
+        erq.encode(R[:1024], B)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        erq.encode(R, B)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print(json.dumps({"metric": "encoder rows/s (Algorithm 1, D = 3072)", "B": B, "value": n / dt,
+                          "unit": "rows/s", "rows": n, "critical_values_per_s": n * d * (2 ** (B - 1) - 1) / dt,
+                          "seconds_per_1e6_rows": 1e6 * dt / n, "data": "synthetic"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "encoder_table4":
+        return run_encoder_sweep(args)
     if args.workload.startswith("backward"):
         return run_backward(args)
     import torch
@@ -398,8 +434,10 @@ def main():
 
     results = {}
     shapes = {}
+    if args.scan_shape:
+        ix.set_scan_config(*[int(x) for x in args.scan_shape.split(",")])
     for prec, p in chosen.items():
-        if prec != "fp32" and not args.no_autotune:     # scan work-item shape, timed on this batch
+        if prec != "fp32" and not args.no_autotune and not args.scan_shape:   # work-item shape timed on this batch
             shapes[prec] = ix.autotune(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
                                        nprobe_per_query=npr_d, reps=3)
         def step():
@@ -536,7 +574,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": bytes_alg / scan_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (bytes_alg / scan_s / 1e9) / peaks["hbm_gbs"], "traffic": None}
-    roof["traffic"] = profiled_traffic(args.workload, R["nprobe"], best)
+    roof["traffic"] = profiled_traffic(args.workload, R["nprobe"], best, R["shape"])
     roof["bytes_alg_per_launch"] = bytes_alg
     roof["kernel"] = "scan_fp32_kernel" if best == "fp32" else "scan_tc_kernel"
     roof["peak_source"] = peaks["source"] if bound_c != "alu" or roof["bound"] == "hbm" else \
