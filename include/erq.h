@@ -121,7 +121,17 @@ typedef enum {
     ERQ_FIELD_F_ADD = 5,          /* float  [N]         ||o'||^2                           */
     ERQ_FIELD_F_RES = 6,          /* float  [N]         -2 ||o'||^2 / <ybar, |o'|>          */
     ERQ_FIELD_P = 7,              /* float  [D][D]                                         */
-    ERQ_FIELD_RAW = 8             /* float  [N][D] original order (keep_raw only)          */
+    ERQ_FIELD_RAW = 8,            /* float  [N][D] original order (keep_raw only)          */
+    ERQ_FIELD_PACKED_CODES = 9    /* uint8  [Np*D*B/8] the tensor-core scan's packed copy:  */
+                                  /* each cluster padded to a multiple of 32 rows (Np rows  */
+                                  /* in all; padding rows hold code 0), stored as 64-bit    */
+                                  /* words [tile of 32 rows][block of 64 coordinates][B][32]*/
+                                  /* (little-endian).  In block k, for codes u[0..63] of a  */
+                                  /* row, the two 32-bit halves h = 0..7 of words 0-3 hold  */
+                                  /* (B >= 4) byte L = u[8h+L] & 15 | (u[8h+4+L] & 15) << 4, */
+                                  /* and word b (b >= 4, or every b < B when B < 4) is bit  */
+                                  /* plane b: bit 8L + (m & 7) of half m >> 3 is bit b of   */
+                                  /* u[4m + L].  B bits per coordinate exactly.             */
 } erq_field;
 
 const char* erq_version(void);

@@ -59,7 +59,7 @@ void free_index_arrays(erq_index* ix) {
     void* ptrs[] = {ix->PT,    ix->eP,    ix->ePT,     ix->eC,   ix->corder,
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
-                    ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_t,
+                    ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_p,
                     ix->dstats, ix->PT_hi, ix->C_hi};   // PT_lo / C_lo live inside those blocks
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -153,13 +153,15 @@ erq_status derive_gemm_arrays(erq_index* ix, cudaStream_t s) {
             return fail(ERQ_ENOMEM, "cudaMalloc padded offsets");
         ERQ_CHECK_CUDA(cudaMemcpyAsync(ix->poff, po.data(), sizeof(int64_t) * (ix->nlist + 1), cudaMemcpyHostToDevice, s));
         const size_t np = (size_t)std::max<int64_t>(ix->Np, 32);
-        if (!ix->codes_t && cudaMalloc(&ix->codes_t, np * D) != cudaSuccess)
-            return fail(ERQ_ENOMEM, "cudaMalloc tiled codes");
+        const size_t np32 = (np + 31) / 32 * 32;
+        const size_t pbytes = np32 * (size_t)D * ix->B / 8;      // B bits per coordinate
+        if (!ix->codes_p && cudaMalloc(&ix->codes_p, pbytes) != cudaSuccess)
+            return fail(ERQ_ENOMEM, "cudaMalloc packed codes");
         if (!ix->rowmeta && cudaMalloc(&ix->rowmeta, sizeof(float4) * np) != cudaSuccess)
             return fail(ERQ_ENOMEM, "cudaMalloc row factors");
-        ix->device_bytes += (int64_t)(np * D + 16 * np + 8 * (ix->nlist + 1));
+        ix->device_bytes += (int64_t)(pbytes + 16 * np + 8 * (ix->nlist + 1));
         if ((e = launch_scan_layout(ix->codes, ix->g_const, ix->f_res, ix->list_ids, ix->list_off, ix->poff, ix->nlist,
-                                    ix->Np, D, ix->codes_t, ix->rowmeta, s)) != cudaSuccess)
+                                    ix->Np, D, ix->B, ix->codes_p, ix->rowmeta, s)) != cudaSuccess)
             return cuda_fail(e, "scan layout");
         ERQ_CHECK_CUDA(cudaStreamSynchronize(s));   // po (host) goes out of scope
     }
@@ -664,7 +666,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
     L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
     L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
-    L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_t = ix->codes_t; L.Np = ix->Np;
+    L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_p = ix->codes_p; L.Np = ix->Np;
     L.tq = (unsigned long long*)sl[22];
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
     int dev = 0, sms = 148;
@@ -802,6 +804,7 @@ static FieldDesc field_of(const erq_index* ix, int f) {
         case ERQ_FIELD_F_RES: return {ix->f_res, N * 4};
         case ERQ_FIELD_P: return {ix->P, D * D * 4};
         case ERQ_FIELD_RAW: return {ix->keep_raw ? ix->X : nullptr, ix->keep_raw ? N * D * 4 : 0};
+        case ERQ_FIELD_PACKED_CODES: return {ix->codes_p, ix->codes_p ? ix->Np * D * ix->B / 8 : 0};
         default: return {nullptr, 0};
     }
 }

@@ -110,7 +110,7 @@ struct erq_index {
     // tiled as [Np/32 tiles][D/64 K blocks][32 rows][64 bytes]
     int64_t Np = 0;              // padded rows
     int64_t* poff = nullptr;     // [nlist+1] padded list offsets
-    uint8_t* codes_t = nullptr;  // [Np * D] tiled codes
+    uint64_t* codes_p = nullptr; // [Np * D * B / 64] packed, tiled codes of the tensor-core scan
     float4* rowmeta = nullptr;   // [Np] {g, f_res/2, id, 0} per padded row (zeros for padding)
     float* X = nullptr;          // [N][D] raw rows, original order (keep_raw)
     uint32_t* status = nullptr;  // device status word

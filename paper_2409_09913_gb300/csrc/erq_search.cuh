@@ -58,7 +58,7 @@ struct ScanLaunch {
     const int4* itemd;          // tensor-core path: per-item {rb0 lo, rb0 hi, rows, queries}
     const int4* itemq;          // tensor-core path: per-item query slots
     const float4* rowmeta;      // tensor-core path: per padded row {g, f_res/2, id, 0}
-    const uint8_t* codes_t;     // tensor-core path: tiled, padded codes
+    const uint64_t* codes_p;    // tensor-core path: packed B-bit codes, tiled and padded
     int64_t Np;                 // tensor-core path: padded rows
     unsigned long long* tq;     // tensor-core path: [nq] query-wide thresholds (all ones at the start)
     int maxp, D, B, kp, RR;
@@ -82,8 +82,8 @@ cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_
                                int4* itemq, unsigned long long* stats, cudaStream_t s);
 bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
-                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
-                               uint8_t* codes_t, float4* rowmeta, cudaStream_t s);
+                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D, int B,
+                               uint64_t* codes_p, float4* rowmeta, cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           cudaStream_t s);

@@ -9,31 +9,37 @@
 //       tensor memory (row = lane, two FP16 values per column);
 //   B = the item's queries (rotated q' in FP16), npad = the query count rounded
 //       up to a multiple of 16, K-major.
-// Codes are read from a scan-specific copy: every inverted list padded to a
-// multiple of 32 rows and stored as [tiles of 32 rows][K blocks of 64][32][64]
-// bytes, so the 128 rows x 64 bytes of one stage are four contiguous 2 KB pieces
-// fetched by one 4-D TMA load.  Tensor memory: columns [0, 256) hold two
-// buffers of RP accumulators (64 columns each), columns [256, 448) the three
-// expanded-code stages of RP x 32 columns.
+// Codes are read from a packed, scan-specific copy: every inverted list padded
+// to a multiple of 32 rows and stored as [tiles of 32 rows][K blocks of 64]
+// [B words][32 rows] of 8 bytes, i.e. exactly B bits per coordinate (the
+// layout is given at unpack_codes); the 128 rows of one stage and K block are
+// four contiguous 256*B-byte pieces fetched by one 3-D TMA load.  Tensor
+// memory: columns [0, 2 RP QN) hold two buffers of RP accumulators (QN columns
+// each), the columns after them the expanded-code stages of RP x 32 columns.
 // The accumulator holds row r in TMEM lane r and query j in column j; the
 // estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
 // stored per-row factors.  The product is exact up to the FP16 rounding of q'
 // (relative 2^-11 per element); accumulation is FP32.
 //
-// Warp roles (320 + 32 (NG + NFX) threads, one CTA per SM, persistent over work items):
+// Warp roles (21 warps = 672 threads with NG = 2, NFX = 4; one CTA per SM,
+// persistent over work items):
 //   warp 9     loader: per stage (128-row block, 64-wide K block) one TMA load
-//              of the raw u8 codes (L2 evict-first); per row block a bulk copy
+//              of the packed codes (L2 evict-first); per row block a bulk copy
 //              of the rows' factors and ids; per item the queries'
 //              ||q_r - c||^2 and output slots.  It runs up to LS stages ahead
 //              of the tensor cores;
 //   warps 10.. gatherers (NG warps): per stage, cp.async of the item's FP16 query rows
 //              (L2 evict-last) into the 128B-swizzled B tile, completion
 //              tracked on the stage's query barrier;
-//   warps 4-7  converters: one thread per row expands the row's 64 raw codes
-//              of a stage (64B-swizzled by the TMA, so reads are conflict-free)
-//              in registers and stores them into the stage's TMEM columns;
+//   warps 4-7, converters, two sets that take alternate stages: one thread
+//   and 17-20  per row unpacks the row's 64 B-bit codes of a stage (B 8-byte
+//              words; a warp reads 256 contiguous bytes per word, conflict-
+//              free) in registers and stores them as FP16 into the stage's
+//              TMEM columns (warp w owns TMEM lanes 32 (w % 4) ..);
 //   warp 8     MMA issuer of row block 0 (one elected thread) and TMEM owner;
-//   last warp  MMA issuer of row block 1;
+//   warp 16    MMA issuer of row block 1.  Each issuer commits once per
+//              stage to the stage's release barrier, which frees its codes,
+//              query tile and TMEM code columns together;
 //   warps 0-3  epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32 rows for
 //              all queries) and stores g + (f_res/2)*acc into a query-major tile
 //              in shared memory; after a named barrier these four warps and the
@@ -70,7 +76,6 @@ namespace tc {
 
 constexpr int MR = 128;          // stored rows per MMA block (MMA M)
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int SA = 3;            // expanded code stages (tensor memory, RP x 32 columns each)
 constexpr int MS = 4;            // row-factor buffers (one per row block)
 constexpr int NMMA = 2;          // MMA issuing warps
 constexpr int KCAP = 128;        // max k' of the tensor-core path
@@ -78,8 +83,9 @@ constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
 constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
 constexpr int NFW = 4 + NFX;     // warps that filter candidates
 constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
-constexpr int THREADS = 32 * (MMA2 + 1);
-constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + SA x RP x 32 columns of codes
+constexpr int CV2 = MMA2 + 1;    // second converter set (warps CV2 .. CV2 + 3; the first is 4-7)
+constexpr int THREADS = 32 * (CV2 + 4);
+constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + LS x RP x 32 columns of codes
 
 // Work-item shapes: QN queries per item (the MMA's N extent), KC-entry
 // candidate lists, RP row blocks per stage, LS load stages, EB estimate tiles.
@@ -92,15 +98,16 @@ struct Cfg {
     static constexpr int EB = EB_;                 // estimate tiles (2: filtering overlaps the next block)
     static constexpr int KS = KC_ <= 64 ? 64 : 256;   // sort width of a list compaction
     static constexpr int TILE_Q = QN * KB * 2;
-    static constexpr int TILE_RAW = RP * MR * KB;  // u8 codes of a stage (TMA staging)
+    static constexpr int TILE_RAW = RP * MR * KB;  // packed codes of a stage (TMA staging; 128 * 8 B <= 8 KB per block)
     static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
-    static_assert(ACOL + SA * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
+    static_assert(ACOL + LS * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
+    static_assert(LS % 2 == 0, "the two converter sets take alternate stages and must see every use of theirs");
     static_assert(QN % (4 * NG) == 0 && QN % NFW == 0 && QN % 32 == 0, "query tile split");
     static_assert(RP >= 1 && RP <= NMMA && (EB == 1 || EB == 2), "stage shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
         static constexpr int q = 0;                                // LS  x [QN queries][64] FP16, swizzled
-        static constexpr int raw = q + LS * TILE_Q;                // LS  x RP x [128 rows][64] u8, 64B-swizzled
+        static constexpr int raw = q + LS * TILE_Q;                // LS  x RP x 8 KB: packed codes of 128 rows
         static constexpr int est = raw + LS * TILE_RAW;            // EB x [QN][MR] f32  g + (f_res/2) acc
         static constexpr int lists = est + EB * QN * MR * 4;       // [QN][KC] u64 candidate keys
         static constexpr int meta = lists + QN * KC * 8;           // MS x [MR] float4 {g, f_res/2, id, 0}
@@ -111,7 +118,7 @@ struct Cfg {
         static constexpr int tau = cnt + QN * 4;                   // [QN] u64   admission threshold
         static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
         static constexpr int bars = tq + 2 * QN * 8;               // mbarriers (8 B each)
-        static constexpr int nbars = 3 * LS + 2 * SA + 4 + 2 * MS + 4 + 1;
+        static constexpr int nbars = 4 * LS + 4 + 2 * MS + 4 + 1;
         static constexpr int tmem_slot = bars + nbars * 8;
         static constexpr int abort_flag = tmem_slot + 4;
         static constexpr int total = abort_flag + 4 + 1024;        // + alignment slack
@@ -120,28 +127,79 @@ struct Cfg {
 };
 using CfgSmall = Cfg<64, 64, 2, 4, 2>;    // k' <= 32, up to 64 queries per item
 using CfgLarge = Cfg<32, 160, 2, 4, 2>;   // k' <= 128, up to 32 queries per item
-using CfgWide = Cfg<128, 64, 1, 3, 1>;    // k' <= 32, up to 128 queries per item (query-heavy lists)
+using CfgWide = Cfg<128, 64, 1, 2, 1>;    // k' <= 32, up to 128 queries per item (query-heavy lists)
 
-// 16 u8 codes -> 16 FP16 values 2u - off, exact: 1024 + u is exact in FP16
-// (byte u as mantissa of 0x6400), fma(1024 + u, 2, -2048) = 2u is exact, and
-// 2u - off is an odd integer of magnitude <= 255 (exact).  off = 2^B - 1 is
-// applied separately because -(2048 + off) itself is not representable.
-__device__ __forceinline__ void expand16(uint4 u, __half2 two, __half2 m2048, __half2 off2, uint4& lo, uint4& hi) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-    uint32_t o[8];
+// Packed codes of one stored row and one 64-coordinate K block -> 32 TMEM
+// columns of FP16 pairs 2u - (2^B - 1) (column c holds coordinates 2c, 2c+1).
+// The row's 8B bytes are B 8-byte words; word j of the 32 rows of a tile is a
+// contiguous 256-byte run, so `base` points at word 0 of this row and word j
+// is at base + 256 j.  With h the 32-bit half index (0..7 over words 0-3) and
+// L a byte lane:
+//   B >= 4: words 0-3 hold the low four bits of every code as nibbles, byte L
+//           of half h = (u[8h + L] & 15) | (u[8h + 4 + L] & 15) << 4, and word
+//           b (4 <= b < B) is bit plane b;
+//   B < 4:  word b (b < B) is bit plane b;
+//   bit plane b: bit 8L + (m & 7) of half (m >> 3) is bit b of u[4m + L].
+// Four coordinates 4m..4m+3 are assembled in the byte lanes of one register
+// (nibble: one shift and mask; each plane: one shift and one masked OR), as
+// 2u for B <= 7 and u for B = 8.  A byte x placed under 0x64 is the FP16
+// value 1024 + x (exact); 2u - off = (1024 + 2u) - (1024 + off) is then one
+// exact subtraction (for B = 8: 2 (1024 + u) - 2048 - off, each step exact).
+template <int B>
+__device__ __forceinline__ void unpack_codes(const unsigned char* base, uint32_t (&w)[32]) {
+    constexpr int T = B <= 7 ? 1 : 0;
+    constexpr int BS = B >= 4 ? 4 : 0;
+    uint2 W[B];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t p0 = __byte_perm(w[i], 0x6464u, 0x4140u);   // {b0, 0x64, b1, 0x64}
-        const uint32_t p1 = __byte_perm(w[i], 0x6464u, 0x4342u);   // {b2, 0x64, b3, 0x64}
+    for (int j = 0; j < B; ++j) W[j] = *reinterpret_cast<const uint2*>(base + 256 * j);
+    const float off = (float)((1 << B) - 1);
+    const __half2 c2 = __floats2half2_rn(1024.f + off, 1024.f + off);
+    const __half2 off2 = __floats2half2_rn(off, off);
+    const __half2 two = __floats2half2_rn(2.f, 2.f);
+    const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        uint32_t V = 0;
+        if constexpr (B >= 4) {
+            const int h = m >> 1;
+            const uint32_t N = (h & 1) ? W[h >> 1].y : W[h >> 1].x;
+            if constexpr (T == 1) V = (m & 1) ? (N >> 3) & 0x1E1E1E1Eu : (N << 1) & 0x1E1E1E1Eu;
+            else V = (m & 1) ? (N >> 4) & 0x0F0F0F0Fu : N & 0x0F0F0F0Fu;
+        }
+#pragma unroll
+        for (int b = BS; b < B; ++b) {
+            const uint32_t P = m < 8 ? W[b].x : W[b].y;
+            const int sh = b + T - (m & 7);
+            const uint32_t x = sh >= 0 ? P << sh : P >> (-sh);
+            V |= x & (0x01010101u << (b + T));
+        }
+        const uint32_t p0 = __byte_perm(V, 0x6464u, 0x4140u);   // {x0, 0x64, x1, 0x64}
+        const uint32_t p1 = __byte_perm(V, 0x6464u, 0x4342u);   // {x2, 0x64, x3, 0x64}
         __half2 h0 = *reinterpret_cast<const __half2*>(&p0);
         __half2 h1 = *reinterpret_cast<const __half2*>(&p1);
-        h0 = __hsub2(__hfma2(h0, two, m2048), off2);
-        h1 = __hsub2(__hfma2(h1, two, m2048), off2);
-        o[2 * i] = *reinterpret_cast<uint32_t*>(&h0);
-        o[2 * i + 1] = *reinterpret_cast<uint32_t*>(&h1);
+        if constexpr (T == 1) {
+            h0 = __hsub2(h0, c2);
+            h1 = __hsub2(h1, c2);
+        } else {
+            h0 = __hsub2(__hfma2(h0, two, m2048), off2);
+            h1 = __hsub2(__hfma2(h1, two, m2048), off2);
+        }
+        w[2 * m] = *reinterpret_cast<uint32_t*>(&h0);
+        w[2 * m + 1] = *reinterpret_cast<uint32_t*>(&h1);
     }
-    lo = make_uint4(o[0], o[1], o[2], o[3]);
-    hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+__device__ __forceinline__ void unpack_codes_b(int B, const unsigned char* base, uint32_t (&w)[32]) {
+    switch (B) {
+        case 1: unpack_codes<1>(base, w); break;
+        case 2: unpack_codes<2>(base, w); break;
+        case 3: unpack_codes<3>(base, w); break;
+        case 4: unpack_codes<4>(base, w); break;
+        case 5: unpack_codes<5>(base, w); break;
+        case 6: unpack_codes<6>(base, w); break;
+        case 7: unpack_codes<7>(base, w); break;
+        default: unpack_codes<8>(base, w); break;
+    }
 }
 
 struct Args {
@@ -244,13 +302,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     // barrier addresses
     const uint32_t full_load0 = smem_u32(&bars[0]), empty_load0 = smem_u32(&bars[LS]);
     const uint32_t full_q0 = smem_u32(&bars[2 * LS]);
-    const uint32_t full_a0 = smem_u32(&bars[3 * LS]), empty_a0 = smem_u32(&bars[3 * LS + SA]);
-    const uint32_t tfull0 = smem_u32(&bars[3 * LS + 2 * SA]), tempty0 = smem_u32(&bars[3 * LS + 2 * SA + 2]);
-    const uint32_t full_meta0 = smem_u32(&bars[3 * LS + 2 * SA + 4]);
-    const uint32_t empty_meta0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + MS]);
-    const uint32_t full_item0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS]);
-    const uint32_t empty_item0 = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS + 2]);
-    const uint32_t done_bar = smem_u32(&bars[3 * LS + 2 * SA + 4 + 2 * MS + 4]);
+    const uint32_t full_a0 = smem_u32(&bars[3 * LS]);
+    const uint32_t tfull0 = smem_u32(&bars[4 * LS]), tempty0 = smem_u32(&bars[4 * LS + 2]);
+    const uint32_t full_meta0 = smem_u32(&bars[4 * LS + 4]);
+    const uint32_t empty_meta0 = smem_u32(&bars[4 * LS + 4 + MS]);
+    const uint32_t full_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS]);
+    const uint32_t empty_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 2]);
+    const uint32_t done_bar = smem_u32(&bars[4 * LS + 4 + 2 * MS + 4]);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, nkb = D / KB;
@@ -259,12 +317,9 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < LS; ++s) {
             mbar_init(full_load0 + 8 * s, 1);      // the TMA expect_tx arrival
-            mbar_init(empty_load0 + 8 * s, NMMA);  // one MMA commit per issuer
+            mbar_init(empty_load0 + 8 * s, NMMA);  // one MMA commit per issuer: codes, queries and TMEM stage free
             mbar_init(full_q0 + 8 * s, 32 * NG);   // one cp.async arrival per gatherer lane
-        }
-        for (int s = 0; s < SA; ++s) {
-            mbar_init(full_a0 + 8 * s, 128);
-            mbar_init(empty_a0 + 8 * s, NMMA);
+            mbar_init(full_a0 + 8 * s, 128);       // the converter set of the stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull0 + 8 * b, NMMA);
@@ -345,10 +400,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     const int s = g % LS;
                     if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)(nb * MR * KB));
+                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)(nb * (MR / 32) * 256 * a.B));
                         for (int bb = 0; bb < nb; ++bb)
-                            tma_load_4d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB), &codes_map, 0, 0,
-                                             kb, (int)((rb0 + r + bb * MR) >> 5), full_load0 + 8 * s, pol_codes);
+                            tma_load_3d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB), &codes_map, 0, kb,
+                                             (int)((rb0 + r + bb * MR) >> 5), full_load0 + 8 * s, pol_codes);
                     }
                     __syncwarp();
                 }
@@ -409,16 +464,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             mbar_wait_drain(full_q0 + 8 * (gg % LS), (gg / LS) & 1);
         }
         __syncwarp();
-    } else if (warp >= 4 && warp < 8) {
+    } else if ((warp >= 4 && warp < 8) || warp >= CV2) {
         // ------------------------------------------------------------ converters
-        // converter thread = one row of the stage (TMEM lane); warp w writes lanes 32 (w - 4)..
-        const int r = tid - 128;
-        const uint32_t lane_addr = (uint32_t)((warp - 4) * 32) << 16;
-        const __half2 two = __floats2half2_rn(2.f, 2.f);
-        const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
-        const float offv = (float)((1 << a.B) - 1);
-        const __half2 off2 = __floats2half2_rn(offv, offv);
-        const int swz = (r >> 1) & 3;                          // 64-byte TMA swizzle of row r
+        // Two sets of four warps take alternate stages (set cs the stages g
+        // with g % 2 == cs).  Converter thread = one row of the stage (TMEM
+        // lane); warp w writes TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
+        const int cs = warp >= CV2 ? 1 : 0;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
+        const int B = a.B;
+        const int roff = (r >> 5) * 256 * B + (r & 31) * 8;   // word 0 of row r in a 128-row block
         uint32_t g = 0, li = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
@@ -427,28 +482,26 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int nrows = s_idesc[ib].z;
             const int nsteps = ((nrows + RP * MR - 1) / (RP * MR)) * nkb;
             for (int t = 0; t < nsteps; ++t, ++g) {
-                const int s = g % LS, sa = g % SA;
+                if ((int)(g & 1) != cs) continue;
+                const int s = g % LS;
                 const int r0 = (t / nkb) * (RP * MR);
                 const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
-                if (!mbar_wait_warp(full_load0 + 8 * s, (g / LS) & 1, abort_flag)) { ok = false; break; }
-                if (!mbar_wait_warp(empty_a0 + 8 * sa, ((g / SA) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                // the codes have landed; the stage's previous MMAs (which read its
+                // TMEM columns) completed before the loader refilled it
+                if (!mbar_wait_warp(full_load0 + 8 * s, (g / LS) & 1, abort_flag) ||
+                    !mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
-                    const unsigned char* rp = sm + Smem::raw + s * TILE_RAW + bb * MR * KB + r * KB;
                     uint32_t w[32];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {                  // 16 codes -> 8 columns of FP16 pairs
-                        const uint4 u = *reinterpret_cast<const uint4*>(rp + ((c ^ swz) << 4));
-                        uint4 lo, hi;
-                        expand16(u, two, m2048, off2, lo, hi);
-                        w[8 * c + 0] = lo.x; w[8 * c + 1] = lo.y; w[8 * c + 2] = lo.z; w[8 * c + 3] = lo.w;
-                        w[8 * c + 4] = hi.x; w[8 * c + 5] = hi.y; w[8 * c + 6] = hi.z; w[8 * c + 7] = hi.w;
-                    }
-                    ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (sa * RP + bb) * (KB / 2), w);
+                    unpack_codes_b(B, sm + Smem::raw + s * TILE_RAW + bb * MR * KB + roff, w);
+                    ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + bb) * (KB / 2), w);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                mbar_arrive(full_a0 + 8 * sa);
+                mbar_arrive(full_a0 + 8 * s);
             }
         }
     } else if (warp == 8 || warp == MMA2) {
@@ -471,8 +524,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 tc_fence_after();
                 const uint32_t dt = tmem + buf * (RP * QN);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int s = g % LS, sa = g % SA;
-                    if (!mbar_wait_warp(full_a0 + 8 * sa, (g / SA) & 1, abort_flag) ||
+                    const int s = g % LS;
+                    if (!mbar_wait_warp(full_a0 + 8 * s, (g / LS) & 1, abort_flag) ||
                         !mbar_wait_warp(full_q0 + 8 * s, (g / LS) & 1, abort_flag)) {
                         ok = false;
                         break;
@@ -481,14 +534,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     tc_fence_after();
                     if (lane == 0) {
                         if (mrb < nb) {
-                            const uint32_t ta = tmem + ACOL + (sa * RP + mrb) * (KB / 2);
+                            const uint32_t ta = tmem + ACOL + (s * RP + mrb) * (KB / 2);
                             const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
 #pragma unroll
                             for (int k = 0; k < KB / 16; ++k)
                                 mma_f16_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
                         }
-                        mma_commit(empty_a0 + 8 * sa);
-                        mma_commit(empty_load0 + 8 * s);
+                        mma_commit(empty_load0 + 8 * s);     // codes, query tile and TMEM stage free
                         if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
                     }
                     __syncwarp();
@@ -697,14 +749,24 @@ cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_
     return cudaGetLastError();
 }
 
-// Scan layout of the index (one warp per padded row p): the row's codes into
-// the tiled array and {g, f_res / 2, id, 0} into rowmeta; padding rows get zeros.
+// Packed scan layout of the index.  One thread per (tile t, K block kb, row r
+// of the tile): padded row p = 32 t + r takes its cluster's stored row (or
+// zeros past the cluster's end), packs the 64 codes of block kb into B 8-byte
+// words (layout at unpack_codes) and writes word j to
+// codes_p[((t * nkb + kb) * B + j) * 32 + r]; the kb = 0 thread also writes the
+// row's {g, f_res / 2, id, 0} to rowmeta[p].
 __global__ void scan_layout_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ g,
                                    const float* __restrict__ f_res, const int64_t* __restrict__ ids,
                                    const int64_t* __restrict__ list_off, const int64_t* __restrict__ poff, int nlist,
-                                   int64_t Np, int D, uint8_t* __restrict__ codes_t, float4* __restrict__ rowmeta) {
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+                                   int64_t Np, int D, int B, uint64_t* __restrict__ codes_p,
+                                   float4* __restrict__ rowmeta) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nkb = D / 64;
+    const int r = (int)(tid & 31);
+    const int64_t tk = tid >> 5;                 // t * nkb + kb
+    const int64_t t = tk / nkb;
+    const int kb = (int)(tk % nkb);
+    const int64_t p = t * 32 + r;
     if (p >= Np) return;
     int lo = 0, hi = nlist;                      // cluster with poff[lo] <= p < poff[lo + 1]
     while (hi - lo > 1) {
@@ -715,32 +777,50 @@ __global__ void scan_layout_kernel(const uint8_t* __restrict__ codes, const floa
     const int64_t j = p - poff[lo];
     const bool valid = j < list_off[lo + 1] - list_off[lo];
     const int64_t src = list_off[lo] + j;
-    const int nkb = D / 64;
-    const int64_t t = p >> 5;
-    const int r = (int)(p & 31);
-    for (int x = lane; x < D / 16; x += 32) {
-        const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + src * D)[x] : make_uint4(0u, 0u, 0u, 0u);
-        const int kb = x >> 2, w = x & 3;
-        reinterpret_cast<uint4*>(codes_t + ((t * nkb + kb) * 32 + r) * 64)[w] = v;
+    uint32_t u[16];                              // 64 codes, four per word (byte i of u[k] = code 4k + i)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + src * D + kb * 64)[x] : make_uint4(0u, 0u, 0u, 0u);
+        u[4 * x] = v.x; u[4 * x + 1] = v.y; u[4 * x + 2] = v.z; u[4 * x + 3] = v.w;
     }
-    if (lane == 0)
+    uint64_t* dst = codes_p + (tk * B) * 32 + r;
+    const int bs = B >= 4 ? 4 : 0;
+    if (B >= 4) {
+        // half h: byte L = (code 8h + L) & 15 | ((code 8h + 4 + L) & 15) << 4
+        uint32_t N[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) N[h] = (u[2 * h] & 0x0F0F0F0Fu) | ((u[2 * h + 1] & 0x0F0F0F0Fu) << 4);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) dst[w * 32] = (uint64_t)N[2 * w] | ((uint64_t)N[2 * w + 1] << 32);
+    }
+    for (int b = bs; b < B; ++b) {
+        // bit 8L + (m & 7) of half (m >> 3) = bit b of code 4m + L
+        uint32_t P[2] = {0u, 0u};
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+            P[m >> 3] |= ((u[m] >> b) & 0x01010101u) << (m & 7);
+        dst[b * 32] = (uint64_t)P[0] | ((uint64_t)P[1] << 32);
+    }
+    if (kb == 0)
         rowmeta[p] = valid ? make_float4(g[src], 0.5f * f_res[src], __uint_as_float((uint32_t)ids[src]), 0.f)
                            : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
-                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D,
-                               uint8_t* codes_t, float4* rowmeta, cudaStream_t s) {
+                               const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D, int B,
+                               uint64_t* codes_p, float4* rowmeta, cudaStream_t s) {
     if (Np <= 0) return cudaSuccess;
     count_launch();
-    scan_layout_kernel<<<(unsigned)ceil_div(Np, 8), 256, 0, s>>>(codes, g, f_res, ids, list_off, poff, nlist, Np, D,
-                                                                 codes_t, rowmeta);
+    const int64_t n = ceil_div(Np, 32) * (D / 64) * 32;
+    scan_layout_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(codes, g, f_res, ids, list_off, poff, nlist, Np, D,
+                                                                  B, codes_p, rowmeta);
     return cudaGetLastError();
 }
 
-// 4-D view of the tiled codes: (64 bytes, 32 rows, K block, tile); a box of
-// (64, 32, 1, 4) is the 128 x 64-byte tile of one stage, rows in order.
-static bool make_codes_map(CUtensorMap* map, const uint8_t* codes_t, int64_t Np, int D) {
+// 3-D view of the packed codes in 8-byte elements: (32 B words of a tile and
+// K block, K block, tile); a box of (32 B, 1, 4) is the 128 rows x 8 B bytes
+// of one stage, four contiguous tiles.
+static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np, int D, int B) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -752,12 +832,12 @@ static bool make_codes_map(CUtensorMap* map, const uint8_t* codes_t, int64_t Np,
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     const int nkb = D / KB;
-    const cuuint64_t dims[4] = {(cuuint64_t)KB, 32, (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
-    const cuuint64_t strides[3] = {(cuuint64_t)KB, (cuuint64_t)KB * 32, (cuuint64_t)KB * 32 * nkb};
-    const cuuint32_t box[4] = {(cuuint32_t)KB, 32, 1, MR / 32};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, (void*)codes_t, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint64_t dims[3] = {(cuuint64_t)(32 * B), (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
+    const cuuint64_t strides[2] = {(cuuint64_t)256 * B, (cuuint64_t)256 * B * nkb};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * B), 1, MR / 32};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)codes_p, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -768,8 +848,8 @@ static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStr
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
     CUtensorMap map;
-    if (!L.codes_t || ((uintptr_t)L.codes_t & 15) != 0 || (L.D % KB) != 0 ||
-        !make_codes_map(&map, L.codes_t, L.Np, L.D))
+    if (!L.codes_p || ((uintptr_t)L.codes_p & 15) != 0 || (L.D % KB) != 0 || L.B < 1 || L.B > 8 ||
+        !make_codes_map(&map, L.codes_p, L.Np, L.D, L.B))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     count_launch();
     scan_tc_kernel<C><<<L.grid, THREADS, smem, s>>>(map, a);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liberq.so")
 ERQ_OK, ERQ_EINVAL, ERQ_ENOMEM, ERQ_ECUDA, ERQ_ETIMEOUT, ERQ_EUNSUPPORTED, ERQ_EIO = range(7)
 PREC = {"fp32": 0, "fp16": 1, "fp8": 2, "int8": 3}
 FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, "codes": 4, "f_add": 5,
-          "f_res": 6, "P": 7, "raw": 8}
+          "f_res": 6, "P": 7, "raw": 8, "packed_codes": 9}
 
 # names of every entry point declared in include/erq.h
 EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index", "erq_index_info_get",
@@ -308,6 +308,10 @@ class Index:
                   "list_offsets": ((nl + 1,), torch.int64), "list_ids": ((N,), torch.int64),
                   "codes": ((N, D), torch.uint8), "f_add": ((N,), torch.float32), "f_res": ((N,), torch.float32),
                   "P": ((D, D), torch.float32), "raw": ((N, D), torch.float32)}
+        if field == "packed_codes":      # clusters padded to 32-row tiles, B bits per coordinate
+            off = self.export("list_offsets")
+            Np = int(((off[1:] - off[:-1] + 31) // 32 * 32).sum())
+            shapes[field] = ((Np * D * inf["B"] // 8,), torch.uint8)
         shape, dt = shapes[field]
         out = torch.empty(shape, dtype=dt)
         torch.cuda.current_stream().synchronize()

@@ -137,3 +137,67 @@ def test_autotune_picks_a_shape(erq):
         gx.set_scan_config(48, 0)
     with pytest.raises(erq.ErqError):
         gx.set_scan_config(0, 1000)
+
+
+def _pack_reference(codes, off, B):
+    """The packed scan layout written out from its definition (64-bit words
+    [tile of 32 rows][block of 64 coordinates][B][32 rows], nibble halves for
+    bits 0-3 when B >= 4, bit planes for the others), with numpy."""
+    D = codes.shape[1]
+    nkb = D // 64
+    parts = []
+    for c in range(len(off) - 1):
+        blk = codes[off[c]:off[c + 1]]
+        parts.append(np.concatenate([blk, np.zeros(((-len(blk)) % 32, D), np.uint8)]))
+    U = np.concatenate(parts).astype(np.uint64)
+    U = U.reshape(-1, 32, nkb, 64).transpose(0, 2, 1, 3)          # [tile, kb, r, 64 codes]
+    W = np.zeros(U.shape[:3] + (B,), np.uint64)                   # [tile, kb, r, word]
+    if B >= 4:
+        half = np.zeros(U.shape[:3] + (8,), np.uint64)
+        for h in range(8):
+            for L in range(4):
+                byte = (U[..., 8 * h + L] & 15) | ((U[..., 8 * h + 4 + L] & 15) << 4)
+                half[..., h] |= byte << (8 * L)
+        for w in range(4):
+            W[..., w] = half[..., 2 * w] | (half[..., 2 * w + 1] << 32)
+    for b in range(4 if B >= 4 else 0, B):
+        half = np.zeros(U.shape[:3] + (2,), np.uint64)
+        for m in range(16):
+            for L in range(4):
+                bit = (U[..., 4 * m + L] >> b) & 1
+                half[..., m >> 3] |= bit << (8 * L + (m & 7))
+        W[..., b] = half[..., 0] | (half[..., 1] << 32)
+    return np.ascontiguousarray(W.transpose(0, 1, 3, 2)).view(np.uint8).ravel()   # [tile, kb, word, r]
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_packed_scan_layout_bit_exact(erq, B):
+    """The scan's packed copy holds exactly the index's codes, B bits each."""
+    X, lab = S.mixture(3000, 128, 8, 3700 + B, scale="aniso")
+    assign = S.kmeans_assign(X, 7, 3, 3701)
+    P = S.random_orthogonal(128, 3702)
+    gx = erq.build_index(to_dev(X), to_dev(P), B, 7, assign=to_dev(assign))
+    codes = gx.export("codes").numpy()
+    off = gx.export("list_offsets").numpy()
+    got = gx.export("packed_codes").numpy()
+    ref = _pack_reference(codes, off, B)
+    assert got.shape == ref.shape and got.size == int(((off[1:] - off[:-1] + 31) // 32 * 32).sum()) * 128 * B // 8
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("B", [1, 2, 6, 8])
+def test_tc_scan_every_code_width(erq, B):
+    """Estimates from the packed codes stay within the FP16 query-rounding
+    bound for code widths the larger tests do not cover."""
+    X, P, gx, ox = _index(erq, 8000, 128, B, 16, 3800 + B)
+    Q, _ = S.mixture(300, 128, 16, 3801, comp_seed=3800 + B, scale="aniso")
+    probe = S.random_probe_lists(300, 16, 4, 3802)
+    ids, dists, cids, cest = gx.search(to_dev(Q), 10, rerank_k=24, probe=to_dev(probe), nprobe=4,
+                                       precision="fp16", return_candidates=True)
+    torch.cuda.synchronize()
+    gid = cids.cpu().numpy()
+    assert (gid >= 0).all()
+    oest = oracle.estimate_rows(ox, Q, gid)
+    bound = _bound(ox, Q, gid) + 2e-5 * (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))
+    viol = np.abs(cest.cpu().numpy().astype(np.float64) - oest) > bound
+    assert not viol.any(), f"{viol.sum()} estimates outside the FP16 bound"
