@@ -83,8 +83,9 @@ constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
 constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
 constexpr int NFW = 4 + NFX;     // warps that filter candidates
 constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
-constexpr int CV2 = MMA2 + 1;    // second converter set (warps CV2 .. CV2 + 3; the first is 4-7)
-constexpr int THREADS = 32 * (CV2 + 4);
+constexpr int NCV = 2;           // converter sets (warps 4-7, and CV2 .. CV2 + 3 when NCV = 2)
+constexpr int CV2 = MMA2 + 1;
+constexpr int THREADS = 32 * (CV2 + (NCV == 2 ? 4 : 0));
 constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + LS x RP x 32 columns of codes
 
 // Work-item shapes: QN queries per item (the MMA's N extent), KC-entry
@@ -101,8 +102,8 @@ struct Cfg {
     static constexpr int TILE_RAW = RP * MR * KB;  // packed codes of a stage (TMA staging; 128 * 8 B <= 8 KB per block)
     static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
     static_assert(ACOL + LS * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
-    static_assert(LS % 2 == 0, "the two converter sets take alternate stages and must see every use of theirs");
-    static_assert(QN % (4 * NG) == 0 && QN % NFW == 0 && QN % 32 == 0, "query tile split");
+    static_assert(NCV == 1 || LS % 2 == 0, "the two converter sets take alternate stages and must see every use of theirs");
+    static_assert(QN % (4 * NG) == 0 && QN % 32 == 0 && (QN + NFW - 1) / NFW <= 32, "query tile split");
     static_assert(RP >= 1 && RP <= NMMA && (EB == 1 || EB == 2), "stage shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int nrows = s_idesc[ib].z;
             const int nsteps = ((nrows + RP * MR - 1) / (RP * MR)) * nkb;
             for (int t = 0; t < nsteps; ++t, ++g) {
-                if ((int)(g & 1) != cs) continue;
+                if (NCV == 2 && (int)(g & 1) != cs) continue;
                 const int s = g % LS;
                 const int r0 = (t / nkb) * (RP * MR);
                 const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int4 d = s_idesc[ib];
             const int nrows = d.z, nqi = d.w, npad = npad_of(nqi);
             const int4* iq = s_iq + ib * QN;
-            if (lane < QN / NFW) {                             // owned queries q = fw + NFW * lane
+            if (lane < (QN + NFW - 1) / NFW) {                 // owned queries q = fw + NFW * lane
                 const int q = fw + NFW * lane;
                 if (q < nqi) {
                     s_cnt[q] = 0;

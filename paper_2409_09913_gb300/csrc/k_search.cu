@@ -23,36 +23,63 @@
 namespace erq {
 
 // ---------------------------------------------------------------------------
-// ||q_r - c||^2 per probed pair, FP32, one warp per pair.
-// ---------------------------------------------------------------------------
 // ||q_r - c||^2 for every probed (query, cluster): one block per query, the
-// query row in shared memory, one warp per probed cluster.
-__global__ void dqc_kernel(const float* __restrict__ Q, const float* __restrict__ C,
-                           const int32_t* __restrict__ probe, const int32_t* __restrict__ npr, int64_t nq,
-                           int maxp, int D, float* __restrict__ dqc) {
+// query row in shared memory, one warp per probed cluster (looping when the
+// query probes more clusters than the block has warps).  Each lane keeps up to
+// eight 16-byte loads of the centroid row in flight (D <= 4096).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) dqc_kernel(const float* __restrict__ Q, const float* __restrict__ C,
+                                                  const int32_t* __restrict__ probe, const int32_t* __restrict__ npr,
+                                                  int64_t nq, int maxp, int D, float* __restrict__ dqc) {
     extern __shared__ float qs[];
     const int64_t q = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int np = npr[q];
+    // the first centroid row's loads are issued before the query row is waited for
+    constexpr int RU = 8;
+    int slot = warp;
+    float4 a[RU];
+    auto issue = [&](int sl) {
+        const int c = sl < np ? probe[q * maxp + sl] : -1;
+        const float* y = C + (int64_t)(c < 0 ? 0 : c) * D;
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int t = 128 * u + lane * 4;
+            if (t < D) a[u] = *reinterpret_cast<const float4*>(y + t);
+        }
+        return c;
+    };
+    int c = slot < np ? issue(slot) : -1;
     for (int k = threadIdx.x * 4; k < D; k += blockDim.x * 4)
         *reinterpret_cast<float4*>(qs + k) = *reinterpret_cast<const float4*>(Q + q * D + k);
     __syncthreads();
-    const int np = npr[q];
-    for (int slot = warp; slot < np; slot += blockDim.x >> 5) {
-        const int c = probe[q * maxp + slot];
-        if (c < 0) continue;  // invalid probe id (reported through the status word)
-        const float* y = C + (int64_t)c * D;
+    for (; slot < np; slot += nw) {
+        if (slot != warp) c = issue(slot);
         float s = 0.f;
-        for (int k = lane * 4; k < D; k += 128) {
-            const float4 a = *reinterpret_cast<const float4*>(qs + k);
-            const float4 b = *reinterpret_cast<const float4*>(y + k);
-            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
-            s = fmaf(d0, d0, s);
-            s = fmaf(d1, d1, s);
-            s = fmaf(d2, d2, s);
-            s = fmaf(d3, d3, s);
+        for (int t0 = 0; t0 < D; t0 += 128 * RU) {
+            if (t0 > 0) {
+                const float* y = C + (int64_t)(c < 0 ? 0 : c) * D;
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int t = t0 + 128 * u + lane * 4;
+                    if (t < D) a[u] = *reinterpret_cast<const float4*>(y + t);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int t = t0 + 128 * u + lane * 4;
+                if (t < D) {
+                    const float4 b = *reinterpret_cast<const float4*>(qs + t);
+                    const float d0 = b.x - a[u].x, d1 = b.y - a[u].y, d2 = b.z - a[u].z, d3 = b.w - a[u].w;
+                    s = fmaf(d0, d0, s);
+                    s = fmaf(d1, d1, s);
+                    s = fmaf(d2, d2, s);
+                    s = fmaf(d3, d3, s);
+                }
+            }
         }
         s = warp_sum(s);
-        if (lane == 0) dqc[q * maxp + slot] = s;
+        if (lane == 0 && c >= 0) dqc[q * maxp + slot] = s;   // invalid probe ids are reported through the status word
     }
 }
 
@@ -118,31 +145,55 @@ __global__ void plan_query_kernel(const int32_t* __restrict__ slot_nr, int64_t n
     qtot[q] = run;
 }
 
-// generic exclusive scan of n int64 (single block); out has n+1 entries
-__global__ void excl_scan_i64_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
-    __shared__ int64_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t a = t * per, b = min(n, a + per);
-    int64_t s = 0;
-    for (int64_t i = a; i < b; ++i) s += in[i];
-    part[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        int64_t run = 0;
-        for (int i = 0; i < 1024; ++i) {
-            const int64_t v = part[i];
-            part[i] = run;
-            run += v;
+// Exclusive scan of n int64 (out has n + 1 entries, out[n] = total), one
+// block of 1024 threads per array (blockIdx.y selects a or b): chunks of
+// 4096 values, four consecutive values per thread, warp shuffles then one
+// pass over the 32 warp totals.
+__global__ void __launch_bounds__(1024) excl_scan_i64_kernel(const int64_t* __restrict__ a, int64_t* __restrict__ out_a,
+                                                             const int64_t* __restrict__ b, int64_t* __restrict__ out_b,
+                                                             int64_t n) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry_s;
+    const int64_t* in = blockIdx.y == 0 ? a : b;
+    int64_t* out = blockIdx.y == 0 ? out_a : out_b;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n; base += 4096) {
+        const int64_t i0 = base + 4 * t;
+        int64_t v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = i0 + j < n ? in[i0 + j] : 0;
+        const int64_t own = v[0] + v[1] + v[2] + v[3];
+        int64_t inc = own;                      // inclusive warp scan of the per-thread sums
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        out[n] = run;
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const int64_t w = wsum[lane];
+            int64_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            wsum[lane] = wi - w;                // exclusive prefix of the warp totals
+            if (lane == 31) carry_s = wi;       // chunk total
+        }
+        __syncthreads();
+        int64_t run = carry + wsum[warp] + inc - own;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j < n) out[i0 + j] = run;
+            run += v[j];
+        }
+        carry += carry_s;
+        __syncthreads();                        // wsum / carry_s are rewritten by the next chunk
     }
-    __syncthreads();
-    s = part[t];
-    for (int64_t i = a; i < b; ++i) {
-        out[i] = s;
-        s += in[i];
-    }
+    if (t == 0) out[n] = carry;
 }
 
 // per cluster: pair count (int64) and item count
@@ -612,7 +663,7 @@ cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, con
     cudaError_t e = cudaFuncSetAttribute(dqc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    dqc_kernel<<<(unsigned)nq, 128, smem, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
+    dqc_kernel<<<(unsigned)nq, 32 * std::min(maxp, 16), smem, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
     return cudaGetLastError();
 }
 
@@ -629,14 +680,12 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     count_launch();
     plan_query_kernel<<<(unsigned)ceil_div(p.nq, 256), 256, 0, s>>>(p.slot_nr, p.nq, p.maxp, p.slot_off, p.qtot);
     count_launch();
-    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.qtot, p.nq, p.qbase);
+    excl_scan_i64_kernel<<<dim3(1, 1), 1024, 0, s>>>(p.qtot, p.qbase, nullptr, nullptr, p.nq);
     count_launch();
     plan_cluster_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.corder, p.nlist,
                                                                           p.QT, p.RR, p.cnt64, p.items_c);
     count_launch();
-    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.cnt64, p.nlist, p.qoff);
-    count_launch();
-    excl_scan_i64_kernel<<<1, 1024, 0, s>>>(p.items_c, p.nlist, p.item_off);
+    excl_scan_i64_kernel<<<dim3(1, 2), 1024, 0, s>>>(p.cnt64, p.qoff, p.items_c, p.item_off, p.nlist);
     count_launch();
     plan_scatter_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(p.probe_c, p.nq, p.maxp, p.qoff, p.pos_c,
                                                                        p.qlist);
@@ -688,41 +737,47 @@ cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const 
     return cudaGetLastError();
 }
 
-// Re-rank for k' <= 32: one block of k' warps per query, one candidate per warp
-// (the query row staged in shared memory, the candidate's raw row read with all
-// of its loads in flight); warp 0 sorts the k' exact distances.
-__global__ void __launch_bounds__(1024) rerank32_kernel(const uint64_t* __restrict__ cand, int kp,
-                                                        const float* __restrict__ X, const float* __restrict__ Q,
-                                                        int D, int k, int64_t* __restrict__ ids,
-                                                        float* __restrict__ dists, int64_t* __restrict__ cand_ids,
-                                                        float* __restrict__ cand_est) {
+// Exact re-rank for k' <= 32: one block of eight warps per query, the query
+// row in shared memory; warp w computes ||x - q||^2 for candidates w, w + 8, ...
+// with each lane keeping up to eight 16-byte loads of the row in flight (the
+// first row's loads are issued before the query row is waited for), then warp
+// 0 sorts the k' keys (distance, id) and writes the top k.
+__global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __restrict__ cand, int kp,
+                                                          const float* __restrict__ X, const float* __restrict__ Q,
+                                                          int D, int k, int64_t* __restrict__ ids,
+                                                          float* __restrict__ dists, int64_t* __restrict__ cand_ids,
+                                                          float* __restrict__ cand_est) {
     extern __shared__ float qrow[];           // [D]
     __shared__ uint64_t keys[32];
     const int64_t q = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t* cq = cand + q * kp;
+    constexpr int RU = 8;
+    float4 a[RU];
+    auto issue = [&](int j, int t0) {
+        const uint64_t kk = cq[j];
+        const float* x = X + (int64_t)(kk == kEmptyKey ? 0u : key_id(kk)) * D;
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int t = t0 + 128 * u + lane * 4;
+            if (t < D) a[u] = *reinterpret_cast<const float4*>(x + t);
+        }
+        return kk;
+    };
+    uint64_t kk = warp < kp ? issue(warp, 0) : kEmptyKey;
     for (int t = threadIdx.x * 4; t < D; t += blockDim.x * 4)
         *reinterpret_cast<float4*>(qrow + t) = *reinterpret_cast<const float4*>(Q + q * D + t);
     if (cand_ids && threadIdx.x < kp) {
-        const uint64_t kk = cq[threadIdx.x];
-        cand_ids[q * kp + threadIdx.x] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
-        cand_est[q * kp + threadIdx.x] = kk == kEmptyKey ? INFINITY : key_value(kk);
+        const uint64_t c = cq[threadIdx.x];
+        cand_ids[q * kp + threadIdx.x] = c == kEmptyKey ? -1 : (int64_t)key_id(c);
+        cand_est[q * kp + threadIdx.x] = c == kEmptyKey ? INFINITY : key_value(c);
     }
     __syncthreads();
-    const uint64_t kk = cq[warp];
-    uint64_t key = kEmptyKey;
-    if (kk != kEmptyKey) {
-        const uint32_t id = key_id(kk);
-        const float* x = X + (int64_t)id * D;
+    for (int j = warp; j < kp; j += 8) {
+        if (j != warp) kk = issue(j, 0);
         float s = 0.f;
-        constexpr int RU = 8;
         for (int t0 = 0; t0 < D; t0 += 128 * RU) {
-            float4 a[RU];
-#pragma unroll
-            for (int u = 0; u < RU; ++u) {
-                const int t = t0 + 128 * u + lane * 4;
-                if (t < D) a[u] = *reinterpret_cast<const float4*>(x + t);
-            }
+            if (t0 > 0) issue(j, t0);
 #pragma unroll
             for (int u = 0; u < RU; ++u) {
                 const int t = t0 + 128 * u + lane * 4;
@@ -737,9 +792,8 @@ __global__ void __launch_bounds__(1024) rerank32_kernel(const uint64_t* __restri
             }
         }
         s = warp_sum(s);
-        key = make_key(s, id);
+        if (lane == 0) keys[j] = kk == kEmptyKey ? kEmptyKey : make_key(s, key_id(kk));
     }
-    if (lane == 0) keys[warp] = key;
     __syncthreads();
     if (warp == 0) {
         const uint64_t v = ws_sort32(lane < kp ? keys[lane] : kEmptyKey, lane);
@@ -759,7 +813,7 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
         cudaError_t e = cudaFuncSetAttribute(rerank32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        rerank32_kernel<<<(unsigned)nq, 32 * kp, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est);
+        rerank32_kernel<<<(unsigned)nq, 256, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est);
         return cudaGetLastError();
     }
     int sortn = 32;
