@@ -13,12 +13,20 @@
 //    searched so that a window holds at most W >= D events (a coordinate's
 //    events all have distinct keys, so one key value never has more than D).
 //  * Inside a window the events are sorted by (key, i) with a warp bitonic
-//    network; runs of equal FP32 keys are then checked with the exact rational
-//    comparison (m+1)*|o'_j| vs (m'+1)*|o'_i| (exact FP64 products) and, if any
-//    run is out of order, re-sorted by it.  Ties of the exact value go to the
-//    lower coordinate.
-//  * One lane accumulates <y_cur, o'> in FP64 in that order (the only serial
-//    dependency); ||y_cur||^2 is an exact integer multiple of 1/4.
+//    network; every run of equal FP32 keys is then re-sorted (one lane per run)
+//    by the exact rational comparison (m+1)*|o'_j| vs (m'+1)*|o'_i| (exact FP64
+//    products).  Ties of the exact value go to the lower coordinate.
+//  * <y_cur, o'> is the FP64 sum of the |o'_i| in that order.  Every |o'_i| is
+//    an integer multiple of u = 2^ue (ue one below the lowest mantissa bit of
+//    the smallest non-zero |o'_i|), and so is every FP64 partial sum.  When the
+//    running sum and all of a window's addends are multiples of 2^g and the
+//    window's final sum has at most 53 + g significant bits (in units of u),
+//    no addition of the window rounds: its partial sums are the exact int64
+//    prefix sums, formed in parallel (chunk sums, warp scan, chunk walk).
+//    Windows that fail the test (a few per vector at large B, from very small
+//    |o'_i|) and rows whose sums could leave int64 are walked serially in FP64
+//    by one lane, rounding at every step.  ||y_cur||^2 is an exact integer
+//    multiple of 1/4.
 //  * All lanes bound each state's cosine in FP32 and only states within 1e-5
 //    of the window's best are re-evaluated with correctly rounded FP64 sqrt and
 //    division; the first state of strictly largest cosine wins.
@@ -37,9 +45,32 @@ struct EncSmem {
     float* a;         // [D] |o'_i|
     uint8_t* cnt;     // [D] events of coordinate i already consumed
     uint64_t* keys;   // [W] (key32 << 32) | (i << 8) | m
-    double* ipk;      // [W] <y, o'> after each event of the window
-    int32_t* n2q;     // [W] 4 ||y||^2 after each event of the window
 };
+
+// Exponent of the lowest mantissa bit of a positive FP32 value.
+__device__ __forceinline__ int lsb_exp(float a) {
+    const uint32_t e = (__float_as_uint(a) >> 23) & 0xffu;
+    return e == 0 ? -149 : (int)e - 150;
+}
+// A positive FP32 value as an integer multiple of 2^ue (ue <= lsb_exp(a), and
+// the result below 2^62 by the caller's range check).
+__device__ __forceinline__ int64_t units_of(float a, int ue) {
+    const uint32_t b = __float_as_uint(a);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t mant = e == 0 ? (b & 0x7fffffu) : ((b & 0x7fffffu) | 0x800000u);
+    return (int64_t)(mant << (lsb_exp(a) - ue));
+}
+__device__ __forceinline__ int64_t warp_excl_scan_i64(int64_t v, int64_t& total) {
+    const int lane = threadIdx.x & 31;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
 
 // k-th event (0-based) of coordinate i has key RN((k+1) * sc / a), sc = 2^e a
 // power of two chosen per row so that every key is a finite normal number
@@ -82,14 +113,12 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const size_t per_warp = (size_t)W * 20 + (size_t)D * 5 + 64;
+    const size_t per_warp = (size_t)W * 8 + (size_t)D * 5 + 64;
     unsigned char* base = smem_raw + (size_t)warp * ((per_warp + 15) / 16 * 16);
     EncSmem sm;
     sm.keys = reinterpret_cast<uint64_t*>(base);
-    sm.ipk = reinterpret_cast<double*>(base + (size_t)W * 8);
-    sm.n2q = reinterpret_cast<int32_t*>(base + (size_t)W * 16);
-    sm.a = reinterpret_cast<float*>(base + (size_t)W * 20);
-    sm.cnt = reinterpret_cast<uint8_t*>(base + (size_t)W * 20 + (size_t)D * 4);
+    sm.a = reinterpret_cast<float*>(base + (size_t)W * 8);
+    sm.cnt = reinterpret_cast<uint8_t*>(base + (size_t)W * 8 + (size_t)D * 4);
 
     const int M = (1 << (B - 1)) - 1;
     const int half = 1 << (B - 1);
@@ -136,6 +165,15 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
         // initial state: all |y_i| = 1/2
         double ip_run = __dmul_rn(0.5, sum_a);    // exact scaling
         int n2q_run = D;                           // 4 * ||y||^2
+        // integer units of the running sum: u = 2^ue divides every |o'_i| / 2
+        int le = 1 << 30;
+        for (int i = lane; i < D; i += 32)
+            if (sm.a[i] > 0.f) le = min(le, lsb_exp(sm.a[i]));
+        le = __reduce_min_sync(0xffffffffu, le);
+        const int ue = le - 1;
+        // every partial sum stays below (M + 1) * sum |o'_i|; int64 holds it with margin
+        const bool in_range = nz > 0 && ldexp((double)(M + 1) * sum_a, -ue) < 0x1p61;
+        int64_t S_int = in_range ? __double2ll_rn(ldexp(ip_run, -ue)) : 0;
         double vmax = __ddiv_rn(ip_run, __dsqrt_rn(0.25 * (double)D));
         double ip_best = ip_run;
         int n2q_best = D;
@@ -224,83 +262,133 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                     __syncwarp();
                 }
             }
-            // ---- exact order inside runs of equal FP32 keys
-            bool bad = false;
+            // ---- exact order inside runs of equal FP32 keys: the lane at a run's
+            // first position insertion-sorts the run (runs are disjoint, and the
+            // FP32 key of every position is unchanged by sorting inside runs)
             for (int j = lane; j + 1 < cnt; j += 32) {
-                const uint64_t x = sm.keys[j], y = sm.keys[j + 1];
-                if ((x >> 32) == (y >> 32)) {
+                const uint32_t kj = (uint32_t)(sm.keys[j] >> 32);
+                if ((uint32_t)(sm.keys[j + 1] >> 32) != kj || (j > 0 && (uint32_t)(sm.keys[j - 1] >> 32) == kj))
+                    continue;
+                int e = j + 2;
+                while (e < cnt && (uint32_t)(sm.keys[e] >> 32) == kj) ++e;
+                for (int h = j + 1; h < e; ++h) {
+                    const uint64_t x = sm.keys[h];
                     const int ix = (int)((x >> 8) & 0xffffffu), mx = (int)(x & 0xffu);
-                    const int iy = (int)((y >> 8) & 0xffffffu), my = (int)(y & 0xffu);
-                    if (!ev_before(sm.a, ix, mx, iy, my)) bad = true;
+                    int g = h - 1;
+                    while (g >= j) {
+                        const uint64_t y = sm.keys[g];
+                        const int iy = (int)((y >> 8) & 0xffffffu), my = (int)(y & 0xffu);
+                        if (!ev_before(sm.a, ix, mx, iy, my)) break;
+                        sm.keys[g + 1] = y;
+                        --g;
+                    }
+                    sm.keys[g + 1] = x;
                 }
             }
-            if (__any_sync(0xffffffffu, bad)) {
-                if (lane == 0) {  // insertion sort by the exact order (runs are tiny)
-                    for (int j = 1; j < cnt; ++j) {
-                        const uint64_t x = sm.keys[j];
-                        const int ix = (int)((x >> 8) & 0xffffffu), mx = (int)(x & 0xffu);
-                        int h = j - 1;
-                        while (h >= 0) {
-                            const uint64_t y = sm.keys[h];
-                            const int iy = (int)((y >> 8) & 0xffffffu), my = (int)(y & 0xffu);
-                            if (!ev_before(sm.a, ix, mx, iy, my)) break;
-                            sm.keys[h + 1] = y;
-                            --h;
-                        }
-                        sm.keys[h + 1] = x;
+            __syncwarp();
+            // ---- the window's states: <y, o'> after each event, 4 ||y||^2, and
+            // the state of largest cosine (first one on ties)
+            const int C = (cnt + 31) >> 5;                     // events per lane (contiguous chunk)
+            const int c0 = min(cnt, lane * C), c1 = min(cnt, c0 + C);
+            int64_t sumA = 0;
+            int sumN = 0, gmin = 64;
+            for (int j = c0; j < c1; ++j) {
+                const uint64_t x = sm.keys[j];
+                sumN += 8 * ((int)(x & 0xffu) + 1);         // 4 * ((m + 3/2)^2 - (m + 1/2)^2)
+                if (in_range) {
+                    const int64_t A = units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
+                    sumA += A;
+                    gmin = min(gmin, __ffsll(A) - 1);
+                }
+            }
+            int64_t totA;
+            const int64_t baseA = warp_excl_scan_i64(sumA, totA);
+            const int baseN = warp_incl_scan(sumN) - sumN;
+            const int totN = __shfl_sync(0xffffffffu, baseN + sumN, 31);
+            bool fast = in_range;
+            if (fast) {
+                // no addition of the window rounds when the running sum and all
+                // addends are multiples of 2^g and the final sum fits in 53 + g bits
+                const int g = min(__reduce_min_sync(0xffffffffu, gmin), S_int > 0 ? __ffsll(S_int) - 1 : 64);
+                const int64_t Pend = S_int + totA;
+                fast = 64 - __clzll(Pend) <= 53 + g;
+            }
+            double bv = -1.0, bip = 0.0;                        // best cosine and its exact <y, o'>
+            int bj = 0x7fffffff, bn = 0;
+            if (fast) {
+                const float vmax_u = (float)ldexp(vmax, -ue);  // cosine bounds in units of u (scale-free)
+                float lmax = 0.f;
+                int64_t P = S_int + baseA;
+                int N = n2q_run + baseN;
+                for (int j = c0; j < c1; ++j) {
+                    const uint64_t x = sm.keys[j];
+                    P += units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
+                    N += 8 * ((int)(x & 0xffu) + 1);
+                    lmax = fmaxf(lmax, (float)P * rsqrtf(0.25f * (float)N));
+                }
+                const float thr = fmaxf(warp_max(lmax), vmax_u) * (1.0f - 1e-5f);
+                P = S_int + baseA;
+                N = n2q_run + baseN;
+                for (int j = c0; j < c1; ++j) {
+                    const uint64_t x = sm.keys[j];
+                    P += units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
+                    N += 8 * ((int)(x & 0xffu) + 1);
+                    if ((float)P * rsqrtf(0.25f * (float)N) >= thr) {
+                        const double ipj = ldexp(__ll2double_rn(P), ue);   // exact: P has <= 53 significant bits
+                        const double ve = __ddiv_rn(ipj, __dsqrt_rn(0.25 * (double)N));
+                        if (ve > bv) { bv = ve; bip = ipj; bj = j; bn = N; }   // j ascending per lane: first max kept
                     }
                 }
-                __syncwarp();
-            }
-            // ---- serial FP64 accumulation of <y_cur, o'> (lane 0)
-            if (lane == 0) {
+            } else if (lane == 0) {
+                // serial FP64 walk, every addition rounded (two passes: bound, then exact check)
+                float lmax = 0.f;
                 double ip = ip_run;
-                int n2 = n2q_run;
+                int N = n2q_run;
                 for (int j = 0; j < cnt; ++j) {
                     const uint64_t x = sm.keys[j];
-                    const int i = (int)((x >> 8) & 0xffffffu), m = (int)(x & 0xffu);
-                    ip = __dadd_rn(ip, (double)sm.a[i]);
-                    n2 += 8 * (m + 1);     // 4 * ((m + 3/2)^2 - (m + 1/2)^2)
-                    sm.ipk[j] = ip;
-                    sm.n2q[j] = n2;
+                    ip = __dadd_rn(ip, (double)sm.a[(int)((x >> 8) & 0xffffffu)]);
+                    N += 8 * ((int)(x & 0xffu) + 1);
+                    lmax = fmaxf(lmax, (float)ip * rsqrtf(0.25f * (float)N));
                 }
-                ip_run = ip;
-                n2q_run = n2;
-            }
-            ip_run = __shfl_sync(0xffffffffu, ip_run, 0);
-            n2q_run = __shfl_sync(0xffffffffu, n2q_run, 0);
-            __syncwarp();
-            // ---- approximate cosines, then exact check of the near-maximal ones
-            float lmax = 0.f;
-            for (int j = lane; j < cnt; j += 32) {
-                const float vf = (float)sm.ipk[j] * rsqrtf(0.25f * (float)sm.n2q[j]);
-                lmax = fmaxf(lmax, vf);
-            }
-            const float wmax = warp_max(lmax);
-            const float thr = fmaxf(wmax, (float)vmax) * (1.0f - 1e-5f);
-            double bv = -1.0;
-            int bj = 0x7fffffff;
-            for (int j = lane; j < cnt; j += 32) {
-                const float vf = (float)sm.ipk[j] * rsqrtf(0.25f * (float)sm.n2q[j]);
-                if (vf >= thr) {
-                    const double ve = __ddiv_rn(sm.ipk[j], __dsqrt_rn(0.25 * (double)sm.n2q[j]));
-                    if (ve > bv) { bv = ve; bj = j; }   // j ascending per lane: first max kept
+                const float thr = fmaxf(lmax, (float)vmax) * (1.0f - 1e-5f);
+                ip = ip_run;
+                N = n2q_run;
+                for (int j = 0; j < cnt; ++j) {
+                    const uint64_t x = sm.keys[j];
+                    ip = __dadd_rn(ip, (double)sm.a[(int)((x >> 8) & 0xffffffu)]);
+                    N += 8 * ((int)(x & 0xffu) + 1);
+                    if ((float)ip * rsqrtf(0.25f * (float)N) >= thr) {
+                        const double ve = __ddiv_rn(ip, __dsqrt_rn(0.25 * (double)N));
+                        if (ve > bv) { bv = ve; bip = ip; bj = j; bn = N; }
+                    }
                 }
+                ip_run = ip;   // lane 0 only; broadcast below
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const double oip = __shfl_xor_sync(0xffffffffu, bip, o);
                 const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+                const int on = __shfl_xor_sync(0xffffffffu, bn, o);
+                if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bip = oip; bj = oj; bn = on; }
             }
             if (bv > vmax) {
                 vmax = bv;
                 const uint64_t x = sm.keys[bj];
                 best_i = (int)((x >> 8) & 0xffffffu);
                 best_m = (int)(x & 0xffu);
-                ip_best = sm.ipk[bj];
-                n2q_best = sm.n2q[bj];
+                ip_best = bip;
+                n2q_best = bn;
             }
+            // advance the running state
+            if (fast) {
+                S_int += totA;
+                ip_run = ldexp(__ll2double_rn(S_int), ue);
+            } else {
+                ip_run = __shfl_sync(0xffffffffu, ip_run, 0);
+                if (in_range) S_int = __double2ll_rn(ldexp(ip_run, -ue));
+            }
+            n2q_run += totN;
             remaining -= cnt;
             T_prev = T;
             __syncwarp();
@@ -349,7 +437,7 @@ cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* c
                           double* stats, uint32_t* status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int W = enc_window(D);
-    const size_t per_warp = ((size_t)W * 20 + (size_t)D * 5 + 64 + 15) / 16 * 16;
+    const size_t per_warp = ((size_t)W * 8 + (size_t)D * 5 + 64 + 15) / 16 * 16;
     int warps = (int)((200 * 1024) / per_warp);
     warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
     const size_t smem = per_warp * warps;

@@ -41,6 +41,17 @@ def test_encode_bit_exact_paper_shapes(erq, D, B, n):
     _check_encode(erq, R, B)
 
 
+@pytest.mark.parametrize("B", [4, 6, 8])
+def test_encode_bit_exact_openai3072(erq, B):
+    """The Table 4 shape (D = 3072), with a few very small coordinates planted
+    in half of the rows: their events make FP64 additions of the running
+    <y, o'> round, which the encoder must reproduce in order."""
+    R = S.random_rotated_residuals(10, 3072, 2600 + B)
+    R[::2, 7:10] *= np.float32(3e-5)
+    R[1::4, 100] = np.float32(1e-7)
+    _check_encode(erq, R, B)
+
+
 def test_encode_degenerate_rows(erq):
     """Zero vector (reading R8), single non-zero, all-equal magnitudes (maximal
     event ties), magnitudes spanning 2^100 both ways."""
