@@ -37,7 +37,9 @@ constexpr int TILE_B = BN * BK * 2;                   // 32 KB
 constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;        // A_hi, A_lo, B_hi, B_lo
 constexpr int OFF_BARS = STAGES * STAGE;
 constexpr int NBARS = 2 * STAGES + 4 + 1;
-constexpr int OFF_TMEM = OFF_BARS + NBARS * 8;
+constexpr int OFF_CF = (OFF_BARS + NBARS * 8 + 15) / 16 * 16;   // 4 epilogue warps x 32 column factors (float2)
+constexpr int OFF_EB = OFF_CF + 4 * 32 * 8;                      // 4 epilogue warps x 32 column exponents
+constexpr int OFF_TMEM = OFF_EB + 4 * 32 * 4;
 constexpr int OFF_ABORT = OFF_TMEM + 4;
 constexpr int SMEM = OFF_ABORT + 4 + 1024;
 static_assert(SMEM <= 227 * 1024, "gemm shared memory");
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(gemm2::THREADS, 1)
     } else {
         // ---------------------------------------------------------------- epilogue
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float2* cf = reinterpret_cast<float2*>(sm + OFF_CF) + warp * 32;   // this warp's column factors
+        int* ebs = reinterpret_cast<int*>(sm + OFF_EB) + warp * 32;
         uint32_t acc = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++acc) {
             const int64_t m0 = (tile / ntn) * BM;
@@ -188,14 +192,40 @@ __global__ void __launch_bounds__(gemm2::THREADS, 1)
                     eb = a.eB[nl];
                     if (a.epi == EPI_DIST) cn = a.coln[nl];
                 }
+                // v * 2^ea * 2^eb in two exact power-of-two multiplications, which
+                // equals ldexpf(v, ea + eb) when 2^ea and 2^eb are normal numbers and
+                // v * 2^ea stays normal: v is 0 or at least 2^-48 (a sum of FP16
+                // products) and below 2^40, so ea in [-78, 87] suffices; other rows
+                // and chunks take ldexpf
+                int ebmin = nl < a.N ? eb : 0, ebmax = nl < a.N ? eb : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ebmin = min(ebmin, __shfl_xor_sync(0xffffffffu, ebmin, o));
+                    ebmax = max(ebmax, __shfl_xor_sync(0xffffffffu, ebmax, o));
+                }
+                const bool fast = ebmin >= -126 && ebmax <= 127 && ea >= -78 && ea <= 87;
+                __syncwarp();                                  // the previous chunk's factors are consumed
+                cf[lane] = make_float2(ebmin >= -126 && ebmax <= 127 ? __int_as_float((eb + 127) << 23) : 0.f, cn);
+                ebs[lane] = eb;
+                __syncwarp();
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 float out[32];
+                if (fast) {
+                    const float sa = __int_as_float((ea + 127) << 23);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int ebj = __shfl_sync(0xffffffffu, eb, j);
-                    const float cnj = __shfl_sync(0xffffffffu, cn, j);
-                    const float v = ldexpf(__uint_as_float(r[j]), ea + ebj);
-                    out[j] = a.epi == EPI_DIST ? rn + cnj - 2.f * v : v;
+                    for (int j = 0; j < 32; j += 2) {
+                        const float4 f = *reinterpret_cast<const float4*>(cf + j);   // same address in every lane
+                        const float v0 = (__uint_as_float(r[j]) * sa) * f.x;
+                        const float v1 = (__uint_as_float(r[j + 1]) * sa) * f.z;
+                        out[j] = a.epi == EPI_DIST ? rn + f.y - 2.f * v0 : v0;
+                        out[j + 1] = a.epi == EPI_DIST ? rn + f.w - 2.f * v1 : v1;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float v = ldexpf(__uint_as_float(r[j]), ea + ebs[j]);
+                        out[j] = a.epi == EPI_DIST ? rn + cf[j].y - 2.f * v : v;
+                    }
                 }
                 if (mok && a.gmin) {                           // group minimum over the valid columns
                     float g = INFINITY;

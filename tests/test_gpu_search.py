@@ -235,6 +235,37 @@ def test_probe_ties_take_lower_cluster(erq):
             assert set(got[i].tolist()) <= allowed, (nprobe, i, ref["probe"][i, :nprobe])
 
 
+def test_probe_far_orthogonal_queries(erq):
+    """Queries far from every centroid and orthogonal to all of them, so all
+    centroid distances agree to ~1e-8 relative: the probed clusters must be
+    among the oracle's nearest up to FP32 rounding, for nprobe below and
+    above the number of 32-cluster groups."""
+    D, nl = 64, 64
+    rng = np.random.default_rng(1700)
+    cent = np.zeros((nl, D), np.float32)
+    for j in range(nl):
+        cent[j, 1 + j // 2] = 1.0 if j % 2 == 0 else -1.0
+    assign = np.repeat(np.arange(nl, dtype=np.int32), 40)
+    X = (cent[assign] + 1e-3 * rng.standard_normal((len(assign), D))).astype(np.float32)
+    X[:, 0] = 0.0
+    P = S.random_orthogonal(D, 1701)
+    gx = erq.build_index(to_dev(X), to_dev(P), 4, nl, assign=to_dev(assign))
+    ox = oracle.build_index(X, P, assign, nl, 4)
+    Q = np.zeros((20, D), np.float32)
+    Q[:, 0] = 100.0
+    Q[:, 1:] = 1e-4 * rng.standard_normal((20, D - 1))
+    cd = oracle.centroid_dists(ox["C"], Q)
+    for nprobe in (1, 5, 32):
+        ids, _, cids, _ = gx.search(to_dev(Q), 5, rerank_k=0, nprobe=nprobe, return_candidates=True)
+        torch.cuda.synchronize()
+        kth = np.sort(cd, 1)[:, nprobe - 1]
+        got = cids.cpu().numpy()                      # original row ids of the candidates
+        for i in range(len(Q)):
+            for r in got[i]:
+                c = int(assign[r])
+                assert cd[i, c] <= kth[i] * (1 + 1e-6), (nprobe, i, c, cd[i, c], kth[i])
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_async_mode_and_cuda_graph(erq, precision):
     """ERQ_SEARCH_ASYNC sizes its buffers from host-side bounds (no read-back),
