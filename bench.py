@@ -183,7 +183,8 @@ def profiled_traffic(workload, nprobe, precision, shape):
     try:
         if kv.get("kernel_source_sha256") != scan_source_sha() or int(kv.get("nprobe", -1)) != nprobe:
             return None
-        if (int(kv.get("queries_per_item", -1)), int(kv.get("rows_per_item", -1))) != tuple(shape):
+        rrs = [int(x) for x in kv.get("rows_per_item", "-1").split(",")]
+        if int(kv.get("queries_per_item", -1)) != shape[0] or shape[1] not in rrs:
             return None
         return float(kv["dram_bytes_per_launch"])
     except (KeyError, ValueError):
