@@ -63,6 +63,22 @@ def parse():
 
 
 # ----------------------------------------------------------------------------- data
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def make_workload(args, rank=0):
     cfg = dict(S.WORKLOADS[args.workload])
     if args.nlist:
@@ -477,16 +493,14 @@ def main():
         launches = erq.kernel_launches() - launches0
         ms = e0.elapsed_time(e1) / args.steps
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, world, dev)
             dist.barrier()
         # per-phase device time averaged over the timed searches (CUDA events on the
         # search stream), and the work counters of the last one
         tot, cnt = ix.timing_total()
         phases = {kk: v / max(cnt, 1) for kk, v in tot.items()}
         work = ix.stats()
-        results[prec] = dict(nprobe=p, ms=ms, qps=len(Q) * world / (ms / 1e3), recall=sweep[prec][p],
+        results[prec] = dict(nprobe=p, ms=ms, qps=job_rate(len(Q), world, ms / 1e3), recall=sweep[prec][p],
                              phases=phases, work=work, clocks=clk.summary(), launches=launches,
                              shape=ix.scan_config(), tuned=prec in shapes)
 
@@ -509,10 +523,7 @@ def main():
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
                        async_mode=not args.sync, nprobe_per_query=npr_d)
     e2e_s = (time.perf_counter() - te) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # the same search recorded once into a CUDA graph and replayed (queries in a
     # static buffer; every replay runs the whole path without host work)
@@ -539,11 +550,15 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         gms = e0.elapsed_time(e1) / args.steps
-        graph = {"value": len(Q) * world / (gms / 1e3), "unit": "queries/s", "ms_per_step": gms,
-                 "recall@10": recall(g_ids)}
+        graph = {"ms_per_step": gms, "recall@10": recall(g_ids)}
         del cg
     except Exception as ex:                      # report, do not hide, a capture failure
         graph = {"error": str(ex)[:200]}
+    # every rank takes part in the reduction, also one whose capture failed
+    gmax = max_over_ranks(graph.get("ms_per_step", float("inf")), world, dev)
+    if "ms_per_step" in graph:
+        graph = {"value": job_rate(len(Q), world, gmax / 1e3), "unit": "queries/s", "ms_per_step": gmax,
+                 "recall@10": graph["recall@10"]}
 
     # index-time kernels on a sample: exact rotation (FP64 accumulation) and the
     # Algorithm 1 encoder, rows per second
@@ -621,7 +636,7 @@ def main():
                      for k, v in results.items()},
             "recall_sweep": sweep,
             "roofline": roof,
-            "e2e": {"value": len(Q) * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+            "e2e": {"value": job_rate(len(Q), world, e2e_s), "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
                     "d2h_bytes_per_step": int(len(Q) * args.k * 12)},
             "gpu_launches": R["launches"],
             "graph": graph,
