@@ -467,6 +467,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int maxp = p->probe ? p->nprobe : (nlist == 1 ? 1 : p->nprobe);
     const bool explicit_probe = p->probe != nullptr;
     const int prec = p->precision;
+    const int64_t Dq = (D + 127) / 128 * 128;           // e4m3 query rows, padded to whole 128-byte stages
     // ---- phase A workspace (sizes known on the host)
     // queries per work item of the scan kernels
     int QT = 64, RR = 4096;
@@ -502,14 +503,16 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((int64_t*)nullptr, (size_t)nq * maxp);                         // 17 qlist
         T((uint64_t*)nullptr, (size_t)nq * kp);                          // 18 cand
         T((uint64_t*)nullptr, 1);                                        // 19 (unused)
-        T((__half*)nullptr, prec == ERQ_PREC_FP32 ? 1 : (size_t)nq * D); // 20 Qh
+        T((__half*)nullptr, prec == ERQ_PREC_FP16 ? (size_t)nq * D : 1); // 20 Qh
         T((int32_t*)nullptr, nq);                                        // 21 eQ
         T((uint64_t*)nullptr, prec == ERQ_PREC_FP32 ? 1 : nq);           // 22 query-wide thresholds
         T((__half*)nullptr, (size_t)nq * D);                              // 23 Q hi
         T((__half*)nullptr, (size_t)nq * D);                              // 24 Q lo
         T((float*)nullptr, (!explicit_probe && nlist > 1) ? (size_t)nq * ((nlist + 31) / 32) : 1);  // 25 group minima
+        T((unsigned char*)nullptr, prec == ERQ_PREC_FP8 ? (size_t)nq * Dq : 1);   // 26 e4m3 queries
+        T((float*)nullptr, prec == ERQ_PREC_FP8 ? (size_t)nq : 1);                // 27 their scales
     };
-    void* sl[26];
+    void* sl[28];
     layout(plan, false, sl);
     ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
     Carver cv(ix->ws, ix->ws_bytes);
@@ -564,7 +567,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
                                  D, 0, nullptr, nullptr, nullptr, ix->status, s)) != cudaSuccess)
             return cuda_fail(e, "query rotation");
     }
-    if (prec != ERQ_PREC_FP32 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
+    if (prec == ERQ_PREC_FP8 &&
+        (e = launch_quant_e4m3(Qrot, nq, D, (int)Dq, (unsigned char*)sl[26], (float*)sl[27], s)) != cudaSuccess)
+        return cuda_fail(e, "query e4m3");
+    if (prec == ERQ_PREC_FP16 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
         return cuda_fail(e, "query half");
     ERQ_TRY(mark(1));
     // ---- probe
@@ -662,7 +668,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     ERQ_TRY(mark(3));
     // ---- scan
     ScanLaunch L;
-    L.Qrot = Qrot; L.Qh = sl[20]; L.status = ix->status; L.N = ix->N; L.codes = ix->codes; L.g_const = ix->g_const; L.f_res = ix->f_res; L.list_off = ix->list_off;
+    L.Qrot = Qrot; L.Qh = sl[20]; L.Q8 = sl[26]; L.qscale = (const float*)sl[27]; L.Dq = Dq; L.status = ix->status; L.N = ix->N; L.codes = ix->codes; L.g_const = ix->g_const; L.f_res = ix->f_res; L.list_off = ix->list_off;
     L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
     L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
     L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
@@ -716,6 +722,8 @@ static erq_status validate_search(const erq_index* ix, const float* Q, int64_t n
     if (p->precision < 0 || p->precision > ERQ_PREC_INT8) return fail(ERQ_EINVAL, "erq_search: unknown precision");
     if (p->precision != ERQ_PREC_FP32 && !tc_available(p->precision, ix->D, kp))
         return fail(ERQ_EUNSUPPORTED, "erq_search: tensor-core path unavailable for this D / k'");
+    if (p->precision == ERQ_PREC_FP8 && ix->B > 4)
+        return fail(ERQ_EUNSUPPORTED, "erq_search: fp8 scan needs B <= 4 (centred codes exact in e4m3)");
     if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
         return fail(ERQ_EUNSUPPORTED, "erq_search: k' too large for the FP32 scan");
     return ERQ_OK;

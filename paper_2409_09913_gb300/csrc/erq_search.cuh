@@ -39,6 +39,9 @@ struct PlanArgs {
 struct ScanLaunch {
     const float* Qrot;
     const void* Qh;             // FP16 rotated queries (tensor-core path)
+    const void* Q8;             // e4m3 rotated queries, rows of Dq bytes (kind::f8f6f4 path)
+    const float* qscale;        // their per-query power-of-two scales
+    int64_t Dq;
     uint32_t* status;
     int64_t N;
     const uint8_t* codes;
@@ -84,6 +87,7 @@ bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
                                const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D, int B,
                                uint64_t* codes_p, float4* rowmeta, cudaStream_t s);
+cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           cudaStream_t s);

@@ -118,7 +118,8 @@ struct Cfg {
         static constexpr int cnt = ids + EB * MR * 4;              // [QN] int   list fill
         static constexpr int tau = cnt + QN * 4;                   // [QN] u64   admission threshold
         static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
-        static constexpr int bars = tq + 2 * QN * 8;               // mbarriers (8 B each)
+        static constexpr int qsc = tq + 2 * QN * 8;                // 2 x [QN] f32 query scales (e4m3 path)
+        static constexpr int bars = qsc + 2 * QN * 4;              // mbarriers (8 B each)
         static constexpr int nbars = 4 * LS + 4 + 2 * MS + 4 + 1;
         static constexpr int tmem_slot = bars + nbars * 8;
         static constexpr int abort_flag = tmem_slot + 4;
@@ -203,8 +204,18 @@ __device__ __forceinline__ void unpack_codes_b(int B, const unsigned char* base,
     }
 }
 
+// Two FP16 values holding odd integers |x| <= 15 (exact in e4m3) -> their
+// e4m3 encodings in bytes 0 and 2: the e4m3 exponent is the FP16 one minus 8
+// (biases 15 and 7) and the three mantissa bits are the FP16 mantissa's top
+// three (the lower seven are zero for these values).
+__device__ __forceinline__ uint32_t half2_to_e4m3_pair(uint32_t w) {
+    return (((w >> 7) & 0x00FF00FFu) - 0x00400040u) | ((w >> 8) & 0x00800080u);
+}
+
 struct Args {
-    const __half* Qh;             // [nq][D] FP16 rotated queries
+    const unsigned char* Qb;      // [nq] rows of the query operand: FP16 (2D bytes) or e4m3 (qrow_bytes)
+    int64_t qrow_bytes;
+    const float* qscale;          // e4m3 path: per-query power-of-two scale of the e4m3 values
     const int4* itemd;            // [items] {rb0 lo, rb0 hi, rows, queries}
     const int4* itemq;            // [items][QN] {query row or -1, dqc bits, output list index lo, hi}
     const float4* rowmeta;        // [N] {g, f_res / 2, id bits, 0} in stored-row order
@@ -287,7 +298,11 @@ __device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, i
     return th;
 }
 
-template <class C>
+// F8: queries in e4m3 with a per-query scale, codes in e4m3 (B <= 4),
+// tcgen05.mma kind::f8f6f4 (K = 32); a stage then covers 128 coordinates (two
+// packed 64-coordinate blocks), which occupy the same 128 bytes per row in
+// tensor memory and in the query tile as 64 FP16 coordinates.
+template <class C, bool F8>
 __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
     constexpr int QN = C::QN, KC = C::KC, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
     constexpr int RP = C::RP, LS = C::LS, EB = C::EB, TILE_RAW = C::TILE_RAW;
@@ -312,7 +327,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     const uint32_t done_bar = smem_u32(&bars[4 * LS + 4 + 2 * MS + 4]);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D = a.D, nkb = D / KB;
+    const int D = a.D;
+    const int nkb = F8 ? (D + 2 * KB - 1) / (2 * KB) : D / KB;   // stages per row group (128 bytes per row)
     const int64_t nitems = *a.n_items;
 
     if (tid == 0) {
@@ -379,6 +395,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             for (int j = 0; j < QN / 32; ++j) {
                 iq[32 * j + lane] = qv[j];
                 tqs[32 * j + lane] = qv[j].x >= 0 ? __ldcg(a.tq + qv[j].x) : kEmptyKey;
+                if (F8) reinterpret_cast<float*>(sm + Smem::qsc)[ib * QN + 32 * j + lane] = qv[j].x >= 0 ? a.qscale[qv[j].x] : 0.f;
             }
             if (lane == 0) s_idesc[ib] = dcur;
             mbar_arrive(full_item0 + 8 * ib);
@@ -401,10 +418,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     const int s = g % LS;
                     if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)(nb * (MR / 32) * 256 * a.B));
-                        for (int bb = 0; bb < nb; ++bb)
-                            tma_load_3d_hint(smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB), &codes_map, 0, kb,
-                                             (int)((rb0 + r + bb * MR) >> 5), full_load0 + 8 * s, pol_codes);
+                        const uint32_t blk = (uint32_t)(MR / 32) * 256 * a.B;   // one packed block of 128 rows
+                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)nb * blk * (F8 ? 2u : 1u));
+                        for (int bb = 0; bb < nb; ++bb) {
+                            const uint32_t dst = smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB);
+                            const int tile = (int)((rb0 + r + bb * MR) >> 5);
+                            // (the second block of the last F8 stage may lie past D: the TMA fills zeros)
+                            tma_load_3d_hint(dst, &codes_map, 0, F8 ? 2 * kb : kb, tile, full_load0 + 8 * s, pol_codes);
+                            if (F8)
+                                tma_load_3d_hint(dst + blk, &codes_map, 0, 2 * kb + 1, tile, full_load0 + 8 * s, pol_codes);
+                        }
                     }
                     __syncwarp();
                 }
@@ -437,11 +460,11 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             const int nq4 = npad_of(d.w) / 4;
             const int nsteps = ((d.z + RP * MR - 1) / (RP * MR)) * nkb;
             // this lane gathers 16-byte chunk ch of query rows (lane >> 3) + 4 (gi + NG i)
-            const __half* qp[QN / 4 / NG];
+            const unsigned char* qp[QN / 4 / NG];
 #pragma unroll
             for (int i = 0; i < QN / 4 / NG; ++i) {
                 const int qrow = iq[(lane >> 3) + 4 * (gi + NG * i)].x;
-                qp[i] = qrow >= 0 ? a.Qh + (int64_t)qrow * D + ch * 8 : nullptr;
+                qp[i] = qrow >= 0 ? a.Qb + (int64_t)qrow * a.qrow_bytes + ch * 16 : nullptr;
             }
             for (int t = 0; t < nsteps; ++t, ++g) {
                 const int s = g % LS, kb = t % nkb;
@@ -452,7 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     if (gi + NG * i < nq4) {
                         const int qq = (lane >> 3) + 4 * (gi + NG * i);
                         const uint32_t dst = qs + qq * 128 + ((ch ^ (qq & 7)) << 4);
-                        cp_async16_hint(dst, qp[i] ? (const void*)(qp[i] + kb * KB) : (const void*)a.Qh,
+                        cp_async16_hint(dst, qp[i] ? (const void*)(qp[i] + kb * 128) : (const void*)a.Qb,
                                         qp[i] ? 16u : 0u, pol_q);
                     }
                 }
@@ -497,7 +520,21 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 tc_fence_after();
                 for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
                     uint32_t w[32];
-                    unpack_codes_b(B, sm + Smem::raw + s * TILE_RAW + bb * MR * KB + roff, w);
+                    const unsigned char* src = sm + Smem::raw + s * TILE_RAW + bb * MR * KB + roff;
+                    if (F8) {
+                        // two packed blocks -> 128 e4m3 codes, four per column
+#pragma unroll
+                        for (int hb = 0; hb < 2; ++hb) {
+                            uint32_t h[32];
+                            unpack_codes_b(B, src + hb * (MR / 32) * 256 * B, h);
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                w[16 * hb + c] = __byte_perm(half2_to_e4m3_pair(h[2 * c]),
+                                                             half2_to_e4m3_pair(h[2 * c + 1]), 0x6420u);
+                        }
+                    } else {
+                        unpack_codes_b(B, src, w);
+                    }
                     ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + bb) * (KB / 2), w);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -538,8 +575,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                             const uint32_t ta = tmem + ACOL + (s * RP + mrb) * (KB / 2);
                             const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
 #pragma unroll
-                            for (int k = 0; k < KB / 16; ++k)
-                                mma_f16_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                            for (int k = 0; k < KB / 16; ++k) {         // 32 bytes of K per instruction
+                                if (F8) mma_f8_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                                else mma_f16_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                            }
                         }
                         mma_commit(empty_load0 + 8 * s);     // codes, query tile and TMEM stage free
                         if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
@@ -608,8 +647,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                         uint32_t v[32];
                         ERQ_TMEM_LD32(tmem + lane_base + buf * (RP * QN) + bb * QN + cc, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
+                            const float* sc = reinterpret_cast<const float*>(sm + Smem::qsc) + ib * QN + cc;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+                            for (int i = 0; i < 32; ++i)
+                                est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]) * sc[i], mt.x);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+                        }
                     }
                     tc_fence_before();
                 }
@@ -684,7 +730,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
 }
 
 bool tc_available(int precision, int D, int kp) {
-    return precision == ERQ_PREC_FP16 && D % KB == 0 && kp <= KCAP;
+    return (precision == ERQ_PREC_FP16 || precision == ERQ_PREC_FP8) && D % KB == 0 && kp <= KCAP;
 }
 
 // Work-item query counts the tensor-core scan is built for, given k'.
@@ -842,10 +888,10 @@ static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class C>
+template <class C, bool F8>
 static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStream_t s) {
     const int smem = C::Smem::total;
-    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
     CUtensorMap map;
@@ -853,7 +899,7 @@ static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStr
         !make_codes_map(&map, L.codes_p, L.Np, L.D, L.B))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     count_launch();
-    scan_tc_kernel<C><<<L.grid, THREADS, smem, s>>>(map, a);
+    scan_tc_kernel<C, F8><<<L.grid, THREADS, smem, s>>>(map, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc launch");
     return ERQ_OK;
@@ -861,17 +907,94 @@ static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStr
 
 erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!tc_available(precision, L.D, L.kp))
-        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 and k' <= 128");
-    if (!L.Qh) return fail(ERQ_EINVAL, "tensor-core scan: FP16 queries missing");
+        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 or fp8 and k' <= 128");
+    const bool f8 = precision == ERQ_PREC_FP8;
+    if (f8 && L.B > 4) return fail(ERQ_EUNSUPPORTED, "tensor-core scan: e4m3 holds the centred codes only for B <= 4");
+    if (!(f8 ? (L.Q8 && L.qscale) : L.Qh != nullptr)) return fail(ERQ_EINVAL, "tensor-core scan: queries missing");
     if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
     tc::Args a;
-    a.Qh = (const __half*)L.Qh; a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
+    a.Qb = f8 ? (const unsigned char*)L.Q8 : (const unsigned char*)L.Qh;
+    a.qrow_bytes = f8 ? L.Dq : 2 * (int64_t)L.D;
+    a.qscale = L.qscale;
+    a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
     a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
     a.tq = L.tq;
     if (!scan_tc_shape_ok(L.qn, L.kp)) return fail(ERQ_EINVAL, "tensor-core scan: no kernel for this item shape");
-    if (L.qn == CfgWide::QN) return scan_tc_launch<CfgWide>(L, a, s);
-    if (L.qn == CfgSmall::QN) return scan_tc_launch<CfgSmall>(L, a, s);
-    return scan_tc_launch<CfgLarge>(L, a, s);
+    if (L.qn == CfgWide::QN) return f8 ? scan_tc_launch<CfgWide, true>(L, a, s) : scan_tc_launch<CfgWide, false>(L, a, s);
+    if (L.qn == CfgSmall::QN)
+        return f8 ? scan_tc_launch<CfgSmall, true>(L, a, s) : scan_tc_launch<CfgSmall, false>(L, a, s);
+    return f8 ? scan_tc_launch<CfgLarge, true>(L, a, s) : scan_tc_launch<CfgLarge, false>(L, a, s);
+}
+
+// Rotated queries -> e4m3 for the kind::f8f6f4 scan.  Per query row a power of
+// two s = 2^(floor(log2 max|q'|) - 7) puts the largest magnitude in [128, 256)
+// (e4m3's largest finite value is 448); every q'_i / s (exact) is rounded to
+// the nearest e4m3 value, ties to even, from its FP32 bits: for |y| >= 2^-6 the
+// 23-bit mantissa keeps its top 3 bits (carry into the exponent on overflow),
+// below it y is a multiple of 2^-9 after rounding |y| * 2^9 to an integer
+// (8 then being the smallest normal's code).  Columns D .. Dq-1 are zero.
+// One warp per query row.
+__device__ __forceinline__ uint32_t e4m3_rn(float y) {
+    const uint32_t bits = __float_as_uint(y);
+    const uint32_t sign = (bits >> 31) << 7;
+    const int ex = (int)((bits >> 23) & 0xffu) - 127;
+    const uint32_t mant = bits & 0x7fffffu;
+    uint32_t code;
+    if (ex >= -6) {
+        uint32_t r = mant >> 20;
+        const uint32_t rem = mant & 0xfffffu;
+        if (rem > 0x80000u || (rem == 0x80000u && (r & 1u))) ++r;
+        int e4 = ex + 7;
+        if (r == 8u) {
+            r = 0u;
+            ++e4;
+        }
+        code = ((uint32_t)e4 << 3) | r;
+    } else if (ex >= -10) {
+        const int sh = 14 - ex;                        // 21 .. 24
+        const uint32_t full = mant | 0x800000u;
+        uint32_t q = full >> sh;
+        const uint32_t rem = full & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        if (rem > half || (rem == half && (q & 1u))) ++q;
+        code = q;
+    } else {
+        code = 0u;                                     // below half of the smallest subnormal
+    }
+    return sign | code;
+}
+
+__global__ void quant_e4m3_kernel(const float* __restrict__ X, int64_t n, int D, int Dq, unsigned char* __restrict__ Y,
+                                  float* __restrict__ scale) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float* x = X + r * D;
+    float m = 0.f;
+    for (int i = lane; i < D; i += 32) m = fmaxf(m, fabsf(x[i]));
+    m = warp_max(m);
+    int e = 0;
+    if (m > 0.f) {
+        frexpf(m, &e);                                 // m in [2^(e-1), 2^e)
+        e -= 8;                                        // m / 2^e in [128, 256)
+    }
+    e = max(-126, min(127, e));
+    const float inv = __int_as_float((127 - e) << 23), s = __int_as_float((127 + e) << 23);
+    if (lane == 0) scale[r] = m > 0.f ? s : 1.f;
+    unsigned char* y = Y + r * Dq;
+    for (int i = lane * 4; i < Dq; i += 128) {
+        uint32_t w = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (i + j < D) w |= e4m3_rn(x[i + j] * inv) << (8 * j);
+        *reinterpret_cast<uint32_t*>(y + i) = w;
+    }
+}
+
+cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    quant_e4m3_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, s>>>(x, n, D, Dq, y, scale);
+    return cudaGetLastError();
 }
 
 // FP32 -> FP16 (round to nearest) of the rotated queries.

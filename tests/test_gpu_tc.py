@@ -201,3 +201,62 @@ def test_tc_scan_every_code_width(erq, B):
     bound = _bound(ox, Q, gid) + 2e-5 * (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))
     viol = np.abs(cest.cpu().numpy().astype(np.float64) - oest) > bound
     assert not viol.any(), f"{viol.sum()} estimates outside the FP16 bound"
+
+
+def _bound_fp8(ox, Q, ids):
+    """Per-result bound of the e4m3 query rounding: every q'_i / s is rounded to
+    the nearest e4m3 value (relative 2^-4, or absolute 2^-10 in the subnormal
+    range), s = 2^(floor(log2 max|q'|) - 7) per query (taken twice as large here
+    to cover the FP32 maximum landing on the other side of a power of two)."""
+    B = ox["B"]
+    qp = Q.astype(np.float64) @ ox["P"].astype(np.float64)
+    s = 2.0 ** (np.floor(np.log2(np.abs(qp).max(1))) - 6)
+    _, f_res = oracle.stored_factors(ox["stats"])
+    rows = ox["row_of"][np.maximum(ids, 0)]
+    y2 = np.abs(2.0 * ox["codes"][rows].astype(np.float64) - (2 ** B - 1))   # [nq, k, D]
+    t = np.einsum("qkd,qd->qk", y2, np.abs(qp)) * 2.0 ** -4 + y2.sum(-1) * (s[:, None] * 2.0 ** -10)
+    return 0.5 * np.abs(f_res[rows]).astype(np.float64) * t
+
+
+@pytest.mark.parametrize("D,B,kp", [(128, 4, 32), (960, 4, 24), (128, 2, 100), (192, 3, 32)])
+def test_fp8_scan_within_e4m3_bound(erq, D, B, kp):
+    """kind::f8f6f4 scan (e4m3 codes and queries, 128 coordinates per stage; D =
+    960 and 192 end in half a stage): every candidate estimate lies within the
+    query-rounding bound of the oracle's exact estimate, and the re-ranked
+    top-10 equals the oracle's exact re-rank of the same candidates."""
+    X, P, gx, ox = _index(erq, 12000, D, B, 32, 3900 + D + B)
+    Q, _ = S.mixture(400, D, 16, 3901 + D, comp_seed=3900 + D + B, scale="aniso")
+    probe = S.random_probe_lists(400, 32, 6, 3902 + D)
+    ids, dists, cids, cest = gx.search(to_dev(Q), 10, rerank_k=kp, probe=to_dev(probe), nprobe=6,
+                                       precision="fp8", return_candidates=True)
+    torch.cuda.synchronize()
+    gid = cids.cpu().numpy()
+    assert (gid >= 0).all()
+    oest = oracle.estimate_rows(ox, Q, gid)
+    bound = _bound_fp8(ox, Q, gid) + 2e-5 * (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))
+    viol = np.abs(cest.cpu().numpy().astype(np.float64) - oest) > bound
+    assert not viol.any(), f"{viol.sum()} estimates outside the e4m3 bound"
+    # the exact re-rank of each query's candidate set is the oracle's
+    d_or = np.stack([((X[gid[i]].astype(np.float64) - Q[i].astype(np.float64)) ** 2).sum(1) for i in range(len(Q))])
+    order = np.lexsort((gid, d_or), axis=1)[:, :10]
+    ref_ids = np.take_along_axis(gid, order, 1)
+    got = ids.cpu().numpy()
+    assert (np.sort(got, 1) == np.sort(ref_ids, 1)).mean() > 0.99
+
+
+def test_fp8_recall_close_to_fp32(erq):
+    X, P, gx, ox = _index(erq, 30000, 128, 4, 32, 4000)
+    Q, _ = S.mixture(500, 128, 16, 4001, comp_seed=4000, scale="aniso")
+    a_ids, _ = gx.search(to_dev(Q), 10, rerank_k=40, nprobe=6, precision="fp32")
+    b_ids, _ = gx.search(to_dev(Q), 10, rerank_k=40, nprobe=6, precision="fp8")
+    gt, _ = oracle.exact_knn(X, Q, 10)
+    rec = lambda ids: np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy(), gt)])
+    ra, rb = rec(a_ids), rec(b_ids)
+    assert rb >= ra - 0.01, (ra, rb)
+
+
+def test_fp8_rejects_wide_codes(erq):
+    X, P, gx, ox = _index(erq, 3000, 128, 5, 8, 4100)
+    Q = to_dev(S.mixture(4, 128, 16, 4101, comp_seed=4100, scale="aniso")[0])
+    with pytest.raises(erq.ErqError, match="B <= 4"):
+        gx.search(Q, 10, rerank_k=20, nprobe=2, precision="fp8")
