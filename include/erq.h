@@ -52,8 +52,10 @@ typedef enum {
     ERQ_PREC_FP32 = 0,       /* CUDA-core FP32 FFMA scan (reference GPU path)           */
     ERQ_PREC_FP16 = 1,       /* tcgen05 kind::f16: codes exact, rotated query in FP16,
                                 FP32 accumulation in tensor memory                       */
-    ERQ_PREC_FP8 = 2,        /* tcgen05 kind::f8f6f4: e4m3 query (per-query scale,
-                                hi+lo split), e4m3 codes, FP32 accumulation              */
+    ERQ_PREC_FP8 = 2,        /* tcgen05 kind::f8f6f4: query rounded to e4m3 after a
+                                per-query power-of-two scale, centred codes in e4m3
+                                (exact; needs B <= 4, else ERQ_EUNSUPPORTED), FP32
+                                accumulation in tensor memory                            */
     ERQ_PREC_INT8 = 3        /* int8 tensor MMA: unavailable on sm_103a (ptxas rejects
                                 tcgen05 kind::i8) -> ERQ_EUNSUPPORTED                    */
 } erq_precision;
