@@ -275,7 +275,7 @@ def run_backward(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     from paper_2409_09913_gb300 import build as erq_build
-    erq_build.build()
+    erq_build.build(checked=os.environ.get("ERQ_CHECKED") == "1")
     from paper_2409_09913_gb300 import erq
     cfg, X, Q, P = make_workload(args)
     args.B = args.B or cfg["B"]
@@ -346,7 +346,7 @@ def run_encoder_sweep(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     from paper_2409_09913_gb300 import build as erq_build
-    erq_build.build()
+    erq_build.build(checked=os.environ.get("ERQ_CHECKED") == "1")
     from paper_2409_09913_gb300 import erq
     d = 3072
     n = args.n or 65_536
@@ -394,7 +394,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2409_09913_gb300 import build as erq_build
-    erq_build.build()
+    erq_build.build(checked=os.environ.get("ERQ_CHECKED") == "1")
     from paper_2409_09913_gb300 import erq
 
     t0 = time.perf_counter()

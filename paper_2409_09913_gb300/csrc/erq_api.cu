@@ -108,7 +108,11 @@ erq_status check_status(erq_index* ix, cudaStream_t s) {
         if (st & kStatusTimeout) return fail(ERQ_ETIMEOUT, "a device-side wait ran out of iterations");
         if (st & kStatusRange)
             return fail(ERQ_EUNSUPPORTED, "a rotated residual has a non-zero coordinate below 2^-118 of its largest");
-        return fail(ERQ_EINVAL, "a device-side bound check failed (cluster id, probe id, nprobe or row id out of range)");
+        char msg[160];
+        snprintf(msg, sizeof(msg),
+                 "a device-side bound check failed (cluster id, probe id, nprobe or row id out of range; "
+                 "checked-build sites 0x%06x)", st >> 8);
+        return fail(ERQ_EINVAL, msg);
     }
     return ERQ_OK;
 }
@@ -607,6 +611,14 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.corder = ix->corder;
     pa.npr = npr;
     pa.status = ix->status;
+    DevChecks ck;
+    ck.status = ix->status;
+    ck.qlist = nq * (int64_t)maxp;
+    ck.rows = ix->N;
+    ck.nlist = nlist;
+    ck.items = 0;                 // set once phase B is sized; the plan kernels below use qlist only
+    ck.lists = 0;
+    pa.ck = ck;
     if ((e = launch_plan(pa, s)) != cudaSuccess) return cuda_fail(e, "plan");
     // dqc needs the validated probe ids
     if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
@@ -659,11 +671,14 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int4* itemd = cb.take<int4>(tcp ? nitems : 0);
     int4* itemq = cb.take<int4>(tcp ? nitems * QT : 0);
     ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + nlist, 8, cudaMemcpyDeviceToDevice, s));
+    ck.items = nitems;
+    ck.lists = Ltot;
+    pa.ck = ck;
     if (Ltot > 0) ERQ_CHECK_CUDA(cudaMemsetAsync(inter_cnt, 0, sizeof(int32_t) * Ltot, s));
 
     if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
     if (tcp && (e = launch_item_tables(items, n_items_d, nitems, ix->list_off, ix->poff, pa.qoff, pa.qlist, dqc,
-                                       pa.qbase, pa.slot_off, maxp, RR, QT, itemd, itemq, pa.stats, s)) != cudaSuccess)
+                                       pa.qbase, pa.slot_off, maxp, RR, QT, itemd, itemq, pa.stats, ck, s)) != cudaSuccess)
         return cuda_fail(e, "item tables");
     ERQ_TRY(mark(3));
     // ---- scan
@@ -674,6 +689,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
     L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_p = ix->codes_p; L.Np = ix->Np;
     L.tq = (unsigned long long*)sl[22];
+    L.ck = ck;
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -686,10 +702,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     }
     ERQ_TRY(mark(4));
     // ---- merge, re-rank
-    if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, lstride, cand, s)) != cudaSuccess)
+    if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, lstride, cand, ck, s)) != cudaSuccess)
         return cuda_fail(e, "merge");
     ERQ_TRY(mark(5));
-    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ids, dists, p->cand_ids, p->cand_est,
+    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ids, dists, p->cand_ids, p->cand_est, ck,
                            s)) != cudaSuccess)
         return cuda_fail(e, "rerank");
     ERQ_TRY(mark(6));

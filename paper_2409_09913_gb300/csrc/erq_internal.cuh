@@ -39,6 +39,27 @@ erq_status cuda_fail(cudaError_t e, const char* what);
 // Device status word bits (written by kernels, read by erq_index_status).
 enum : uint32_t { kStatusTimeout = 1u, kStatusBounds = 2u, kStatusRange = 4u };
 
+// Checked build (-DERQ_CHECKS): bound checks on indices that kernels derive
+// from device data.  A failed check sets kStatusBounds and bit 8 + site of the
+// status word and the access is skipped (no trap); the next call that reads
+// the status reports the sites.  In the normal build the checks compile away.
+#ifdef ERQ_CHECKS
+#define ERQ_DCHECK(cond, status, site) \
+    ((cond) || (atomicOr((status), kStatusBounds | (1u << (8 + (site)))), false))
+#else
+#define ERQ_DCHECK(cond, status, site) true
+#endif
+
+// Limits the checked build compares device-derived indices against.
+struct DevChecks {
+    uint32_t* status = nullptr;
+    int64_t lists = 0;       // candidate lists allocated (per-(query, item) lists)
+    int64_t items = 0;       // work items allocated
+    int64_t qlist = 0;       // entries of the per-cluster query lists
+    int64_t rows = 0;        // stored rows N
+    int nlist = 0;
+};
+
 // ---------------------------------------------------------------- keys
 // Order-preserving map of an FP32 value to uint32 (NaN sorts last).
 __host__ __device__ inline uint32_t float_to_ordered(float f) {

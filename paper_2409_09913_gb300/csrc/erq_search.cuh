@@ -32,6 +32,7 @@ struct PlanArgs {
     int64_t* item_off;          // [nlist+1]
     int64_t* qlist;             // [nq*maxp]
     uint32_t* status;
+    DevChecks ck;
     unsigned long long* stats;  // [4]: (query, candidate) pairs, rows of distinct probed clusters,
                                 //      tensor-core row blocks, row blocks x padded queries (item tables)
 };
@@ -67,6 +68,7 @@ struct ScanLaunch {
     int maxp, D, B, kp, RR;
     int qn;                     // tensor-core path: queries per work item (32, 64 or 128)
     int grid;
+    DevChecks ck;
 };
 
 cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
@@ -77,12 +79,12 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
 size_t scan_fp32_smem(int kp);
 int merge_sortn(int kp, int lstride);
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
-                         int lstride, uint64_t* cand, cudaStream_t s);
+                         int lstride, uint64_t* cand, const DevChecks& ck, cudaStream_t s);
 int scan_list_stride(int precision, int kp, int qn);
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
                                const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
-                               int4* itemq, unsigned long long* stats, cudaStream_t s);
+                               int4* itemq, unsigned long long* stats, const DevChecks& ck, cudaStream_t s);
 bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
                                const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D, int B,
@@ -90,7 +92,7 @@ cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float
 cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
-                          cudaStream_t s);
+                          const DevChecks& ck, cudaStream_t s);
 cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
                             const erq_index* ix, float* est, cudaStream_t s);
 cudaError_t launch_backward_gather(const float* Q, const int64_t* ids, const float* gs, int64_t nq, int nc,

@@ -225,6 +225,7 @@ struct Args {
     unsigned long long* tq;       // [nq] query-wide admission threshold (k'-th key of a finished item)
     uint32_t* status;
     int D, B, kp;
+    DevChecks ck;
 };
 
 __device__ __forceinline__ int npad_of(int nqi) { return nqi <= 16 ? 16 : (nqi + 15) & ~15; }
@@ -329,7 +330,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D;
     const int nkb = F8 ? (D + 2 * KB - 1) / (2 * KB) : D / KB;   // stages per row group (128 bytes per row)
-    const int64_t nitems = *a.n_items;
+    int64_t nitems = *a.n_items;
+    if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 7)) nitems = 0;   // uniform: every thread reads it
 
     if (tid == 0) {
         for (int s = 0; s < LS; ++s) {
@@ -712,6 +714,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     if (lane == 0) atomicMin(a.tq + iq[q].x, (unsigned long long)th);
                 }
                 const int64_t L = (int64_t)(uint32_t)iq[q].z | ((int64_t)iq[q].w << 32);
+                if (!ERQ_DCHECK(L >= 0 && L < a.ck.lists && cnt >= 0 && cnt <= KC, a.ck.status, 6)) continue;
                 uint64_t* dst = a.inter + L * KC;
                 for (int e = lane; e < cnt; e += 32) dst[e] = lists[q * KC + e];
                 if (lane == 0) a.inter_cnt[L] = cnt;
@@ -755,10 +758,11 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
                                    const float* __restrict__ dqc, const int64_t* __restrict__ qbase,
                                    const int32_t* __restrict__ slot_off, int maxp, int RR, int QN,
                                    int4* __restrict__ itemd, int4* __restrict__ itemq,
-                                   unsigned long long* __restrict__ stats) {
+                                   unsigned long long* __restrict__ stats, DevChecks ck) {
     const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (it >= *n_items) return;
+    if (!ERQ_DCHECK(it < ck.items, ck.status, 8)) return;
     const int4 w = items[it];
     const int c = w.x;
     const int64_t qb = qoff[c] + (int64_t)w.y * QN;
@@ -775,7 +779,7 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
     }
     for (int q = lane; q < QN; q += 32) {
         int4 v = make_int4(-1, 0, 0, 0);
-        if (q < nqi) {
+        if (q < nqi && ERQ_DCHECK(qb + q >= 0 && qb + q < ck.qlist, ck.status, 8)) {
             const int64_t e = qlist[qb + q];
             const int64_t qr = e / maxp;
             const int64_t L = qbase[qr] + slot_off[e] + w.z;
@@ -788,11 +792,11 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
                                const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
-                               int4* itemq, unsigned long long* stats, cudaStream_t s) {
+                               int4* itemq, unsigned long long* stats, const DevChecks& ck, cudaStream_t s) {
     if (items_bound <= 0) return cudaSuccess;
     count_launch();
     item_tables_kernel<<<(unsigned)ceil_div(items_bound, 8), 256, 0, s>>>(
-        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, qn, itemd, itemq, stats);
+        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, qn, itemd, itemq, stats, ck);
     return cudaGetLastError();
 }
 
@@ -913,6 +917,7 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!(f8 ? (L.Q8 && L.qscale) : L.Qh != nullptr)) return fail(ERQ_EINVAL, "tensor-core scan: queries missing");
     if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
     tc::Args a;
+    a.ck = L.ck;
     a.Qb = f8 ? (const unsigned char*)L.Q8 : (const unsigned char*)L.Qh;
     a.qrow_bytes = f8 ? L.Dq : 2 * (int64_t)L.D;
     a.qscale = L.qscale;

@@ -213,18 +213,18 @@ __global__ void plan_cluster_kernel(const int32_t* __restrict__ cnt_c, const int
 
 __global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t nq, int maxp,
                                     const int64_t* __restrict__ qoff, int32_t* __restrict__ pos_c,
-                                    int64_t* __restrict__ qlist) {
+                                    int64_t* __restrict__ qlist, DevChecks ck) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nq * maxp) return;
     const int c = probe_c[t];
     if (c < 0) return;
     const int p = atomicAdd(&pos_c[c], 1);
-    qlist[qoff[c] + p] = t;  // t = q * maxp + slot
+    if (ERQ_DCHECK(qoff[c] + p >= 0 && qoff[c] + p < ck.qlist, ck.status, 9)) qlist[qoff[c] + p] = t;  // t = q * maxp + slot
 }
 
 __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64_t* __restrict__ list_off,
                                   const int64_t* __restrict__ item_off, const int32_t* __restrict__ corder,
-                                  int nlist, int QT, int RR, int4* __restrict__ items) {
+                                  int nlist, int QT, int RR, int4* __restrict__ items, DevChecks ck) {
     const int rk = blockIdx.x * blockDim.x + threadIdx.x;
     if (rk >= nlist) return;
     const int c = corder ? corder[rk] : rk;
@@ -234,6 +234,7 @@ __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64
     const int nranges = (int)((size + RR - 1) / RR);
     int64_t w = b;
     const int nchunks = (int)((cnt64[c] + QT - 1) / QT);
+    if (!ERQ_DCHECK(b >= 0 && e <= ck.items, ck.status, 10)) return;
     for (int r = 0; r < nranges; ++r)
         for (int ch = 0; ch < nchunks; ++ch) items[w++] = make_int4(c, ch, r, 0);
 }
@@ -264,6 +265,7 @@ struct ScanArgs {
     uint64_t* inter;            // [L][kp]
     int32_t* inter_cnt;         // [L]
     int maxp, D, B, kp, RR;
+    DevChecks ck;
 };
 
 __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
@@ -285,7 +287,8 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
     const int tq = tid % 16, tr = tid / 16;
     const int D = a.D;
     const float off = (float)((1 << a.B) - 1);
-    const int64_t nitems = *a.n_items;
+    int64_t nitems = *a.n_items;
+    if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 5)) nitems = 0;
 
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 item = a.items[it];
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
             __syncthreads();
         }
         // write the item's lists
-        if (tid < nqi) {
+        if (tid < nqi && ERQ_DCHECK(s_list[tid] >= 0 && s_list[tid] < a.ck.lists, a.ck.status, 4)) {
             const int hs = s_hsize[tid];
             const int64_t L = s_list[tid];
             uint64_t* dst = a.inter + L * a.kp;
@@ -447,7 +450,7 @@ __device__ void block_bitonic_u64(uint64_t* v, int n) {
 __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__ inter,
                                                     const int32_t* __restrict__ inter_cnt,
                                                     const int64_t* __restrict__ qbase, int kp, int lstride,
-                                                    int sortn, uint64_t* __restrict__ cand) {
+                                                    int sortn, uint64_t* __restrict__ cand, DevChecks ck) {
     extern __shared__ uint64_t buf[];  // [sortn]
     __shared__ int s_fill;
     __shared__ uint64_t s_tau;         // entries >= s_tau cannot enter the top k'
@@ -457,7 +460,9 @@ __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__
     if (threadIdx.x == 0) { s_fill = kp; s_tau = kEmptyKey; }
     __syncthreads();
     for (int64_t L = L0; L < L1; ++L) {
-        const int n = inter_cnt[L];
+        if (!ERQ_DCHECK(L >= 0 && L < ck.lists, ck.status, 0)) break;
+        int n = inter_cnt[L];
+        if (!ERQ_DCHECK(n >= 0 && n <= lstride, ck.status, 0)) n = 0;
         if (s_fill + n > sortn) {          // uniform: s_fill is shared
             block_bitonic_u64(buf, sortn);
             for (int i = kp + threadIdx.x; i < sortn; i += blockDim.x) buf[i] = kEmptyKey;
@@ -482,15 +487,17 @@ __global__ void __launch_bounds__(256) merge_kernel(const uint64_t* __restrict__
 __global__ void __launch_bounds__(256) merge_warp_kernel(const uint64_t* __restrict__ inter,
                                                          const int32_t* __restrict__ inter_cnt,
                                                          const int64_t* __restrict__ qbase, int64_t nq, int kp,
-                                                         int lstride, uint64_t* __restrict__ cand) {
+                                                         int lstride, uint64_t* __restrict__ cand, DevChecks ck) {
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= nq) return;
     const int64_t L0 = qbase[q], L1 = qbase[q + 1];
     uint64_t list = kEmptyKey, th = kEmptyKey;
     for (int64_t Lb = L0; Lb < L1; Lb += 32) {
+        if (!ERQ_DCHECK(Lb >= 0 && L1 <= ck.lists, ck.status, 1)) break;
         const int nl = (int)imin64(32, L1 - Lb);
-        const int myn = lane < nl ? inter_cnt[Lb + lane] : 0;     // counts of up to 32 lists at once
+        int myn = lane < nl ? inter_cnt[Lb + lane] : 0;           // counts of up to 32 lists at once
+        if (!ERQ_DCHECK(myn >= 0 && myn <= lstride, ck.status, 1)) myn = 0;
         for (int i = 0; i < nl; ++i) {
             const int n = __shfl_sync(0xffffffffu, myn, i);
             const uint64_t* src = inter + (Lb + i) * lstride;
@@ -513,7 +520,8 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const uint64_t* __restr
 __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict__ cand, int kp, const float* __restrict__ X,
                                                      const float* __restrict__ Q, int D, int k, int do_rerank,
                                                      int sortn, int64_t* __restrict__ ids, float* __restrict__ dists,
-                                                     int64_t* __restrict__ cand_ids, float* __restrict__ cand_est) {
+                                                     int64_t* __restrict__ cand_ids, float* __restrict__ cand_est,
+                                                     DevChecks ck) {
     extern __shared__ uint64_t keys[];  // [sortn]
     const int64_t q = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -539,6 +547,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict_
         const uint64_t kk = cq[j];
         if (kk == kEmptyKey) continue;
         const uint32_t id = key_id(kk);
+        if (!ERQ_DCHECK((int64_t)id < ck.rows, ck.status, 2)) continue;
         const float* x = X + (int64_t)id * D;
         float s = 0.f;
         constexpr int RU = 8;                 // float4 loads per lane in flight
@@ -688,19 +697,20 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     excl_scan_i64_kernel<<<dim3(1, 2), 1024, 0, s>>>(p.cnt64, p.qoff, p.items_c, p.item_off, p.nlist);
     count_launch();
     plan_scatter_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(p.probe_c, p.nq, p.maxp, p.qoff, p.pos_c,
-                                                                       p.qlist);
+                                                                       p.qlist, p.ck);
     return cudaGetLastError();
 }
 
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s) {
     count_launch();
     plan_items_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off, p.corder,
-                                                                       p.nlist, p.QT, p.RR, items);
+                                                                       p.nlist, p.QT, p.RR, items, p.ck);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     ScanArgs a;
+    a.ck = L.ck;
     a.Qrot = L.Qrot; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;
     a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
     a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
@@ -721,19 +731,19 @@ int merge_sortn(int kp, int lstride) {
 }
 
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
-                         int lstride, uint64_t* cand, cudaStream_t s) {
+                         int lstride, uint64_t* cand, const DevChecks& ck, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     if (kp <= 32) {
         count_launch();
         merge_warp_kernel<<<(unsigned)ceil_div(nq * 32, 256), 256, 0, s>>>(inter, inter_cnt, qbase, nq, kp, lstride,
-                                                                          cand);
+                                                                          cand, ck);
         return cudaGetLastError();
     }
     const int sortn = merge_sortn(kp, lstride);
     cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
     if (e != cudaSuccess) return e;
     count_launch();
-    merge_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(inter, inter_cnt, qbase, kp, lstride, sortn, cand);
+    merge_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(inter, inter_cnt, qbase, kp, lstride, sortn, cand, ck);
     return cudaGetLastError();
 }
 
@@ -746,7 +756,7 @@ __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __rest
                                                           const float* __restrict__ X, const float* __restrict__ Q,
                                                           int D, int k, int64_t* __restrict__ ids,
                                                           float* __restrict__ dists, int64_t* __restrict__ cand_ids,
-                                                          float* __restrict__ cand_est) {
+                                                          float* __restrict__ cand_est, DevChecks ck) {
     extern __shared__ float qrow[];           // [D]
     __shared__ uint64_t keys[32];
     const int64_t q = blockIdx.x;
@@ -755,7 +765,8 @@ __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __rest
     constexpr int RU = 8;
     float4 a[RU];
     auto issue = [&](int j, int t0) {
-        const uint64_t kk = cq[j];
+        uint64_t kk = cq[j];
+        if (kk != kEmptyKey && !ERQ_DCHECK((int64_t)key_id(kk) < ck.rows, ck.status, 3)) kk = kEmptyKey;
         const float* x = X + (int64_t)(kk == kEmptyKey ? 0u : key_id(kk)) * D;
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
@@ -806,14 +817,14 @@ __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __rest
 
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
-                          cudaStream_t s) {
+                          const DevChecks& ck, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     if (do_rerank && kp <= 32) {
         const size_t smem = (size_t)D * sizeof(float);
         cudaError_t e = cudaFuncSetAttribute(rerank32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        rerank32_kernel<<<(unsigned)nq, 256, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est);
+        rerank32_kernel<<<(unsigned)nq, 256, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est, ck);
         return cudaGetLastError();
     }
     int sortn = 32;
@@ -822,7 +833,7 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
     if (e != cudaSuccess) return e;
     count_launch();
     rerank_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(cand, kp, X, Q, D, k, do_rerank, sortn, ids, dists, cand_ids,
-                                                       cand_est);
+                                                       cand_est, ck);
     return cudaGetLastError();
 }
 

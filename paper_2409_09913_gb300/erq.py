@@ -59,7 +59,9 @@ def lib(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    # ERQ_CHECKED=1 selects the build with device-side bound checks (liberq_checked.so)
+    p = path or (LIB_PATH.replace("liberq.so", "liberq_checked.so") if os.environ.get("ERQ_CHECKED") == "1"
+                 else LIB_PATH)
     if not os.path.exists(p):
         raise RuntimeError(f"liberq.so not found at {p}: run __graft_entry__.build() (or "
                            f"python -m paper_2409_09913_gb300.build) first; there is no CPU fallback")
