@@ -21,7 +21,7 @@
 // stored per-row factors.  The product is exact up to the FP16 rounding of q'
 // (relative 2^-11 per element); accumulation is FP32.
 //
-// Warp roles (21 warps = 672 threads with NG = 2, NFX = 4; one CTA per SM,
+// Warp roles (27 warps = 864 threads with NG = 2, NFX = 10; one CTA per SM,
 // persistent over work items):
 //   warp 9     loader: per stage (128-row block, 64-wide K block) one TMA load
 //              of the packed codes (L2 evict-first); per row block a bulk copy
@@ -32,34 +32,36 @@
 //              (L2 evict-last) into the 128B-swizzled B tile, completion
 //              tracked on the stage's query barrier;
 //   warps 4-7, converters, two sets that take alternate stages: one thread
-//   and 17-20  per row unpacks the row's 64 B-bit codes of a stage (B 8-byte
+//   and 23-26  per row unpacks the row's 64 B-bit codes of a stage (B 8-byte
 //              words; a warp reads 256 contiguous bytes per word, conflict-
 //              free) in registers and stores them as FP16 into the stage's
 //              TMEM columns (warp w owns TMEM lanes 32 (w % 4) ..);
 //   warp 8     MMA issuer of row block 0 (one elected thread) and TMEM owner;
-//   warp 16    MMA issuer of row block 1.  Each issuer commits once per
+//   warp 22    MMA issuer of row block 1.  Each issuer commits once per
 //              stage to the stage's release barrier, which frees its codes,
 //              query tile and TMEM code columns together;
-//   warps 0-3  epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32 rows for
-//              all queries) and stores g + (f_res/2)*acc into a query-major tile
-//              in shared memory; after a named barrier these four warps and the
-//              NFX filter-only warps each filter the rows of the queries they
-//              own (q = filter-warp index mod NFW) against per-query thresholds
-//              into per-query candidate lists (warp ballots, compaction by a
-//              warp bitonic sort; k' <= 32).  A query's threshold starts at the
-//              smallest k'-th key published by its items finished so far (every
-//              item publishes its own k'-th key with atomicMin), which is never
-//              below the query's final k'-th key, so each list stays a superset
-//              of what the item contributes to the query's top-k'.
+//   warps 0-3  estimate tiles: warp w reads TMEM lanes 32w..32w+31 (its 32
+//              rows for all queries) and stores g + (f_res/2)*acc into one of
+//              EB query-major tiles in shared memory;
+//   warps 12-21 filters (NFX warps, pipelined behind the tiles through
+//              full/empty barriers): warp f filters the rows of the query
+//              slots f + NFX j against per-query thresholds into per-query
+//              candidate lists (warp ballots; when a list is full, a warp
+//              bitonic sort keeps the k' smallest).  A query's threshold
+//              starts at the smallest k'-th key published so far by its items
+//              (an item publishes its list's k'-th key with atomicMin after
+//              every compaction and at its end), which is never below the
+//              query's final k'-th key, so each list stays a superset of what
+//              the item contributes to the query's top-k'.
 // A stage covers up to RP = 2 row blocks that share the stage's query tile and
 // accumulate into separate TMEM accumulators, so two MMA dependency chains are
 // in flight and the query gather is amortised over 256 rows.  Accumulators are
 // double-buffered per stage group, so the epilogue of one group overlaps the
-// MMAs of the next; two estimate tiles let one epilogue warp start a block while
-// the others still filter the previous one.  Every mbarrier wait is bounded: on expiry the kernel
-// records ERQ_ETIMEOUT in the status word, stops issuing work, drains the copies
-// and MMAs it issued (bounded), frees TMEM and returns; the epilogue warps take
-// every early exit together through a reducing named barrier.
+// MMAs of the next; two estimate tiles let the tile warps fill a block while
+// the filter warps still work on the previous one.  Every mbarrier wait is
+// bounded: on expiry the kernel records ERQ_ETIMEOUT in the status word, every
+// role stops at its next wait (the abort flag), the copies and MMAs already
+// issued are drained (bounded), TMEM is freed and the kernel returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -75,13 +77,14 @@ namespace erq {
 namespace tc {
 
 constexpr int MR = 128;          // stored rows per MMA block (MMA M)
+static_assert(MR == 128, "four 32-row groups per row block (TMEM lane quarters, filter masks)");
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
 constexpr int MS = 4;            // row-factor buffers (one per row block)
 constexpr int NMMA = 2;          // MMA issuing warps
 constexpr int KCAP = 128;        // max k' of the tensor-core path
 constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
-constexpr int NFX = 4;           // filter-only warps (10 + NG ..), beside the epilogue warps 0-3
-constexpr int NFW = 4 + NFX;     // warps that filter candidates
+constexpr int NFX = 10;          // filter warps (10 + NG ..)
+constexpr int NEPI = 4 + NFX;    // epilogue warps: four estimate-tile warps and the filter warps
 constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
 constexpr int NCV = 2;           // converter sets (warps 4-7, and CV2 .. CV2 + 3 when NCV = 2)
 constexpr int CV2 = MMA2 + 1;
@@ -103,7 +106,7 @@ struct Cfg {
     static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
     static_assert(ACOL + LS * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
     static_assert(NCV == 1 || LS % 2 == 0, "the two converter sets take alternate stages and must see every use of theirs");
-    static_assert(QN % (4 * NG) == 0 && QN % 32 == 0 && (QN + NFW - 1) / NFW <= 32, "query tile split");
+    static_assert(QN % (4 * NG) == 0 && QN % 32 == 0 && (QN + NFX - 1) / NFX <= 32, "query tile split");
     static_assert(RP >= 1 && RP <= NMMA && (EB == 1 || EB == 2), "stage shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
@@ -120,7 +123,7 @@ struct Cfg {
         static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
         static constexpr int qsc = tq + 2 * QN * 8;                // 2 x [QN] f32 query scales (e4m3 path)
         static constexpr int bars = qsc + 2 * QN * 4;              // mbarriers (8 B each)
-        static constexpr int nbars = 4 * LS + 4 + 2 * MS + 4 + 1;
+        static constexpr int nbars = 4 * LS + 4 + 2 * MS + 4 + 1 + 4;
         static constexpr int tmem_slot = bars + nbars * 8;
         static constexpr int abort_flag = tmem_slot + 4;
         static constexpr int total = abort_flag + 4 + 1024;        // + alignment slack
@@ -326,6 +329,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     const uint32_t full_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS]);
     const uint32_t empty_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 2]);
     const uint32_t done_bar = smem_u32(&bars[4 * LS + 4 + 2 * MS + 4]);
+    const uint32_t tile_full0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 5]);
+    const uint32_t tile_empty0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 7]);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D;
@@ -344,13 +349,17 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
             mbar_init(tfull0 + 8 * b, NMMA);
             mbar_init(tempty0 + 8 * b, 128);
             mbar_init(full_item0 + 8 * b, 32);
-            mbar_init(empty_item0 + 8 * b, 32 * NFW);
+            mbar_init(empty_item0 + 8 * b, 32 * NEPI);
         }
         for (int m = 0; m < MS; ++m) {
             mbar_init(full_meta0 + 8 * m, 1);
             mbar_init(empty_meta0 + 8 * m, 128);
         }
         mbar_init(done_bar, NMMA);
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(tile_full0 + 8 * t, 128);        // the four estimate-tile warps
+            mbar_init(tile_empty0 + 8 * t, 32 * NFX);  // the filter warps
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -594,84 +603,99 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
         __syncwarp();
         mbar_wait_drain(done_bar, 0);
         __syncwarp();
-    } else {
-        // ------------------------------------------------------------ epilogue
+    } else if (warp < 4) {
+        // ------------------------------------------------------------ estimate tiles
+        // Warp w moves TMEM lanes 32w..32w+31 (its 32 rows, all queries) of a
+        // finished accumulator into a query-major estimate tile.
         float* s_est = reinterpret_cast<float*>(sm + Smem::est);
-        uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
         uint32_t* s_ids = reinterpret_cast<uint32_t*>(sm + Smem::ids);
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int row = warp * 32 + lane;
+        uint32_t blk = 0, pc = 0, rbg = 0, li = 0;     // row blocks, stage groups, meta slots, items
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int4 d = s_idesc[ib];
+            const int nrows = d.z, npad = npad_of(d.w);
+            for (int r = 0; r < nrows; r += MR, ++blk, ++rbg) {
+                const int bb = (r / MR) % RP;                   // block within its stage group
+                const int nb = min(RP, (nrows - (r - bb * MR) + MR - 1) / MR);
+                const int buf = pc & 1, m = rbg % MS, t = blk % EB;
+                if (!mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag) ||
+                    (bb == 0 && !mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag)) ||
+                    !mbar_wait_warp(tile_empty0 + 8 * t, ((blk / EB) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float* est_t = s_est + t * (QN * MR);
+                const float4 mt = s_meta[m * MR + row];
+                s_ids[t * MR + row] = __float_as_uint(mt.z);
+#pragma unroll 1
+                for (int cc = 0; cc < npad; cc += 32) {
+                    uint32_t v[32];
+                    ERQ_TMEM_LD32(tmem + lane_base + buf * (RP * QN) + bb * QN + cc, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
+                        const float* sc = reinterpret_cast<const float*>(sm + Smem::qsc) + ib * QN + cc;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]) * sc[i], mt.x);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+                    }
+                }
+                tc_fence_before();
+                if (bb == nb - 1) {                             // the group's accumulators are free
+                    mbar_arrive(tempty0 + 8 * buf);
+                    ++pc;
+                }
+                mbar_arrive(empty_meta0 + 8 * m);
+                mbar_arrive(tile_full0 + 8 * t);
+            }
+            if (!ok) break;
+            mbar_arrive(empty_item0 + 8 * ib);
+        }
+    } else {
+        // ------------------------------------------------------------ filters
+        // NFX warps; warp f owns the query slots q = f + NFX j of every item.
+        const float* s_est = reinterpret_cast<const float*>(sm + Smem::est);
+        uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
+        const uint32_t* s_ids = reinterpret_cast<const uint32_t*>(sm + Smem::ids);
         int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
         uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
-        // warps 0-3 also move their TMEM lane quarter into the estimate tile
-        const bool tm = warp < 4;
-        const int fw = tm ? warp : warp - (10 + NG) + 4;     // filter warp index 0 .. NFW-1
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const int fw = warp - (10 + NG);
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
-        const int row = (warp & 3) * 32 + lane;
-        uint32_t blk = 0, pc = 0, rbg = 0, li = 0;     // row blocks, stage groups, meta slots, items
-        bool okp = true;
-        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+        uint32_t blk = 0, li = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
             const int ib = li & 1;
-            const bool got = mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag);
-            if (bar_or(1, 32 * NFW, !got || *abort_flag != 0)) break;
+            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
             const int4 d = s_idesc[ib];
-            const int nrows = d.z, nqi = d.w, npad = npad_of(nqi);
+            const int nrows = d.z, nqi = d.w;
             const int4* iq = s_iq + ib * QN;
-            if (lane < (QN + NFW - 1) / NFW) {                 // owned queries q = fw + NFW * lane
-                const int q = fw + NFW * lane;
+            if (lane < (QN + NFX - 1) / NFX) {
+                const int q = fw + NFX * lane;
                 if (q < nqi) {
                     s_cnt[q] = 0;
                     s_tau[q] = reinterpret_cast<const unsigned long long*>(sm + Smem::tq)[ib * QN + q];
                 }
             }
             __syncwarp();
-            bool stop = false;
-            for (int r = 0; r < nrows; r += MR, ++blk, ++rbg) {
-                const int bb = (r / MR) % RP;                   // block within its stage group
-                const int nb = min(RP, (nrows - (r - bb * MR) + MR - 1) / MR);
+            for (int r = 0; r < nrows; r += MR, ++blk) {
                 const int nr = min(MR, nrows - r);
-                const int buf = pc & 1, m = rbg % MS;
-                bool okw = true;
-                if (tm) {
-                    okw = mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag);
-                    if (bb == 0) okp = mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag);
-                    okw = okw && okp;
-                }
-                float* est_t = s_est + (blk % EB) * (QN * MR);  // tiles alternate between row blocks
-                uint32_t* ids_t = s_ids + (blk % EB) * MR;
-                if (tm && okw) {
-                    // phase 1: own 32 rows x all queries -> query-major tile
-                    tc_fence_after();
-                    const float4 mt = s_meta[m * MR + row];
-                    ids_t[row] = __float_as_uint(mt.z);
-#pragma unroll 1
-                    for (int cc = 0; cc < npad; cc += 32) {
-                        uint32_t v[32];
-                        ERQ_TMEM_LD32(tmem + lane_base + buf * (RP * QN) + bb * QN + cc, v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
-                            const float* sc = reinterpret_cast<const float*>(sm + Smem::qsc) + ib * QN + cc;
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]) * sc[i], mt.x);
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
-                        }
-                    }
-                    tc_fence_before();
-                }
-                if (bb == nb - 1) {                             // the group's accumulators are free
-                    if (tm) mbar_arrive(tempty0 + 8 * buf);
-                    ++pc;
-                }
-                if (tm) mbar_arrive(empty_meta0 + 8 * m);
-                if (bar_or(1, 32 * NFW, !okw || *abort_flag != 0)) { stop = true; break; }
-                // phase 2: the 128 rows of each owned query; the four 32-row
-                // groups' estimates are loaded together, compared as floats
-                // against the threshold's estimate (a superset of the key
-                // test), and only groups with a candidate form exact keys
-                for (int q = fw; q < nqi; q += NFW) {
+                const int t = blk % EB;
+                if (!mbar_wait_warp(tile_full0 + 8 * t, (blk / EB) & 1, abort_flag)) { ok = false; break; }
+                const float* est_t = s_est + t * (QN * MR);
+                const uint32_t* ids_t = s_ids + t * MR;
+                // the 128 rows of each owned query; the four 32-row groups'
+                // estimates are loaded together, compared as floats against
+                // the threshold's estimate (a superset of the key test), and
+                // only groups with a candidate form exact keys
+                for (int q = fw; q < nqi; q += NFX) {
                     const float dq = __int_as_float(iq[q].y);
                     uint64_t tau = s_tau[q];
                     float tf = tau == kEmptyKey ? INFINITY : key_value(tau);
@@ -685,17 +709,26 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                         const bool pre = rr < nr && e[j] <= tf;
                         if (!__any_sync(0xffffffffu, pre)) continue;
                         const uint64_t key = make_key(e[j], ids_t[rr]);
-                        const bool pass = pre && key < tau;
-                        const uint32_t msk = __ballot_sync(0xffffffffu, pass);
+                        bool pass = pre && key < tau;
+                        uint32_t msk = __ballot_sync(0xffffffffu, pass);
                         if (msk == 0u) continue;
-                        if (pass) lists[q * KC + cnt + __popc(msk & below)] = key;
-                        cnt += __popc(msk);
-                        __syncwarp();
-                        if (cnt > KC - 32) {
+                        if (cnt + __popc(msk) > KC) {
+                            // full: keep the k' smallest (KC - k' >= 32 leaves
+                            // room for a group), then test the group again
                             tau = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
                             tf = key_value(tau);
                             cnt = kp;
+                            // k' keys of this query are now <= tau and stay in
+                            // its lists (a later compaction keeps the k'
+                            // smallest), so tau bounds its other items too
+                            if (lane == 0) atomicMin(a.tq + iq[q].x, (unsigned long long)tau);
+                            pass = pass && key < tau;
+                            msk = __ballot_sync(0xffffffffu, pass);
+                            if (msk == 0u) continue;
                         }
+                        if (pass) lists[q * KC + cnt + __popc(msk & below)] = key;
+                        cnt += __popc(msk);
+                        __syncwarp();
                     }
                     if (lane == 0) {
                         s_cnt[q] = cnt;
@@ -703,10 +736,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     }
                     __syncwarp();
                 }
-                if (EB == 1) bar_sync(1, 32 * NFW);            // the single tile is free again
+                mbar_arrive(tile_empty0 + 8 * t);
             }
-            if (stop) break;
-            for (int q = fw; q < nqi; q += NFW) {               // write this warp's lists
+            if (!ok) break;
+            for (int q = fw; q < nqi; q += NFX) {               // write this warp's lists
                 int cnt = s_cnt[q];
                 if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
                     const uint64_t th = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
