@@ -186,26 +186,33 @@ def scan_source_sha():
 def profiled_traffic(workload, nprobe, precision, shape, items=None):
     """DRAM bytes per launch of the tensor-core scan from the committed ncu
     capture (profiles/scan_tc_traffic_*.txt), only while the kernel source is
-    the one that was profiled; None otherwise."""
+    the one that was profiled and the run's work-item shape was captured (same
+    queries per item and a listed row limit, else an item count within 0.5 %);
+    None otherwise."""
     path = os.path.join(ROOT, "profiles", f"scan_tc_traffic_{workload}.txt")
     if precision == "fp32" or not os.path.exists(path):
         return None
-    kv = {}
+    kv, records = {}, []
     with open(path) as f:
         for line in f:
             if ":" in line and not line.lstrip().startswith("#"):
                 k, v = line.split(":", 1)
-                kv[k.strip()] = v.strip()
+                if k.strip() == "record":       # queries_per_item=.. rows_per_item=.. work_items=.. dram_bytes_per_launch=..
+                    records.append(dict(t.split("=", 1) for t in v.split()))
+                else:
+                    kv[k.strip()] = v.strip()
     try:
         if kv.get("kernel_source_sha256") != scan_source_sha() or int(kv.get("nprobe", -1)) != nprobe:
             return None
-        # the same work items (queries per item, and either a listed row limit or the
-        # same item count) give the same kernel work
-        rrs = [int(x) for x in kv.get("rows_per_item", "-1").split(",")]
-        same_items = items is not None and int(kv.get("work_items", -1)) == int(items)
-        if int(kv.get("queries_per_item", -1)) != shape[0] or (shape[1] not in rrs and not same_items):
-            return None
-        return float(kv["dram_bytes_per_launch"])
+        for rec in records:       # the captured work-item shape first, then one with the same item count
+            rrs = [int(x) for x in rec.get("rows_per_item", "-1").split(",")]
+            if int(rec.get("queries_per_item", -1)) == shape[0] and shape[1] in rrs:
+                return float(rec["dram_bytes_per_launch"])
+        for rec in records:       # (item counts differ by a few between index builds: k-means on the GPU)
+            n = int(rec.get("work_items", -1))
+            if int(rec.get("queries_per_item", -1)) == shape[0] and items is not None and abs(n - int(items)) <= 0.005 * n:
+                return float(rec["dram_bytes_per_launch"])
+        return None
     except (KeyError, ValueError):
         return None
 
