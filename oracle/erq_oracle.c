@@ -37,6 +37,14 @@
  *      in place of the printed ||y_u||, as Eq. 3.3 requires).
  *  R8  o_r = c (zero residual): code of all +1/2 entries, both factors 0, so
  *      the estimate is ||q_r - c||^2.
+ *  R9  inner-product metric (Section 7 points to RaBitQ for it): split
+ *      <o_r, q_r> = <c, q_r> + ||o_r - c|| <o, q_r> with o the unit residual,
+ *      and estimate <o, q^> for the unit query q^ = q_r/||q_r|| (no centroid
+ *      subtracted) by the same unbiased estimator <obar, q^>/<obar, o> as the
+ *      distance (Section 3.3); so est = <c, q_r> + ||o_r - c|| ||q_r|| *
+ *      <obar, q^>/<obar, o>.  Probing takes the nprobe largest <q_r, c_j>,
+ *      the re-rank the exact <o_r, q_r>; results are ordered by decreasing
+ *      inner product, ties by lower id (internally: ascending -<.,.>).
  */
 #include <math.h>
 #include <stdint.h>
@@ -263,6 +271,40 @@ static double estimate_one(const uint8_t* code, const double* st, int d, int B,
     return nr * nr + qc_norm * qc_norm - 2.0 * nr * qc_norm * ip_est;
 }
 
+/* R9: estimated inner product <o_r, q_r>.  qp = P^{-1} q^ with q^ = q_r/||q_r||
+ * (query_ip_side), sum_qp = sum_i qp[i], q_norm = ||q_r||, c_q = <c, q_r>. */
+static double estimate_ip_one(const uint8_t* code, const double* st, int d, int B,
+                              const double* qp, double sum_qp, double q_norm, double c_q)
+{
+    double nr, inv;
+    vec_factors(st, &nr, &inv);
+    double ipu = 0.0;                            /* <ybar_u, q'> */
+    for (int j = 0; j < d; ++j) ipu += (double)code[j] * qp[j];
+    const double obar_q = ipu - 0.5 * (double)((1 << B) - 1) * sum_qp;  /* ||ybar|| <obar, q^> */
+    return c_q + nr * q_norm * (obar_q * inv);
+}
+
+/* Query-side quantities of the inner-product metric for one centroid:
+ * q' = P^{-1} q_r/||q_r||, its coordinate sum, ||q_r|| and <c, q_r>. */
+static void query_ip_side(const double* q, const float* c, const float* P, int d,
+                          double* qn, double* qp, double* sum_qp, double* q_norm, double* c_q)
+{
+    double n2 = 0.0, cq = 0.0;
+    for (int k = 0; k < d; ++k) { qn[k] = q[k]; n2 += q[k] * q[k]; cq += (double)c[k] * q[k]; }
+    *q_norm = sqrt(n2);
+    *c_q = cq;
+    if (n2 > 0.0)
+        for (int k = 0; k < d; ++k) qn[k] /= *q_norm;
+    for (int j = 0; j < d; ++j) qp[j] = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const float* p = P + (size_t)k * d;
+        for (int j = 0; j < d; ++j) qp[j] += qn[k] * (double)p[j];
+    }
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += qp[j];
+    *sum_qp = s;
+}
+
 /* Index arrays (cluster-major): list_off[nlist+1] row offsets, list_ids[n]
  * original row id of each stored row, codes[n][d], stats[n][5] from
  * orc_quantize, X[n][d] raw rows in ORIGINAL order (for exact distances). */
@@ -295,15 +337,21 @@ static double exact_dist(const float* x, const double* q, int d)
     return s;
 }
 
-/* IVF probe (Section 4.1): the nprobe centroids nearest to q, ties by id. */
-static void probe_one(const orc_index* ix, const double* q, int nprobe, int32_t* out)
+static double exact_ip(const float* x, const double* q, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += (double)x[k] * q[k];
+    return s;
+}
+
+/* IVF probe (Section 4.1): the nprobe centroids nearest to q (metric 0) or
+ * with the largest <q, c> (metric 1, R9), ties by id. */
+static void probe_one(const orc_index* ix, const double* q, int nprobe, int metric, int32_t* out)
 {
     orc_pair* cd = (orc_pair*)malloc(sizeof(orc_pair) * ix->nlist);
     for (int j = 0; j < ix->nlist; ++j) {
-        double s = 0.0;
         const float* c = ix->C + (size_t)j * ix->d;
-        for (int k = 0; k < ix->d; ++k) { double t = q[k] - (double)c[k]; s += t * t; }
-        cd[j].key = s;
+        cd[j].key = metric ? -exact_ip(c, q, ix->d) : exact_dist(c, q, ix->d);
         cd[j].id = j;
     }
     qsort(cd, ix->nlist, sizeof(orc_pair), pair_cmp);
@@ -314,15 +362,18 @@ static void probe_one(const orc_index* ix, const double* q, int nprobe, int32_t*
 /* One query of the search path: probe -> estimate every candidate -> top-k'
  * by estimate -> exact re-rank of those k' -> top-k.  With kprime <= 0 the
  * estimated top-k is returned (the paper's no-re-rank setting, Section 4.1).
- * probe may be given (nprobe entries) or computed when probe_in is NULL. */
+ * probe may be given (nprobe entries) or computed when probe_in is NULL.
+ * metric 0: squared distances, ascending; metric 1: inner products (R9),
+ * descending -- sorted as ascending -<.,.> and reported with their sign. */
 static void search_one(const orc_index* ix, const double* q, int nprobe, const int32_t* probe_in,
-                       int kprime, int k, int64_t* ids, double* dists,
+                       int kprime, int k, int metric, int64_t* ids, double* dists,
                        int64_t* cand_ids, double* cand_est, int32_t* probe_out)
 {
     const int d = ix->d;
+    const double sgn = metric ? -1.0 : 1.0;
     int32_t* probe = (int32_t*)malloc(sizeof(int32_t) * (nprobe > 0 ? nprobe : 1));
     if (probe_in) memcpy(probe, probe_in, sizeof(int32_t) * nprobe);
-    else probe_one(ix, q, nprobe, probe);
+    else probe_one(ix, q, nprobe, metric, probe);
     if (probe_out) memcpy(probe_out, probe, sizeof(int32_t) * nprobe);
     int64_t ncand = 0;
     for (int p = 0; p < nprobe; ++p) ncand += ix->list_off[probe[p] + 1] - ix->list_off[probe[p]];
@@ -332,11 +383,16 @@ static void search_one(const orc_index* ix, const double* q, int nprobe, const i
     int64_t w = 0;
     for (int p = 0; p < nprobe; ++p) {
         const int c = probe[p];
-        double sum_qp, qc_norm;
-        query_side(q, ix->C + (size_t)c * d, ix->P, d, qn, qp, &sum_qp, &qc_norm);
+        double sum_qp, qc_norm, q_norm, c_q;
+        if (metric)
+            query_ip_side(q, ix->C + (size_t)c * d, ix->P, d, qn, qp, &sum_qp, &q_norm, &c_q);
+        else
+            query_side(q, ix->C + (size_t)c * d, ix->P, d, qn, qp, &sum_qp, &qc_norm);
         for (int64_t r = ix->list_off[c]; r < ix->list_off[c + 1]; ++r) {
-            cand[w].key = estimate_one(ix->codes + (size_t)r * d, ix->stats + (size_t)r * 5, d, ix->B,
-                                       qp, sum_qp, qc_norm);
+            const uint8_t* code = ix->codes + (size_t)r * d;
+            const double* st = ix->stats + (size_t)r * 5;
+            cand[w].key = metric ? -estimate_ip_one(code, st, d, ix->B, qp, sum_qp, q_norm, c_q)
+                                 : estimate_one(code, st, d, ix->B, qp, sum_qp, qc_norm);
             cand[w].id = ix->list_ids[r];
             ++w;
         }
@@ -346,15 +402,18 @@ static void search_one(const orc_index* ix, const double* q, int nprobe, const i
     const int64_t nk = ncand < kp ? ncand : kp;
     for (int j = 0; j < kp; ++j) {
         if (cand_ids) cand_ids[j] = j < nk ? cand[j].id : -1;
-        if (cand_est) cand_est[j] = j < nk ? cand[j].key : INFINITY;
+        if (cand_est) cand_est[j] = j < nk ? sgn * cand[j].key : sgn * INFINITY;
     }
     if (kprime > 0) {
-        for (int64_t j = 0; j < nk; ++j) cand[j].key = exact_dist(ix->X + (size_t)cand[j].id * d, q, d);
+        for (int64_t j = 0; j < nk; ++j) {
+            const float* x = ix->X + (size_t)cand[j].id * d;
+            cand[j].key = metric ? -exact_ip(x, q, d) : exact_dist(x, q, d);
+        }
         qsort(cand, (size_t)nk, sizeof(orc_pair), pair_cmp);
     }
     for (int j = 0; j < k; ++j) {
         ids[j] = j < nk ? cand[j].id : -1;
-        dists[j] = j < nk ? cand[j].key : INFINITY;
+        dists[j] = j < nk ? sgn * cand[j].key : sgn * INFINITY;
     }
     free(probe); free(cand); free(qn); free(qp);
 }
@@ -362,7 +421,7 @@ static void search_one(const orc_index* ix, const double* q, int nprobe, const i
 void orc_search(int d, int B, int nlist, const float* P, const float* C, const int64_t* list_off,
                 const int64_t* list_ids, const uint8_t* codes, const double* stats, const float* X,
                 const double* Q, int64_t nq, const int32_t* nprobe, const int32_t* probe_in, int max_probe,
-                int kprime, int k, int64_t* ids, double* dists, int64_t* cand_ids, double* cand_est,
+                int kprime, int k, int metric, int64_t* ids, double* dists, int64_t* cand_ids, double* cand_est,
                 int32_t* probe_out)
 {
     orc_index ix = {d, B, nlist, P, C, list_off, list_ids, codes, stats, X};
@@ -370,7 +429,7 @@ void orc_search(int d, int B, int nlist, const float* P, const float* C, const i
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < nq; ++i)
         search_one(&ix, Q + (size_t)i * d, nprobe[i], probe_in ? probe_in + (size_t)i * max_probe : NULL,
-                   kprime, k, ids + (size_t)i * k, dists + (size_t)i * k,
+                   kprime, k, metric, ids + (size_t)i * k, dists + (size_t)i * k,
                    cand_ids ? cand_ids + (size_t)i * kp : NULL, cand_est ? cand_est + (size_t)i * kp : NULL,
                    probe_out ? probe_out + (size_t)i * max_probe : NULL);
 }

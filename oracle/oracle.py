@@ -8,7 +8,8 @@ TEST INFRASTRUCTURE ONLY.  Follows arXiv 2409.09913:
 * ``build_index``               -- IVF index: clusters from an input assignment
   (Section 4.1), codes and per-vector factors (Section 5.1 metrics paragraph).
 * ``search``                    -- probe, Eq. 3.3 + Eq. (eq:dis to ip) estimates, top-k',
-  exact re-rank, top-k.
+  exact re-rank, top-k; or the same for inner products (reading R9: Section 7
+  defers the inner-product metric to RaBitQ's estimator).
 * ``estimate_rows`` / ``backward`` -- estimated distances of given pairs and their
   gradient w.r.t. the raw query.
 * ``brute_force_quantize``      -- exhaustive argmax of Eq. 3.2 (optimization) over the
@@ -60,7 +61,7 @@ def lib():
         L.orc_rotate.argtypes = [_f32, _Opt(np.float32), _Opt(np.int32), ct.c_int64, ct.c_int, _f32, _f32]
         L.orc_quantize_batch.argtypes = [_f32, ct.c_int64, ct.c_int, ct.c_int, _u8, _f64]
         L.orc_search.argtypes = [ct.c_int, ct.c_int, ct.c_int, _f32, _f32, _i64, _i64, _u8, _f64, _f32,
-                                 _f64, ct.c_int64, _i32, _Opt(np.int32), ct.c_int, ct.c_int, ct.c_int,
+                                 _f64, ct.c_int64, _i32, _Opt(np.int32), ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                  _i64, _f64, _Opt(np.int64), _Opt(np.float64), _Opt(np.int32)]
         L.orc_centroid_dists.argtypes = [_f32, ct.c_int, ct.c_int, _f64, ct.c_int64, _f64]
         L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
@@ -146,11 +147,15 @@ def _q64(Q):
     return np.ascontiguousarray(np.atleast_2d(Q), dtype=np.float64)
 
 
-def search(ix, Q, k, kprime=0, nprobe=None, probe=None):
+def search(ix, Q, k, kprime=0, nprobe=None, probe=None, metric="l2"):
     """Batched search; returns dict(ids, dists, cand_ids, cand_est, probe).
 
     ``nprobe``: int or per-query array; ``probe``: optional explicit [nq, maxp]
-    probe lists (then nprobe per query defaults to maxp)."""
+    probe lists (then nprobe per query defaults to maxp).  ``metric``: "l2"
+    (squared distances, ascending) or "ip" (inner products, descending; reading
+    R9 of erq_oracle.c)."""
+    if metric not in ("l2", "ip"):
+        raise ValueError(metric)
     Q = _q64(Q)
     nq = Q.shape[0]
     if probe is not None:
@@ -169,7 +174,7 @@ def search(ix, Q, k, kprime=0, nprobe=None, probe=None):
     probe_out = np.full((nq, maxp), -1, np.int32)
     lib().orc_search(ix["d"], ix["B"], ix["nlist"], ix["P"], ix["C"], ix["list_off"], ix["list_ids"],
                      ix["codes"], ix["stats"], ix["X"], Q, nq, np.ascontiguousarray(npr), probe, maxp,
-                     int(kprime), int(k), ids, dists, cand_ids, cand_est, probe_out)
+                     int(kprime), int(k), 1 if metric == "ip" else 0, ids, dists, cand_ids, cand_est, probe_out)
     return dict(ids=ids, dists=dists, cand_ids=cand_ids, cand_est=cand_est, probe=probe_out)
 
 

@@ -348,3 +348,92 @@ def test_stored_factors_reproduce_estimate():
         ybar = ix["codes"].astype(np.float64) - (2 ** 5 - 1) / 2
         ref = f_add + ((Q[i][None, :] - ix["C"][cl]) ** 2).sum(1) + f_res * (ybar * qt).sum(1)
         np.testing.assert_allclose(est[i], ref, rtol=2e-6)
+
+
+# --------------------------------------------------------------------------
+# Inner-product metric (reading R9 of erq_oracle.c)
+# --------------------------------------------------------------------------
+def _ip_est_single(o, c, q, B, P):
+    """Estimated <o, q> of one stored vector o (centroid c) through the
+    oracle's inner-product search (one row, one cluster, no re-rank)."""
+    d = o.shape[0]
+    ix = oracle.build_index(o[None].astype(np.float32), P, np.zeros(1, np.int32), 1, B,
+                            centroids_in=c[None].astype(np.float32))
+    res = oracle.search(ix, q[None], 1, kprime=0, nprobe=1, metric="ip")
+    return res["dists"][0, 0], res["cand_est"][0, 0]
+
+
+def test_ip_search_full_rerank_is_exact_mips():
+    """Probing every cluster and re-ranking every candidate by the exact inner
+    product returns the exact top-k by <o, q> (ties by lower id), reported
+    with their inner products in decreasing order."""
+    X, lab = S.mixture(1500, 32, 6, 150)
+    X[20] = X[21] = 4.0 * X[21]                       # an exact tie, near the top for most queries
+    Q = np.concatenate([X[20:21], S.mixture(5, 32, 6, 151, comp_seed=150)[0]]).astype(np.float64)
+    ix = oracle.build_index(X, S.random_orthogonal(32, 152), lab, 6, 3)
+    res = oracle.search(ix, Q, 10, kprime=len(X), nprobe=6, metric="ip")
+    ip = Q @ X.astype(np.float64).T
+    ref = np.stack([np.lexsort((np.arange(len(X)), -row))[:10] for row in ip])
+    np.testing.assert_array_equal(res["ids"], ref)
+    np.testing.assert_allclose(res["dists"], np.take_along_axis(ip, ref, 1), rtol=1e-12)
+    assert (np.diff(res["dists"], axis=1) <= 0).all()
+    assert res["ids"][0, 0] == 20 and res["ids"][0, 1] == 21      # <x, x> is the largest for q = x here
+
+
+def test_ip_probe_is_largest_inner_products():
+    X, lab = S.mixture(2000, 16, 10, 160)
+    ix = oracle.build_index(X, S.random_orthogonal(16, 161), lab, 10, 2)
+    Q = S.mixture(20, 16, 10, 162, comp_seed=160)[0].astype(np.float64)
+    res = oracle.search(ix, Q, 5, nprobe=3, metric="ip")
+    ref = np.argsort(-(Q @ ix["C"].astype(np.float64).T), axis=1, kind="stable")[:, :3]
+    np.testing.assert_array_equal(res["probe"], ref)
+
+
+@pytest.mark.parametrize("B", [2, 4, 7])
+def test_ip_estimate_exact_for_residual_on_the_grid(B):
+    """When the rotated residual is a multiple of a grid vector ybar (Eq.
+    equ:shift), <obar, o> = 1 and the estimate equals the exact inner product:
+    this ties together the <c, q> term, the ||o_r - c|| ||q_r|| scale, the
+    (2^B - 1)/2 shift and the factor 1/(||ybar|| <obar, o>)."""
+    d = 12
+    g = S.rng(170 + B)
+    perm = g.permutation(d)
+    P = np.zeros((d, d), np.float32)
+    P[perm, np.arange(d)] = g.choice([-1.0, 1.0], d)           # signed permutation: exact in FP32
+    c = (g.integers(-8, 9, d) / 4.0).astype(np.float32)
+    for t in range(5):
+        yu = g.integers(0, 2 ** B, d)
+        ybar = yu - (2 ** B - 1) / 2.0
+        o_rot = 0.5 * ybar                                       # on the grid direction, exact in FP32
+        o = (c.astype(np.float64) + P.astype(np.float64) @ o_rot).astype(np.float32)
+        assert np.array_equal(P.astype(np.float64).T @ (o.astype(np.float64) - c), o_rot)
+        q = g.standard_normal(d) * 3.0
+        est, cand = _ip_est_single(o, c, q, B, P)
+        true = float(o.astype(np.float64) @ q)
+        scale = abs(float(c @ q)) + np.linalg.norm(o_rot) * np.linalg.norm(q)
+        assert abs(est - true) <= 1e-12 * scale, (B, t, est, true)
+        assert est == cand
+
+
+def test_ip_zero_residual_gives_centroid_term():
+    """o_r = c: the estimate is <c, q_r> (reading R8 carried to R9)."""
+    c = np.array([1.0, -2.0, 0.5, 3.0], np.float32)
+    q = np.array([0.25, 1.0, -2.0, 0.75])
+    est, _ = _ip_est_single(c.copy(), c, q, 3, S.random_orthogonal(4, 3))
+    assert est == pytest.approx(float(c.astype(np.float64) @ q), rel=1e-12)
+
+
+@pytest.mark.parametrize("B", [2, 3])
+def test_ip_estimator_unbiased_over_rotations(B):
+    """Lemma 2.1 carried to R9: averaged over random orthogonal P, the estimated
+    <o_r, q_r> equals the exact one (nonzero centroid, unnormalised vectors)."""
+    d, trials = 16, 1500
+    g = S.rng(180 + B)
+    o = g.standard_normal(d).astype(np.float32)
+    c = (0.5 * g.standard_normal(d)).astype(np.float32)
+    q = g.standard_normal(d) * 2.0
+    true = float(o.astype(np.float64) @ q)
+    vals = np.array([_ip_est_single(o, c, q, B, S.random_orthogonal(d, 2000 + t))[0] for t in range(trials)])
+    se = vals.std() / math.sqrt(trials)
+    assert abs(vals.mean() - true) < 4 * se + 1e-12
+    assert vals.std() > 1e-4
