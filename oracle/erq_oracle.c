@@ -446,10 +446,12 @@ void orc_centroid_dists(const float* C, int nlist, int d, const double* Q, int64
         }
 }
 
-/* Estimated distance for explicit (query, stored row) pairs; rows index the
- * cluster-major arrays and cl gives the cluster of each row. */
+/* Estimated distance (metric 0) or inner product (metric 1, R9) for explicit
+ * (query, stored row) pairs; rows index the cluster-major arrays and cl gives
+ * the cluster of each row. */
 void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint8_t* codes, const double* stats,
-                       const double* Q, int64_t nq, int nc, const int64_t* rows, const int32_t* cl, double* out)
+                       const double* Q, int64_t nq, int nc, const int64_t* rows, const int32_t* cl, int metric,
+                       double* out)
 {
 #pragma omp parallel
     {
@@ -460,10 +462,16 @@ void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint8
             for (int j = 0; j < nc; ++j) {
                 const int64_t r = rows[(size_t)i * nc + j];
                 if (r < 0) { out[(size_t)i * nc + j] = NAN; continue; }
-                double sum_qp, qc_norm;
-                query_side(Q + (size_t)i * d, C + (size_t)cl[r] * d, P, d, qn, qp, &sum_qp, &qc_norm);
-                out[(size_t)i * nc + j] = estimate_one(codes + (size_t)r * d, stats + (size_t)r * 5, d, B,
-                                                       qp, sum_qp, qc_norm);
+                double sum_qp, qc_norm, q_norm, c_q;
+                if (metric) {
+                    query_ip_side(Q + (size_t)i * d, C + (size_t)cl[r] * d, P, d, qn, qp, &sum_qp, &q_norm, &c_q);
+                    out[(size_t)i * nc + j] = estimate_ip_one(codes + (size_t)r * d, stats + (size_t)r * 5, d, B,
+                                                              qp, sum_qp, q_norm, c_q);
+                } else {
+                    query_side(Q + (size_t)i * d, C + (size_t)cl[r] * d, P, d, qn, qp, &sum_qp, &qc_norm);
+                    out[(size_t)i * nc + j] = estimate_one(codes + (size_t)r * d, stats + (size_t)r * 5, d, B,
+                                                           qp, sum_qp, qc_norm);
+                }
             }
         free(qn);
         free(qp);

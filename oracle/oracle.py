@@ -65,7 +65,7 @@ def lib():
                                  _i64, _f64, _Opt(np.int64), _Opt(np.float64), _Opt(np.int32)]
         L.orc_centroid_dists.argtypes = [_f32, ct.c_int, ct.c_int, _f64, ct.c_int64, _f64]
         L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
-                                        _i64, _i32, _f64]
+                                        _i64, _i32, ct.c_int, _f64]
         L.orc_backward.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
                                    _i64, _i32, _f64, _f64]
         L.orc_num_threads.restype = ct.c_int
@@ -185,14 +185,17 @@ def _rows_and_clusters(ix, ids):
     return np.ascontiguousarray(rows), np.ascontiguousarray(cl)
 
 
-def estimate_rows(ix, Q, ids):
-    """Estimated squared distance of query i to each original id in ids[i, :]."""
+def estimate_rows(ix, Q, ids, metric="l2"):
+    """Estimated squared distance (metric "l2") or inner product (metric "ip",
+    reading R9) of query i to each original id in ids[i, :]."""
+    if metric not in ("l2", "ip"):
+        raise ValueError(metric)
     Q = _q64(Q)
     ids = np.atleast_2d(ids)
     rows, cl = _rows_and_clusters(ix, ids)
     out = np.empty(ids.shape, np.float64)
     lib().orc_estimate_rows(ix["d"], ix["B"], ix["P"], ix["C"], ix["codes"], ix["stats"], Q, Q.shape[0],
-                            ids.shape[1], rows, cl, out)
+                            ids.shape[1], rows, cl, 1 if metric == "ip" else 0, out)
     return out
 
 

@@ -437,3 +437,14 @@ def test_ip_estimator_unbiased_over_rotations(B):
     se = vals.std() / math.sqrt(trials)
     assert abs(vals.mean() - true) < 4 * se + 1e-12
     assert vals.std() > 1e-4
+
+
+def test_ip_estimate_rows_agree_with_search():
+    """The pairwise inner-product estimate is the one the search ranks by."""
+    X, lab = S.mixture(800, 24, 4, 190)
+    ix = oracle.build_index(X, S.random_orthogonal(24, 191), lab, 4, 4)
+    Q = S.mixture(6, 24, 4, 192, comp_seed=190)[0].astype(np.float64)
+    res = oracle.search(ix, Q, 5, kprime=0, nprobe=4, metric="ip")
+    est = oracle.estimate_rows(ix, Q, res["cand_ids"], metric="ip")
+    np.testing.assert_allclose(est, res["cand_est"], rtol=0, atol=0)
+    assert (np.diff(res["cand_est"], axis=1) <= 0).all()
