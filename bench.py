@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--rerank-k", type=int, default=20)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--recall", type=float, default=0.95)
+    ap.add_argument("--metric", default="l2", choices=["l2", "ip"],
+                    help="l2: nearest by squared distance; ip: largest inner product (recall against exact MIPS)")
     ap.add_argument("--cpu-sample", type=int, default=16, help="queries in the timed oracle sample")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of N and nq (smoke runs only)")
     ap.add_argument("--n", type=int, default=0, help="override N (profiling cases)")
@@ -225,7 +227,7 @@ def oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, rank_queries):
     import oracle
     C = oracle.centroids(X, assign, cfg["nlist"])
     Qs = Q[:rank_queries]
-    cd = oracle.centroid_dists(C, Qs)
+    cd = -(Qs.astype(np.float64) @ C.astype(np.float64).T) if args.metric == "ip" else oracle.centroid_dists(C, Qs)
     probed = np.unique(np.argsort(cd, axis=1, kind="stable")[:, :nprobe])
     rows = np.nonzero(np.isin(assign, probed))[0]
     ox = oracle.build_index(X[rows], P, assign[rows], cfg["nlist"], args.B, centroids_in=C)
@@ -236,7 +238,7 @@ def time_oracle(ox, Qs, args, nprobe, kp, reps=1):
     import oracle
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.search(ox, Qs, args.k, kprime=kp, nprobe=nprobe)
+        oracle.search(ox, Qs, args.k, kprime=kp, nprobe=nprobe, metric=args.metric)
     return (time.perf_counter() - t0) / reps
 
 
@@ -266,7 +268,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "nprobe": nprobe, "B": args.B,
-                                             "rerank_k": kp, "k": args.k},
+                                             "rerank_k": kp, "k": args.k, "similarity": args.metric},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe {nprobe}"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -427,7 +429,10 @@ def main():
         q = Qd[s0:s0 + 1024]
         best_d = best_i = None
         for x0 in range(0, len(X), 1 << 18):
-            d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
+            if args.metric == "ip":
+                d = -(q @ Xd[x0:x0 + (1 << 18)].T)
+            else:
+                d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
             v, i = torch.topk(d, RK, dim=1, largest=False)
             i = i + x0
             if best_d is None:
@@ -459,7 +464,7 @@ def main():
         for p in ([args.nprobe] if args.nprobe else cfg.get("nprobes", (16, 32, 64, 128, 256))):
             try:
                 ids, _ = ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
-                                   nprobe_per_query=npr_d)
+                                   nprobe_per_query=npr_d, metric=args.metric)
             except erq.ErqError as e:
                 sweep[prec] = f"unavailable: {e}"
                 break
@@ -477,10 +482,10 @@ def main():
     for prec, p in chosen.items():
         if prec != "fp32" and not args.no_autotune and not args.scan_shape:   # work-item shape timed on this batch
             shapes[prec] = ix.autotune(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
-                                       nprobe_per_query=npr_d, reps=3)
+                                       nprobe_per_query=npr_d, reps=3, metric=args.metric)
         def step():
             ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True,
-                      async_mode=not args.sync, nprobe_per_query=npr_d)
+                      async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -523,12 +528,12 @@ def main():
     Qh = torch.from_numpy(Q).pin_memory()
     for _ in range(max(1, args.warmup)):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                       async_mode=not args.sync, nprobe_per_query=npr_d)
+                       async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(args.steps):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                       async_mode=not args.sync, nprobe_per_query=npr_d)
+                       async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
     e2e_s = (time.perf_counter() - te) / args.steps
     e2e_s = max_over_ranks(e2e_s, world, dev)
 
@@ -541,12 +546,12 @@ def main():
         sg.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(sg):
             ix.search(static_q, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                      async_mode=True, nprobe_per_query=npr_d)
+                      async_mode=True, nprobe_per_query=npr_d, metric=args.metric)
         torch.cuda.current_stream().wait_stream(sg)
         cg = torch.cuda.CUDAGraph()
         with torch.cuda.graph(cg):
             g_ids, _ = ix.search(static_q, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
-                                 async_mode=True, nprobe_per_query=npr_d)
+                                 async_mode=True, nprobe_per_query=npr_d, metric=args.metric)
         for _ in range(args.warmup):
             cg.replay()
         torch.cuda.synchronize()
@@ -634,7 +639,8 @@ def main():
                        "nq": len(Q), "k": args.k, "rerank_k": kp, "precision": best,
                        "nprobe": ("per query U{%d..%d}" % (cfg["nprobe_lo"], cfg["nprobe_hi"])) if npr_d is not None
                        else R["nprobe"],
-                       "recall@10": R["recall"], "l2": "inputs larger than L2 (codes > 129 MB)"},
+                       "recall@10": R["recall"], "similarity": args.metric,
+                       "l2": "inputs larger than L2 (codes > 129 MB)"},
             "gcodes_per_s": R["work"]["pairs"] / (R["ms"] / 1e3) / 1e9,
             "arms": {k: {"qps": v["qps"], "nprobe": v["nprobe"], "recall@10": v["recall"], "ms": v["ms"],
                          "phases_ms": v["phases"], "pairs": v["work"]["pairs"],

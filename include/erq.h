@@ -93,7 +93,14 @@ typedef struct {
     int64_t* cand_ids;        /* optional device out [nq][kc], kc = max(k, rerank_k):
                                  ids of the estimated top-kc, ascending by estimate      */
     float* cand_est;          /* optional device out [nq][kc]: their estimates            */
+    int32_t metric;           /* erq_metric (0 = ERQ_METRIC_L2)                          */
 } erq_search_params;
+
+/* erq_search_params.metric */
+typedef enum {
+    ERQ_METRIC_L2 = 0,        /* squared Euclidean distance, smallest first               */
+    ERQ_METRIC_IP = 1         /* inner product, largest first (see erq_search)            */
+} erq_metric;
 
 /* erq_search_params.flags */
 #define ERQ_SEARCH_TIMING 1      /* record per-phase CUDA events (erq_search_timing)        */
@@ -184,6 +191,14 @@ erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_
  *   lower id), and -- when rerank_k > 0 -- re-rank them by exact squared distance.
  * ids[nq][k] (int64, -1 where fewer than k candidates exist) and dists[nq][k]
  * (FP32: exact squared distances after re-rank, estimates otherwise).
+ * metric = ERQ_METRIC_IP (the inner-product adaptation Section 7 refers to
+ * RaBitQ for): probe the nprobe centroids with the largest <q_r, c> (ties by
+ * lower id); estimate <o_r, q_r> = <c, q_r> + ||o_r - c|| <o, q_r> with the
+ * same unbiased estimator of <o, q_r> and the same codes and factors, i.e.
+ * <c, q_r> - (f_res / 2) <ybar, q'>; keep the k' largest estimates (ties by
+ * lower id) and re-rank them by the exact inner product.  ids are then in
+ * decreasing order of inner product and dists (and cand_est) hold the inner
+ * products themselves (-INFINITY where fewer than k exist).
  * Errors: EINVAL (k, nprobe, probe ids, rerank without raw rows), EUNSUPPORTED
  * (precision), ENOMEM (workspace), ECUDA, ETIMEOUT (device status). */
 erq_status erq_search(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params,

@@ -471,6 +471,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int maxp = p->probe ? p->nprobe : (nlist == 1 ? 1 : p->nprobe);
     const bool explicit_probe = p->probe != nullptr;
     const int prec = p->precision;
+    const int ip = p->metric == ERQ_METRIC_IP ? 1 : 0;   // rank by -<o_r, q_r> (probe: -<q_r, c_j>)
     const int64_t Dq = (D + 127) / 128 * 128;           // e4m3 query rows, padded to whole 128-byte stages
     // ---- phase A workspace (sizes known on the host)
     // queries per work item of the scan kernels
@@ -586,11 +587,14 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     } else if (nlist == 1) {
         if ((e = launch_fill_i32(probe, nq, 0, s)) != cudaSuccess) return cuda_fail(e, "probe fill");
     } else {
-        if ((e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
-        e = simt ? launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s)
-                 : launch_gemm_tma((__half*)sl[23], (__half*)sl[24], eQ, nq, ix->C_hi, ix->C_lo, ix->eC, nlist, D, sqd,
-                                   nlist, 1, qn, ix->cnorm2, (!simt && maxp <= 32) ? (float*)sl[25] : nullptr,
-                                   ix->status, s);
+        if (!ip && (e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
+        if (simt)
+            e = ip ? launch_sgemm(true, Q, ix->C, sqd, nq, nlist, D, -1.f, nullptr, s)
+                   : launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s);
+        else
+            e = launch_gemm_tma((__half*)sl[23], (__half*)sl[24], eQ, nq, ix->C_hi, ix->C_lo, ix->eC, nlist, D, sqd,
+                                nlist, ip ? 2 : 1, ip ? nullptr : qn, ip ? nullptr : ix->cnorm2,
+                                maxp <= 32 ? (float*)sl[25] : nullptr, ix->status, s);
         if (e != cudaSuccess) return cuda_fail(e, "centroid distances");
         e = (!simt && maxp <= 32) ? launch_row_topk_groups(sqd, (float*)sl[25], nq, nlist, nlist, maxp, probe, maxp, s)
                                   : launch_row_topk_fast(sqd, nq, nlist, nlist, maxp, probe, nullptr, maxp, s);
@@ -621,7 +625,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.ck = ck;
     if ((e = launch_plan(pa, s)) != cudaSuccess) return cuda_fail(e, "plan");
     // dqc needs the validated probe ids
-    if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
+    if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, ip, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
     int64_t Ltot = 0, nitems = 0;
     const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0;
     if (async) {
@@ -689,6 +693,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
     L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_p = ix->codes_p; L.Np = ix->Np;
     L.tq = (unsigned long long*)sl[22];
+    L.ip = ip;
     L.ck = ck;
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
     int dev = 0, sms = 148;
@@ -705,8 +710,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     if ((e = launch_merge(inter, inter_cnt, pa.qbase, nq, kp, lstride, cand, ck, s)) != cudaSuccess)
         return cuda_fail(e, "merge");
     ERQ_TRY(mark(5));
-    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ids, dists, p->cand_ids, p->cand_est, ck,
-                           s)) != cudaSuccess)
+    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, ip, ids, dists, p->cand_ids, p->cand_est,
+                           ck, s)) != cudaSuccess)
         return cuda_fail(e, "rerank");
     ERQ_TRY(mark(6));
     if (timed) {
@@ -742,6 +747,7 @@ static erq_status validate_search(const erq_index* ix, const float* Q, int64_t n
         return fail(ERQ_EUNSUPPORTED, "erq_search: fp8 scan needs B <= 4 (centred codes exact in e4m3)");
     if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
         return fail(ERQ_EUNSUPPORTED, "erq_search: k' too large for the FP32 scan");
+    if (p->metric != ERQ_METRIC_L2 && p->metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_search: unknown metric");
     return ERQ_OK;
 }
 

@@ -68,11 +68,12 @@ struct ScanLaunch {
     int maxp, D, B, kp, RR;
     int qn;                     // tensor-core path: queries per work item (32, 64 or 128)
     int grid;
+    int ip;                     // inner-product metric (per-row factor f_res / 4, no g; dqc holds -<c, q_r>)
     DevChecks ck;
 };
 
 cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
-                       int D, float* dqc, cudaStream_t s);
+                       int D, int ip, float* dqc, cudaStream_t s);
 cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s);
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
@@ -91,7 +92,7 @@ cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float
                                uint64_t* codes_p, float4* rowmeta, cudaStream_t s);
 cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
-                          int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
+                          int do_rerank, int ip, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           const DevChecks& ck, cudaStream_t s);
 cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
                             const erq_index* ix, float* est, cudaStream_t s);

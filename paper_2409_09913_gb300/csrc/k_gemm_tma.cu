@@ -12,8 +12,9 @@
 // rounding of lo are below 2^-21 relative, the order of FP32 SGEMM error.  The
 // epilogue multiplies back by 2^(e_a + e_b).
 //
-// For the distances the epilogue can also write the minimum of every 32-column
-// group of a row (used by the probe selection).
+// The epilogue writes C, the distances, or -C (inner-product probe); for the
+// last two it can also write the minimum of every 32-column group of a row
+// (used by the probe selection).
 // Tile 128 x 256, K block 64 (one 128-byte swizzle row of FP16); a stage is
 // four TMA tiles (A_hi, A_lo 16 KB each; B_hi, B_lo 32 KB each), two stages;
 // two TMEM accumulators of 256 columns, persistent CTAs over output tiles.
@@ -44,7 +45,7 @@ constexpr int OFF_ABORT = OFF_TMEM + 4;
 constexpr int SMEM = OFF_ABORT + 4 + 1024;
 static_assert(SMEM <= 227 * 1024, "gemm shared memory");
 
-enum { EPI_PLAIN = 0, EPI_DIST = 1 };
+enum { EPI_PLAIN = 0, EPI_DIST = 1, EPI_NEGIP = 2 };   // C, ||a||^2 + ||b||^2 - 2C, -C
 
 struct Args {
     const int32_t* eA;       // [M] row exponents of A
@@ -217,14 +218,14 @@ __global__ void __launch_bounds__(gemm2::THREADS, 1)
                         const float4 f = *reinterpret_cast<const float4*>(cf + j);   // same address in every lane
                         const float v0 = (__uint_as_float(r[j]) * sa) * f.x;
                         const float v1 = (__uint_as_float(r[j + 1]) * sa) * f.z;
-                        out[j] = a.epi == EPI_DIST ? rn + f.y - 2.f * v0 : v0;
-                        out[j + 1] = a.epi == EPI_DIST ? rn + f.w - 2.f * v1 : v1;
+                        out[j] = a.epi == EPI_DIST ? rn + f.y - 2.f * v0 : (a.epi == EPI_NEGIP ? -v0 : v0);
+                        out[j + 1] = a.epi == EPI_DIST ? rn + f.w - 2.f * v1 : (a.epi == EPI_NEGIP ? -v1 : v1);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const float v = ldexpf(__uint_as_float(r[j]), ea + ebs[j]);
-                        out[j] = a.epi == EPI_DIST ? rn + cf[j].y - 2.f * v : v;
+                        out[j] = a.epi == EPI_DIST ? rn + cf[j].y - 2.f * v : (a.epi == EPI_NEGIP ? -v : v);
                     }
                 }
                 if (mok && a.gmin) {                           // group minimum over the valid columns

@@ -18,8 +18,10 @@
 // each), the columns after them the expanded-code stages of RP x 32 columns.
 // The accumulator holds row r in TMEM lane r and query j in column j; the
 // estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
-// stored per-row factors.  The product is exact up to the FP16 rounding of q'
-// (relative 2^-11 per element); accumulation is FP32.
+// stored per-row factors, or for the inner-product metric the ranking score
+// -<c, q_r> + (f_res / 4) * acc = -(estimated <o_r, q_r>).  The product is
+// exact up to the FP16 rounding of q' (relative 2^-11 per element);
+// accumulation is FP32.
 //
 // Warp roles (27 warps = 864 threads with NG = 2, NFX = 10; one CTA per SM,
 // persistent over work items):
@@ -228,6 +230,7 @@ struct Args {
     unsigned long long* tq;       // [nq] query-wide admission threshold (k'-th key of a finished item)
     uint32_t* status;
     int D, B, kp;
+    int ip;                       // inner-product metric: est = -<c, q_r> + (f_res / 4) * acc
     DevChecks ck;
 };
 
@@ -630,8 +633,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 }
                 tc_fence_after();
                 float* est_t = s_est + t * (QN * MR);
-                const float4 mt = s_meta[m * MR + row];
+                float4 mt = s_meta[m * MR + row];
                 s_ids[t * MR + row] = __float_as_uint(mt.z);
+                if (a.ip) {                                     // -<c, q_r> + (f_res / 4) acc: no g, half the factor
+                    mt.x = 0.f;
+                    mt.y *= 0.5f;
+                }
 #pragma unroll 1
                 for (int cc = 0; cc < npad; cc += 32) {
                     uint32_t v[32];
@@ -957,6 +964,7 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
     a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
     a.tq = L.tq;
+    a.ip = L.ip;
     if (!scan_tc_shape_ok(L.qn, L.kp)) return fail(ERQ_EINVAL, "tensor-core scan: no kernel for this item shape");
     if (L.qn == CfgWide::QN) return f8 ? scan_tc_launch<CfgWide, true>(L, a, s) : scan_tc_launch<CfgWide, false>(L, a, s);
     if (L.qn == CfgSmall::QN)

@@ -23,14 +23,15 @@
 namespace erq {
 
 // ---------------------------------------------------------------------------
-// ||q_r - c||^2 for every probed (query, cluster): one block per query, the
-// query row in shared memory, one warp per probed cluster (looping when the
-// query probes more clusters than the block has warps).  Each lane keeps up to
-// eight 16-byte loads of the centroid row in flight (D <= 4096).
+// ||q_r - c||^2 (or, for the inner-product metric, -<q_r, c>) for every probed
+// (query, cluster): one block per query, the query row in shared memory, one
+// warp per probed cluster (looping when the query probes more clusters than
+// the block has warps).  Each lane keeps up to eight 16-byte loads of the
+// centroid row in flight (D <= 4096).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) dqc_kernel(const float* __restrict__ Q, const float* __restrict__ C,
                                                   const int32_t* __restrict__ probe, const int32_t* __restrict__ npr,
-                                                  int64_t nq, int maxp, int D, float* __restrict__ dqc) {
+                                                  int64_t nq, int maxp, int D, int ip, float* __restrict__ dqc) {
     extern __shared__ float qs[];
     const int64_t q = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -70,16 +71,24 @@ __global__ void __launch_bounds__(512) dqc_kernel(const float* __restrict__ Q, c
                 const int t = t0 + 128 * u + lane * 4;
                 if (t < D) {
                     const float4 b = *reinterpret_cast<const float4*>(qs + t);
-                    const float d0 = b.x - a[u].x, d1 = b.y - a[u].y, d2 = b.z - a[u].z, d3 = b.w - a[u].w;
-                    s = fmaf(d0, d0, s);
-                    s = fmaf(d1, d1, s);
-                    s = fmaf(d2, d2, s);
-                    s = fmaf(d3, d3, s);
+                    if (ip) {
+                        s = fmaf(b.x, a[u].x, s);
+                        s = fmaf(b.y, a[u].y, s);
+                        s = fmaf(b.z, a[u].z, s);
+                        s = fmaf(b.w, a[u].w, s);
+                    } else {
+                        const float d0 = b.x - a[u].x, d1 = b.y - a[u].y, d2 = b.z - a[u].z, d3 = b.w - a[u].w;
+                        s = fmaf(d0, d0, s);
+                        s = fmaf(d1, d1, s);
+                        s = fmaf(d2, d2, s);
+                        s = fmaf(d3, d3, s);
+                    }
                 }
             }
         }
         s = warp_sum(s);
-        if (lane == 0 && c >= 0) dqc[q * maxp + slot] = s;   // invalid probe ids are reported through the status word
+        // invalid probe ids are reported through the status word
+        if (lane == 0 && c >= 0) dqc[q * maxp + slot] = ip ? -s : s;
     }
 }
 
@@ -265,6 +274,7 @@ struct ScanArgs {
     uint64_t* inter;            // [L][kp]
     int32_t* inter_cnt;         // [L]
     int maxp, D, B, kp, RR;
+    int ip;                     // inner-product metric: est = -<c, q_r> + (f_res / 4) <2 ybar, q'>
     DevChecks ck;
 };
 
@@ -314,8 +324,8 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
             const int nr = (int)imin64(SC_RB, rb1 - r0);
             if (tid < SC_RB) {
                 if (tid < nr) {
-                    s_g[tid] = a.g_const[r0 + tid];
-                    s_fh[tid] = 0.5f * a.f_res[r0 + tid];
+                    s_g[tid] = a.ip ? 0.f : a.g_const[r0 + tid];
+                    s_fh[tid] = (a.ip ? 0.25f : 0.5f) * a.f_res[r0 + tid];
                     s_id[tid] = (uint32_t)a.list_ids[r0 + tid];
                 }
             }
@@ -514,14 +524,16 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const uint64_t* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Re-rank: exact squared distances of the k' candidates (FP32), top-k.
+// Re-rank: exact squared distances (or inner products, ranked by -<o, q>) of
+// the k' candidates (FP32), top-k; inner products are reported with their sign.
 // Also writes cand_ids / cand_est when requested.  One block per query.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict__ cand, int kp, const float* __restrict__ X,
                                                      const float* __restrict__ Q, int D, int k, int do_rerank,
-                                                     int sortn, int64_t* __restrict__ ids, float* __restrict__ dists,
-                                                     int64_t* __restrict__ cand_ids, float* __restrict__ cand_est,
-                                                     DevChecks ck) {
+                                                     int ip, int sortn, int64_t* __restrict__ ids,
+                                                     float* __restrict__ dists, int64_t* __restrict__ cand_ids,
+                                                     float* __restrict__ cand_est, DevChecks ck) {
+    const float sgn = ip ? -1.f : 1.f;       // keys hold -<o, q> for the inner-product metric
     extern __shared__ uint64_t keys[];  // [sortn]
     const int64_t q = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -530,13 +542,13 @@ __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict_
         for (int j = threadIdx.x; j < kp; j += blockDim.x) {
             const uint64_t kk = cq[j];
             cand_ids[q * kp + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
-            cand_est[q * kp + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+            cand_est[q * kp + j] = sgn * (kk == kEmptyKey ? INFINITY : key_value(kk));
         }
     if (!do_rerank) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) {
             const uint64_t kk = j < kp ? cq[j] : kEmptyKey;
             ids[q * k + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
-            dists[q * k + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+            dists[q * k + j] = sgn * (kk == kEmptyKey ? INFINITY : key_value(kk));
         }
         return;
     }
@@ -564,23 +576,31 @@ __global__ void __launch_bounds__(256) rerank_kernel(const uint64_t* __restrict_
 #pragma unroll
             for (int u = 0; u < RU; ++u) {
                 if (t0 + 128 * u + lane * 4 < D) {
-                    const float d0 = a[u].x - b[u].x, d1 = a[u].y - b[u].y, d2 = a[u].z - b[u].z, d3 = a[u].w - b[u].w;
-                    s = fmaf(d0, d0, s);
-                    s = fmaf(d1, d1, s);
-                    s = fmaf(d2, d2, s);
-                    s = fmaf(d3, d3, s);
+                    if (ip) {
+                        s = fmaf(a[u].x, b[u].x, s);
+                        s = fmaf(a[u].y, b[u].y, s);
+                        s = fmaf(a[u].z, b[u].z, s);
+                        s = fmaf(a[u].w, b[u].w, s);
+                    } else {
+                        const float d0 = a[u].x - b[u].x, d1 = a[u].y - b[u].y, d2 = a[u].z - b[u].z,
+                                    d3 = a[u].w - b[u].w;
+                        s = fmaf(d0, d0, s);
+                        s = fmaf(d1, d1, s);
+                        s = fmaf(d2, d2, s);
+                        s = fmaf(d3, d3, s);
+                    }
                 }
             }
         }
         s = warp_sum(s);
-        if (lane == 0) keys[j] = make_key(s, id);
+        if (lane == 0) keys[j] = make_key(sgn * s, id);
     }
     __syncthreads();
     block_bitonic_u64(keys, sortn);
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const uint64_t kk = keys[j];
         ids[q * k + j] = kk == kEmptyKey ? -1 : (int64_t)key_id(kk);
-        dists[q * k + j] = kk == kEmptyKey ? INFINITY : key_value(kk);
+        dists[q * k + j] = sgn * (kk == kEmptyKey ? INFINITY : key_value(kk));
     }
 }
 
@@ -666,13 +686,13 @@ __global__ void __launch_bounds__(256) backward_gather_kernel(const float* __res
 // Host-side launch helpers
 // ---------------------------------------------------------------------------
 cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
-                       int D, float* dqc, cudaStream_t s) {
+                       int D, int ip, float* dqc, cudaStream_t s) {
     if (nq <= 0 || maxp <= 0) return cudaSuccess;
     const size_t smem = (size_t)D * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(dqc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    dqc_kernel<<<(unsigned)nq, 32 * std::min(maxp, 16), smem, s>>>(Q, C, probe, npr, nq, maxp, D, dqc);
+    dqc_kernel<<<(unsigned)nq, 32 * std::min(maxp, 16), smem, s>>>(Q, C, probe, npr, nq, maxp, D, ip, dqc);
     return cudaGetLastError();
 }
 
@@ -714,7 +734,7 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     a.Qrot = L.Qrot; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;
     a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
     a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
-    a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR;
+    a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip;
     const size_t smem = scan_fp32_smem(L.kp);
     cudaError_t e = cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -754,9 +774,10 @@ cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const 
 // 0 sorts the k' keys (distance, id) and writes the top k.
 __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __restrict__ cand, int kp,
                                                           const float* __restrict__ X, const float* __restrict__ Q,
-                                                          int D, int k, int64_t* __restrict__ ids,
+                                                          int D, int k, int ip, int64_t* __restrict__ ids,
                                                           float* __restrict__ dists, int64_t* __restrict__ cand_ids,
                                                           float* __restrict__ cand_est, DevChecks ck) {
+    const float sgn = ip ? -1.f : 1.f;       // keys hold -<o, q> for the inner-product metric
     extern __shared__ float qrow[];           // [D]
     __shared__ uint64_t keys[32];
     const int64_t q = blockIdx.x;
@@ -781,7 +802,7 @@ __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __rest
     if (cand_ids && threadIdx.x < kp) {
         const uint64_t c = cq[threadIdx.x];
         cand_ids[q * kp + threadIdx.x] = c == kEmptyKey ? -1 : (int64_t)key_id(c);
-        cand_est[q * kp + threadIdx.x] = c == kEmptyKey ? INFINITY : key_value(c);
+        cand_est[q * kp + threadIdx.x] = sgn * (c == kEmptyKey ? INFINITY : key_value(c));
     }
     __syncthreads();
     for (int j = warp; j < kp; j += 8) {
@@ -794,29 +815,36 @@ __global__ void __launch_bounds__(256, 4) rerank32_kernel(const uint64_t* __rest
                 const int t = t0 + 128 * u + lane * 4;
                 if (t < D) {
                     const float4 b = *reinterpret_cast<const float4*>(qrow + t);
-                    const float d0 = a[u].x - b.x, d1 = a[u].y - b.y, d2 = a[u].z - b.z, d3 = a[u].w - b.w;
-                    s = fmaf(d0, d0, s);
-                    s = fmaf(d1, d1, s);
-                    s = fmaf(d2, d2, s);
-                    s = fmaf(d3, d3, s);
+                    if (ip) {
+                        s = fmaf(a[u].x, b.x, s);
+                        s = fmaf(a[u].y, b.y, s);
+                        s = fmaf(a[u].z, b.z, s);
+                        s = fmaf(a[u].w, b.w, s);
+                    } else {
+                        const float d0 = a[u].x - b.x, d1 = a[u].y - b.y, d2 = a[u].z - b.z, d3 = a[u].w - b.w;
+                        s = fmaf(d0, d0, s);
+                        s = fmaf(d1, d1, s);
+                        s = fmaf(d2, d2, s);
+                        s = fmaf(d3, d3, s);
+                    }
                 }
             }
         }
         s = warp_sum(s);
-        if (lane == 0) keys[j] = kk == kEmptyKey ? kEmptyKey : make_key(s, key_id(kk));
+        if (lane == 0) keys[j] = kk == kEmptyKey ? kEmptyKey : make_key(sgn * s, key_id(kk));
     }
     __syncthreads();
     if (warp == 0) {
         const uint64_t v = ws_sort32(lane < kp ? keys[lane] : kEmptyKey, lane);
         if (lane < k) {
             ids[q * k + lane] = v == kEmptyKey ? -1 : (int64_t)key_id(v);
-            dists[q * k + lane] = v == kEmptyKey ? INFINITY : key_value(v);
+            dists[q * k + lane] = sgn * (v == kEmptyKey ? INFINITY : key_value(v));
         }
     }
 }
 
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
-                          int do_rerank, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
+                          int do_rerank, int ip, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           const DevChecks& ck, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     if (do_rerank && kp <= 32) {
@@ -824,7 +852,7 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
         cudaError_t e = cudaFuncSetAttribute(rerank32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        rerank32_kernel<<<(unsigned)nq, 256, smem, s>>>(cand, kp, X, Q, D, k, ids, dists, cand_ids, cand_est, ck);
+        rerank32_kernel<<<(unsigned)nq, 256, smem, s>>>(cand, kp, X, Q, D, k, ip, ids, dists, cand_ids, cand_est, ck);
         return cudaGetLastError();
     }
     int sortn = 32;
@@ -832,8 +860,8 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
     cudaError_t e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sortn * 8);
     if (e != cudaSuccess) return e;
     count_launch();
-    rerank_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(cand, kp, X, Q, D, k, do_rerank, sortn, ids, dists, cand_ids,
-                                                       cand_est, ck);
+    rerank_kernel<<<(unsigned)nq, 256, sortn * 8, s>>>(cand, kp, X, Q, D, k, do_rerank, ip, sortn, ids, dists,
+                                                       cand_ids, cand_est, ck);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liberq.so")
 
 ERQ_OK, ERQ_EINVAL, ERQ_ENOMEM, ERQ_ECUDA, ERQ_ETIMEOUT, ERQ_EUNSUPPORTED, ERQ_EIO = range(7)
 PREC = {"fp32": 0, "fp16": 1, "fp8": 2, "int8": 3}
+METRIC = {"l2": 0, "ip": 1}
 FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, "codes": 4, "f_add": 5,
           "f_res": 6, "P": 7, "raw": 8, "packed_codes": 9}
 
@@ -43,7 +44,7 @@ class BuildParams(ct.Structure):
 class SearchParams(ct.Structure):
     _fields_ = [("k", ct.c_int32), ("rerank_k", ct.c_int32), ("nprobe", ct.c_int32), ("precision", ct.c_int32),
                 ("nprobe_per_query", ct.c_void_p), ("probe", ct.c_void_p), ("probe_stride", ct.c_int32),
-                ("flags", ct.c_int32), ("cand_ids", ct.c_void_p), ("cand_est", ct.c_void_p)]
+                ("flags", ct.c_int32), ("cand_ids", ct.c_void_p), ("cand_est", ct.c_void_p), ("metric", ct.c_int32)]
 
 
 class IndexInfo(ct.Structure):
@@ -182,11 +183,14 @@ class Index:
         _check(lib().erq_index_status(self._h, _stream()))
 
     def search(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp32", probe=None, nprobe_per_query=None,
-               return_candidates=False, timing=False, simt_gemm=False, async_mode=False):
+               return_candidates=False, timing=False, simt_gemm=False, async_mode=False, metric="l2"):
+        """erq_search.  metric "l2": squared distances, ascending; "ip": inner
+        products, descending."""
         Q = _dev(Q, torch.float32, "Q", 2)
         nq = Q.shape[0]
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        sp.metric = METRIC[metric]
         sp.flags = (1 if timing else 0) | (2 if simt_gemm else 0) | (4 if async_mode else 0)
         keep = []
         if nprobe_per_query is not None:
@@ -217,13 +221,14 @@ class Index:
         _check(lib().erq_search_timing(self._h, ms, 6))
         return dict(zip(("rotate", "probe", "plan", "scan", "merge", "rerank"), list(ms)))
 
-    def autotune(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp16", nprobe_per_query=None, reps=3):
+    def autotune(self, Q, k, *, rerank_k=0, nprobe=1, precision="fp16", nprobe_per_query=None, reps=3, metric="l2"):
         """Time every supported scan work-item shape on this query batch and keep
         the fastest for later searches of this size; returns (queries per item,
         rows per item)."""
         Q = _dev(Q, torch.float32, "Q", 2)
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        sp.metric = METRIC[metric]
         keep = None
         if nprobe_per_query is not None:
             keep = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
@@ -256,7 +261,7 @@ class Index:
         return dict(zip(("pairs", "rows", "items", "lists", "blocks", "slot_blocks"), list(out)))
 
     def search_host(self, Q_host, k, *, rerank_k=0, nprobe=1, precision="fp32", async_mode=False,
-                    nprobe_per_query=None):
+                    nprobe_per_query=None, metric="l2"):
         """Search from host memory (pinned for asynchronous copies); returns host tensors.
         ``nprobe_per_query`` (optional) is a device int32 tensor [nq]."""
         if Q_host.is_cuda or Q_host.dtype != torch.float32:
@@ -265,6 +270,7 @@ class Index:
         nq = Q_host.shape[0]
         sp = SearchParams()
         sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC[precision]
+        sp.metric = METRIC[metric]
         sp.flags = 4 if async_mode else 0
         if nprobe_per_query is not None:
             nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)

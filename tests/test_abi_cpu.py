@@ -94,3 +94,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(erq, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         erq.lib(str(tmp_path / "missing.so"))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the header's size and field offsets."""
+    import shutil
+    import subprocess
+    from paper_2409_09913_gb300 import erq
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "erq.h"\n'
+                   'int main(void) {\n'
+                   '  printf("%zu %zu %zu %zu\\n", sizeof(erq_search_params), offsetof(erq_search_params, metric),\n'
+                   '         offsetof(erq_search_params, cand_est), sizeof(erq_build_params));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    size, off_metric, off_est, bsize = map(int, subprocess.run([str(exe)], check=True, capture_output=True,
+                                                               text=True).stdout.split())
+    assert ct.sizeof(erq.SearchParams) == size
+    assert erq.SearchParams.metric.offset == off_metric
+    assert erq.SearchParams.cand_est.offset == off_est
+    assert ct.sizeof(erq.BuildParams) == bsize
