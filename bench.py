@@ -511,6 +511,11 @@ def main():
         # search stream), and the work counters of the last one
         tot, cnt = ix.timing_total()
         phases = {kk: v / max(cnt, 1) for kk, v in tot.items()}
+        # work counters of one synchronous search of the same configuration
+        # (asynchronous searches size their buffers from bounds and leave the
+        # counters of the last synchronous one)
+        ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, nprobe_per_query=npr_d,
+                  metric=args.metric)
         work = ix.stats()
         results[prec] = dict(nprobe=p, ms=ms, qps=job_rate(len(Q), world, ms / 1e3), recall=sweep[prec][p],
                              phases=phases, work=work, clocks=clk.summary(), launches=launches,

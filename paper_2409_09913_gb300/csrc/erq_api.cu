@@ -615,6 +615,12 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.corder = ix->corder;
     pa.npr = npr;
     pa.status = ix->status;
+    // ||q_r - c||^2 (or -<q_r, c>) of the probed pairs: the probe's own values
+    // when it computed them (the FP32 expansion ||q_r||^2 + ||c||^2 - 2<q_r, c>
+    // with an FP32-accurate product), else computed directly below
+    const bool dqc_from_probe = !explicit_probe && nlist > 1;
+    pa.sqd = dqc_from_probe ? sqd : nullptr;
+    pa.dqc = dqc;
     DevChecks ck;
     ck.status = ix->status;
     ck.qlist = nq * (int64_t)maxp;
@@ -625,7 +631,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.ck = ck;
     if ((e = launch_plan(pa, s)) != cudaSuccess) return cuda_fail(e, "plan");
     // dqc needs the validated probe ids
-    if ((e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, ip, dqc, s)) != cudaSuccess) return cuda_fail(e, "dqc");
+    if (!dqc_from_probe && (e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, ip, dqc, s)) != cudaSuccess)
+        return cuda_fail(e, "dqc");
     int64_t Ltot = 0, nitems = 0;
     const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0;
     if (async) {

@@ -32,6 +32,8 @@ struct PlanArgs {
     int64_t* item_off;          // [nlist+1]
     int64_t* qlist;             // [nq*maxp]
     uint32_t* status;
+    const float* sqd;           // optional [nq][nlist] probe values (||q_r - c||^2, or -<q_r, c>): when given,
+    float* dqc;                 //   the plan copies the probed pairs' values into dqc [nq][maxp]
     DevChecks ck;
     unsigned long long* stats;  // [4]: (query, candidate) pairs, rows of distinct probed clusters,
                                 //      tensor-core row blocks, row blocks x padded queries (item tables)

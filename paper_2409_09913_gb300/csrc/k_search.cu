@@ -100,6 +100,7 @@ __global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t pro
                                   int nlist, const int64_t* __restrict__ list_off, int RR,
                                   int32_t* __restrict__ npr, int32_t* __restrict__ probe_c,
                                   int32_t* __restrict__ cnt_c, int32_t* __restrict__ slot_nr,
+                                  const float* __restrict__ sqd, float* __restrict__ dqc,
                                   uint32_t* __restrict__ status, unsigned long long* __restrict__ stats) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long add_pairs = 0, add_rows = 0;
@@ -124,6 +125,7 @@ __global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t pro
                 nr = (int)((size + RR - 1) / RR);
                 if (atomicAdd(&cnt_c[c], 1) == 0) add_rows = (unsigned long long)size;
                 add_pairs = (unsigned long long)size;
+                if (sqd) dqc[t] = sqd[q * nlist + c];      // the probe's value of this pair
             }
         }
         probe_c[t] = c;
@@ -705,7 +707,7 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     count_launch();
     plan_count_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(
         p.probe, p.probe_stride, p.npr_in, p.npr_uniform, p.nq, p.maxp, p.nlist, p.list_off, p.RR, p.npr, p.probe_c,
-        p.cnt_c, p.slot_nr, p.status, p.stats);
+        p.cnt_c, p.slot_nr, p.sqd, p.dqc, p.status, p.stats);
     count_launch();
     plan_query_kernel<<<(unsigned)ceil_div(p.nq, 256), 256, 0, s>>>(p.slot_nr, p.nq, p.maxp, p.slot_off, p.qtot);
     count_launch();
