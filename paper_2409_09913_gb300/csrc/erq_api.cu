@@ -561,21 +561,29 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     // ---- q' = P^T q_r
     const bool simt = (p->flags & ERQ_SEARCH_SIMT_GEMM) != 0;
     int32_t* eQ = (int32_t*)sl[21];
+    const bool need_qn = !explicit_probe && nlist > 1 && !ip;   // ||q_r||^2 for the distance probe
+    bool qn_done = false, qh_done = false;
     if (simt) {
         if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, D, D, 1.f, nullptr, s)) != cudaSuccess)
             return cuda_fail(e, "query rotation");
     } else {
-        if ((e = launch_row_exp(Q, nq, D, eQ, s)) != cudaSuccess) return cuda_fail(e, "query exponents");
-        if ((e = launch_split_hilo(Q, eQ, nq, D, (__half*)sl[23], (__half*)sl[24], s)) != cudaSuccess)
+        // row exponents, ||q_r||^2 and the hi/lo split in one pass; the rotation
+        // GEMM also writes the FP16 copy of q' that the tensor-core scan reads
+        if ((e = launch_query_prep(Q, nq, D, eQ, need_qn ? qn : nullptr, (__half*)sl[23], (__half*)sl[24], s)) !=
+            cudaSuccess)
             return cuda_fail(e, "query split");
+        qn_done = need_qn;
+        __half* qh = prec == ERQ_PREC_FP16 ? (__half*)sl[20] : nullptr;
         if ((e = launch_gemm_tma((__half*)sl[23], (__half*)sl[24], eQ, nq, ix->PT_hi, ix->PT_lo, ix->ePT, D, D, Qrot,
-                                 D, 0, nullptr, nullptr, nullptr, ix->status, s)) != cudaSuccess)
+                                 D, 0, nullptr, nullptr, nullptr, ix->status, s, qh)) != cudaSuccess)
             return cuda_fail(e, "query rotation");
+        qh_done = qh != nullptr;
     }
     if (prec == ERQ_PREC_FP8 &&
         (e = launch_quant_e4m3(Qrot, nq, D, (int)Dq, (unsigned char*)sl[26], (float*)sl[27], s)) != cudaSuccess)
         return cuda_fail(e, "query e4m3");
-    if (prec == ERQ_PREC_FP16 && (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
+    if (prec == ERQ_PREC_FP16 && !qh_done &&
+        (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
         return cuda_fail(e, "query half");
     ERQ_TRY(mark(1));
     // ---- probe
@@ -587,7 +595,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     } else if (nlist == 1) {
         if ((e = launch_fill_i32(probe, nq, 0, s)) != cudaSuccess) return cuda_fail(e, "probe fill");
     } else {
-        if (!ip && (e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess) return cuda_fail(e, "query norms");
+        if (need_qn && !qn_done && (e = launch_row_sqnorm(Q, nq, D, qn, s)) != cudaSuccess)
+            return cuda_fail(e, "query norms");
         if (simt)
             e = ip ? launch_sgemm(true, Q, ix->C, sqd, nq, nlist, D, -1.f, nullptr, s)
                    : launch_sqdist(Q, qn, ix->C, ix->cnorm2, sqd, nq, nlist, D, s);

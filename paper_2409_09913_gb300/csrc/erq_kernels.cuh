@@ -67,9 +67,12 @@ cudaError_t launch_row_topk_fast(const float* V, int64_t rows, int ncols, int64_
 cudaError_t launch_row_exp(const float* X, int64_t n, int K, int32_t* e, cudaStream_t s);
 cudaError_t launch_split_hilo(const float* X, const int32_t* e, int64_t M, int K, __half* hi, __half* lo,
                               cudaStream_t s);
+cudaError_t launch_query_prep(const float* X, int64_t M, int K, int32_t* e, float* sqn, __half* hi, __half* lo,
+                              cudaStream_t s);
 cudaError_t launch_gemm_tma(const __half* Ahi, const __half* Alo, const int32_t* eA, int64_t M, const __half* Bhi,
                             const __half* Blo, const int32_t* eB, int N, int K, float* C, int64_t ldc, int epi,
-                            const float* rown, const float* coln, float* gmin, uint32_t* status, cudaStream_t s);
+                            const float* rown, const float* coln, float* gmin, uint32_t* status, cudaStream_t s,
+                            __half* Ch = nullptr);
 cudaError_t launch_row_topk_groups(const float* V, const float* gmin, int64_t rows, int ncols, int64_t ld, int p,
                                    int32_t* out_idx, int64_t ld_out, cudaStream_t s);
 cudaError_t launch_gemm_tc(const float* A, const int32_t* eA, int64_t M, const float* B, const int32_t* eB, int N,

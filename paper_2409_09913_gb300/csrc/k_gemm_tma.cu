@@ -57,6 +57,7 @@ struct Args {
     const float* rown;       // EPI_DIST: [M]
     const float* coln;       // EPI_DIST: [N]
     float* gmin;             // EPI_DIST, optional: [M][ceil(N / 32)] minimum of each 32-column group
+    __half* Ch;              // optional: an FP16 copy of the output (round to nearest), same layout
     uint32_t* status;
 };
 }  // namespace gemm2
@@ -246,6 +247,25 @@ __global__ void __launch_bounds__(gemm2::THREADS, 1)
                         for (int j = 0; j < 32; ++j)
                             if (nb + j < a.N) crow[j] = out[j];
                     }
+                    if (a.Ch) {                                // FP16 copy (16-byte stores when aligned)
+                        __half* hrow = a.Ch + m * a.ldc + nb;
+                        if (nb + 32 <= a.N && (a.ldc % 8) == 0) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 8) {
+                                const __half2 h0 = __floats2half2_rn(out[j], out[j + 1]);
+                                const __half2 h1 = __floats2half2_rn(out[j + 2], out[j + 3]);
+                                const __half2 h2 = __floats2half2_rn(out[j + 4], out[j + 5]);
+                                const __half2 h3 = __floats2half2_rn(out[j + 6], out[j + 7]);
+                                *reinterpret_cast<uint4*>(hrow + j) = make_uint4(
+                                    *reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
+                                    *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (nb + j < a.N) hrow[j] = __float2half_rn(out[j]);
+                        }
+                    }
                 }
             }
             tc_fence_before();
@@ -286,6 +306,68 @@ __global__ void split_hilo_kernel(const float* __restrict__ X, const int32_t* __
     reinterpret_cast<uint4*>(lo)[t] = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Per-search query preparation in one pass per row (one warp per row): the
+// row exponent of row_exp_kernel, optionally the squared norm in the order of
+// row_sqnorm_kernel, and the hi/lo split of split_hilo_kernel -- the same
+// operations, so the same bits, with the row read twice (the second time from
+// cache) instead of three times by three launches.
+__global__ void query_prep_kernel(const float* __restrict__ X, int64_t M, int K, int32_t* __restrict__ e,
+                                  float* __restrict__ sqn, __half* __restrict__ hi, __half* __restrict__ lo) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= M) return;
+    const float* x = X + w * K;
+    float mx = 0.f, ss = 0.f;
+    for (int k = lane * 4; k < K; k += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(x + k);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        ss = fmaf(v.x, v.x, ss);
+        ss = fmaf(v.y, v.y, ss);
+        ss = fmaf(v.z, v.z, ss);
+        ss = fmaf(v.w, v.w, ss);
+    }
+    mx = warp_max(mx);
+    ss = warp_sum(ss);
+    int ex = 0;
+    if (mx > 0.f) {
+        frexpf(mx, &ex);               // mx in [2^(ex-1), 2^ex)
+        ex = ex - 14;                  // mx * 2^-ex in [2^13, 2^14)
+        ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+    }
+    if (lane == 0) {
+        e[w] = ex;
+        if (sqn) sqn[w] = ss;
+    }
+    const float s = __int_as_float((127 - ex) << 23);          // 2^-e
+    const int per = K / 8;
+    for (int c = lane; c < per; c += 32) {
+        const float4 a = reinterpret_cast<const float4*>(x)[2 * c];
+        const float4 b = reinterpret_cast<const float4*>(x)[2 * c + 1];
+        const float v[8] = {a.x * s, a.y * s, a.z * s, a.w * s, b.x * s, b.y * s, b.z * s, b.w * s};
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half h0 = __float2half_rn(v[2 * i]), h1 = __float2half_rn(v[2 * i + 1]);
+            const __half l0 = __float2half_rn(v[2 * i] - __half2float(h0));
+            const __half l1 = __float2half_rn(v[2 * i + 1] - __half2float(h1));
+            const __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+            h[i] = *reinterpret_cast<const uint32_t*>(&hh);
+            l[i] = *reinterpret_cast<const uint32_t*>(&ll);
+        }
+        reinterpret_cast<uint4*>(hi)[w * per + c] = make_uint4(h[0], h[1], h[2], h[3]);
+        reinterpret_cast<uint4*>(lo)[w * per + c] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+cudaError_t launch_query_prep(const float* X, int64_t M, int K, int32_t* e, float* sqn, __half* hi, __half* lo,
+                              cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    if (K % 8 != 0) return cudaErrorInvalidValue;
+    count_launch();
+    query_prep_kernel<<<(unsigned)ceil_div(M * 32, 256), 256, 0, s>>>(X, M, K, e, sqn, hi, lo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_hilo(const float* X, const int32_t* e, int64_t M, int K, __half* hi, __half* lo,
                               cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
@@ -317,7 +399,8 @@ static bool make_half_map(CUtensorMap* map, const __half* base, int64_t rows, in
 
 cudaError_t launch_gemm_tma(const __half* Ahi, const __half* Alo, const int32_t* eA, int64_t M, const __half* Bhi,
                             const __half* Blo, const int32_t* eB, int N, int K, float* C, int64_t ldc, int epi,
-                            const float* rown, const float* coln, float* gmin, uint32_t* status, cudaStream_t s) {
+                            const float* rown, const float* coln, float* gmin, uint32_t* status, cudaStream_t s,
+                            __half* Ch) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K % gemm2::BK != 0 || M > 0x7fffffff) return cudaErrorInvalidValue;
     CUtensorMap mAh, mAl, mBh, mBl;
@@ -326,7 +409,7 @@ cudaError_t launch_gemm_tma(const __half* Ahi, const __half* Alo, const int32_t*
         return cudaErrorInvalidValue;
     gemm2::Args a;
     a.eA = eA; a.eB = eB; a.C = C; a.ldc = ldc; a.M = M; a.N = N; a.K = K; a.epi = epi;
-    a.rown = rown; a.coln = coln; a.gmin = gmin; a.status = status;
+    a.rown = rown; a.coln = coln; a.gmin = gmin; a.Ch = Ch; a.status = status;
     cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm2::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
