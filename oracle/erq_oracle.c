@@ -485,7 +485,7 @@ void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint8
  * so d est / d q_r = 2 (q_r - c) + f * P ybar.  grad_q = sum_j g_j d est_j/d q_r. */
 void orc_backward(int d, int B, const float* P, const float* C, const uint8_t* codes, const double* stats,
                   const double* Q, int64_t nq, int nc, const int64_t* rows, const int32_t* cl,
-                  const double* g, double* grad)
+                  const double* g, int metric, double* grad)
 {
 #pragma omp parallel
     {
@@ -508,7 +508,10 @@ void orc_backward(int d, int B, const float* P, const float* C, const uint8_t* c
                     double pv = 0.0;                /* (P ybar)[k] */
                     const float* p = P + (size_t)k * d;
                     for (int m = 0; m < d; ++m) pv += (double)p[m] * v[m];
-                    gq[k] += gj * (2.0 * (Q[(size_t)i * d + k] - (double)c[k]) + f * pv);
+                    /* R9: est = <c, q_r> + ||o_r - c|| inv <ybar, P^T q_r>, so
+                     * d est / d q_r = c - (f / 2) P ybar */
+                    gq[k] += metric ? gj * ((double)c[k] - 0.5 * f * pv)
+                                    : gj * (2.0 * (Q[(size_t)i * d + k] - (double)c[k]) + f * pv);
                 }
             }
         }

@@ -67,7 +67,7 @@ def lib():
         L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
                                         _i64, _i32, ct.c_int, _f64]
         L.orc_backward.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
-                                   _i64, _i32, _f64, _f64]
+                                   _i64, _i32, _f64, ct.c_int, _f64]
         L.orc_num_threads.restype = ct.c_int
         _lib = L
     return _lib
@@ -199,14 +199,17 @@ def estimate_rows(ix, Q, ids, metric="l2"):
     return out
 
 
-def backward(ix, Q, ids, g):
-    """sum_j g[i,j] * d est(q_i, ids[i,j]) / d q_i  (FP64)."""
+def backward(ix, Q, ids, g, metric="l2"):
+    """sum_j g[i,j] * d est(q_i, ids[i,j]) / d q_i  (FP64); est is the estimated
+    squared distance (metric "l2") or inner product (metric "ip")."""
+    if metric not in ("l2", "ip"):
+        raise ValueError(metric)
     Q = _q64(Q)
     ids = np.atleast_2d(ids)
     rows, cl = _rows_and_clusters(ix, ids)
     out = np.empty(Q.shape, np.float64)
     lib().orc_backward(ix["d"], ix["B"], ix["P"], ix["C"], ix["codes"], ix["stats"], Q, Q.shape[0],
-                       ids.shape[1], rows, cl, np.ascontiguousarray(g, np.float64), out)
+                       ids.shape[1], rows, cl, np.ascontiguousarray(g, np.float64), 1 if metric == "ip" else 0, out)
     return out
 
 

@@ -448,3 +448,24 @@ def test_ip_estimate_rows_agree_with_search():
     est = oracle.estimate_rows(ix, Q, res["cand_ids"], metric="ip")
     np.testing.assert_allclose(est, res["cand_est"], rtol=0, atol=0)
     assert (np.diff(res["cand_est"], axis=1) <= 0).all()
+
+
+def test_ip_backward_matches_finite_differences():
+    """The gradient of the estimated inner products w.r.t. the raw query equals
+    central finite differences (h = 1e-3, FP64) of the oracle's estimate; the
+    estimate is linear in q_r, so the differences are exact up to rounding."""
+    X, lab = S.mixture(300, 16, 3, 195)
+    ix = oracle.build_index(X, S.random_orthogonal(16, 196), lab, 3, 4)
+    Q = S.mixture(3, 16, 3, 197, comp_seed=195)[0].astype(np.float64)
+    ids = np.stack([S.rng(198 + i).choice(300, 7, replace=False) for i in range(3)])
+    g = S.normal((3, 7), 199).astype(np.float64)
+    grad = oracle.backward(ix, Q, ids, g, metric="ip")
+    h = 1e-3
+    fd = np.zeros_like(Q)
+    for k in range(16):
+        e = np.zeros(16)
+        e[k] = h
+        fp = (oracle.estimate_rows(ix, Q + e, ids, metric="ip") * g).sum(1)
+        fm = (oracle.estimate_rows(ix, Q - e, ids, metric="ip") * g).sum(1)
+        fd[:, k] = (fp - fm) / (2 * h)
+    np.testing.assert_allclose(grad, fd, rtol=1e-7, atol=1e-7)
