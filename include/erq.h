@@ -225,6 +225,19 @@ erq_status erq_estimate(erq_index* index, const float* Q, int64_t nq, int32_t nc
 erq_status erq_search_backward(erq_index* index, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
                                const float* grad_scores, float* grad_Q, void* stream);
 
+/* erq_estimate and erq_search_backward for a given erq_metric.  With
+ * ERQ_METRIC_IP, est is the estimated inner product
+ *   <c, q_r> - (f_res / 2) <ybar, P^T q_r>   (see erq_search)
+ * and its gradient is d est / d q_r = c - (f_res / 2) P ybar, evaluated as
+ * grad_Q = sum_j g_j c_j - (sum_j g_j (f_res,j / 2) ybar_j) P^T.  ERQ_METRIC_L2
+ * is exactly erq_estimate / erq_search_backward.  Errors: as those, and EINVAL
+ * for an unknown metric. */
+erq_status erq_estimate_metric(erq_index* index, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                               int32_t metric, float* est, void* stream);
+erq_status erq_search_backward_metric(erq_index* index, const float* Q, int64_t nq, int32_t nc,
+                                      const int64_t* ids, const float* grad_scores, int32_t metric,
+                                      float* grad_Q, void* stream);
+
 /* Copy one field of the index to host memory (dst_host must hold dst_bytes).
  * Errors: EINVAL (field, size), ECUDA. */
 erq_status erq_index_export(const erq_index* index, int32_t field, void* dst_host, int64_t dst_bytes);

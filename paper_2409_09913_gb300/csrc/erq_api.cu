@@ -793,9 +793,10 @@ extern "C" erq_status erq_search_host(erq_index* ix, const float* Q_host, int64_
     return ERQ_OK;
 }
 
-extern "C" erq_status erq_estimate(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
-                                   float* est, void* stream) {
+extern "C" erq_status erq_estimate_metric(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                          int32_t metric, float* est, void* stream) {
     if (!ix || nq < 0 || nc < 0) return fail(ERQ_EINVAL, "erq_estimate: bad arguments");
+    if (metric != ERQ_METRIC_L2 && metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_estimate: unknown metric");
     if (nq == 0 || nc == 0) return ERQ_OK;
     if (!Q || !ids || !est) return fail(ERQ_EINVAL, "erq_estimate: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -804,13 +805,22 @@ extern "C" erq_status erq_estimate(erq_index* ix, const float* Q, int64_t nq, in
     cudaError_t e;
     if ((e = launch_sgemm(false, Q, ix->P, Qrot, nq, ix->D, ix->D, 1.f, nullptr, s)) != cudaSuccess)
         return cuda_fail(e, "estimate rotation");
-    if ((e = launch_estimate(Q, Qrot, ids, nq, nc, ix, est, s)) != cudaSuccess) return cuda_fail(e, "estimate");
+    if ((e = launch_estimate(Q, Qrot, ids, nq, nc, ix, metric == ERQ_METRIC_IP ? 1 : 0, est, s)) != cudaSuccess)
+        return cuda_fail(e, "estimate");
     return ERQ_OK;
 }
 
-extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
-                                          const float* grad_scores, float* grad_Q, void* stream) {
+extern "C" erq_status erq_estimate(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                   float* est, void* stream) {
+    return erq_estimate_metric(ix, Q, nq, nc, ids, ERQ_METRIC_L2, est, stream);
+}
+
+extern "C" erq_status erq_search_backward_metric(erq_index* ix, const float* Q, int64_t nq, int32_t nc,
+                                                 const int64_t* ids, const float* grad_scores, int32_t metric,
+                                                 float* grad_Q, void* stream) {
     if (!ix || nq < 0 || nc < 0) return fail(ERQ_EINVAL, "erq_search_backward: bad arguments");
+    if (metric != ERQ_METRIC_L2 && metric != ERQ_METRIC_IP)
+        return fail(ERQ_EINVAL, "erq_search_backward: unknown metric");
     if (nq == 0) return ERQ_OK;
     if (!Q || !grad_Q || (nc > 0 && (!ids || !grad_scores))) return fail(ERQ_EINVAL, "erq_search_backward: null pointer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -820,7 +830,8 @@ extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t
     float* Wv = V + (mat + 63) / 64 * 64;
     int32_t* eV = (int32_t*)(Wv + (mat + 63) / 64 * 64);
     cudaError_t e;
-    if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, V, Wv, s)) != cudaSuccess)
+    if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, metric == ERQ_METRIC_IP ? 1 : 0, V, Wv, s)) !=
+        cudaSuccess)
         return cuda_fail(e, "backward gather");
     // grad_Q = V P^T + Wv  (B = P read as [n][k])
     if ((e = launch_row_exp(V, nq, ix->D, eV, s)) != cudaSuccess) return cuda_fail(e, "backward exponents");
@@ -828,6 +839,11 @@ extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t
                             s)) != cudaSuccess)
         return cuda_fail(e, "backward gemm");
     return ERQ_OK;
+}
+
+extern "C" erq_status erq_search_backward(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                          const float* grad_scores, float* grad_Q, void* stream) {
+    return erq_search_backward_metric(ix, Q, nq, nc, ids, grad_scores, ERQ_METRIC_L2, grad_Q, stream);
 }
 
 // ---------------------------------------------------------------------------

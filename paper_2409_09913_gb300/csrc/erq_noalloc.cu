@@ -71,7 +71,7 @@ extern "C" erq_status erq_search_backward_noalloc(erq_index* ix, const float* Q,
     int32_t* eV = (int32_t*)(Wv + mat_pad);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, V, Wv, s)) != cudaSuccess)
+    if ((e = launch_backward_gather(Q, ids, grad_scores, nq, nc, ix, 0, V, Wv, s)) != cudaSuccess)
         return cuda_fail(e, "backward gather");
     if ((e = launch_row_exp(V, nq, ix->D, eV, s)) != cudaSuccess) return cuda_fail(e, "backward exponents");
     if ((e = launch_gemm_tc(V, eV, nq, ix->P, ix->eP, ix->D, ix->D, grad_Q, ix->D, 0, Wv, nullptr, nullptr, ix->status,

@@ -97,8 +97,8 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
                           int do_rerank, int ip, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           const DevChecks& ck, cudaStream_t s);
 cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
-                            const erq_index* ix, float* est, cudaStream_t s);
+                            const erq_index* ix, int ipm, float* est, cudaStream_t s);
 cudaError_t launch_backward_gather(const float* Q, const int64_t* ids, const float* gs, int64_t nq, int nc,
-                                   const erq_index* ix, float* V, float* Wv, cudaStream_t s);
+                                   const erq_index* ix, int ipm, float* V, float* Wv, cudaStream_t s);
 
 }  // namespace erq

@@ -614,7 +614,7 @@ __global__ void estimate_kernel(const float* __restrict__ Q, const float* __rest
                                 const int64_t* __restrict__ row_of, const int32_t* __restrict__ cl_of_row,
                                 const float* __restrict__ C, const uint8_t* __restrict__ codes,
                                 const float* __restrict__ g_const, const float* __restrict__ f_res, int D, int B,
-                                float* __restrict__ est, uint32_t* __restrict__ status) {
+                                int ipm, float* __restrict__ est, uint32_t* __restrict__ status) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nq * nc) return;
@@ -635,13 +635,19 @@ __global__ void estimate_kernel(const float* __restrict__ Q, const float* __rest
     const float off = (float)((1 << B) - 1);
     float dq = 0.f, ip = 0.f;
     for (int k = lane; k < D; k += 32) {
-        const float d = x[k] - c[k];
-        dq = fmaf(d, d, dq);
+        if (ipm) {
+            dq = fmaf(c[k], x[k], dq);                     // <c, q_r>
+        } else {
+            const float d = x[k] - c[k];
+            dq = fmaf(d, d, dq);
+        }
         ip = fmaf(2.f * (float)code[k] - off, xr[k], ip);
     }
     dq = warp_sum(dq);
     ip = warp_sum(ip);
-    if (lane == 0) est[w] = dq + g_const[row] + 0.5f * f_res[row] * ip;
+    // squared distance ||q_r - c||^2 + g + (f_res/2) <2 ybar, q'>, or inner
+    // product <c, q_r> - (f_res/4) <2 ybar, q'>
+    if (lane == 0) est[w] = ipm ? dq - 0.25f * f_res[row] * ip : dq + g_const[row] + 0.5f * f_res[row] * ip;
 }
 
 // ---------------------------------------------------------------------------
@@ -659,10 +665,13 @@ __global__ void __launch_bounds__(256) backward_gather_kernel(const float* __res
                                                               const float* __restrict__ C,
                                                               const uint8_t* __restrict__ codes,
                                                               const float* __restrict__ f_res, int D, int B,
-                                                              float* __restrict__ V, float* __restrict__ Wv,
+                                                              int ipm, float* __restrict__ V, float* __restrict__ Wv,
                                                               uint32_t* __restrict__ status) {
+    // squared distance: d est / d q_r = 2 (q_r - c) + f_res P ybar;
+    // inner product:    d est / d q_r = c - (f_res / 2) P ybar
     const int64_t q = blockIdx.x;
     const float off = 0.5f * (float)((1 << B) - 1);
+    const float fs = ipm ? -0.5f : 1.f;
     for (int k = threadIdx.x; k < D; k += blockDim.x) {
         float v = 0.f, wc = 0.f, G = 0.f;
         for (int j = 0; j < nc; ++j) {
@@ -675,12 +684,12 @@ __global__ void __launch_bounds__(256) backward_gather_kernel(const float* __res
             const float g = gs[q * nc + j];
             const int64_t row = row_of[id];
             const float yb = (float)codes[row * D + k] - off;
-            v = fmaf(g * f_res[row], yb, v);
+            v = fmaf(g * (fs * f_res[row]), yb, v);
             wc = fmaf(g, C[(int64_t)cl_of_row[row] * D + k], wc);
             G += g;
         }
         V[q * D + k] = v;
-        Wv[q * D + k] = 2.f * (G * Q[q * D + k] - wc);
+        Wv[q * D + k] = ipm ? wc : 2.f * (G * Q[q * D + k] - wc);
     }
 }
 
@@ -868,22 +877,22 @@ cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float*
 }
 
 cudaError_t launch_estimate(const float* Q, const float* Qrot, const int64_t* ids, int64_t nq, int nc,
-                            const erq_index* ix, float* est, cudaStream_t s) {
+                            const erq_index* ix, int ipm, float* est, cudaStream_t s) {
     const int64_t w = nq * nc;
     if (w <= 0) return cudaSuccess;
     count_launch();
     estimate_kernel<<<(unsigned)ceil_div(w * 32, 256), 256, 0, s>>>(Q, Qrot, ids, nq, nc, ix->N, ix->row_of,
                                                                     ix->cl_of_row, ix->C, ix->codes, ix->g_const,
-                                                                    ix->f_res, ix->D, ix->B, est, ix->status);
+                                                                    ix->f_res, ix->D, ix->B, ipm, est, ix->status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backward_gather(const float* Q, const int64_t* ids, const float* gs, int64_t nq, int nc,
-                                   const erq_index* ix, float* V, float* Wv, cudaStream_t s) {
+                                   const erq_index* ix, int ipm, float* V, float* Wv, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     count_launch();
     backward_gather_kernel<<<(unsigned)nq, 256, 0, s>>>(Q, ids, gs, nc, ix->N, ix->row_of, ix->cl_of_row, ix->C,
-                                                        ix->codes, ix->f_res, ix->D, ix->B, V, Wv, ix->status);
+                                                        ix->codes, ix->f_res, ix->D, ix->B, ipm, V, Wv, ix->status);
     return cudaGetLastError();
 }
 

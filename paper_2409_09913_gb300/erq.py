@@ -26,7 +26,8 @@ EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index",
            "erq_index_status", "erq_rotate", "erq_encode", "erq_search", "erq_search_host", "erq_estimate",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
            "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total",
-           "erq_autotune", "erq_set_scan_config", "erq_scan_config"]
+           "erq_autotune", "erq_set_scan_config", "erq_scan_config", "erq_estimate_metric",
+           "erq_search_backward_metric"]
 
 
 class ErqError(RuntimeError):
@@ -81,6 +82,8 @@ def lib(path: str | None = None):
     L.erq_search_host.argtypes = [vp, vp, i64, ct.POINTER(SearchParams), vp, vp, vp]
     L.erq_estimate.argtypes = [vp, vp, i64, i32, vp, vp, vp]
     L.erq_search_backward.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+    L.erq_estimate_metric.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp]
+    L.erq_search_backward_metric.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp, vp]
     L.erq_index_export.argtypes = [vp, i32, vp, i64]
     L.erq_index_save.argtypes = [vp, ct.c_char_p]
     L.erq_index_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
@@ -281,20 +284,22 @@ class Index:
         _check(lib().erq_search_host(self._h, _ptr(Q_host), nq, ct.byref(sp), _ptr(ids), _ptr(dists), _stream()))
         return ids, dists
 
-    def estimate(self, Q, ids):
+    def estimate(self, Q, ids, metric="l2"):
+        """Estimated squared distances ("l2") or inner products ("ip") of Q[i] to ids[i, :]."""
         Q = _dev(Q, torch.float32, "Q", 2)
         ids = _dev(ids, torch.int64, "ids", 2)
         est = torch.empty(ids.shape, dtype=torch.float32, device=Q.device)
-        _check(lib().erq_estimate(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(est), _stream()))
+        _check(lib().erq_estimate_metric(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), METRIC[metric],
+                                         _ptr(est), _stream()))
         return est
 
-    def search_backward(self, Q, ids, grad_scores):
+    def search_backward(self, Q, ids, grad_scores, metric="l2"):
         Q = _dev(Q, torch.float32, "Q", 2)
         ids = _dev(ids, torch.int64, "ids", 2)
         g = _dev(grad_scores, torch.float32, "grad_scores", 2)
         out = torch.empty_like(Q)
-        _check(lib().erq_search_backward(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
-                                         _ptr(out), _stream()))
+        _check(lib().erq_search_backward_metric(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
+                                                METRIC[metric], _ptr(out), _stream()))
         return out
 
     def search_backward_noalloc(self, Q, ids, grad_scores, out=None):

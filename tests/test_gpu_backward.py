@@ -63,3 +63,26 @@ def test_backward_empty_candidates(erq):
     ids[:] = -1
     got = gx.search_backward(to_dev(Q), to_dev(ids), to_dev(g)).cpu().numpy()
     assert np.all(got == 0)
+
+
+def test_ip_estimate_and_backward_match_oracle(erq):
+    """Inner-product metric: estimates <c, q_r> - (f_res/2) <ybar, P^T q_r> and
+    their gradient c - (f_res/2) P ybar against the FP64 oracle (absolute
+    tolerance scaled by ||q_r|| max ||o_r||, as inner products can be ~0)."""
+    X, P, gx, ox, Q, ids, g = _setup(erq, seed=2300)
+    ids[1, 3] = -1                              # ignored candidate
+    est = gx.estimate(to_dev(Q), to_dev(ids), metric="ip").cpu().numpy().astype(np.float64)
+    ref = oracle.estimate_rows(ox, Q, ids, metric="ip")
+    assert np.isnan(est[1, 3]) and np.isnan(ref[1, 3])
+    ok = ids >= 0
+    sc = np.linalg.norm(Q.astype(np.float64), axis=1)[:, None] * np.linalg.norm(X.astype(np.float64), axis=1).max()
+    assert (np.abs(est - ref)[ok] <= 1e-5 * np.broadcast_to(sc, est.shape)[ok]).all()
+    got = gx.search_backward(to_dev(Q), to_dev(ids), to_dev(g), metric="ip").cpu().numpy().astype(np.float64)
+    refg = oracle.backward(ox, Q, ids, g.astype(np.float64), metric="ip")
+    scale = np.abs(refg).max(1, keepdims=True)
+    assert (np.abs(got - refg) / scale).max() < 2e-5
+    # autograd over the inner products
+    from paper_2409_09913_gb300.autograd import EstimatedScores
+    Qt = to_dev(Q).requires_grad_(True)
+    (EstimatedScores.apply(Qt, gx, to_dev(ids), "ip").nan_to_num() * to_dev(g)).sum().backward()
+    assert (np.abs(Qt.grad.cpu().numpy() - refg) / scale).max() < 2e-5
