@@ -6,10 +6,12 @@
  * o' = P^{-1}(o_r - c), to a B-bit-per-coordinate code ybar_u (Section 3.1,
  * Algorithm 1) and estimates squared distances to a query q_r from the code,
  * two per-vector floats and the rotated query (Eq. 3.3 with
- * Eq. (eq:dis to ip)).  Combined with an IVF index (Section 4.1) this gives
- * approximate nearest-neighbour search; the library adds exact re-ranking of
- * the estimated top-k' and the gradient of the estimated scores with respect
- * to the query.
+ * Eq. (eq:dis to ip)), or inner products with the same estimator (the
+ * adaptation Section 7 defers to RaBitQ; see erq_search).  Combined with an
+ * IVF index (Section 4.1) this gives approximate nearest-neighbour or
+ * maximum-inner-product search; the library adds exact re-ranking of the
+ * estimated top-k' and the gradient of the estimated scores with respect to
+ * the query.
  *
  * Conventions for every entry point:
  *  - Array arguments are caller-owned CUDA device pointers unless the name
