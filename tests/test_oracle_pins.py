@@ -469,3 +469,18 @@ def test_ip_backward_matches_finite_differences():
         fm = (oracle.estimate_rows(ix, Q - e, ids, metric="ip") * g).sum(1)
         fd[:, k] = (fp - fm) / (2 * h)
     np.testing.assert_allclose(grad, fd, rtol=1e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("case", _golden()["inner_product"], ids=lambda c: f"B{c['B']}-c{c['c']}")
+def test_ip_estimator_hand_examples(case):
+    """Hand-derived inner-product estimates (tests/golden), P = I."""
+    o = np.array(case["o"], np.float32)
+    c = np.array(case["c"], np.float32)
+    q = np.array(case["q"], np.float64)
+    est, _ = _ip_est_single(o, c, q, case["B"], np.eye(2, dtype=np.float32))
+    assert est == pytest.approx(eval(case["est"]), rel=1e-6)
+    X = o[None].astype(np.float32)
+    ix = oracle.build_index(X, np.eye(2, dtype=np.float32), np.zeros(1, np.int32), 1, case["B"],
+                            centroids_in=c[None])
+    ex = oracle.search(ix, q[None], 1, kprime=1, nprobe=1, metric="ip")
+    assert ex["dists"][0, 0] == pytest.approx(eval(case["true"]), rel=1e-6)
