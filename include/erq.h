@@ -45,7 +45,7 @@ typedef enum {
     ERQ_ENOMEM = 2,          /* device or host allocation failed               */
     ERQ_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed    */
     ERQ_ETIMEOUT = 4,        /* a bounded device-side wait ran out             */
-    ERQ_EUNSUPPORTED = 5,    /* valid request this build or GPU cannot serve   */
+    ERQ_EUNSUPPORTED = 5,    /* valid request the library or GPU cannot serve  */
     ERQ_EIO = 6              /* file error in save/load                        */
 } erq_status;
 
