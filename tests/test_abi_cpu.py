@@ -119,3 +119,11 @@ def test_struct_layouts_match_header(tmp_path):
     assert erq.SearchParams.metric.offset == off_metric
     assert erq.SearchParams.cand_est.offset == off_est
     assert ct.sizeof(erq.BuildParams) == bsize
+
+
+def test_metric_entry_points_validate_on_host(L):
+    """The metric variants reject bad arguments before any device work."""
+    from paper_2409_09913_gb300 import erq
+    assert L.erq_estimate_metric(_vp(0), _vp(8), 1, 1, _vp(8), 1, _vp(8), _vp()) == erq.ERQ_EINVAL
+    assert L.erq_search_backward_metric(_vp(0), _vp(8), 1, 1, _vp(8), _vp(8), 1, _vp(8), _vp()) == erq.ERQ_EINVAL
+    assert b"bad arguments" in L.erq_last_error()
