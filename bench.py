@@ -267,8 +267,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "nprobe": nprobe, "B": args.B,
-                                             "rerank_k": kp, "k": args.k, "similarity": args.metric},
+            "data": "synthetic", "config": {"workload": args.workload, "N": len(X), "D": cfg["d"],
+                                             "nlist": cfg["nlist"], "B": args.B, "nq": len(Q), "k": args.k,
+                                             "rerank_k": kp, "precision": "fp64 (oracle)", "nprobe": nprobe,
+                                             "similarity": args.metric,
+                                             "l2": "inputs larger than L2 (codes > 129 MB)"},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe {nprobe}"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
