@@ -300,9 +300,12 @@ erq_status erq_scan_config(const erq_index* index, int32_t* out, int32_t n);
  * intermediates (2 * nq * D floats and nq ints) live in one static device array
  * of ERQ_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
  * keeps until the process exits; requests with 8*nq*D + 4*nq + 512 bytes above
- * that size are rejected with ERQ_EINVAL.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) and should be made before
- * any stream capture.  All calls share the array and the previous call's
+ * that size are rejected with ERQ_EINVAL (at D = 1024: nq <= 2046).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of the process; it should be made before any
+ * stream capture, and the kept address is no longer valid once the device's
+ * primary context is destroyed (cudaDeviceReset), after which this entry point
+ * must not be called again in that process.  All calls share the array and the previous call's
  * contents are never read, but calls that can overlap on the GPU (different
  * streams or threads) race on it and must be serialised by the caller.  No
  * memory is allocated or freed by this call. */

@@ -10,6 +10,7 @@ TEST INFRASTRUCTURE ONLY.  Follows arXiv 2409.09913:
 * ``search``                    -- probe, Eq. 3.3 + Eq. (eq:dis to ip) estimates, top-k',
   exact re-rank, top-k; or the same for inner products (reading R9: Section 7
   defers the inner-product metric to RaBitQ's estimator).
+* ``rerank``                    -- exact re-rank of given candidate sets (FP64, numpy).
 * ``estimate_rows`` / ``backward`` -- estimated distances of given pairs and their
   gradient w.r.t. the raw query.
 * ``brute_force_quantize``      -- exhaustive argmax of Eq. 3.2 (optimization) over the
@@ -27,7 +28,7 @@ from . import build as _build
 
 __all__ = [
     "lib", "centroids", "rotate", "quantize", "build_index", "search", "estimate_rows",
-    "backward", "centroid_dists", "brute_force_quantize", "exact_knn", "num_threads",
+    "backward", "rerank", "centroid_dists", "brute_force_quantize", "exact_knn", "num_threads",
     "stored_factors",
 ]
 
@@ -211,6 +212,35 @@ def backward(ix, Q, ids, g, metric="l2"):
     lib().orc_backward(ix["d"], ix["B"], ix["P"], ix["C"], ix["codes"], ix["stats"], Q, Q.shape[0],
                        ids.shape[1], rows, cl, np.ascontiguousarray(g, np.float64), 1 if metric == "ip" else 0, out)
     return out
+
+
+def rerank(X, Q, cand_ids, k, metric="l2"):
+    """Exact re-rank of given candidate sets (the last step of the search):
+    for query i, the FP64 squared distance ||x_j - q_i||^2 (metric "l2") or
+    inner product <x_j, q_i> (metric "ip") of every candidate id j >= 0 in
+    cand_ids[i], ordered by (distance, id) ascending (inner products: by
+    (-<x_j, q_i>, id)), first k kept.  Returns (ids int64 [nq, k], values
+    float64 [nq, k]) with -1 / +inf (ip: -inf) where fewer than k candidates
+    exist.  Written out from the definition with numpy, independent of the C
+    file."""
+    if metric not in ("l2", "ip"):
+        raise ValueError(metric)
+    X = np.asarray(X)
+    Q = _q64(Q)
+    cand_ids = np.atleast_2d(np.asarray(cand_ids, np.int64))
+    nq = Q.shape[0]
+    ids = np.full((nq, k), -1, np.int64)
+    vals = np.full((nq, k), np.inf if metric == "l2" else -np.inf, np.float64)
+    for i in range(nq):
+        c = np.unique(cand_ids[i][cand_ids[i] >= 0])
+        if len(c) == 0:
+            continue
+        x = X[c].astype(np.float64)
+        v = ((x - Q[i]) ** 2).sum(1) if metric == "l2" else -(x @ Q[i])
+        o = np.lexsort((c, v))[:k]
+        ids[i, :len(o)] = c[o]
+        vals[i, :len(o)] = v[o] if metric == "l2" else -v[o]
+    return ids, vals
 
 
 def centroid_dists(C, Q):

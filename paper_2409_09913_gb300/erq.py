@@ -129,6 +129,24 @@ def _dev(t, dtype, name, ndim=None):
     return t.contiguous()
 
 
+def _check_out(out, like, name="out"):
+    """A caller-supplied output buffer that the library writes through its raw
+    pointer: a tensor of ``like``'s dtype and shape, contiguous, on the same
+    CUDA device (anything else would be written out of bounds or in the wrong
+    layout)."""
+    if not isinstance(out, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if out.dtype != like.dtype:
+        raise TypeError(f"{name} must be {like.dtype}, got {out.dtype}")
+    if tuple(out.shape) != tuple(like.shape):
+        raise ValueError(f"{name} must have shape {tuple(like.shape)}, got {tuple(out.shape)}")
+    if not out.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not out.is_cuda or out.device != like.device:
+        raise ValueError(f"{name} must be on {like.device}, got {out.device}")
+    return out
+
+
 def kernel_launches() -> int:
     return int(lib().erq_kernel_launches())
 
@@ -305,11 +323,12 @@ class Index:
     def search_backward_noalloc(self, Q, ids, grad_scores, out=None):
         """erq_search_backward without device allocation inside the call (its
         intermediates live in the library's fixed scratch array); ``out`` may be
-        a preallocated [nq, D] float32 CUDA tensor."""
+        a preallocated contiguous [nq, D] float32 tensor on Q's device (checked:
+        TypeError / ValueError otherwise)."""
         Q = _dev(Q, torch.float32, "Q", 2)
         ids = _dev(ids, torch.int64, "ids", 2)
         g = _dev(grad_scores, torch.float32, "grad_scores", 2)
-        out = torch.empty_like(Q) if out is None else out
+        out = torch.empty_like(Q) if out is None else _check_out(out, Q)
         _check(lib().erq_search_backward_noalloc(self._h, _ptr(Q), Q.shape[0], ids.shape[1], _ptr(ids), _ptr(g),
                                                  _ptr(out), _stream()))
         return out

@@ -35,6 +35,33 @@ def assert_close_rel(got, ref, rtol=FP32_RTOL, what="values"):
     return err.max(initial=0.0)
 
 
+def check_final_vs_own_candidates(X, Q, cand_ids, ids, dists, k, metric="l2", what="re-ranked", max_excluded=0.01):
+    """The search's final output for EVERY query against the exact FP64
+    re-rank (oracle.rerank) of the candidate set the GPU itself selected:
+    distances within 1e-5 relative (inner products: within 1e-5 * ||q|| *
+    max ||x||, absolute), ids bit-exact at every slot not decided by a near-tie
+    of that size.  Returns the fraction of excluded slots."""
+    import oracle
+    cand = np.asarray(cand_ids)
+    got_i = np.asarray(ids)
+    got_d = np.asarray(dists, np.float64)
+    ref_i, ref_d = oracle.rerank(X, Q, cand, k + 1, metric=metric)
+    if metric == "l2":
+        derr = assert_close_rel(got_d, ref_d[:, :k], FP32_RTOL, f"{what} distances")
+        radius = None
+        tol = 1.5 * max(derr, 1e-7)
+    else:
+        Q64 = np.asarray(Q, np.float64)
+        fin = np.isfinite(ref_d[:, :k])
+        assert (np.isfinite(got_d) == fin).all(), f"{what}: finiteness differs"
+        scale = np.linalg.norm(Q64, axis=1, keepdims=True) * np.linalg.norm(np.asarray(X, np.float64), axis=1).max()
+        err = np.abs(got_d - ref_d[:, :k])[fin] / np.broadcast_to(scale, got_d.shape)[fin]
+        assert err.max(initial=0.0) <= FP32_RTOL, f"{what} inner products: max err {err.max():.3e}"
+        radius = np.broadcast_to(1.5 * max(err.max(initial=0.0), 1e-7) * scale, ref_d.shape)
+        tol = None
+    return compare_topk_ids(got_i, ref_i, ref_d, tol, f"{what} ids", max_excluded=max_excluded, radius=radius)
+
+
 def compare_topk_ids(got_ids, ref_ids, ref_vals, tol=None, what="ids", max_excluded=0.02, radius=None):
     """Ids must match bit-exactly wherever the oracle's ranking is not decided
     by a near-tie.  ``ref_ids``/``ref_vals`` may carry one extra column (the

@@ -127,3 +127,24 @@ def test_metric_entry_points_validate_on_host(L):
     assert L.erq_estimate_metric(_vp(0), _vp(8), 1, 1, _vp(8), 1, _vp(8), _vp()) == erq.ERQ_EINVAL
     assert L.erq_search_backward_metric(_vp(0), _vp(8), 1, 1, _vp(8), _vp(8), 1, _vp(8), _vp()) == erq.ERQ_EINVAL
     assert b"bad arguments" in L.erq_last_error()
+
+
+def test_noalloc_output_buffer_is_checked_before_the_call():
+    """The allocation-free backward writes nq * D floats through the raw
+    pointer of a caller-supplied ``out``; the binding rejects a buffer of the
+    wrong dtype, shape, layout or device before any library call."""
+    import torch
+    from paper_2409_09913_gb300 import erq
+    like = torch.zeros((3, 64))
+    with pytest.raises(ValueError, match="shape"):
+        erq._check_out(torch.zeros((3, 63)), like)
+    with pytest.raises(ValueError, match="shape"):
+        erq._check_out(torch.zeros((2, 64)), like)
+    with pytest.raises(TypeError, match="float32"):
+        erq._check_out(torch.zeros((3, 64), dtype=torch.float64), like)
+    with pytest.raises(ValueError, match="contiguous"):
+        erq._check_out(torch.zeros((64, 3)).t(), like)
+    with pytest.raises(ValueError, match="must be on"):
+        erq._check_out(torch.zeros((3, 64)), like)          # not a CUDA tensor
+    with pytest.raises(TypeError):
+        erq._check_out(None, like)

@@ -1,16 +1,23 @@
-"""Parity at the full size of the benchmark workload (1M x 960 IVF, 4,096
-lists, B = 5, 10,000 queries, nprobe 16, k = 10, exact re-rank of the top 20)
-in the configuration the benchmark times (FP16 tensor-core scan, autotuned
-work items, asynchronous searches).  A seeded sample of queries is checked
-against the FP64 oracle built on just the clusters those queries probe (with
-the full set of centroids), so its answer for them is the full index's."""
+"""Parity at the full size of the 1M x 960 IVF workload (4,096 lists, B = 5,
+10,000 queries, nprobe 16, k = 10, exact re-rank of the top 20) in the
+configuration the benchmark times (FP16 tensor-core scan, autotuned work
+items, asynchronous searches):
+
+* every one of the 10,000 queries: the final top-10 is the exact FP64 re-rank
+  of the candidate set the GPU selected (ids and distances);
+* 256 seeded queries: every candidate estimate lies within the FP16 bound of
+  the FP64 oracle's estimate (oracle codes of the candidate rows, encoded with
+  the full set of centroids);
+* 24 seeded queries: the candidate sets against the oracle's own top-k' over
+  the clusters those queries probe (plus two more each, with the full set of
+  centroids), so its answer for them is the full index's."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synthetic as S
-from gpu_common import compare_topk_ids, erq, to_dev  # noqa: F401
+from gpu_common import check_final_vs_own_candidates, compare_topk_ids, erq, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +52,26 @@ def test_fullsize_bench_configuration_sampled(erq):
     gx.status()                                  # no device-side error in the asynchronous searches
 
     C = oracle.centroids(X, assign, cfg["nlist"])
+    gid_all = cids.cpu().numpy()
+    assert (gid_all >= 0).all()
+    # every query: final top-k = exact re-rank of its own candidates
+    frac = check_final_vs_own_candidates(X, Q, gid_all, ids.cpu().numpy(), dists.cpu().numpy(), k,
+                                         what="full-size re-ranked")
+    print(f"full size, all {len(Q)} queries: {frac:.5f} of final slots within a near-tie")
+    # 256 queries: estimates of the GPU's candidates against the oracle's
+    s256 = np.sort(S.rng(5151).choice(len(Q), 256, replace=False))
+    crow = np.unique(gid_all[s256])
+    oxc = oracle.build_index(X[crow], P, assign[crow], cfg["nlist"], cfg["B"], centroids_in=C)
+    pc = np.searchsorted(crow, gid_all[s256])
+    Q256 = Q[s256].astype(np.float64)
+    oest = oracle.estimate_rows(oxc, Q256, pc)
+    ge = cest.cpu().numpy()[s256].astype(np.float64)
+    bound = _fp16_bound(oxc, Q256, pc) + 2e-5 * (np.abs(oest) + 1e-3 * np.median(np.abs(oest)))
+    assert (np.abs(ge - oest) <= bound).all(), "estimates outside the FP16 bound"
+    probed = np.argsort(oracle.centroid_dists(C, Q256), axis=1, kind="stable")[:, :nprobe + 2]
+    for i in range(len(s256)):          # every candidate lies in one of the query's nearest clusters
+        assert np.isin(assign[gid_all[s256[i]]], probed[i]).all()
+    # 24 queries: candidate sets against the oracle's own top-k'
     cand = np.sort(S.rng(5150).choice(len(Q), 32, replace=False))
     cd = oracle.centroid_dists(C, Q[cand].astype(np.float64))
     srt = np.sort(cd, axis=1)

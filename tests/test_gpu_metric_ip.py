@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synthetic as S
-from gpu_common import compare_topk_ids, erq, to_dev  # noqa: F401
+from gpu_common import check_final_vs_own_candidates, compare_topk_ids, erq, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +92,8 @@ def _check(gx, ox, X, Q, k, kp, precision, nprobe=None, probe=None, simt=False):
         assert (verr <= RTOL * sc[same]).all(), "re-ranked inner products"
         compare_topk_ids(ids.cpu().numpy()[same], refr["ids"][same], refr["dists"][same], what="re-ranked ip ids",
                          radius=1.5 * RTOL * np.repeat(sc[same], k, axis=1), max_excluded=0.05)
+        # every query's final top-k: the exact re-rank of its own candidates
+        check_final_vs_own_candidates(X, Q, gid, ids.cpu().numpy(), gv, k, metric="ip")
     return ids, vals
 
 

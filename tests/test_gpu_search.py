@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synthetic as S
-from gpu_common import FP32_RTOL, assert_close_rel, compare_topk_ids, erq, to_dev  # noqa: F401
+from gpu_common import FP32_RTOL, assert_close_rel, check_final_vs_own_candidates, compare_topk_ids, erq, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +54,8 @@ def _check_search(erq, gx, ox, Q, k, kp, nprobe=None, probe=None, precision="fp3
         derr = assert_close_rel(gd[same], refr["dists"][same], rtol, "re-ranked distances")
         compare_topk_ids(gi[same], refr["ids"][same], refr["dists"][same], 1.5 * max(derr, 1e-7), "re-ranked ids",
                          max_excluded=0.05)
+        # every query's final top-k: the exact re-rank of its own candidate set
+        check_final_vs_own_candidates(ox["X"], Q, gid, gi, gd, k)
     return ids, dists, cids, cest
 
 

@@ -289,6 +289,35 @@ def test_search_full_rerank_is_exact_knn():
     assert res["ids"][0, 0] == 10 and res["ids"][0, 1] == 11
 
 
+def test_rerank_hand_example_and_ties():
+    """Exact re-rank of a given candidate set, worked by hand: points at
+    squared distances 4, 1, 1, 9 and 0 from q = 0 (ids 7, 3, 5, 2, 9; id 9
+    not a candidate, id 3 listed twice, one empty slot): (3, 1), (5, 1) with
+    the tie by lower id, then (7, 4), then (2, 9); a fifth slot stays empty."""
+    X = np.zeros((10, 2), np.float32)
+    X[7], X[3], X[5], X[2], X[9] = (2, 0), (0, 1), (-1, 0), (0, -3), (0, 0)
+    ids, vals = oracle.rerank(X, np.zeros((1, 2)), np.array([[7, 3, 5, -1, 2, 3]]), 5)
+    np.testing.assert_array_equal(ids[0], [3, 5, 7, 2, -1])
+    np.testing.assert_array_equal(vals[0], [1.0, 1.0, 4.0, 9.0, np.inf])
+    ids, vals = oracle.rerank(X, np.array([[1.0, 1.0]]), np.array([[7, 3, 5, 2]]), 2, metric="ip")
+    np.testing.assert_array_equal(ids[0], [7, 3])          # <x, q> = 2, 1, -1, -3
+    np.testing.assert_array_equal(vals[0], [2.0, 1.0])
+
+
+def test_rerank_matches_the_c_search():
+    """The numpy re-rank of the C search's own candidate sets gives the C
+    search's re-ranked ids and distances (two independent codings of the
+    exact re-rank), for both metrics."""
+    X, lab = S.mixture(3000, 48, 8, 104)
+    ix = oracle.build_index(X, S.random_orthogonal(48, 105), lab, 8, 4)
+    Q = S.mixture(30, 48, 8, 106, comp_seed=104)[0]
+    for metric in ("l2", "ip"):
+        res = oracle.search(ix, Q, 10, kprime=40, nprobe=3, metric=metric)
+        ids, vals = oracle.rerank(X, Q, res["cand_ids"], 10, metric=metric)
+        np.testing.assert_array_equal(ids, res["ids"])
+        np.testing.assert_allclose(vals, res["dists"], rtol=1e-12)
+
+
 def test_search_probe_is_nearest_centroids():
     X, lab = S.mixture(2000, 16, 10, 110)
     ix = oracle.build_index(X, S.random_orthogonal(16, 111), lab, 10, 2)

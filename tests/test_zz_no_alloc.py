@@ -53,16 +53,30 @@ def test_noalloc_backward_matches_allocating_entry_point():
         assert np.abs(a - b).max() <= 2e-5 * np.abs(b).max()
 
 
-def test_noalloc_backward_rejects_oversize():
+def test_noalloc_backward_size_limit_and_output_buffer():
     from paper_2409_09913_gb300 import erq
     dev = torch.device("cuda:0")
     X, lab, _, _, _ = _case(5400, N=1000, D=1024)
     P = S.random_orthogonal(1024, 5401)
     ix = erq.build_index(torch.from_numpy(X).to(dev), torch.from_numpy(P).to(dev), 3, 5,
                          assign=torch.from_numpy(lab).to(dev))
-    nq = (16 << 20) // (8 * 1024) + 1                      # one query more than the scratch holds
+    # 8 nq D + 4 nq + 512 <= 16 MiB holds for nq = 2046 at D = 1024 and not for 2047
+    nq = 2046
+    Q = torch.from_numpy(S.normal((nq, 1024), 5402)).to(dev)
+    ids = torch.from_numpy(S.rng(5403).integers(0, 1000, size=(nq, 2))).to(dev)
+    g = torch.from_numpy(S.normal((nq, 2), 5404)).to(dev)
+    out = torch.full_like(Q, float("nan"))
+    got = ix.search_backward_noalloc(Q, ids, g, out=out)   # a preallocated output is written in place
+    ref = ix.search_backward(Q, ids, g)
+    torch.cuda.synchronize()
+    assert got.data_ptr() == out.data_ptr()
+    a, b = out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+    assert np.isfinite(a).all() and np.abs(a - b).max() <= 2e-5 * np.abs(b).max()
+    nq = 2047                                              # one query more than the scratch holds
     Q = torch.zeros((nq, 1024), device=dev)
     ids = torch.zeros((nq, 1), dtype=torch.int64, device=dev)
     g = torch.zeros((nq, 1), device=dev)
     with pytest.raises(erq.ErqError, match="scratch"):
         ix.search_backward_noalloc(Q, ids, g)
+    with pytest.raises(ValueError, match="shape"):        # a wrong-shaped output is refused by the binding
+        ix.search_backward_noalloc(Q[:5], ids[:5], g[:5], out=torch.empty((5, 512), device=dev))
