@@ -40,7 +40,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="erq", choices=["erq", "reference"])
-    ap.add_argument("--workload", default="ivf_n1m_d960_nlist4096")
+    ap.add_argument("--workload", default="zipf_n5m_d768_nlist8192",
+                    help="the headline workload (default: 5M x 768, 8,192 Zipf-sized lists, 16,384 queries with "
+                         "per-query nprobe U{8..256})")
+    ap.add_argument("--secondary", default="ivf_n1m_d960_nlist4096,embed_n2m_d1536_b7,backward_n1m_d1024_b4",
+                    help="further workloads measured after the headline one (fewer steps each, one GPU only; "
+                         "'none' to skip)")
     ap.add_argument("--B", type=int, default=0, help="bits per coordinate (0 = the workload's)")
     ap.add_argument("--precision", default="auto", help="fp32 | fp16 | fp8 | auto (best meeting recall)")
     ap.add_argument("--nprobe", type=int, default=0, help="0 = smallest meeting the recall target")
@@ -49,7 +54,10 @@ def parse():
     ap.add_argument("--recall", type=float, default=0.95)
     ap.add_argument("--metric", default="l2", choices=["l2", "ip"],
                     help="l2: nearest by squared distance; ip: largest inner product (recall against exact MIPS)")
-    ap.add_argument("--cpu-sample", type=int, default=16, help="queries in the timed oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="at most this many queries in the timed oracle sample")
+    ap.add_argument("--cpu-rows", type=int, default=150_000,
+                    help="the oracle sample takes queries in order while the rows of their probed clusters stay "
+                         "within this many (at least one query)")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of N and nq (smoke runs only)")
     ap.add_argument("--n", type=int, default=0, help="override N (profiling cases)")
     ap.add_argument("--nq", type=int, default=0, help="override the query count")
@@ -115,6 +123,7 @@ class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index=0):
         self.rows = []
@@ -124,7 +133,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -157,7 +166,7 @@ class ClockSampler:
                 if v.strip().lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(mhz)}
+                "reasons": sorted(reasons), "samples": len(mhz), "period_ms": self.PERIOD_MS}
 
 
 # ----------------------------------------------------------------------------- peaks
@@ -204,7 +213,7 @@ def profiled_traffic(workload, nprobe, precision, shape, items=None):
                 else:
                     kv[k.strip()] = v.strip()
     try:
-        if kv.get("kernel_source_sha256") != scan_source_sha() or int(kv.get("nprobe", -1)) != nprobe:
+        if kv.get("kernel_source_sha256") != scan_source_sha() or str(kv.get("nprobe", "")) != str(nprobe):
             return None
         for rec in records:       # the captured work-item shape first, then one with the same item count
             rrs = [int(x) for x in rec.get("rows_per_item", "-1").split(",")]
@@ -220,18 +229,30 @@ def profiled_traffic(workload, nprobe, precision, shape, items=None):
 
 
 # ----------------------------------------------------------------------------- oracle sample
-def oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, rank_queries):
-    """Bounded CPU sample: the FP64 oracle over the probed clusters of
-    ``rank_queries`` queries (all of them present, so its answer is the full
-    index's).  Returns (partial index, query rows)."""
+def oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, max_queries, npr=None):
+    """Bounded CPU sample: the FP64 oracle over the probed clusters of the first
+    queries (all of their probed clusters present, so its answer is the full
+    index's), taken in order while the rows of those clusters stay within
+    ``args.cpu_rows`` (at least one query, at most ``max_queries``).  ``npr``:
+    per-query nprobe of the workload, else ``nprobe`` for every query.
+    Returns (partial index, query rows, encoded row ids, nprobe per sampled query)."""
     import oracle
     C = oracle.centroids(X, assign, cfg["nlist"])
-    Qs = Q[:rank_queries]
-    cd = -(Qs.astype(np.float64) @ C.astype(np.float64).T) if args.metric == "ip" else oracle.centroid_dists(C, Qs)
-    probed = np.unique(np.argsort(cd, axis=1, kind="stable")[:, :nprobe])
-    rows = np.nonzero(np.isin(assign, probed))[0]
+    counts = np.bincount(assign, minlength=cfg["nlist"])
+    nmax = min(max_queries, len(Q))
+    Qc = Q[:nmax]
+    cd = -(Qc.astype(np.float64) @ C.astype(np.float64).T) if args.metric == "ip" else oracle.centroid_dists(C, Qc)
+    order = np.argsort(cd, axis=1, kind="stable")
+    npq = np.full(nmax, nprobe, np.int64) if npr is None else np.asarray(npr[:nmax], np.int64)
+    probed, n = set(), 0
+    for i in range(nmax):
+        cand = probed | set(order[i, :npq[i]].tolist())
+        if n > 0 and counts[list(cand)].sum() > args.cpu_rows:
+            break
+        probed, n = cand, i + 1
+    rows = np.nonzero(np.isin(assign, np.array(sorted(probed))))[0]
     ox = oracle.build_index(X[rows], P, assign[rows], cfg["nlist"], args.B, centroids_in=C)
-    return ox, Qs, rows
+    return ox, Q[:n], rows, npq[:n]
 
 
 def time_oracle(ox, Qs, args, nprobe, kp, reps=1):
@@ -254,14 +275,20 @@ def run_reference(args):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     assign = ivf_assign(cfg, X, args, dev)
     # the GPU arm's choice on this workload: the smallest swept nprobe meets the recall
-    # target (recall@10 0.998 at nprobe 16 on the 1M x 960 workload)
+    # target (recall@10 0.998 at nprobe 16 on the 1M x 960 workload); the Zipf
+    # workload's per-query nprobe comes from its seeded draw
     nprobe = args.nprobe or cfg.get("nprobes", (16,))[0]
+    npr = None
+    if "nprobe_lo" in cfg and not args.nprobe:
+        npr = S.rng(cfg["nprobe_seed"]).integers(cfg["nprobe_lo"], cfg["nprobe_hi"] + 1, size=len(Q))
+        nprobe = "per query U{%d..%d}" % (cfg["nprobe_lo"], cfg["nprobe_hi"])
     kp = max(args.k, args.rerank_k)
     import oracle
-    ox, Qs, _ = oracle_sample(cfg, X, Q, P, assign, args, nprobe, kp, args.cpu_sample)
+    ox, Qs, rows, npq = oracle_sample(cfg, X, Q, P, assign, args, 0 if npr is not None else nprobe, kp,
+                                      args.cpu_sample, npr=npr)
     for _ in range(args.warmup):
-        time_oracle(ox, Qs[:2], args, nprobe, kp)
-    times = [time_oracle(ox, Qs, args, nprobe, kp) for _ in range(args.steps)]
+        time_oracle(ox, Qs[:2], args, npq[:2], kp)
+    times = [time_oracle(ox, Qs, args, npq, kp) for _ in range(args.steps)]
     qps = len(Qs) / statistics.mean(times)
     cores = min(oracle.num_threads(), len(Qs))
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
@@ -273,16 +300,19 @@ def run_reference(args):
                                              "similarity": args.metric,
                                              "l2": "inputs larger than L2 (codes > 129 MB)"},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe {nprobe}"},
+                             "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe "
+                                       f"{describe_nprobe(npq)}, {len(rows)} rows encoded"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_backward(args):
+def run_backward(args, emit=True, steps=None):
     """Backward workload: gradient of the top-k' estimated scores of a query
     batch with respect to the queries (erq_search_backward), one step = one
-    backward call for the whole batch."""
+    backward call for the whole batch.  Prints the JSON line, or returns it
+    when emit is False."""
+    steps = steps or args.steps
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -314,11 +344,11 @@ def run_backward(args):
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         e0.record(st)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record(st)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     launches = erq.kernel_launches() - launches0
     ix.status()
     # end to end: queries and upstream gradients from pinned host memory, gradient back
@@ -326,17 +356,17 @@ def run_backward(args):
     outh = torch.empty_like(Qh).pin_memory()
     torch.cuda.synchronize()
     te = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         Qd.copy_(Qh, non_blocking=True)
         gs.copy_(gh, non_blocking=True)
         step()
         outh.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - te) / args.steps
+    e2e_s = (time.perf_counter() - te) / steps
     D = cfg["d"]
     flops = 2.0 * len(Q) * D * D * 3 + 4.0 * len(Q) * kc * D      # GEMM (3 split-FP16 passes) + gather
     line = {"metric": "backward queries/s (d top-k' estimated scores / d queries)", "value": len(Q) / (ms / 1e3),
-            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "unit": "queries/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N": len(X), "D": D, "B": args.B, "nlist": cfg["nlist"],
                        "nq": len(Q), "k_scores": kc, "nprobe": nprobe},
@@ -344,6 +374,9 @@ def run_backward(args):
             "e2e": {"value": len(Q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes + gs.numel() * 4),
                     "d2h_bytes_per_step": int(Q.nbytes)},
             "gpu_launches": launches, "clocks": clk.summary()}
+    del ix
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
@@ -387,28 +420,71 @@ def run_encoder_sweep(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "encoder_table4":
-        return run_encoder_sweep(args)
-    if args.workload.startswith("backward"):
-        return run_backward(args)
+def gt_knn(Xd, Qd, metric, RK=10):
+    """Exact top-RK ids (FP32 GEMM on the device; a measurement helper only)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    xn = (Xd * Xd).sum(1)
+    gt = torch.empty((len(Qd), RK), dtype=torch.int64, device=Qd.device)
+    for s0 in range(0, len(Qd), 1024):
+        q = Qd[s0:s0 + 1024]
+        best_d = best_i = None
+        for x0 in range(0, len(Xd), 1 << 18):
+            if metric == "ip":
+                d = -(q @ Xd[x0:x0 + (1 << 18)].T)
+            else:
+                d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
+            v, i = torch.topk(d, RK, dim=1, largest=False)
+            i = i + x0
+            if best_d is None:
+                best_d, best_i = v, i
+            else:
+                cat_d, cat_i = torch.cat([best_d, v], 1), torch.cat([best_i, i], 1)
+                best_d, j = torch.topk(cat_d, RK, dim=1, largest=False)
+                best_i = torch.gather(cat_i, 1, j)
+        gt[s0:s0 + len(q)] = best_i
+    return gt.cpu().numpy()
+
+
+def roofline(args, cfg, R, best, nq):
+    """Roofline of the dominant kernel (the code scan) for one arm."""
+    peaks = measured_peaks()
+    D, B = cfg["d"], args.B
+    scan_s = R["phases"]["scan"] / 1e3
+    flops = 2.0 * D * R["work"]["pairs"]
+    bytes_alg = (B * D / 8 + 8) * R["work"]["rows"] + nq * D * 4
+    sm_mhz = R["clocks"]["sm_mhz"] or 2070.0
+    if best == "fp32":
+        peak_c, unit_c, bound_c = ffma_peak_tflops(sm_mhz), "TFLOP/s", "alu"
+    else:
+        peak_c = peaks["bf16_tflops"] * (2.0 if best == "fp8" else 1.0)
+        unit_c, bound_c = "TFLOP/s", "tensor"
+    t_c = flops / (peak_c * 1e12)
+    t_m = bytes_alg / (peaks["hbm_gbs"] * 1e9)
+    if t_c >= t_m:
+        roof = {"bound": bound_c, "achieved": flops / scan_s / 1e12, "peak": peak_c, "unit": unit_c,
+                "frac": (flops / scan_s / 1e12) / peak_c, "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_alg / scan_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (bytes_alg / scan_s / 1e9) / peaks["hbm_gbs"], "traffic": None}
+    roof["traffic"] = profiled_traffic(args.workload, R["nprobe_key"], best, R["shape"], R["work"].get("items"))
+    roof["bytes_alg_per_launch"] = bytes_alg
+    roof["flops_per_launch"] = flops
+    roof["kernel"] = "scan_fp32_kernel" if best == "fp32" else "scan_tc_kernel"
+    roof["peak_source"] = (peaks["source"] + (" (bf16 x 2 for e4m3)" if best == "fp8" and roof["bound"] == "tensor"
+                                              else "")) if bound_c != "alu" or roof["bound"] == "hbm" else \
+        f"152 SMs x 128 FFMA x 2 at {sm_mhz:.0f} MHz"
+    return roof
+
+
+def search_workload(args, env, erq, steps, warmup, headline):
+    """Build the workload's index, pick nprobe per precision (smallest meeting
+    the recall target), time every arm and return the measurements.  The
+    headline workload also gets the end-to-end host-buffer loop, the CUDA-graph
+    replay, the index-path rates and the oracle's CPU baseline."""
     import torch
     import torch.distributed as dist
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2409_09913_gb300 import build as erq_build
-    erq_build.build(checked=os.environ.get("ERQ_CHECKED") == "1")
-    from paper_2409_09913_gb300 import erq
-
+    world, rank, local, dev = env["world"], env["rank"], env["local"], env["dev"]
     t0 = time.perf_counter()
     cfg, X, Q, P = make_workload(args, rank)
     args.B = args.B or cfg["B"]
@@ -422,31 +498,8 @@ def main():
                          assign=torch.from_numpy(assign).to(dev))
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t1
-
-    # exact ground truth (FP32 GEMM, measurement helper only)
-    torch.backends.cuda.matmul.allow_tf32 = False
-    xn = (Xd * Xd).sum(1)
     RK = 10                                   # recall@10
-    gt = torch.empty((len(Q), RK), dtype=torch.int64, device=dev)
-    for s0 in range(0, len(Q), 1024):
-        q = Qd[s0:s0 + 1024]
-        best_d = best_i = None
-        for x0 in range(0, len(X), 1 << 18):
-            if args.metric == "ip":
-                d = -(q @ Xd[x0:x0 + (1 << 18)].T)
-            else:
-                d = xn[x0:x0 + (1 << 18)][None, :] - 2.0 * (q @ Xd[x0:x0 + (1 << 18)].T)
-            v, i = torch.topk(d, RK, dim=1, largest=False)
-            i = i + x0
-            if best_d is None:
-                best_d, best_i = v, i
-            else:
-                cat_d, cat_i = torch.cat([best_d, v], 1), torch.cat([best_i, i], 1)
-                best_d, j = torch.topk(cat_d, RK, dim=1, largest=False)
-                best_i = torch.gather(cat_i, 1, j)
-        gt[s0:s0 + len(q)] = best_i
-    gt_np = gt.cpu().numpy()
-    del xn
+    gt_np = gt_knn(Xd, Qd, args.metric, RK)
 
     def recall(ids):
         ids = ids[:, :RK].cpu().numpy()
@@ -461,8 +514,7 @@ def main():
 
     kp = max(args.k, args.rerank_k)
     precisions = ["fp32", "fp16", "fp8"] if args.precision == "auto" else [args.precision]
-    sweep = {}
-    chosen = {}
+    sweep, chosen = {}, {}
     for prec in precisions:
         for p in ([args.nprobe] if args.nprobe else cfg.get("nprobes", (16, 32, 64, 128, 256))):
             try:
@@ -478,18 +530,18 @@ def main():
                 chosen[prec] = p
                 break
 
-    results = {}
-    shapes = {}
+    results, shapes = {}, {}
     if args.scan_shape:
         ix.set_scan_config(*[int(x) for x in args.scan_shape.split(",")])
     for prec, p in chosen.items():
         if prec != "fp32" and not args.no_autotune and not args.scan_shape:   # work-item shape timed on this batch
             shapes[prec] = ix.autotune(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec,
                                        nprobe_per_query=npr_d, reps=3, metric=args.metric)
+
         def step():
             ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, timing=True,
                       async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         if world > 1:
@@ -501,17 +553,17 @@ def main():
         with ClockSampler(local) as clk:
             torch.cuda.synchronize()
             e0.record(st)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 step()
             e1.record(st)
             torch.cuda.synchronize()
         launches = erq.kernel_launches() - launches0
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         if world > 1:
             ms = max_over_ranks(ms, world, dev)
             dist.barrier()
         # per-phase device time averaged over the timed searches (CUDA events on the
-        # search stream), and the work counters of the last one
+        # search stream)
         tot, cnt = ix.timing_total()
         phases = {kk: v / max(cnt, 1) for kk, v in tot.items()}
         # work counters of one synchronous search of the same configuration
@@ -520,30 +572,38 @@ def main():
         ix.search(Qd, args.k, rerank_k=args.rerank_k, nprobe=p, precision=prec, nprobe_per_query=npr_d,
                   metric=args.metric)
         work = ix.stats()
+        ix.status()                        # no device-side error in the timed searches
         results[prec] = dict(nprobe=p, ms=ms, qps=job_rate(len(Q), world, ms / 1e3), recall=sweep[prec][p],
                              phases=phases, work=work, clocks=clk.summary(), launches=launches,
-                             shape=ix.scan_config(), tuned=prec in shapes)
-
+                             shape=ix.scan_config(), tuned=prec in shapes,
+                             nprobe_key="per-query" if npr_d is not None else p)
+    out = dict(cfg=cfg, sweep=sweep, results=results, nq=len(Q), N=len(X), t_build=t_build, t_data=t_data,
+               npr_d=npr_d, kp=kp)
     if not results:
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": None, "error": "recall target not reached",
-                              "sweep": sweep}), flush=True)
-        return 1
+        return out
     best = max(results, key=lambda k: results[k]["qps"])
     R = results[best]
+    out["best"] = best
+    for prec in results:
+        results[prec]["roofline"] = roofline(args, cfg, results[prec], prec, len(Q))
 
     # end to end through the C ABI from pinned host buffers
     Qh = torch.from_numpy(Q).pin_memory()
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
                        async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
     torch.cuda.synchronize()
     te = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         ix.search_host(Qh, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
                        async_mode=not args.sync, nprobe_per_query=npr_d, metric=args.metric)
-    e2e_s = (time.perf_counter() - te) / args.steps
+    e2e_s = (time.perf_counter() - te) / steps
     e2e_s = max_over_ranks(e2e_s, world, dev)
+    out["e2e"] = {"value": job_rate(len(Q), world, e2e_s), "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+                  "d2h_bytes_per_step": int(len(Q) * args.k * 12)}
+    if not headline:
+        del ix
+        return out
 
     # the same search recorded once into a CUDA graph and replayed (queries in a
     # static buffer; every replay runs the whole path without host work)
@@ -560,16 +620,16 @@ def main():
         with torch.cuda.graph(cg):
             g_ids, _ = ix.search(static_q, args.k, rerank_k=args.rerank_k, nprobe=R["nprobe"], precision=best,
                                  async_mode=True, nprobe_per_query=npr_d, metric=args.metric)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             cg.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             cg.replay()
         e1.record()
         torch.cuda.synchronize()
-        gms = e0.elapsed_time(e1) / args.steps
+        gms = e0.elapsed_time(e1) / steps
         graph = {"ms_per_step": gms, "recall@10": recall(g_ids)}
         del cg
     except Exception as ex:                      # report, do not hide, a capture failure
@@ -579,6 +639,7 @@ def main():
     if "ms_per_step" in graph:
         graph = {"value": job_rate(len(Q), world, gmax / 1e3), "unit": "queries/s", "ms_per_step": gmax,
                  "recall@10": graph["recall@10"]}
+    out["graph"] = graph
 
     # index-time kernels on a sample: exact rotation (FP64 accumulation) and the
     # Algorithm 1 encoder, rows per second
@@ -603,68 +664,121 @@ def main():
         del Xs, Rs
     except Exception as ex:
         idx = {"error": str(ex)[:200]}
-
-    # roofline of the dominant kernel (the code scan)
-    peaks = measured_peaks()
-    D, B = cfg["d"], args.B
-    scan_s = R["phases"]["scan"] / 1e3
-    flops = 2.0 * D * R["work"]["pairs"]
-    bytes_alg = (B * D / 8 + 8) * R["work"]["rows"] + len(Q) * D * 4
-    sm_mhz = R["clocks"]["sm_mhz"] or 2070.0
-    if best == "fp32":
-        peak_c, unit_c, bound_c = ffma_peak_tflops(sm_mhz), "TFLOP/s", "alu"
-    else:
-        peak_c = peaks["bf16_tflops"] * (2.0 if best == "fp8" else 1.0)
-        unit_c, bound_c = "TFLOP/s", "tensor"
-    t_c = flops / (peak_c * 1e12)
-    t_m = bytes_alg / (peaks["hbm_gbs"] * 1e9)
-    if t_c >= t_m:
-        roof = {"bound": bound_c, "achieved": flops / scan_s / 1e12, "peak": peak_c, "unit": unit_c,
-                "frac": (flops / scan_s / 1e12) / peak_c, "traffic": None}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_alg / scan_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": (bytes_alg / scan_s / 1e9) / peaks["hbm_gbs"], "traffic": None}
-    roof["traffic"] = profiled_traffic(args.workload, R["nprobe"], best, R["shape"], R["work"].get("items"))
-    roof["bytes_alg_per_launch"] = bytes_alg
-    roof["kernel"] = "scan_fp32_kernel" if best == "fp32" else "scan_tc_kernel"
-    roof["peak_source"] = peaks["source"] if bound_c != "alu" or roof["bound"] == "hbm" else \
-        f"152 SMs x 128 FFMA x 2 at {sm_mhz:.0f} MHz"
+    out["index_path"] = idx
+    del ix, Xd, Qd
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        npr_np = npr_d.cpu().numpy() if npr_d is not None else None
+        ox, Qs, rows, npq = oracle_sample(cfg, X, Q, P, assign, args, R["nprobe"], kp, args.cpu_sample,
+                                          npr=npr_np)
+        t_cpu = time_oracle(ox, Qs, args, npq, kp)
         import oracle
-        ox, Qs, rows = oracle_sample(cfg, X, Q, P, assign, args, R["nprobe"], kp, args.cpu_sample)
-        t_cpu = time_oracle(ox, Qs, args, R["nprobe"], kp)
         cpu = {"value": len(Qs) / t_cpu, "unit": "queries/s", "cores": min(oracle.num_threads(), len(Qs)),
-               "kind": "oracle", "sample": f"{len(Qs)} queries, nprobe {R['nprobe']}, {len(rows)} rows encoded"}
+               "kind": "oracle", "sample": f"{len(Qs)} queries, nprobe {describe_nprobe(npq)}, {len(rows)} rows encoded"}
+    out["cpu"] = cpu
+    return out
+
+
+def describe_nprobe(npq):
+    a = np.atleast_1d(npq)
+    return str(int(a[0])) if a.min() == a.max() else f"{int(a.min())}..{int(a.max())} per query"
+
+
+def arm_summary(res):
+    return {k: {"qps": v["qps"], "nprobe": v["nprobe_key"], "recall@10": v["recall"], "ms": v["ms"],
+                "phases_ms": v["phases"], "pairs": v["work"]["pairs"], "roofline": v.get("roofline"),
+                "clocks": v["clocks"],
+                "scan_shape": {"queries_per_item": v["shape"][0], "rows_per_item": v["shape"][1],
+                               "autotuned": v["tuned"], "work_items": v["work"].get("items")}}
+            for k, v in res.items()}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "encoder_table4":
+        return run_encoder_sweep(args)
+    if args.workload.startswith("backward"):
+        return run_backward(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2409_09913_gb300 import build as erq_build
+    erq_build.build(checked=os.environ.get("ERQ_CHECKED") == "1")
+    from paper_2409_09913_gb300 import erq
+    env = dict(world=world, rank=rank, local=local, dev=dev)
+
+    H = search_workload(args, env, erq, args.steps, args.warmup, headline=True)
+    cfg = H["cfg"]
+    if not H["results"]:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": None, "error": "recall target not reached",
+                              "sweep": H["sweep"]}), flush=True)
+        return 1
+    best = H["best"]
+    R = H["results"][best]
+
+    # the other workloads of the same metric, fewer steps each, on one GPU only
+    secondary = {}
+    names = [w for w in args.secondary.split(",") if w and w != "none"] if world == 1 else []
+    for name in names:
+        if name == args.workload:
+            continue
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.B, sub.nprobe, sub.scan_shape = name, 0, 0, ""
+        try:
+            if name.startswith("backward"):
+                secondary[name] = run_backward(sub, emit=False, steps=min(args.steps, 50))
+                continue
+            W = search_workload(sub, env, erq, min(args.steps, 50), args.warmup, headline=False)
+        except Exception as ex:                  # report, do not hide, a failed secondary workload
+            secondary[name] = {"error": str(ex)[:300]}
+            continue
+        torch.cuda.empty_cache()
+        if not W["results"]:
+            secondary[name] = {"error": "recall target not reached", "sweep": W["sweep"]}
+            continue
+        Wb = W["results"][W["best"]]
+        c = W["cfg"]
+        secondary[name] = {"value": Wb["qps"], "unit": "queries/s", "ms_per_step": Wb["ms"], "precision": W["best"],
+                           "config": {"N": W["N"], "D": c["d"], "nlist": c["nlist"], "B": sub.B, "nq": W["nq"],
+                                      "k": args.k, "rerank_k": W["kp"], "nprobe": Wb["nprobe_key"]},
+                           "recall@10": Wb["recall"], "roofline": Wb["roofline"], "e2e": W["e2e"],
+                           "arms": arm_summary(W["results"]), "recall_sweep": W["sweep"]}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": R["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[best], "data": "synthetic",
-            "config": {"workload": args.workload, "N": len(X), "D": cfg["d"], "nlist": cfg["nlist"], "B": args.B,
-                       "nq": len(Q), "k": args.k, "rerank_k": kp, "precision": best,
-                       "nprobe": ("per query U{%d..%d}" % (cfg["nprobe_lo"], cfg["nprobe_hi"])) if npr_d is not None
-                       else R["nprobe"],
+            "config": {"workload": args.workload, "N": H["N"], "D": cfg["d"], "nlist": cfg["nlist"], "B": args.B,
+                       "nq": H["nq"], "k": args.k, "rerank_k": H["kp"], "precision": best,
+                       "nprobe": ("per query U{%d..%d}" % (cfg["nprobe_lo"], cfg["nprobe_hi"]))
+                       if H["npr_d"] is not None else R["nprobe"],
                        "recall@10": R["recall"], "similarity": args.metric,
                        "l2": "inputs larger than L2 (codes > 129 MB)"},
             "gcodes_per_s": R["work"]["pairs"] / (R["ms"] / 1e3) / 1e9,
-            "arms": {k: {"qps": v["qps"], "nprobe": v["nprobe"], "recall@10": v["recall"], "ms": v["ms"],
-                         "phases_ms": v["phases"], "pairs": v["work"]["pairs"],
-                         "scan_shape": {"queries_per_item": v["shape"][0], "rows_per_item": v["shape"][1],
-                                        "autotuned": v["tuned"], "work_items": v["work"].get("items")}}
-                     for k, v in results.items()},
-            "recall_sweep": sweep,
-            "roofline": roof,
-            "e2e": {"value": job_rate(len(Q), world, e2e_s), "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
-                    "d2h_bytes_per_step": int(len(Q) * args.k * 12)},
+            "arms": arm_summary(H["results"]),
+            "recall_sweep": H["sweep"],
+            "roofline": R["roofline"],
+            "e2e": H["e2e"],
             "gpu_launches": R["launches"],
-            "graph": graph,
-            "index_path": idx,
+            "graph": H.get("graph"),
+            "index_path": H.get("index_path"),
             "clocks": R["clocks"],
-            "cpu_baseline": cpu,
-            "build_s": t_build, "data_s": t_data,
+            "cpu_baseline": H.get("cpu"),
+            "secondary": secondary,
+            "build_s": H["t_build"], "data_s": H["t_data"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

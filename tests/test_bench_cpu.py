@@ -41,3 +41,26 @@ def test_traffic_dropped_when_kernel_source_changes(bench_mod, monkeypatch):
     monkeypatch.setattr(bench_mod, "scan_source_sha", lambda: "def")
     assert bench_mod.profiled_traffic("w", 16, "fp16", (64, 4096), 1000) is None
 
+
+
+def test_oracle_sample_respects_row_cap():
+    """The timed CPU sample takes queries in order while the rows of their
+    probed clusters stay within --cpu-rows (at least one query), with the
+    workload's per-query nprobe."""
+    import argparse
+
+    import numpy as np
+
+    import bench
+    import synthetic as S
+    X, lab = S.mixture(4000, 64, 8, 11)
+    Q, _ = S.mixture(6, 64, 8, 12, comp_seed=11)
+    P = S.random_orthogonal(64, 13)
+    cfg = {"nlist": 8}
+    args = argparse.Namespace(metric="l2", B=3, cpu_rows=10 ** 9)
+    ox, Qs, rows, npq = bench.oracle_sample(cfg, X, Q, P, lab, args, 2, 10, 16)
+    assert len(Qs) == 6 and (npq == 2).all()
+    args.cpu_rows = 1
+    ox, Qs, rows, npq = bench.oracle_sample(cfg, X, Q, P, lab, args, 0, 10, 16, npr=np.array([3, 1, 1, 1, 1, 1]))
+    assert len(Qs) == 1 and npq.tolist() == [3]
+    assert len(np.unique(lab[rows])) == 3 and len(rows) == np.isin(lab, np.unique(lab[rows])).sum()
