@@ -77,6 +77,10 @@ typedef struct {
     uint64_t seed;            /* k-means initialisation seed                             */
     int32_t keep_raw;         /* keep the FP32 rows in the index (exact re-rank needs it)*/
     int32_t reserved;
+    const float* centroids;   /* optional device [nlist][D] centroids to use instead of the
+                                 means of the rows (requires assign; lists may then be
+                                 empty): an index over one shard of a larger index's lists
+                                 keeps the larger index's centroids, codes and probe      */
 } erq_build_params;
 
 /* Search parameters. */
@@ -278,19 +282,54 @@ erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);
  * queries_per_item of the queries that probe it, up to rows_per_item of its
  * rows); on the tensor-core path queries_per_item is the MMA's N extent.
  * erq_autotune: times erq_search over the caller's query batch and params for
- * every supported shape (queries_per_item in {32, 64, 128} as k' allows,
+ * every supported shape (queries_per_item 32 or 64 for k' <= 32, 32 for larger k',
  * rows_per_item in {2048, 4096, 8192}), reps searches each after one warm-up,
  * and keeps the fastest for later searches on this index whose nq * nprobe is
  * within 4x of the tuned one (one entry for k' <= 32, one for larger k');
  * best_out (optional, host [2]) receives it.  Synchronises the stream.  Errors
  * as erq_search; EUNSUPPORTED for the FP32 path.
  * erq_set_scan_config: force the shape (0 = automatic) for later searches;
- * EINVAL for values other than 0/32/64/128 and 0 or multiples of 256.
+ * EINVAL for values other than 0/32/64 and 0 or multiples of 256.
  * erq_scan_config: out[0..1] = the shape used by the last search. */
 erq_status erq_autotune(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params, int32_t reps,
                         void* stream, int32_t* best_out);
 erq_status erq_set_scan_config(erq_index* index, int32_t queries_per_item, int32_t rows_per_item);
 erq_status erq_scan_config(const erq_index* index, int32_t* out, int32_t n);
+
+/* Merge of caller-given candidate lists (no counterpart in the paper; the
+ * exchange step of a search whose IVF lists are split over several indices,
+ * one per GPU, see Section 4.1 for the single-index search it reproduces).
+ * For query i, the k smallest (values[i][j], cand_ids[i][j]) pairs over
+ * j < m, ascending by value and then by id (ERQ_METRIC_IP: the k largest
+ * values, descending, ties by lower id); ids < 0 are empty.  ids_out[nq][k]
+ * gets -1 and vals_out[nq][k] +inf (-inf for ERQ_METRIC_IP) past the
+ * available pairs.  All arrays are device memory; the call allocates and
+ * frees its workspace in stream order.  Errors: EINVAL (m outside [1, 8192],
+ * k outside [1, 1024], null pointer, metric), ECUDA. */
+erq_status erq_merge_topk(const int64_t* cand_ids, const float* values, int64_t nq, int32_t m, int32_t k,
+                          int32_t metric, int64_t* ids_out, float* vals_out, void* stream);
+
+/* Exact re-rank of caller-given ids (the re-rank step of erq_search, which the
+ * paper's search leaves to the caller, Section 4.1): for query i, the exact
+ * squared distance (ERQ_METRIC_IP: inner product) to every id in
+ * ids[i][0..nc-1] that the index holds (0 <= id < N; other ids are skipped),
+ * the k best by (distance, id) ascending (ERQ_METRIC_IP: largest inner
+ * product first, ties by lower id) into ids_out[nq][k] / dists_out[nq][k],
+ * with -1 / +inf (-inf) past the available ones.  Needs keep_raw.  Q device
+ * [nq][D].  Errors: EINVAL (k, nc outside 1 <= k <= nc <= 1024, no raw rows,
+ * metric), ECUDA. */
+erq_status erq_rerank_ids(erq_index* index, const float* Q, int64_t nq, int32_t nc, const int64_t* ids, int32_t k,
+                          int32_t metric, int64_t* ids_out, float* dists_out, void* stream);
+
+/* Limit of every bounded device-side wait of the tensor-core scan on this
+ * index, in nanoseconds (0 = the default, 2 s); no counterpart in the paper.
+ * A wait that runs out makes the scan stop, drain its copies, free its tensor
+ * memory and report ERQ_ETIMEOUT through the index's status word; the index
+ * stays usable.  stall_stage >= 0 is a test of that path: in later scans the
+ * first MMA issuer of every CTA, at its stage number stall_stage, waits on a
+ * barrier that nothing arrives on, so the wait runs out after the limit;
+ * -1 turns it off.  Errors: EINVAL (null index, stall_stage < -1). */
+erq_status erq_set_wait_limit(erq_index* index, uint64_t ns, int64_t stall_stage);
 
 /* Allocation-free variant of erq_search_backward (no counterpart in the paper;
  * an interface for callers that cannot allocate device memory while they run,

@@ -60,7 +60,7 @@ void free_index_arrays(erq_index* ix) {
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_p,
-                    ix->dstats, ix->PT_hi, ix->C_hi};   // PT_lo / C_lo live inside those blocks
+                    ix->dstats, ix->PT_hi, ix->C_hi, ix->dctr};   // PT_lo / C_lo live inside those blocks
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
@@ -332,7 +332,9 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     if (N < 1 || N >= (1ll << 31)) return fail(ERQ_EINVAL, "erq_build_index: N must be in [1, 2^31)");
     if (!valid_d(D)) return fail(ERQ_EINVAL, "erq_build_index: D must be a multiple of 64 in [64, 4096]");
     if (p->B < 1 || p->B > 8) return fail(ERQ_EINVAL, "erq_build_index: B must be in [1, 8]");
-    if (p->nlist < 1 || p->nlist > 65536 || p->nlist > N)
+    if (p->centroids && (!p->assign || p->nlist < 2))
+        return fail(ERQ_EINVAL, "erq_build_index: explicit centroids need an explicit assignment and nlist >= 2");
+    if (p->nlist < 1 || p->nlist > 65536 || (p->nlist > N && !p->centroids))
         return fail(ERQ_EINVAL, "erq_build_index: nlist must be in [1, min(N, 65536)]");
     cudaStream_t s = (cudaStream_t)stream;
     erq_index* ix = new erq_index();
@@ -399,8 +401,13 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
         if ((st = check_status(ix, s)) != ERQ_OK)
             return bail2(fail(ERQ_EINVAL, "erq_build_index: assign holds a cluster id outside [0, nlist)"));
     }
-    if ((e = launch_centroids(X, ix->list_off, ix->list_ids, nlist, D, ix->C, 0, s)) != cudaSuccess)
+    if (p->centroids) {
+        if ((e = cudaMemcpyAsync(ix->C, p->centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyDeviceToDevice,
+                                 s)) != cudaSuccess)
+            return bail2(cuda_fail(e, "copy centroids"));
+    } else if ((e = launch_centroids(X, ix->list_off, ix->list_ids, nlist, D, ix->C, 0, s)) != cudaSuccess) {
         return bail2(cuda_fail(e, "centroids"));
+    }
     if ((e = launch_rotate_fp64(ix->C, nullptr, nullptr, nullptr, ix->P, ix->Cp, nlist, D, s)) != cudaSuccess)
         return bail2(cuda_fail(e, "rotate centroids"));
     if ((e = launch_row_sqnorm(ix->C, nlist, D, ix->cnorm2, s)) != cudaSuccess) return bail2(cuda_fail(e, "cnorm"));
@@ -440,8 +447,8 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
 // Search
 // ---------------------------------------------------------------------------
 // Work-item shape of the scan: queries per item (the tensor-core MMA's N
-// extent) and rows per item.  Heuristic: wide items when clusters are probed by
-// many queries on average (nq * nprobe / nlist > 96).
+// extent) and rows per item.  Heuristic: 64 queries per item for k' <= 32,
+// else 32, and 4,096 rows; the autotuned or forced shape wins.
 static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq, int maxp, int* qn, int* rr) {
     if (prec == ERQ_PREC_FP32) {
         *qn = 64;
@@ -450,7 +457,7 @@ static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq,
     }
     const int cls = kp <= 32 ? 0 : 1;
     const int64_t work = nq * (int64_t)maxp;
-    int q = cls == 0 ? ((double)work / ix->nlist > 96.0 ? 128 : 64) : 32, r = 4096;
+    int q = cls == 0 ? 64 : 32, r = 4096;
     const erq_index::ScanTune& t = ix->tune[cls];
     if (t.valid && work <= 4 * t.work && 4 * work >= t.work) {
         q = t.qn;
@@ -499,12 +506,12 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((int32_t*)nullptr, (size_t)nq * maxp);                         // 8 slot_off
         T((int64_t*)nullptr, nq);                                        // 9 qtot
         T((int64_t*)nullptr, nq + 1);                                    // 10 qbase
-        T((int32_t*)nullptr, nlist);                                     // 11 cnt_c
-        T((int32_t*)nullptr, nlist);                                     // 12 pos_c
-        T((int64_t*)nullptr, nlist);                                     // 13 cnt64
-        T((int64_t*)nullptr, nlist);                                     // 14 items_c
-        T((int64_t*)nullptr, nlist + 1);                                 // 15 qoff
-        T((int64_t*)nullptr, nlist + 1);                                 // 16 item_off
+        T((int32_t*)nullptr, 2 * (size_t)nlist);                         // 11 cnt_c (per phase cluster)
+        T((int32_t*)nullptr, 2 * (size_t)nlist);                         // 12 pos_c
+        T((int64_t*)nullptr, 2 * (size_t)nlist);                         // 13 cnt64
+        T((int64_t*)nullptr, 2 * (size_t)nlist);                         // 14 items_c
+        T((int64_t*)nullptr, 2 * (size_t)nlist + 1);                     // 15 qoff
+        T((int64_t*)nullptr, 2 * (size_t)nlist + 1);                     // 16 item_off
         T((int64_t*)nullptr, (size_t)nq * maxp);                         // 17 qlist
         T((uint64_t*)nullptr, (size_t)nq * kp);                          // 18 cand
         T((uint64_t*)nullptr, 1);                                        // 19 (unused)
@@ -516,8 +523,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         T((float*)nullptr, (!explicit_probe && nlist > 1) ? (size_t)nq * ((nlist + 31) / 32) : 1);  // 25 group minima
         T((unsigned char*)nullptr, prec == ERQ_PREC_FP8 ? (size_t)nq * Dq : 1);   // 26 e4m3 queries
         T((float*)nullptr, prec == ERQ_PREC_FP8 ? (size_t)nq : 1);                // 27 their scales
+        T((int32_t*)nullptr, nlist);                                     // 28 touch_c
     };
-    void* sl[28];
+    void* sl[29];
     layout(plan, false, sl);
     ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, plan.off));
     Carver cv(ix->ws, ix->ws_bytes);
@@ -541,9 +549,11 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     pa.qoff = (int64_t*)sl[15];
     pa.item_off = (int64_t*)sl[16];
     pa.qlist = (int64_t*)sl[17];
+    pa.touch_c = (int32_t*)sl[28];
     uint64_t* cand = (uint64_t*)sl[18];
     if (!ix->dstats && cudaMalloc(&ix->dstats, 4 * sizeof(unsigned long long)) != cudaSuccess)
         return fail(ERQ_ENOMEM, "cudaMalloc search counters");
+    if (!ix->dctr && cudaMalloc(&ix->dctr, 256) != cudaSuccess) return fail(ERQ_ENOMEM, "cudaMalloc scan counter");
     pa.stats = ix->dstats;
     cudaError_t e;
     const bool timed = (p->flags & ERQ_SEARCH_TIMING) != 0;
@@ -658,12 +668,12 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         std::partial_sort(nr.begin(), nr.begin() + std::min(maxp, nlist), nr.end(), std::greater<int64_t>());
         int64_t topR = 0;
         for (int i = 0; i < std::min(maxp, nlist); ++i) topR += nr[i];
-        nitems = maxR * ceil_div(nq * (int64_t)maxp, QT) + sumR;
+        nitems = maxR * ceil_div(nq * (int64_t)maxp, QT) + 2 * sumR;   // two phases per cluster
         Ltot = nq * topR;
     } else {
         int64_t tot[2] = {0, 0};
         ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[0], pa.qbase + nq, 8, cudaMemcpyDeviceToHost, s));
-        ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + nlist, 8, cudaMemcpyDeviceToHost, s));
+        ERQ_CHECK_CUDA(cudaMemcpyAsync(&tot[1], pa.item_off + 2 * nlist, 8, cudaMemcpyDeviceToHost, s));
         ERQ_TRY(check_status(ix, s));
         Ltot = tot[0];
         nitems = tot[1];
@@ -690,7 +700,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int64_t* n_items_d = cb.take<int64_t>(1);
     int4* itemd = cb.take<int4>(tcp ? nitems : 0);
     int4* itemq = cb.take<int4>(tcp ? nitems * QT : 0);
-    ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + nlist, 8, cudaMemcpyDeviceToDevice, s));
+    ERQ_CHECK_CUDA(cudaMemcpyAsync(n_items_d, pa.item_off + 2 * nlist, 8, cudaMemcpyDeviceToDevice, s));
     ck.items = nitems;
     ck.lists = Ltot;
     pa.ck = ck;
@@ -698,7 +708,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
 
     if ((e = launch_plan_items(pa, items, s)) != cudaSuccess) return cuda_fail(e, "plan items");
     if (tcp && (e = launch_item_tables(items, n_items_d, nitems, ix->list_off, ix->poff, pa.qoff, pa.qlist, dqc,
-                                       pa.qbase, pa.slot_off, maxp, RR, QT, itemd, itemq, pa.stats, ck, s)) != cudaSuccess)
+                                       pa.qbase, pa.slot_off, maxp, RR, QT, nlist, itemd, itemq, pa.stats, ck, s)) !=
+                   cudaSuccess)
         return cuda_fail(e, "item tables");
     ERQ_TRY(mark(3));
     // ---- scan
@@ -706,12 +717,17 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.Qrot = Qrot; L.Qh = sl[20]; L.Q8 = sl[26]; L.qscale = (const float*)sl[27]; L.Dq = Dq; L.status = ix->status; L.N = ix->N; L.codes = ix->codes; L.g_const = ix->g_const; L.f_res = ix->f_res; L.list_off = ix->list_off;
     L.list_ids = ix->list_ids; L.qlist = pa.qlist; L.qoff = pa.qoff; L.items = items; L.n_items = n_items_d;
     L.dqc = dqc; L.slot_off = pa.slot_off; L.qbase = pa.qbase; L.inter = inter; L.inter_cnt = inter_cnt;
-    L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT;
+    L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.RR = RR; L.qn = QT; L.nlist = nlist;
     L.itemd = itemd; L.itemq = itemq; L.rowmeta = ix->rowmeta; L.codes_p = ix->codes_p; L.Np = ix->Np;
     L.tq = (unsigned long long*)sl[22];
     L.ip = ip;
     L.ck = ck;
+    L.nq = nq;
+    L.work_ctr = ix->dctr;
+    L.wait_ns = ix->wait_ns;
+    L.stall_stage = ix->stall_stage;
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
+    if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(ix->dctr, 0, sizeof(unsigned int), s));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -999,8 +1015,8 @@ extern "C" erq_status erq_search_timing_total(erq_index* ix, float* ms, int32_t 
 
 extern "C" erq_status erq_set_scan_config(erq_index* ix, int32_t queries_per_item, int32_t rows_per_item) {
     if (!ix) return fail(ERQ_EINVAL, "erq_set_scan_config: null index");
-    if (queries_per_item != 0 && queries_per_item != 32 && queries_per_item != 64 && queries_per_item != 128)
-        return fail(ERQ_EINVAL, "erq_set_scan_config: queries_per_item must be 0, 32, 64 or 128");
+    if (queries_per_item != 0 && queries_per_item != 32 && queries_per_item != 64)
+        return fail(ERQ_EINVAL, "erq_set_scan_config: queries_per_item must be 0, 32 or 64");
     if (rows_per_item != 0 && (rows_per_item < 256 || rows_per_item % 256 != 0 || rows_per_item > (1 << 20)))
         return fail(ERQ_EINVAL, "erq_set_scan_config: rows_per_item must be 0 or a multiple of 256 in [256, 2^20]");
     ix->force_qn = queries_per_item;
@@ -1024,7 +1040,7 @@ extern "C" erq_status erq_autotune(erq_index* ix, const float* Q, int64_t nq, co
     const int kp = std::max(p->k, p->rerank_k);
     const int cls = kp <= 32 ? 0 : 1;
     const int maxp = p->probe ? p->nprobe : (ix->nlist == 1 ? 1 : p->nprobe);
-    const int qns[3] = {32, 64, 128};
+    const int qns[2] = {32, 64};
     const int rrs[3] = {2048, 4096, 8192};
     int64_t* ids = nullptr;
     float* dists = nullptr;
@@ -1042,7 +1058,7 @@ extern "C" erq_status erq_autotune(erq_index* ix, const float* Q, int64_t nq, co
     pp.flags &= ~ERQ_SEARCH_TIMING;
     pp.cand_ids = nullptr;
     pp.cand_est = nullptr;
-    for (int qi = 0; qi < 3 && st == ERQ_OK; ++qi) {
+    for (int qi = 0; qi < 2 && st == ERQ_OK; ++qi) {
         if (!scan_tc_shape_ok(qns[qi], kp)) continue;
         for (int ri = 0; ri < 3 && st == ERQ_OK; ++ri) {
             ix->force_qn = qns[qi];
@@ -1096,5 +1112,75 @@ extern "C" erq_status erq_search_stats(const erq_index* ix, int64_t* out, int32_
     const int64_t v[6] = {(int64_t)d[0], (int64_t)d[1], ix->last_stats[2], ix->last_stats[3], (int64_t)d[2],
                           (int64_t)d[3]};
     for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
+    return ERQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Merging and re-ranking of caller-given candidate lists (cluster-sharded
+// search: each shard's top-k' are merged into the single index's top-k', whose
+// exact distances each shard then computes for the rows it holds).
+// ---------------------------------------------------------------------------
+extern "C" erq_status erq_merge_topk(const int64_t* cand_ids, const float* values, int64_t nq, int32_t m, int32_t k,
+                                     int32_t metric, int64_t* ids_out, float* vals_out, void* stream) {
+    if (nq < 0 || m < 1 || m > 8192 || k < 1 || k > 1024)
+        return fail(ERQ_EINVAL, "erq_merge_topk: need nq >= 0, 1 <= m <= 8192, 1 <= k <= 1024");
+    if (metric != ERQ_METRIC_L2 && metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_merge_topk: unknown metric");
+    if (nq == 0) return ERQ_OK;
+    if (!cand_ids || !values || !ids_out || !vals_out) return fail(ERQ_EINVAL, "erq_merge_topk: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int neg = metric == ERQ_METRIC_IP ? 1 : 0;
+    Carver plan(nullptr, 0);
+    plan.take<uint64_t>((size_t)nq * m);
+    plan.take<int32_t>(nq);
+    plan.take<int64_t>(nq + 1);
+    plan.take<uint64_t>((size_t)nq * k);
+    void* ws = nullptr;
+    ERQ_CHECK_CUDA(cudaMallocAsync(&ws, plan.off, s));
+    Carver cv(ws, plan.off);
+    uint64_t* keys = cv.take<uint64_t>((size_t)nq * m);
+    int32_t* counts = cv.take<int32_t>(nq);
+    int64_t* off = cv.take<int64_t>(nq + 1);
+    uint64_t* cand = cv.take<uint64_t>((size_t)nq * k);
+    DevChecks ck;
+    ck.lists = nq;
+    cudaError_t e = launch_make_keys(cand_ids, values, nq * (int64_t)m, 0, neg, keys, s);
+    if (e == cudaSuccess) e = launch_one_list_per_query(nq, m, counts, off, s);
+    if (e == cudaSuccess) e = launch_merge(keys, counts, off, nq, k, m, cand, ck, s);
+    if (e == cudaSuccess) e = launch_keys_to_pairs(cand, nq * (int64_t)k, neg, ids_out, vals_out, s);
+    const cudaError_t ef = cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) return cuda_fail(e, "erq_merge_topk");
+    if (ef != cudaSuccess) return cuda_fail(ef, "erq_merge_topk: cudaFreeAsync");
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_rerank_ids(erq_index* ix, const float* Q, int64_t nq, int32_t nc, const int64_t* ids,
+                                     int32_t k, int32_t metric, int64_t* ids_out, float* dists_out, void* stream) {
+    if (!ix || nq < 0 || nc < 1 || nc > 1024 || k < 1 || k > nc)
+        return fail(ERQ_EINVAL, "erq_rerank_ids: need an index, 1 <= k <= nc <= 1024");
+    if (metric != ERQ_METRIC_L2 && metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_rerank_ids: unknown metric");
+    if (!ix->keep_raw) return fail(ERQ_EINVAL, "erq_rerank_ids: the index keeps no raw rows (keep_raw = 0)");
+    if (nq == 0) return ERQ_OK;
+    if (!Q || !ids || !ids_out || !dists_out) return fail(ERQ_EINVAL, "erq_rerank_ids: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* keys = nullptr;
+    ERQ_CHECK_CUDA(cudaMallocAsync((void**)&keys, sizeof(uint64_t) * (size_t)nq * nc, s));
+    DevChecks ck;
+    ck.status = ix->status;
+    ck.rows = ix->N;
+    cudaError_t e = launch_make_keys(ids, nullptr, nq * (int64_t)nc, ix->N, 0, keys, s);
+    if (e == cudaSuccess)
+        e = launch_rerank(keys, nq, nc, ix->X, Q, ix->D, k, 1, metric == ERQ_METRIC_IP ? 1 : 0, ids_out, dists_out,
+                          nullptr, nullptr, ck, s);
+    const cudaError_t ef = cudaFreeAsync(keys, s);
+    if (e != cudaSuccess) return cuda_fail(e, "erq_rerank_ids");
+    if (ef != cudaSuccess) return cuda_fail(ef, "erq_rerank_ids: cudaFreeAsync");
+    return ERQ_OK;
+}
+
+extern "C" erq_status erq_set_wait_limit(erq_index* ix, uint64_t ns, int64_t stall_stage) {
+    if (!ix) return fail(ERQ_EINVAL, "erq_set_wait_limit: null index");
+    if (stall_stage < -1) return fail(ERQ_EINVAL, "erq_set_wait_limit: stall_stage must be >= -1");
+    ix->wait_ns = ns;
+    ix->stall_stage = stall_stage;
     return ERQ_OK;
 }

@@ -157,6 +157,9 @@ struct erq_index {
     int force_qn = 0, force_rr = 0;
     struct ScanTune { int valid = 0; int64_t work = 0; int qn = 0, rr = 0; } tune[2];
     int last_qn = 0, last_rr = 0;
+    unsigned int* dctr = nullptr;          // dynamic work-item counter of the tensor-core scan
+    unsigned long long wait_ns = 0;        // limit of the scan's bounded waits (0 = the default 2 s)
+    long long stall_stage = -1;            // test stall of the scan's bounded-wait path (-1 = none)
     unsigned long long* dstats = nullptr;  // [4] device counters of the last search: pairs, distinct rows,
                                            //     tensor-core row blocks, row blocks x padded queries
     size_t pinned_bytes = 0;

@@ -16,20 +16,22 @@ struct PlanArgs {
     int npr_uniform;
     int64_t nq;
     int maxp, nlist, QT, RR;
+    int two_phase = 0;          // nearest probed cluster of every query in a first phase of work items
     const int64_t* list_off;
     const int32_t* corder;      // [nlist] clusters by decreasing size
     int32_t* npr;               // [nq] effective nprobe
     int32_t* probe_c;           // [nq][maxp] validated cluster or -1
-    int32_t* cnt_c;             // [nlist]
-    int32_t* pos_c;             // [nlist]
+    int32_t* cnt_c;             // [2 nlist] queries per phase cluster (v = c: nearest probe, nlist + c: others)
+    int32_t* pos_c;             // [2 nlist]
+    int32_t* touch_c;           // [nlist] probes per cluster (distinct probed rows)
     int32_t* slot_nr;           // [nq][maxp] ranges of the slot's cluster
     int32_t* slot_off;          // [nq][maxp]
     int64_t* qtot;              // [nq]
     int64_t* qbase;             // [nq+1]
-    int64_t* cnt64;             // [nlist]
-    int64_t* items_c;           // [nlist]
-    int64_t* qoff;              // [nlist+1]
-    int64_t* item_off;          // [nlist+1]
+    int64_t* cnt64;             // [2 nlist]
+    int64_t* items_c;           // [2 nlist]
+    int64_t* qoff;              // [2 nlist + 1]
+    int64_t* item_off;          // [2 nlist + 1]
     int64_t* qlist;             // [nq*maxp]
     uint32_t* status;
     const float* sqd;           // optional [nq][nlist] probe values (||q_r - c||^2, or -<q_r, c>): when given,
@@ -67,8 +69,12 @@ struct ScanLaunch {
     const uint64_t* codes_p;    // tensor-core path: packed B-bit codes, tiled and padded
     int64_t Np;                 // tensor-core path: padded rows
     unsigned long long* tq;     // tensor-core path: [nq] query-wide thresholds (all ones at the start)
-    int maxp, D, B, kp, RR;
+    int maxp, D, B, kp, RR, nlist;
     int qn;                     // tensor-core path: queries per work item (32, 64 or 128)
+    int64_t nq;                 // tensor-core path: query rows (extent of the gathered query matrix)
+    unsigned int* work_ctr;     // tensor-core path: dynamic work-item counter, zero at launch
+    unsigned long long wait_ns; // tensor-core path: limit of every bounded device-side wait (0 = default)
+    long long stall_stage = -1; // tensor-core path: test stall of the bounded-wait path (-1 = none)
     int grid;
     int ip;                     // inner-product metric (per-row factor f_res / 4, no g; dqc holds -<c, q_r>)
     DevChecks ck;
@@ -81,12 +87,17 @@ cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
 size_t scan_fp32_smem(int kp);
 int merge_sortn(int kp, int lstride);
+cudaError_t launch_make_keys(const int64_t* ids, const float* vals, int64_t n, int64_t id_limit, int neg,
+                             uint64_t* keys, cudaStream_t s);
+cudaError_t launch_keys_to_pairs(const uint64_t* keys, int64_t n, int neg, int64_t* ids, float* vals, cudaStream_t s);
+cudaError_t launch_one_list_per_query(int64_t nq, int m, int32_t* counts, int64_t* off, cudaStream_t s);
 cudaError_t launch_merge(const uint64_t* inter, const int32_t* inter_cnt, const int64_t* qbase, int64_t nq, int kp,
                          int lstride, uint64_t* cand, const DevChecks& ck, cudaStream_t s);
 int scan_list_stride(int precision, int kp, int qn);
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
-                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int nlist,
+                               int4* itemd,
                                int4* itemq, unsigned long long* stats, const DevChecks& ck, cudaStream_t s);
 bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,

@@ -2,68 +2,63 @@
 // <2 ybar, q'> for every (query, candidate) pair of a work item, on the
 // 5th-generation tensor cores with FP32 accumulation in tensor memory.
 //
-// A work item is (cluster, up to 64 of the queries that probe it, up to RR
+// A work item is (cluster, up to QN of the queries that probe it, up to RR
 // stored rows).  Operands of one MMA (kind::f16, M = 128, N = npad, K = 16):
 //   A = 128 stored rows of the cluster, codes expanded to 2*ybar_u - (2^B-1),
 //       odd integers in [-255, 255] and therefore exact in FP16, held in
 //       tensor memory (row = lane, two FP16 values per column);
 //   B = the item's queries (rotated q' in FP16), npad = the query count rounded
-//       up to a multiple of 16, K-major.
+//       up to a multiple of 16, K-major, 128-byte swizzled rows gathered from
+//       the query matrix by TMA (tile::gather4, four rows per copy).
 // Codes are read from a packed, scan-specific copy: every inverted list padded
 // to a multiple of 32 rows and stored as [tiles of 32 rows][K blocks of 64]
 // [B words][32 rows] of 8 bytes, i.e. exactly B bits per coordinate (the
-// layout is given at unpack_codes); the 128 rows of one stage and K block are
-// four contiguous 256*B-byte pieces fetched by one 3-D TMA load.  Tensor
-// memory: columns [0, 2 RP QN) hold two buffers of RP accumulators (QN columns
-// each), the columns after them the expanded-code stages of RP x 32 columns.
-// The accumulator holds row r in TMEM lane r and query j in column j; the
-// estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
+// layout is given at unpack_codes); the 128 rows of one row block and K block
+// are four contiguous 256*B-byte pieces fetched by one 3-D TMA load.
+//
+// The estimate is est = ||q_r - c||^2 + g + (f_res / 2) * acc with g, f_res the
 // stored per-row factors, or for the inner-product metric the ranking score
 // -<c, q_r> + (f_res / 4) * acc = -(estimated <o_r, q_r>).  The product is
 // exact up to the FP16 rounding of q' (relative 2^-11 per element);
 // accumulation is FP32.
 //
-// Warp roles (27 warps = 864 threads with NG = 2, NFX = 10; one CTA per SM,
-// persistent over work items):
-//   warp 9     loader: per stage (128-row block, 64-wide K block) one TMA load
-//              of the packed codes (L2 evict-first); per row block a bulk copy
-//              of the rows' factors and ids; per item the queries'
-//              ||q_r - c||^2 and output slots.  It runs up to LS stages ahead
-//              of the tensor cores;
-//   warps 10.. gatherers (NG warps): per stage, cp.async of the item's FP16 query rows
-//              (L2 evict-last) into the 128B-swizzled B tile, completion
-//              tracked on the stage's query barrier;
-//   warps 4-7, converters, two sets that take alternate stages: one thread
-//   and 23-26  per row unpacks the row's 64 B-bit codes of a stage (B 8-byte
-//              words; a warp reads 256 contiguous bytes per word, conflict-
-//              free) in registers and stores them as FP16 into the stage's
-//              TMEM columns (warp w owns TMEM lanes 32 (w % 4) ..);
-//   warp 8     MMA issuer of row block 0 (one elected thread) and TMEM owner;
-//   warp 22    MMA issuer of row block 1.  Each issuer commits once per
-//              stage to the stage's release barrier, which frees its codes,
-//              query tile and TMEM code columns together;
-//   warps 0-3  estimate tiles: warp w reads TMEM lanes 32w..32w+31 (its 32
-//              rows for all queries) and stores g + (f_res/2)*acc into one of
-//              EB query-major tiles in shared memory;
-//   warps 12-21 filters (NFX warps, pipelined behind the tiles through
-//              full/empty barriers): warp f filters the rows of the query
-//              slots f + NFX j against per-query thresholds into per-query
-//              candidate lists (warp ballots; when a list is full, a warp
-//              bitonic sort keeps the k' smallest).  A query's threshold
-//              starts at the smallest k'-th key published so far by its items
-//              (an item publishes its list's k'-th key with atomicMin after
-//              every compaction and at its end), which is never below the
-//              query's final k'-th key, so each list stays a superset of what
-//              the item contributes to the query's top-k'.
-// A stage covers up to RP = 2 row blocks that share the stage's query tile and
-// accumulate into separate TMEM accumulators, so two MMA dependency chains are
-// in flight and the query gather is amortised over 256 rows.  Accumulators are
-// double-buffered per stage group, so the epilogue of one group overlaps the
-// MMAs of the next; two estimate tiles let the tile warps fill a block while
-// the filter warps still work on the previous one.  Every mbarrier wait is
-// bounded: on expiry the kernel records ERQ_ETIMEOUT in the status word, every
-// role stops at its next wait (the abort flag), the copies and MMAs already
-// issued are drained (bounded), TMEM is freed and the kernel returns.
+// One persistent CTA per SM takes work items from a global counter (items are
+// ordered by decreasing cluster size).  A stage group is up to RP = 2 row
+// blocks of 128 rows that share the stage's query tile; a stage is one
+// 64-coordinate K block of the group.  Warp roles (26 warps):
+//   warps 0-3    estimate tiles: warp w reads TMEM lanes 32w .. 32w + 31 (its
+//                32 rows, all queries) of each finished row-block accumulator,
+//                stores g + (f_res/2) acc into one of EB query-major tiles in
+//                shared memory and frees the accumulator;
+//   warps 4-11   converters: warp w unpacks the codes of rows 32 (w % 4) ..
+//                + 31 of row block (w - 4) / 4 from the raw stage in shared
+//                memory into FP16 (or e4m3) values in the stage's TMEM columns;
+//   warp 12      code loader: publishes the items, per row block a bulk copy of
+//                the rows' factors and ids, per stage one TMA load of the packed
+//                codes per row block into a raw ring that is released as soon as
+//                the converters have read it (so loads run up to RS stages
+//                ahead, independent of the tensor cores);
+//   warps 13-16  query loaders: per stage the item's query rows (128 bytes
+//                each) by TMA gather4 into the stage's swizzled B tile, the
+//                stages taken in turn by the four warps;
+//   warps 17, 18 MMA issuers of row blocks 0 and 1 (one elected thread each;
+//                warp 17 owns the tensor memory); each commits once per stage to
+//                the stage's release barrier, which frees the query tile and the
+//                stage's TMEM code columns;
+//   warps 19-26  filters (NFX = 8), pipelined behind the tiles through full /
+//                empty tile barriers: warp f owns the query slots f + NFX j and
+//                filters their rows (float pre-filter against the threshold,
+//                exact keys, ballots) into per-query candidate lists; a full
+//                list is compacted by a warp bitonic sort to its k' smallest.
+//                A query starts from the smallest k'-th key published so far by
+//                its items, which is never below its final k'-th key, so each
+//                list stays a superset of what the item contributes.
+// Accumulators are double-buffered per row block, so the epilogue of one stage
+// group overlaps the MMAs of the next.
+// Every mbarrier wait is bounded (the limit is a kernel argument): on expiry
+// the kernel records ERQ_ETIMEOUT in the status word, every role stops at its
+// next wait (the abort flag), the copies and MMAs already issued are drained
+// (bounded), TMEM is freed and the kernel returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -78,63 +73,83 @@ namespace erq {
 
 namespace tc {
 
-constexpr int MR = 128;          // stored rows per MMA block (MMA M)
-static_assert(MR == 128, "four 32-row groups per row block (TMEM lane quarters, filter masks)");
+constexpr int MR = 128;          // stored rows per row block (MMA M = TMEM lanes)
+static_assert(MR == 128, "four 32-row lane quarters per row block");
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
-constexpr int MS = 4;            // row-factor buffers (one per row block)
-constexpr int NMMA = 2;          // MMA issuing warps
-constexpr int KCAP = 128;        // max k' of the tensor-core path
-constexpr int NG = 2;            // query-gather warps (10 .. 10 + NG - 1)
-constexpr int NFX = 10;          // filter warps (10 + NG ..)
-constexpr int NEPI = 4 + NFX;    // epilogue warps: four estimate-tile warps and the filter warps
-constexpr int MMA2 = 10 + NG + NFX;   // second MMA issuer (row block 1 of a stage group)
-constexpr int NCV = 2;           // converter sets (warps 4-7, and CV2 .. CV2 + 3 when NCV = 2)
-constexpr int CV2 = MMA2 + 1;
-constexpr int THREADS = 32 * (CV2 + (NCV == 2 ? 4 : 0));
-constexpr int TMEM_COLS = 512;     // accumulators 2 x RP x QN columns + LS x RP x 32 columns of codes
+constexpr int RP = 2;            // row blocks per stage group (one accumulator and one issuer each)
+constexpr int MS = 8;            // row-factor buffers
+constexpr int EB = 2;            // estimate tiles (the filters work on one while the other fills)
+constexpr int RSMAX = 8;         // raw-code ring slots at most
+constexpr int RAW_BYTES = 64 * 1024;
+constexpr int W_CV = 4;          // converter warps 4..11 (row block (w - 4) / 4, lane quarter w % 4)
+constexpr int W_LD = 12;         // code loader and item publisher
+constexpr int W_QL = 13;         // query-tile loaders 13 .. 13 + NQL - 1 (stage g: loader g % NQL)
+constexpr int NQL = 4;
+constexpr int W_MMA = W_QL + NQL;   // MMA issuers (row block 0, TMEM owner; row block 1)
+constexpr int W_FX = W_MMA + 2;     // filter warps W_FX .. W_FX + NFX - 1
+constexpr int NFX = 8;
+constexpr int NWARP = W_FX + NFX;
+constexpr int THREADS = 32 * NWARP;
+constexpr int TMEM_COLS = 512;
+constexpr int KCAP = 128;        // largest k' of the tensor-core path
 
-// Work-item shapes: QN queries per item (the MMA's N extent), KC-entry
-// candidate lists, RP row blocks per stage, LS load stages, EB estimate tiles.
-template <int QN_, int KC_, int RP_, int LS_, int EB_>
+// Work-item capacities: QN queries per item at most (the MMA's N extent), KC
+// list entries per query, NBUF accumulator buffers per row block, LS stages of
+// query tiles and TMEM code columns.
+template <int QN_, int KC_, int NBUF_, int LS_>
 struct Cfg {
-    static constexpr int QN = QN_;                 // queries per item (MMA N <= QN)
-    static constexpr int KC = KC_;                 // per-query list capacity (list stride of the output)
-    static constexpr int RP = RP_;                 // 128-row blocks per stage (independent accumulators)
-    static constexpr int LS = LS_;                 // load stages (raw codes + query tile) in flight
-    static constexpr int EB = EB_;                 // estimate tiles (2: filtering overlaps the next block)
-    static constexpr int KS = KC_ <= 64 ? 64 : 256;   // sort width of a list compaction
-    static constexpr int TILE_Q = QN * KB * 2;
-    static constexpr int TILE_RAW = RP * MR * KB;  // packed codes of a stage (TMA staging; 128 * 8 B <= 8 KB per block)
-    static constexpr int ACOL = 2 * RP * QN;       // first TMEM column of the expanded-code stages
+    static constexpr int QN = QN_, KC = KC_, NBUF = NBUF_, LS = LS_;
+    static constexpr int KS = KC <= 64 ? 64 : 256;   // sort width of a list compaction
+    static constexpr int TILE_Q = QN * 128;          // one stage's query tile: QN rows of 128 bytes
+    static constexpr int ACOL = NBUF * RP * QN;      // first TMEM column of the code stages
     static_assert(ACOL + LS * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
-    static_assert(NCV == 1 || LS % 2 == 0, "the two converter sets take alternate stages and must see every use of theirs");
-    static_assert(QN % (4 * NG) == 0 && QN % 32 == 0 && (QN + NFX - 1) / NFX <= 32, "query tile split");
-    static_assert(RP >= 1 && RP <= NMMA && (EB == 1 || EB == 2), "stage shape");
+    static_assert(QN % 32 == 0 && KC >= 64 && (QN + NFX - 1) / NFX <= 32, "item shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
-        static constexpr int q = 0;                                // LS  x [QN queries][64] FP16, swizzled
-        static constexpr int raw = q + LS * TILE_Q;                // LS  x RP x 8 KB: packed codes of 128 rows
-        static constexpr int est = raw + LS * TILE_RAW;            // EB x [QN][MR] f32  g + (f_res/2) acc
-        static constexpr int lists = est + EB * QN * MR * 4;       // [QN][KC] u64 candidate keys
-        static constexpr int meta = lists + QN * KC * 8;           // MS x [MR] float4 {g, f_res/2, id, 0}
-        static constexpr int iq = meta + MS * MR * 16;             // 2 x [QN] int4 {query row, dqc, slot lo, hi}
-        static constexpr int idesc = iq + 2 * QN * 16;             // 2 x int4 {rb0 lo, rb0 hi, rows, queries}
-        static constexpr int ids = idesc + 2 * 16;                 // EB x [MR] u32 ids of the row block
-        static constexpr int cnt = ids + EB * MR * 4;              // [QN] int   list fill
-        static constexpr int tau = cnt + QN * 4;                   // [QN] u64   admission threshold
-        static constexpr int tq = tau + QN * 8;                    // 2 x [QN] u64 query-wide threshold at item start
-        static constexpr int qsc = tq + 2 * QN * 8;                // 2 x [QN] f32 query scales (e4m3 path)
-        static constexpr int bars = qsc + 2 * QN * 4;              // mbarriers (8 B each)
-        static constexpr int nbars = 4 * LS + 4 + 2 * MS + 4 + 1 + 4;
+        static constexpr int q = 0;                              // LS x [QN][128 B] query tiles, swizzled
+        static constexpr int raw = q + LS * TILE_Q;              // raw-code ring (RS slots of RP x B KB)
+        static constexpr int est = raw + RAW_BYTES;              // EB x [QN][MR] f32 g + (f_res/2) acc
+        static constexpr int lists = est + EB * QN * MR * 4;     // [QN][KC] u64 candidate keys
+        static constexpr int meta = lists + QN * KC * 8;         // MS x [MR] float4 {g, f_res/2, id, 0}
+        static constexpr int iq = meta + MS * MR * 16;           // 2 x [QN] int4 {query row, dqc bits, list lo, hi}
+        static constexpr int tq = iq + 2 * QN * 16;              // 2 x [QN] u64 query-wide threshold at publication
+        static constexpr int qsc = tq + 2 * QN * 8;              // 2 x [QN] f32 query scale (e4m3 path)
+        static constexpr int itd = qsc + 2 * QN * 4;             // 2 x int4 {rb0 lo, rb0 hi, rows, queries | -1}
+        static constexpr int ids = itd + 2 * 16;                 // EB x [MR] u32 ids of the tile's rows
+        static constexpr int cnt = ids + EB * MR * 4;            // [QN] int list fill
+        static constexpr int tau = cnt + QN * 4;                 // [QN] u64 admission threshold
+        static constexpr int bars = tau + QN * 8;
+        static constexpr int nbars = 2 * RSMAX + 2 * LS + LS * RP + 2 * NBUF * RP + 2 * MS + 4 + 2 + 2 * EB;
         static constexpr int tmem_slot = bars + nbars * 8;
         static constexpr int abort_flag = tmem_slot + 4;
-        static constexpr int total = abort_flag + 4 + 1024;        // + alignment slack
+        static constexpr int total = abort_flag + 4 + 1024;      // + alignment slack
     };
     static_assert(Smem::total <= 227 * 1024, "scan_tc shared memory");
+    // barrier byte offsets from Smem::bars
+    static constexpr int b_full_raw(int s) { return 8 * s; }
+    static constexpr int b_empty_raw(int s) { return 8 * (RSMAX + s); }
+    static constexpr int b_full_q(int s) { return 8 * (2 * RSMAX + s); }
+    static constexpr int b_empty_st(int s) { return 8 * (2 * RSMAX + LS + s); }
+    static constexpr int b_full_a(int s, int b) { return 8 * (2 * RSMAX + 2 * LS + s * RP + b); }
+    static constexpr int b_tfull(int u, int b) { return 8 * (2 * RSMAX + 2 * LS + LS * RP + u * RP + b); }
+    static constexpr int b_tempty(int u, int b) { return 8 * (2 * RSMAX + 2 * LS + LS * RP + NBUF * RP + u * RP + b); }
+    static constexpr int B0 = 2 * RSMAX + 2 * LS + LS * RP + 2 * NBUF * RP;
+    static constexpr int b_full_meta(int m) { return 8 * (B0 + m); }
+    static constexpr int b_empty_meta(int m) { return 8 * (B0 + MS + m); }
+    static constexpr int b_full_item(int i) { return 8 * (B0 + 2 * MS + i); }
+    static constexpr int b_empty_item(int i) { return 8 * (B0 + 2 * MS + 2 + i); }
+    static constexpr int b_done() { return 8 * (B0 + 2 * MS + 4); }
+    // a barrier nothing arrives on (the test stall of the bounded-wait path)
+    static constexpr int b_never() { return 8 * (B0 + 2 * MS + 5); }
+    static constexpr int b_tile_full(int t) { return 8 * (B0 + 2 * MS + 6 + t); }
+    static constexpr int b_tile_empty(int t) { return 8 * (B0 + 2 * MS + 6 + EB + t); }
 };
-using CfgSmall = Cfg<64, 64, 2, 4, 2>;    // k' <= 32, up to 64 queries per item
-using CfgLarge = Cfg<32, 160, 2, 4, 2>;   // k' <= 128, up to 32 queries per item
-using CfgWide = Cfg<128, 64, 1, 2, 1>;    // k' <= 32, up to 128 queries per item (query-heavy lists)
+using CfgA = Cfg<64, 64, 2, 4>;     // k' <= 32, up to 64 queries per item
+using CfgB = Cfg<32, 160, 2, 4>;    // k' <= 128, up to 32 queries per item
+
+// arrivals that complete a phase of the item-release barrier: every lane of the
+// query loader, the converters, the two issuers, the tile warps and the filters
+constexpr int kItemReleasers = 32 * (NQL + 8 + 2 + 4 + NFX);
 
 // Packed codes of one stored row and one 64-coordinate K block -> 32 TMEM
 // columns of FP16 pairs 2u - (2^B - 1) (column c holds coordinates 2c, 2c+1).
@@ -218,19 +233,21 @@ __device__ __forceinline__ uint32_t half2_to_e4m3_pair(uint32_t w) {
 }
 
 struct Args {
-    const unsigned char* Qb;      // [nq] rows of the query operand: FP16 (2D bytes) or e4m3 (qrow_bytes)
-    int64_t qrow_bytes;
-    const float* qscale;          // e4m3 path: per-query power-of-two scale of the e4m3 values
     const int4* itemd;            // [items] {rb0 lo, rb0 hi, rows, queries}
-    const int4* itemq;            // [items][QN] {query row or -1, dqc bits, output list index lo, hi}
-    const float4* rowmeta;        // [N] {g, f_res / 2, id bits, 0} in stored-row order
+    const int4* itemq;            // [items][qn] {query row or -1, dqc bits, output list index lo, hi}
+    int qn;                       // queries per item of the plan (row stride of itemq)
+    const float4* rowmeta;        // [Np] {g, f_res / 2, id bits, 0} in padded stored-row order
     const int64_t* n_items;
+    unsigned int* work_ctr;       // items taken after the first grid-size ones (zero at launch)
     uint64_t* inter;
     int32_t* inter_cnt;
     unsigned long long* tq;       // [nq] query-wide admission threshold (k'-th key of a finished item)
+    const float* qscale;          // e4m3 path: per-query power-of-two scale of the e4m3 values
     uint32_t* status;
-    int D, B, kp;
+    int D, B, kp, nkb;            // nkb: stages per row group (64 FP16 or 128 e4m3 coordinates each)
     int ip;                       // inner-product metric: est = -<c, q_r> + (f_res / 4) * acc
+    unsigned long long wait_ns;   // limit of every bounded wait
+    long long stall_stage;        // >= 0: the first issuer waits at this stage on a barrier nothing arrives on
     DevChecks ck;
 };
 
@@ -310,63 +327,64 @@ __device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, i
 // packed 64-coordinate blocks), which occupy the same 128 bytes per row in
 // tensor memory and in the query tile as 64 FP16 coordinates.
 template <class C, bool F8>
-__global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, tc::Args a) {
-    constexpr int QN = C::QN, KC = C::KC, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
-    constexpr int RP = C::RP, LS = C::LS, EB = C::EB, TILE_RAW = C::TILE_RAW;
+__global__ void __launch_bounds__(THREADS, 1)
+    scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, const __grid_constant__ CUtensorMap q_map,
+                   tc::Args a) {
+    constexpr int QN = C::QN, KC = C::KC, LS = C::LS, NBUF = C::NBUF, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
     using Smem = typename C::Smem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars);
+    const uint32_t bars = smem_u32(sm + Smem::bars);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Smem::tmem_slot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + Smem::abort_flag);
     int4* s_iq = reinterpret_cast<int4*>(sm + Smem::iq);
-    int4* s_idesc = reinterpret_cast<int4*>(sm + Smem::idesc);
+    int4* s_itd = reinterpret_cast<int4*>(sm + Smem::itd);
+    unsigned long long* s_tq = reinterpret_cast<unsigned long long*>(sm + Smem::tq);
+    float* s_qsc = reinterpret_cast<float*>(sm + Smem::qsc);
     const float4* s_meta = reinterpret_cast<const float4*>(sm + Smem::meta);
-    // barrier addresses
-    const uint32_t full_load0 = smem_u32(&bars[0]), empty_load0 = smem_u32(&bars[LS]);
-    const uint32_t full_q0 = smem_u32(&bars[2 * LS]);
-    const uint32_t full_a0 = smem_u32(&bars[3 * LS]);
-    const uint32_t tfull0 = smem_u32(&bars[4 * LS]), tempty0 = smem_u32(&bars[4 * LS + 2]);
-    const uint32_t full_meta0 = smem_u32(&bars[4 * LS + 4]);
-    const uint32_t empty_meta0 = smem_u32(&bars[4 * LS + 4 + MS]);
-    const uint32_t full_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS]);
-    const uint32_t empty_item0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 2]);
-    const uint32_t done_bar = smem_u32(&bars[4 * LS + 4 + 2 * MS + 4]);
-    const uint32_t tile_full0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 5]);
-    const uint32_t tile_empty0 = smem_u32(&bars[4 * LS + 4 + 2 * MS + 7]);
+    const unsigned long long wlim = a.wait_ns;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D = a.D;
-    const int nkb = F8 ? (D + 2 * KB - 1) / (2 * KB) : D / KB;   // stages per row group (128 bytes per row)
+    const int nkb = a.nkb;
+    const uint32_t blk = (uint32_t)(MR / 32) * 256u * (uint32_t)a.B;    // packed codes of one 128-row K block
+    const uint32_t slot_bytes = (uint32_t)RP * blk * (F8 ? 2u : 1u);
+    const int RS = min(RSMAX, (int)(RAW_BYTES / slot_bytes));
     int64_t nitems = *a.n_items;
     if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 7)) nitems = 0;   // uniform: every thread reads it
 
     if (tid == 0) {
+        for (int s = 0; s < RSMAX; ++s) {
+            mbar_init(bars + C::b_full_raw(s), 1);
+            mbar_init(bars + C::b_empty_raw(s), 32 * 8);
+        }
         for (int s = 0; s < LS; ++s) {
-            mbar_init(full_load0 + 8 * s, 1);      // the TMA expect_tx arrival
-            mbar_init(empty_load0 + 8 * s, NMMA);  // one MMA commit per issuer: codes, queries and TMEM stage free
-            mbar_init(full_q0 + 8 * s, 32 * NG);   // one cp.async arrival per gatherer lane
-            mbar_init(full_a0 + 8 * s, 128);       // the converter set of the stage
+            mbar_init(bars + C::b_full_q(s), 1);
+            mbar_init(bars + C::b_empty_st(s), RP);
+            for (int b = 0; b < RP; ++b) mbar_init(bars + C::b_full_a(s, b), 128);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(tfull0 + 8 * b, NMMA);
-            mbar_init(tempty0 + 8 * b, 128);
-            mbar_init(full_item0 + 8 * b, 32);
-            mbar_init(empty_item0 + 8 * b, 32 * NEPI);
-        }
+        for (int u = 0; u < NBUF; ++u)
+            for (int b = 0; b < RP; ++b) {
+                mbar_init(bars + C::b_tfull(u, b), 1);
+                mbar_init(bars + C::b_tempty(u, b), 128);
+            }
         for (int m = 0; m < MS; ++m) {
-            mbar_init(full_meta0 + 8 * m, 1);
-            mbar_init(empty_meta0 + 8 * m, 128);
+            mbar_init(bars + C::b_full_meta(m), 1);
+            mbar_init(bars + C::b_empty_meta(m), 128);
         }
-        mbar_init(done_bar, NMMA);
-        for (int t = 0; t < 2; ++t) {
-            mbar_init(tile_full0 + 8 * t, 128);        // the four estimate-tile warps
-            mbar_init(tile_empty0 + 8 * t, 32 * NFX);  // the filter warps
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bars + C::b_full_item(i), 32);
+            mbar_init(bars + C::b_empty_item(i), kItemReleasers);
+        }
+        mbar_init(bars + C::b_done(), RP);
+        mbar_init(bars + C::b_never(), 1);
+        for (int t = 0; t < EB; ++t) {
+            mbar_init(bars + C::b_tile_full(t), 128);       // the four estimate-tile warps
+            mbar_init(bars + C::b_tile_empty(t), 32 * NFX); // the filter warps
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "n"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -376,326 +394,359 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 9) {
-        // ------------------------------------------------------------ loader
+    if (warp == W_LD) {
+        // ------------------------------------------------------------ code loader, item publisher
         uint32_t g = 0, rbg = 0, li = 0;
         bool ok = true;
         int64_t item = blockIdx.x;
-        int4 dcur = make_int4(0, 0, 0, 0), qv[QN / 32];
-#pragma unroll
-        for (int j = 0; j < QN / 32; ++j) qv[j] = dcur;
-        if (item < nitems) {
-            dcur = a.itemd[item];
-#pragma unroll
-            for (int j = 0; j < QN / 32; ++j) qv[j] = a.itemq[item * QN + 32 * j + lane];
-        }
         const uint64_t pol_codes = l2_evict_first();
-        for (; item < nitems && ok; item += gridDim.x, ++li) {
-            // next item's descriptors are fetched while this one streams
-            const int64_t nxt = item + gridDim.x;
-            int4 dn = make_int4(0, 0, 0, 0), nv[QN / 32];
-#pragma unroll
-            for (int j = 0; j < QN / 32; ++j) nv[j] = dn;
-            if (nxt < nitems) {
-                dn = a.itemd[nxt];
-#pragma unroll
-                for (int j = 0; j < QN / 32; ++j) nv[j] = a.itemq[nxt * QN + 32 * j + lane];
-            }
+        for (;; ++li) {
             const int ib = li & 1;
-            if (!mbar_wait_warp(empty_item0 + 8 * ib, ((li >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
-            int4* iq = s_iq + ib * QN;
-            unsigned long long* tqs = reinterpret_cast<unsigned long long*>(sm + Smem::tq) + ib * QN;
-#pragma unroll
-            for (int j = 0; j < QN / 32; ++j) {
-                iq[32 * j + lane] = qv[j];
-                tqs[32 * j + lane] = qv[j].x >= 0 ? __ldcg(a.tq + qv[j].x) : kEmptyKey;
-                if (F8) reinterpret_cast<float*>(sm + Smem::qsc)[ib * QN + 32 * j + lane] = qv[j].x >= 0 ? a.qscale[qv[j].x] : 0.f;
+            if (!mbar_wait_warp(bars + C::b_empty_item(ib), ((li >> 1) & 1) ^ 1, abort_flag, wlim)) {
+                ok = false;
+                break;
             }
-            if (lane == 0) s_idesc[ib] = dcur;
-            mbar_arrive(full_item0 + 8 * ib);
+            const bool have = item < nitems;
+            int4 d = make_int4(0, 0, 0, -1);
+            if (have) {
+                d = a.itemd[item];
+                for (int q = lane; q < QN; q += 32) {
+                    const int4 v = q < a.qn ? a.itemq[item * a.qn + q] : make_int4(-1, 0, 0, 0);
+                    s_iq[ib * QN + q] = v;
+                    s_tq[ib * QN + q] = v.x >= 0 ? __ldcg(a.tq + v.x) : kEmptyKey;
+                    if (F8) s_qsc[ib * QN + q] = v.x >= 0 ? a.qscale[v.x] : 0.f;
+                }
+            }
+            if (lane == 0) s_itd[ib] = d;
             __syncwarp();
-            const int64_t rb0 = rb0_of(dcur);                 // first padded row (multiple of 32)
-            const int nrows = dcur.z;
+            mbar_arrive(bars + C::b_full_item(ib));
+            if (!have) break;
+            const int64_t rb0 = rb0_of(d);                 // first padded row (multiple of 32)
+            const int nrows = d.z;
             for (int r = 0; r < nrows && ok; r += RP * MR) {
-                const int nb = min(RP, (nrows - r + MR - 1) / MR);     // 128-row blocks in this stage group
+                const int nb = min(RP, (nrows - r + MR - 1) / MR);     // row blocks in this stage group
                 for (int bb = 0; bb < nb && ok; ++bb, ++rbg) {
                     const int nr = min(MR, nrows - r - bb * MR);
                     const int m = rbg % MS;
-                    if (!mbar_wait_warp(empty_meta0 + 8 * m, ((rbg / MS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    if (lane == 0) {
-                        mbar_arrive_expect_tx(full_meta0 + 8 * m, (uint32_t)nr * 16u);
-                        bulk_load(smem_u32(sm + Smem::meta + m * MR * 16), a.rowmeta + rb0 + r + bb * MR,
-                                  (uint32_t)nr * 16u, full_meta0 + 8 * m);
-                    }
-                }
-                for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
-                    const int s = g % LS;
-                    if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    if (lane == 0) {
-                        const uint32_t blk = (uint32_t)(MR / 32) * 256 * a.B;   // one packed block of 128 rows
-                        mbar_arrive_expect_tx(full_load0 + 8 * s, (uint32_t)nb * blk * (F8 ? 2u : 1u));
-                        for (int bb = 0; bb < nb; ++bb) {
-                            const uint32_t dst = smem_u32(sm + Smem::raw + s * TILE_RAW + bb * MR * KB);
-                            const int tile = (int)((rb0 + r + bb * MR) >> 5);
-                            // (the second block of the last F8 stage may lie past D: the TMA fills zeros)
-                            tma_load_3d_hint(dst, &codes_map, 0, F8 ? 2 * kb : kb, tile, full_load0 + 8 * s, pol_codes);
-                            if (F8)
-                                tma_load_3d_hint(dst + blk, &codes_map, 0, 2 * kb + 1, tile, full_load0 + 8 * s, pol_codes);
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            dcur = dn;
-#pragma unroll
-            for (int j = 0; j < QN / 32; ++j) qv[j] = nv[j];
-        }
-        // drain: every copy this warp issued has landed before the CTA exits
-        for (uint32_t k = 0; k < LS && k < g; ++k) {
-            const uint32_t gg = g - 1 - k;
-            mbar_wait_drain(full_load0 + 8 * (gg % LS), (gg / LS) & 1);
-        }
-        for (uint32_t k = 0; k < MS && k < rbg; ++k) {
-            const uint32_t gg = rbg - 1 - k;
-            mbar_wait_drain(full_meta0 + 8 * (gg % MS), (gg / MS) & 1);
-        }
-        __syncwarp();
-    } else if (warp >= 10 && warp < 10 + NG) {
-        // ------------------------------------------------------------ gatherers
-        const uint64_t pol_q = l2_evict_last();
-        const int ch = lane & 7, gi = warp - 10;
-        uint32_t g = 0, li = 0;
-        bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-            const int ib = li & 1;
-            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
-            const int4* iq = s_iq + ib * QN;
-            const int4 d = s_idesc[ib];
-            const int nq4 = npad_of(d.w) / 4;
-            const int nsteps = ((d.z + RP * MR - 1) / (RP * MR)) * nkb;
-            // this lane gathers 16-byte chunk ch of query rows (lane >> 3) + 4 (gi + NG i)
-            const unsigned char* qp[QN / 4 / NG];
-#pragma unroll
-            for (int i = 0; i < QN / 4 / NG; ++i) {
-                const int qrow = iq[(lane >> 3) + 4 * (gi + NG * i)].x;
-                qp[i] = qrow >= 0 ? a.Qb + (int64_t)qrow * a.qrow_bytes + ch * 16 : nullptr;
-            }
-            for (int t = 0; t < nsteps; ++t, ++g) {
-                const int s = g % LS, kb = t % nkb;
-                if (!mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                const uint32_t qs = smem_u32(sm + Smem::q + s * TILE_Q);
-#pragma unroll
-                for (int i = 0; i < QN / 4 / NG; ++i) {
-                    if (gi + NG * i < nq4) {
-                        const int qq = (lane >> 3) + 4 * (gi + NG * i);
-                        const uint32_t dst = qs + qq * 128 + ((ch ^ (qq & 7)) << 4);
-                        cp_async16_hint(dst, qp[i] ? (const void*)(qp[i] + kb * 128) : (const void*)a.Qb,
-                                        qp[i] ? 16u : 0u, pol_q);
-                    }
-                }
-                cp_async_mbar_arrive(full_q0 + 8 * s);
-            }
-        }
-        cp_async_wait<0>();
-        for (uint32_t k = 0; k < LS && k < g; ++k) {
-            const uint32_t gg = g - 1 - k;
-            mbar_wait_drain(full_q0 + 8 * (gg % LS), (gg / LS) & 1);
-        }
-        __syncwarp();
-    } else if ((warp >= 4 && warp < 8) || warp >= CV2) {
-        // ------------------------------------------------------------ converters
-        // Two sets of four warps take alternate stages (set cs the stages g
-        // with g % 2 == cs).  Converter thread = one row of the stage (TMEM
-        // lane); warp w writes TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
-        const int cs = warp >= CV2 ? 1 : 0;
-        const int r = (warp & 3) * 32 + lane;
-        const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
-        const int B = a.B;
-        const int roff = (r >> 5) * 256 * B + (r & 31) * 8;   // word 0 of row r in a 128-row block
-        uint32_t g = 0, li = 0;
-        bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-            const int ib = li & 1;
-            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
-            const int nrows = s_idesc[ib].z;
-            const int nsteps = ((nrows + RP * MR - 1) / (RP * MR)) * nkb;
-            for (int t = 0; t < nsteps; ++t, ++g) {
-                if (NCV == 2 && (int)(g & 1) != cs) continue;
-                const int s = g % LS;
-                const int r0 = (t / nkb) * (RP * MR);
-                const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
-                // the codes have landed; the stage's previous MMAs (which read its
-                // TMEM columns) completed before the loader refilled it
-                if (!mbar_wait_warp(full_load0 + 8 * s, (g / LS) & 1, abort_flag) ||
-                    !mbar_wait_warp(empty_load0 + 8 * s, ((g / LS) & 1) ^ 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
-                    uint32_t w[32];
-                    const unsigned char* src = sm + Smem::raw + s * TILE_RAW + bb * MR * KB + roff;
-                    if (F8) {
-                        // two packed blocks -> 128 e4m3 codes, four per column
-#pragma unroll
-                        for (int hb = 0; hb < 2; ++hb) {
-                            uint32_t h[32];
-                            unpack_codes_b(B, src + hb * (MR / 32) * 256 * B, h);
-#pragma unroll
-                            for (int c = 0; c < 16; ++c)
-                                w[16 * hb + c] = __byte_perm(half2_to_e4m3_pair(h[2 * c]),
-                                                             half2_to_e4m3_pair(h[2 * c + 1]), 0x6420u);
-                        }
-                    } else {
-                        unpack_codes_b(B, src, w);
-                    }
-                    ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + bb) * (KB / 2), w);
-                }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                tc_fence_before();
-                mbar_arrive(full_a0 + 8 * s);
-            }
-        }
-    } else if (warp == 8 || warp == MMA2) {
-        // ------------------------------------------------------------ MMA issuers
-        // Each issuer runs the accumulation chain of one row block of a stage
-        // group (tcgen05.mma issue stalls the issuing thread, so two issuers
-        // keep two chains in flight); both commit to the stage and tile barriers.
-        const int mrb = warp == 8 ? 0 : 1;
-        uint32_t g = 0, acc = 0, li = 0;
-        bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-            const int ib = li & 1;
-            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
-            const int4 d = s_idesc[ib];
-            const uint32_t idesc = idesc_f16(MR, npad_of(d.w));
-            for (int r0 = 0; r0 < d.z && ok; r0 += RP * MR, ++acc) {   // acc counts stage groups
-                const int nb = min(RP, (d.z - r0 + MR - 1) / MR);
-                const int buf = acc & 1;
-                if (!mbar_wait_warp(tempty0 + 8 * buf, ((acc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t dt = tmem + buf * (RP * QN);
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int s = g % LS;
-                    if (!mbar_wait_warp(full_a0 + 8 * s, (g / LS) & 1, abort_flag) ||
-                        !mbar_wait_warp(full_q0 + 8 * s, (g / LS) & 1, abort_flag)) {
+                    if (!mbar_wait_warp(bars + C::b_empty_meta(m), ((rbg / MS) & 1) ^ 1, abort_flag, wlim)) {
                         ok = false;
                         break;
                     }
-                    fence_proxy_async();       // query tile written by cp.async (generic proxy)
-                    tc_fence_after();
                     if (lane == 0) {
-                        if (mrb < nb) {
-                            const uint32_t ta = tmem + ACOL + (s * RP + mrb) * (KB / 2);
-                            const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
-#pragma unroll
-                            for (int k = 0; k < KB / 16; ++k) {         // 32 bytes of K per instruction
-                                if (F8) mma_f8_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
-                                else mma_f16_ta(dt + mrb * QN, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
-                            }
+                        mbar_arrive_expect_tx(bars + C::b_full_meta(m), (uint32_t)nr * 16u);
+                        bulk_load(smem_u32(sm + Smem::meta + m * MR * 16), a.rowmeta + rb0 + r + bb * MR,
+                                  (uint32_t)nr * 16u, bars + C::b_full_meta(m));
+                    }
+                }
+                for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+                    const int s = g % RS;
+                    if (!mbar_wait_warp(bars + C::b_empty_raw(s), ((g / RS) & 1) ^ 1, abort_flag, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(bars + C::b_full_raw(s), (uint32_t)nb * blk * (F8 ? 2u : 1u));
+                        for (int bb = 0; bb < nb; ++bb) {
+                            const uint32_t dst = smem_u32(sm + Smem::raw + s * slot_bytes + bb * blk * (F8 ? 2 : 1));
+                            const int tile = (int)((rb0 + r + bb * MR) >> 5);
+                            // (the second block of the last F8 stage may lie past D: the TMA fills zeros)
+                            tma_load_3d_hint(dst, &codes_map, 0, F8 ? 2 * kb : kb, tile, bars + C::b_full_raw(s),
+                                             pol_codes);
+                            if (F8)
+                                tma_load_3d_hint(dst + blk, &codes_map, 0, 2 * kb + 1, tile, bars + C::b_full_raw(s),
+                                                 pol_codes);
                         }
-                        mma_commit(empty_load0 + 8 * s);     // codes, query tile and TMEM stage free
-                        if (kb == nkb - 1) mma_commit(tfull0 + 8 * buf);
                     }
                     __syncwarp();
                 }
             }
+            if (!ok) break;
+            int nx = 0;
+            if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
+            item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
+        }
+        // drain: every copy this warp issued has landed before the CTA exits
+        for (uint32_t k = 0; k < (uint32_t)RS && k < g; ++k) {
+            const uint32_t gg = g - 1 - k;
+            mbar_wait_drain(bars + C::b_full_raw(gg % RS), (gg / RS) & 1);
+        }
+        for (uint32_t k = 0; k < MS && k < rbg; ++k) {
+            const uint32_t gg = rbg - 1 - k;
+            mbar_wait_drain(bars + C::b_full_meta(gg % MS), (gg / MS) & 1);
+        }
+        __syncwarp();
+    } else if (warp >= W_QL && warp < W_QL + NQL) {
+        // ------------------------------------------------------------ query loaders (TMA gather4)
+        // Loader j issues the query tiles of the stages g with g % NQL == j.
+        const uint32_t qj = (uint32_t)(warp - W_QL);
+        const uint64_t pol_q = l2_evict_last();           // the query rows are read by many items
+        uint32_t g = 0;
+        bool ok = true;
+        for (uint32_t li = 0; ok; ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(bars + C::b_full_item(ib), (li >> 1) & 1, abort_flag, wlim)) break;
+            const int4 d = s_itd[ib];
+            if (d.w < 0) break;
+            const int npad = npad_of(d.w);
+            const int nsteps = ((d.z + RP * MR - 1) / (RP * MR)) * nkb;
+            // lane i gathers query slots 4i .. 4i+3 (padding slots repeat slot 0's row)
+            const int4* iq = s_iq + ib * QN;
+            const int r0 = iq[0].x;
+            int y[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int qs = 4 * lane + j;
+                const int qr = qs < QN ? iq[qs].x : -1;
+                y[j] = qr >= 0 ? qr : r0;
+            }
+            for (int t = 0; t < nsteps; ++t, ++g) {
+                if (g % NQL != qj) continue;
+                const int s = g % LS, kb = t % nkb;
+                if (!mbar_wait_warp(bars + C::b_empty_st(s), ((g / LS) & 1) ^ 1, abort_flag, wlim)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) mbar_arrive_expect_tx(bars + C::b_full_q(s), (uint32_t)npad * 128u);
+                __syncwarp();
+                if (4 * lane < npad)
+                    tma_gather4_hint(smem_u32(sm + Smem::q + s * TILE_Q + lane * 512), &q_map, kb * 128, y[0], y[1],
+                                     y[2], y[3], bars + C::b_full_q(s), pol_q);
+                __syncwarp();
+            }
+            if (!ok) break;
+            mbar_arrive(bars + C::b_empty_item(ib));
+        }
+        for (uint32_t k = 0; k < LS && k < g; ++k) {     // (the stages this loader issued)
+            const uint32_t gg = g - 1 - k;
+            if (gg % NQL == qj) mbar_wait_drain(bars + C::b_full_q(gg % LS), (gg / LS) & 1);
+        }
+        __syncwarp();
+    } else if (warp >= W_CV && warp < W_CV + 8) {
+        // ------------------------------------------------------------ converters
+        // Set b (warps 8 + 4b .. 11 + 4b) converts row block b of every stage;
+        // thread = one row of the block (TMEM lane).
+        const int b = (warp - W_CV) >> 2, qt = warp & 3;
+        const int r = qt * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(qt * 32) << 16;
+        const int B = a.B;
+        const int roff = (r >> 5) * 256 * B + (r & 31) * 8;   // word 0 of row r in a 128-row block
+        uint32_t g = 0;
+        bool ok = true;
+        for (uint32_t li = 0; ok; ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(bars + C::b_full_item(ib), (li >> 1) & 1, abort_flag, wlim)) break;
+            const int4 d = s_itd[ib];
+            if (d.w < 0) break;
+            const int nrows = d.z;
+            for (int r0 = 0; r0 < nrows && ok; r0 += RP * MR) {
+                const bool has = b < min(RP, (nrows - r0 + MR - 1) / MR);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % LS, rs = g % RS;
+                    // the stage's TMEM columns are free (its previous MMAs completed)
+                    // and its raw codes have landed
+                    if (!mbar_wait_warp(bars + C::b_empty_st(s), ((g / LS) & 1) ^ 1, abort_flag, wlim) ||
+                        !mbar_wait_warp(bars + C::b_full_raw(rs), (g / RS) & 1, abort_flag, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint32_t w[32];
+                    if (has) {
+                        const unsigned char* src = sm + Smem::raw + rs * slot_bytes + b * blk * (F8 ? 2 : 1) + roff;
+                        if (F8) {
+                            // two packed blocks -> 128 e4m3 codes, four per column
+#pragma unroll
+                            for (int hb = 0; hb < 2; ++hb) {
+                                uint32_t h[32];
+                                unpack_codes_b(B, src + hb * blk, h);
+#pragma unroll
+                                for (int c = 0; c < 16; ++c)
+                                    w[16 * hb + c] = __byte_perm(half2_to_e4m3_pair(h[2 * c]),
+                                                                 half2_to_e4m3_pair(h[2 * c + 1]), 0x6420u);
+                            }
+                        } else {
+                            unpack_codes_b(B, src, w);
+                        }
+                    }
+                    mbar_arrive(bars + C::b_empty_raw(rs));        // the raw slot may be refilled
+                    if (has) {
+                        ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + b) * (KB / 2), w);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    }
+                    tc_fence_before();
+                    mbar_arrive(bars + C::b_full_a(s, b));
+                }
+            }
+            if (!ok) break;
+            mbar_arrive(bars + C::b_empty_item(ib));
+        }
+    } else if (warp == W_MMA || warp == W_MMA + 1) {
+        // ------------------------------------------------------------ MMA issuers
+        // Issuer b runs the accumulation chain of row block b of each stage group
+        // (tcgen05.mma issue stalls the issuing thread, so two issuers keep two
+        // chains in flight); both commit every stage to its release barrier.
+        const int b = warp - W_MMA;
+        uint32_t g = 0, u = 0;
+        bool ok = true;
+        for (uint32_t li = 0; ok; ++li) {
+            const int ib = li & 1;
+            if (!mbar_wait_warp(bars + C::b_full_item(ib), (li >> 1) & 1, abort_flag, wlim)) break;
+            const int4 d = s_itd[ib];
+            if (d.w < 0) break;
+            const uint32_t idesc = idesc_f16(MR, npad_of(d.w));
+            for (int r0 = 0; r0 < d.z && ok; r0 += RP * MR) {
+                const bool has = b < min(RP, (d.z - r0 + MR - 1) / MR);
+                const int buf = u % NBUF;
+                if (has) {
+                    if (!mbar_wait_warp(bars + C::b_tempty(buf, b), ((u / NBUF) & 1) ^ 1, abort_flag, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const uint32_t dt = tmem + (uint32_t)((buf * RP + b) * QN);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % LS;
+                    if (b == 0 && (long long)g == a.stall_stage &&
+                        !mbar_wait_warp(bars + C::b_never(), 0, abort_flag, wlim)) {
+                        ok = false;                                // (always: nothing arrives on it)
+                        break;
+                    }
+                    if (!mbar_wait_warp(bars + C::b_full_a(s, b), (g / LS) & 1, abort_flag, wlim) ||
+                        !mbar_wait_warp(bars + C::b_full_q(s), (g / LS) & 1, abort_flag, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (lane == 0) {
+                        if (has) {
+                            const uint32_t ta = tmem + ACOL + (s * RP + b) * (KB / 2);
+                            const uint32_t tq = smem_u32(sm + Smem::q + s * TILE_Q);
+#pragma unroll
+                            for (int k = 0; k < KB / 16; ++k) {         // 32 bytes of K per instruction
+                                if (F8) mma_f8_ta(dt, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                                else mma_f16_ta(dt, ta + k * 8, sdesc(tq + k * 32), idesc, (kb | k) != 0);
+                            }
+                        }
+                        mma_commit(bars + C::b_empty_st(s));          // query tile and TMEM stage free
+                        if (has && kb == nkb - 1) mma_commit(bars + C::b_tfull(buf, b));
+                    }
+                    __syncwarp();
+                }
+                if (has) ++u;
+            }
+            if (!ok) break;
+            mbar_arrive(bars + C::b_empty_item(ib));
         }
         // all issued MMAs complete before TMEM is released
-        if (lane == 0) mma_commit(done_bar);
+        if (lane == 0) mma_commit(bars + C::b_done());
         __syncwarp();
-        mbar_wait_drain(done_bar, 0);
+        mbar_wait_drain(bars + C::b_done(), 0);
         __syncwarp();
-    } else if (warp < 4) {
+    } else if (warp < W_CV) {
         // ------------------------------------------------------------ estimate tiles
-        // Warp w moves TMEM lanes 32w..32w+31 (its 32 rows, all queries) of a
-        // finished accumulator into a query-major estimate tile.
+        // Warp w moves TMEM lanes 32w..32w+31 (its 32 rows, all queries) of each
+        // finished row-block accumulator into a query-major estimate tile and
+        // frees the accumulator.
         float* s_est = reinterpret_cast<float*>(sm + Smem::est);
         uint32_t* s_ids = reinterpret_cast<uint32_t*>(sm + Smem::ids);
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         const int row = warp * 32 + lane;
-        uint32_t blk = 0, pc = 0, rbg = 0, li = 0;     // row blocks, stage groups, meta slots, items
+        uint32_t blk = 0, rbg = 0, u[RP] = {};
         bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+        for (uint32_t li = 0; ok; ++li) {
             const int ib = li & 1;
-            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
-            const int4 d = s_idesc[ib];
+            if (!mbar_wait_warp(bars + C::b_full_item(ib), (li >> 1) & 1, abort_flag, wlim)) break;
+            const int4 d = s_itd[ib];
+            if (d.w < 0) break;
             const int nrows = d.z, npad = npad_of(d.w);
-            for (int r = 0; r < nrows; r += MR, ++blk, ++rbg) {
-                const int bb = (r / MR) % RP;                   // block within its stage group
-                const int nb = min(RP, (nrows - (r - bb * MR) + MR - 1) / MR);
-                const int buf = pc & 1, m = rbg % MS, t = blk % EB;
-                if (!mbar_wait_warp(full_meta0 + 8 * m, (rbg / MS) & 1, abort_flag) ||
-                    (bb == 0 && !mbar_wait_warp(tfull0 + 8 * buf, (pc >> 1) & 1, abort_flag)) ||
-                    !mbar_wait_warp(tile_empty0 + 8 * t, ((blk / EB) & 1) ^ 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                float* est_t = s_est + t * (QN * MR);
-                float4 mt = s_meta[m * MR + row];
-                s_ids[t * MR + row] = __float_as_uint(mt.z);
-                if (a.ip) {                                     // -<c, q_r> + (f_res / 4) acc: no g, half the factor
-                    mt.x = 0.f;
-                    mt.y *= 0.5f;
-                }
-#pragma unroll 1
-                for (int cc = 0; cc < npad; cc += 32) {
-                    uint32_t v[32];
-                    ERQ_TMEM_LD32(tmem + lane_base + buf * (RP * QN) + bb * QN + cc, v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
-                        const float* sc = reinterpret_cast<const float*>(sm + Smem::qsc) + ib * QN + cc;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]) * sc[i], mt.x);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+            for (int r0 = 0; r0 < nrows && ok; r0 += RP * MR) {
+                const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
+                for (int rb = 0; rb < nb; ++rb, ++blk) {
+                    const uint32_t mrb = rbg + rb;
+                    const int m = mrb % MS, t = blk % EB, buf = u[rb] % NBUF;
+                    if (!mbar_wait_warp(bars + C::b_full_meta(m), (mrb / MS) & 1, abort_flag, wlim) ||
+                        !mbar_wait_warp(bars + C::b_tfull(buf, rb), (u[rb] / NBUF) & 1, abort_flag, wlim) ||
+                        !mbar_wait_warp(bars + C::b_tile_empty(t), ((blk / EB) & 1) ^ 1, abort_flag, wlim)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    float* est_t = s_est + t * (QN * MR);
+                    float4 mt = s_meta[m * MR + row];
+                    s_ids[t * MR + row] = __float_as_uint(mt.z);
+                    if (a.ip) {                                     // -<c, q_r> + (f_res / 4) acc: no g, half the factor
+                        mt.x = 0.f;
+                        mt.y *= 0.5f;
+                    }
+                    const uint32_t tacc = tmem + lane_base + (uint32_t)((buf * RP + rb) * QN);
+#pragma unroll 1
+                    for (int cc = 0; cc < npad; cc += 32) {
+                        uint32_t v[32];
+                        ERQ_TMEM_LD32(tacc + cc, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
+                            const float* sc = s_qsc + ib * QN + cc;
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]) * sc[i], mt.x);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(bars + C::b_tempty(buf, rb));       // the accumulator is free
+                    ++u[rb];
+                    mbar_arrive(bars + C::b_empty_meta(m));
+                    mbar_arrive(bars + C::b_tile_full(t));
                 }
-                tc_fence_before();
-                if (bb == nb - 1) {                             // the group's accumulators are free
-                    mbar_arrive(tempty0 + 8 * buf);
-                    ++pc;
-                }
-                mbar_arrive(empty_meta0 + 8 * m);
-                mbar_arrive(tile_full0 + 8 * t);
+                rbg += nb;
             }
             if (!ok) break;
-            mbar_arrive(empty_item0 + 8 * ib);
+            mbar_arrive(bars + C::b_empty_item(ib));
         }
     } else {
         // ------------------------------------------------------------ filters
-        // NFX warps; warp f owns the query slots q = f + NFX j of every item.
+        // NFX warps; warp f owns the query slots q = f + NFX j of every item and
+        // filters their rows of each estimate tile (float pre-filter against the
+        // threshold, exact keys, ballots) into per-query candidate lists; a full
+        // list is compacted by a warp bitonic sort to its k' smallest.  A query
+        // starts from the smallest k'-th key published so far by its items, which
+        // is never below its final k'-th key, so each list stays a superset of
+        // what the item contributes to the query's top-k'.
         const float* s_est = reinterpret_cast<const float*>(sm + Smem::est);
         uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
         const uint32_t* s_ids = reinterpret_cast<const uint32_t*>(sm + Smem::ids);
         int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
         uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
-        const int fw = warp - (10 + NG);
+        const int fw = warp - W_FX;
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
-        uint32_t blk = 0, li = 0;
+        uint32_t blk = 0;
         bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+        for (uint32_t li = 0; ok; ++li) {
             const int ib = li & 1;
-            if (!mbar_wait_warp(full_item0 + 8 * ib, (li >> 1) & 1, abort_flag)) { ok = false; break; }
-            const int4 d = s_idesc[ib];
+            if (!mbar_wait_warp(bars + C::b_full_item(ib), (li >> 1) & 1, abort_flag, wlim)) break;
+            const int4 d = s_itd[ib];
+            if (d.w < 0) break;
             const int nrows = d.z, nqi = d.w;
             const int4* iq = s_iq + ib * QN;
             if (lane < (QN + NFX - 1) / NFX) {
                 const int q = fw + NFX * lane;
                 if (q < nqi) {
                     s_cnt[q] = 0;
-                    s_tau[q] = reinterpret_cast<const unsigned long long*>(sm + Smem::tq)[ib * QN + q];
+                    s_tau[q] = s_tq[ib * QN + q];
                 }
             }
             __syncwarp();
             for (int r = 0; r < nrows; r += MR, ++blk) {
                 const int nr = min(MR, nrows - r);
                 const int t = blk % EB;
-                if (!mbar_wait_warp(tile_full0 + 8 * t, (blk / EB) & 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait_warp(bars + C::b_tile_full(t), (blk / EB) & 1, abort_flag, wlim)) {
+                    ok = false;
+                    break;
+                }
                 const float* est_t = s_est + t * (QN * MR);
                 const uint32_t* ids_t = s_ids + t * MR;
                 // the 128 rows of each owned query; the four 32-row groups'
@@ -743,7 +794,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                     }
                     __syncwarp();
                 }
-                mbar_arrive(tile_empty0 + 8 * t);
+                mbar_arrive(bars + C::b_tile_empty(t));
             }
             if (!ok) break;
             for (int q = fw; q < nqi; q += NFX) {               // write this warp's lists
@@ -760,13 +811,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_tc_kernel(const __grid_consta
                 if (lane == 0) a.inter_cnt[L] = cnt;
             }
             __syncwarp();
-            mbar_arrive(empty_item0 + 8 * ib);
+            mbar_arrive(bars + C::b_empty_item(ib));
         }
     }
     tc_fence_before();
     __syncthreads();
     if (*abort_flag && tid == 0) atomicOr(a.status, kStatusTimeout);
-    if (warp == 8) {
+    if (warp == W_MMA) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
     }
@@ -778,16 +829,18 @@ bool tc_available(int precision, int D, int kp) {
 
 // Work-item query counts the tensor-core scan is built for, given k'.
 bool scan_tc_shape_ok(int qn, int kp) {
-    return (qn == CfgSmall::QN && kp <= 32) || (qn == CfgWide::QN && kp <= 32) || (qn == CfgLarge::QN && kp <= KCAP);
+    return (kp <= 32 && (qn == 32 || qn == CfgA::QN)) || (kp <= KCAP && qn == CfgB::QN);
 }
 
 // Capacity (stride) of the per-(query, item) candidate lists written by the scan.
 int scan_list_stride(int precision, int kp, int qn) {
+    (void)qn;
     if (precision == ERQ_PREC_FP32) return kp;
-    return qn == CfgLarge::QN ? CfgLarge::KC : CfgSmall::KC;   // CfgWide shares CfgSmall's list capacity
+    return kp <= 32 ? CfgA::KC : CfgB::KC;
 }
 
 cudaError_t launch_to_half(const float* x, __half* y, int64_t n, cudaStream_t s);
+
 
 
 // Per work item: {first padded row (lo, hi), rows, queries} and, per query slot,
@@ -796,7 +849,7 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
                                    const int64_t* __restrict__ list_off, const int64_t* __restrict__ poff,
                                    const int64_t* __restrict__ qoff, const int64_t* __restrict__ qlist,
                                    const float* __restrict__ dqc, const int64_t* __restrict__ qbase,
-                                   const int32_t* __restrict__ slot_off, int maxp, int RR, int QN,
+                                   const int32_t* __restrict__ slot_off, int maxp, int RR, int QN, int nlist,
                                    int4* __restrict__ itemd, int4* __restrict__ itemq,
                                    unsigned long long* __restrict__ stats, DevChecks ck) {
     const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -804,9 +857,9 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
     if (it >= *n_items) return;
     if (!ERQ_DCHECK(it < ck.items, ck.status, 8)) return;
     const int4 w = items[it];
-    const int c = w.x;
-    const int64_t qb = qoff[c] + (int64_t)w.y * QN;
-    const int nqi = (int)imin64(QN, qoff[c + 1] - qb);
+    const int v = w.x, c = v % nlist;                   // phase cluster -> cluster
+    const int64_t qb = qoff[v] + (int64_t)w.y * QN;
+    const int nqi = (int)imin64(QN, qoff[v + 1] - qb);
     const int64_t size = list_off[c + 1] - list_off[c];
     const int64_t r0 = (int64_t)w.z * RR;
     const int64_t rb0 = poff[c] + r0;
@@ -831,12 +884,14 @@ __global__ void item_tables_kernel(const int4* __restrict__ items, const int64_t
 
 cudaError_t launch_item_tables(const int4* items, const int64_t* n_items, int64_t items_bound, const int64_t* list_off,
                                const int64_t* poff, const int64_t* qoff, const int64_t* qlist, const float* dqc,
-                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int4* itemd,
-                               int4* itemq, unsigned long long* stats, const DevChecks& ck, cudaStream_t s) {
+                               const int64_t* qbase, const int32_t* slot_off, int maxp, int RR, int qn, int nlist,
+                               int4* itemd, int4* itemq, unsigned long long* stats, const DevChecks& ck,
+                               cudaStream_t s) {
     if (items_bound <= 0) return cudaSuccess;
     count_launch();
     item_tables_kernel<<<(unsigned)ceil_div(items_bound, 8), 256, 0, s>>>(
-        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, qn, itemd, itemq, stats, ck);
+        items, n_items, list_off, poff, qoff, qlist, dqc, qbase, slot_off, maxp, RR, qn, nlist, itemd, itemq, stats,
+        ck);
     return cudaGetLastError();
 }
 
@@ -932,18 +987,45 @@ static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D view of the query operand (FP16 or e4m3 rows of row_bytes bytes) for
+// tile::gather4: a box of one row of 128 bytes, 128-byte swizzle, so that four
+// gathered rows land as consecutive 128-byte rows of the MMA's B tile.
+static bool make_query_map(CUtensorMap* map, const void* base, int64_t nq, int64_t row_bytes) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)row_bytes, (cuuint64_t)nq};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {128, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <class C, bool F8>
-static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, cudaStream_t s) {
+static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, const void* qbase, int64_t qrow_bytes,
+                                 cudaStream_t s) {
     const int smem = C::Smem::total;
     cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
-    CUtensorMap map;
+    CUtensorMap cmap, qmap;
     if (!L.codes_p || ((uintptr_t)L.codes_p & 15) != 0 || (L.D % KB) != 0 || L.B < 1 || L.B > 8 ||
-        !make_codes_map(&map, L.codes_p, L.Np, L.D, L.B))
+        !make_codes_map(&cmap, L.codes_p, L.Np, L.D, L.B))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
+    if (!qbase || ((uintptr_t)qbase & 15) != 0 || qrow_bytes % 128 != 0 || L.nq < 1 ||
+        !make_query_map(&qmap, qbase, L.nq, qrow_bytes))
+        return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the query array");
     count_launch();
-    scan_tc_kernel<C, F8><<<L.grid, THREADS, smem, s>>>(map, a);
+    scan_tc_kernel<C, F8><<<L.grid, THREADS, smem, s>>>(cmap, qmap, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc launch");
     return ERQ_OK;
@@ -955,21 +1037,22 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     const bool f8 = precision == ERQ_PREC_FP8;
     if (f8 && L.B > 4) return fail(ERQ_EUNSUPPORTED, "tensor-core scan: e4m3 holds the centred codes only for B <= 4");
     if (!(f8 ? (L.Q8 && L.qscale) : L.Qh != nullptr)) return fail(ERQ_EINVAL, "tensor-core scan: queries missing");
-    if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq) return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
+    if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq || !L.work_ctr)
+        return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
+    if (!scan_tc_shape_ok(L.qn, L.kp)) return fail(ERQ_EINVAL, "tensor-core scan: no kernel for this item shape");
     tc::Args a;
     a.ck = L.ck;
-    a.Qb = f8 ? (const unsigned char*)L.Q8 : (const unsigned char*)L.Qh;
-    a.qrow_bytes = f8 ? L.Dq : 2 * (int64_t)L.D;
-    a.qscale = L.qscale;
-    a.itemd = L.itemd; a.itemq = L.itemq; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
-    a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.status = L.status; a.D = L.D; a.B = L.B; a.kp = L.kp;
-    a.tq = L.tq;
-    a.ip = L.ip;
-    if (!scan_tc_shape_ok(L.qn, L.kp)) return fail(ERQ_EINVAL, "tensor-core scan: no kernel for this item shape");
-    if (L.qn == CfgWide::QN) return f8 ? scan_tc_launch<CfgWide, true>(L, a, s) : scan_tc_launch<CfgWide, false>(L, a, s);
-    if (L.qn == CfgSmall::QN)
-        return f8 ? scan_tc_launch<CfgSmall, true>(L, a, s) : scan_tc_launch<CfgSmall, false>(L, a, s);
-    return f8 ? scan_tc_launch<CfgLarge, true>(L, a, s) : scan_tc_launch<CfgLarge, false>(L, a, s);
+    a.itemd = L.itemd; a.itemq = L.itemq; a.qn = L.qn; a.rowmeta = L.rowmeta; a.n_items = L.n_items;
+    a.work_ctr = L.work_ctr;
+    a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.tq = L.tq; a.qscale = L.qscale; a.status = L.status;
+    a.D = L.D; a.B = L.B; a.kp = L.kp; a.ip = L.ip;
+    a.nkb = f8 ? (int)(L.Dq / 128) : L.D / KB;
+    a.wait_ns = L.wait_ns ? L.wait_ns : kWaitNs;
+    a.stall_stage = L.stall_stage;
+    const void* qb = f8 ? L.Q8 : L.Qh;
+    const int64_t qrow = f8 ? L.Dq : 2 * (int64_t)L.D;
+    if (L.kp <= 32) return f8 ? scan_tc_launch<CfgA, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgA, false>(L, a, qb, qrow, s);
+    return f8 ? scan_tc_launch<CfgB, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgB, false>(L, a, qb, qrow, s);
 }
 
 // Rotated queries -> e4m3 for the kind::f8f6f4 scan.  Per query row a power of

@@ -99,9 +99,10 @@ __global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t pro
                                   const int32_t* __restrict__ npr_in, int npr_uniform, int64_t nq, int maxp,
                                   int nlist, const int64_t* __restrict__ list_off, int RR,
                                   int32_t* __restrict__ npr, int32_t* __restrict__ probe_c,
-                                  int32_t* __restrict__ cnt_c, int32_t* __restrict__ slot_nr,
-                                  const float* __restrict__ sqd, float* __restrict__ dqc,
-                                  uint32_t* __restrict__ status, unsigned long long* __restrict__ stats) {
+                                  int32_t* __restrict__ cnt_c, int32_t* __restrict__ touch_c,
+                                  int32_t* __restrict__ slot_nr, const float* __restrict__ sqd,
+                                  float* __restrict__ dqc, uint32_t* __restrict__ status,
+                                  unsigned long long* __restrict__ stats, int two_phase) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long add_pairs = 0, add_rows = 0;
     if (t < nq * maxp) {
@@ -123,7 +124,10 @@ __global__ void plan_count_kernel(const int32_t* __restrict__ probe, int64_t pro
             } else {
                 const int64_t size = list_off[c + 1] - list_off[c];
                 nr = (int)((size + RR - 1) / RR);
-                if (atomicAdd(&cnt_c[c], 1) == 0) add_rows = (unsigned long long)size;
+                // queries per (phase, cluster): with two phases, phase 0 holds each
+                // query's first (nearest) probed cluster, phase 1 the others (ids nlist + c)
+                atomicAdd(&cnt_c[(two_phase && slot > 0) ? nlist + c : c], 1);
+                if (atomicAdd(&touch_c[c], 1) == 0) add_rows = (unsigned long long)size;
                 add_pairs = (unsigned long long)size;
                 if (sqd) dqc[t] = sqd[q * nlist + c];      // the probe's value of this pair
             }
@@ -207,47 +211,58 @@ __global__ void __launch_bounds__(1024) excl_scan_i64_kernel(const int64_t* __re
     if (t == 0) out[n] = carry;
 }
 
-// per cluster: pair count (int64) and item count
-// per cluster: pair count (int64) and, at the cluster's rank in `corder`
-// (decreasing size), its number of work items
+// Work items may come in two phases (PlanArgs::two_phase): phase 0 pairs every
+// query with its first (nearest) probed cluster, phase 1 with the others, so
+// that a query's candidate threshold is set by its nearest cluster before its
+// other clusters are scanned (at the price of reading a cluster's codes once
+// per phase).  Phase cluster ids: v = c (phase 0), nlist + c (phase 1); with
+// one phase every pair is in phase 0.
+// Rank rk in [0, 2 nlist): phase rk / nlist, clusters by decreasing size (`corder`).
+__device__ __forceinline__ int phase_cluster(const int32_t* corder, int nlist, int rk) {
+    const int r = rk % nlist;
+    return (corder ? corder[r] : r) + (rk >= nlist ? nlist : 0);
+}
+
+// per phase cluster: pair count (int64) and, at its rank, its number of work items
 __global__ void plan_cluster_kernel(const int32_t* __restrict__ cnt_c, const int64_t* __restrict__ list_off,
                                     const int32_t* __restrict__ corder, int nlist, int QT, int RR,
                                     int64_t* __restrict__ cnt64, int64_t* __restrict__ items_r) {
     const int rk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (rk >= nlist) return;
-    const int c = corder ? corder[rk] : rk;
+    if (rk >= 2 * nlist) return;
+    const int v = phase_cluster(corder, nlist, rk), c = v % nlist;
     const int64_t size = list_off[c + 1] - list_off[c];
-    const int64_t n = cnt_c[c];
-    cnt64[c] = n;
+    const int64_t n = cnt_c[v];
+    cnt64[v] = n;
     items_r[rk] = (n > 0 && size > 0) ? ((n + QT - 1) / QT) * ((size + RR - 1) / RR) : 0;
 }
 
-__global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t nq, int maxp,
+__global__ void plan_scatter_kernel(const int32_t* __restrict__ probe_c, int64_t nq, int maxp, int nlist, int two_phase,
                                     const int64_t* __restrict__ qoff, int32_t* __restrict__ pos_c,
                                     int64_t* __restrict__ qlist, DevChecks ck) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nq * maxp) return;
     const int c = probe_c[t];
     if (c < 0) return;
-    const int p = atomicAdd(&pos_c[c], 1);
-    if (ERQ_DCHECK(qoff[c] + p >= 0 && qoff[c] + p < ck.qlist, ck.status, 9)) qlist[qoff[c] + p] = t;  // t = q * maxp + slot
+    const int v = c + ((two_phase && t % maxp != 0) ? nlist : 0);
+    const int p = atomicAdd(&pos_c[v], 1);
+    if (ERQ_DCHECK(qoff[v] + p >= 0 && qoff[v] + p < ck.qlist, ck.status, 9)) qlist[qoff[v] + p] = t;  // t = q * maxp + slot
 }
 
 __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64_t* __restrict__ list_off,
                                   const int64_t* __restrict__ item_off, const int32_t* __restrict__ corder,
                                   int nlist, int QT, int RR, int4* __restrict__ items, DevChecks ck) {
     const int rk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (rk >= nlist) return;
-    const int c = corder ? corder[rk] : rk;
+    if (rk >= 2 * nlist) return;
+    const int v = phase_cluster(corder, nlist, rk), c = v % nlist;
     const int64_t b = item_off[rk], e = item_off[rk + 1];
     if (b == e) return;
     const int64_t size = list_off[c + 1] - list_off[c];
     const int nranges = (int)((size + RR - 1) / RR);
     int64_t w = b;
-    const int nchunks = (int)((cnt64[c] + QT - 1) / QT);
+    const int nchunks = (int)((cnt64[v] + QT - 1) / QT);
     if (!ERQ_DCHECK(b >= 0 && e <= ck.items, ck.status, 10)) return;
     for (int r = 0; r < nranges; ++r)
-        for (int ch = 0; ch < nchunks; ++ch) items[w++] = make_int4(c, ch, r, 0);
+        for (int ch = 0; ch < nchunks; ++ch) items[w++] = make_int4(v, ch, r, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -275,7 +290,7 @@ struct ScanArgs {
     const int64_t* qbase;       // [nq+1]
     uint64_t* inter;            // [L][kp]
     int32_t* inter_cnt;         // [L]
-    int maxp, D, B, kp, RR;
+    int maxp, D, B, kp, RR, nlist;
     int ip;                     // inner-product metric: est = -<c, q_r> + (f_res / 4) <2 ybar, q'>
     DevChecks ck;
 };
@@ -304,9 +319,9 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
 
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 item = a.items[it];
-        const int c = item.x;
-        const int64_t qb = a.qoff[c] + (int64_t)item.y * SC_QT;
-        const int nqi = (int)imin64(SC_QT, a.qoff[c + 1] - qb);
+        const int v = item.x, c = v % a.nlist;                  // phase cluster -> cluster
+        const int64_t qb = a.qoff[v] + (int64_t)item.y * SC_QT;
+        const int nqi = (int)imin64(SC_QT, a.qoff[v + 1] - qb);
         const int64_t rb0 = a.list_off[c] + (int64_t)item.z * a.RR;
         const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
         if (tid < SC_QT) {
@@ -710,32 +725,33 @@ cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, con
 cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     const int64_t pairs = p.nq * p.maxp;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p.cnt_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p.pos_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.cnt_c, 0, sizeof(int32_t) * 2 * p.nlist, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.pos_c, 0, sizeof(int32_t) * 2 * p.nlist, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.touch_c, 0, sizeof(int32_t) * p.nlist, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     count_launch();
     plan_count_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(
         p.probe, p.probe_stride, p.npr_in, p.npr_uniform, p.nq, p.maxp, p.nlist, p.list_off, p.RR, p.npr, p.probe_c,
-        p.cnt_c, p.slot_nr, p.sqd, p.dqc, p.status, p.stats);
+        p.cnt_c, p.touch_c, p.slot_nr, p.sqd, p.dqc, p.status, p.stats, p.two_phase);
     count_launch();
     plan_query_kernel<<<(unsigned)ceil_div(p.nq, 256), 256, 0, s>>>(p.slot_nr, p.nq, p.maxp, p.slot_off, p.qtot);
     count_launch();
     excl_scan_i64_kernel<<<dim3(1, 1), 1024, 0, s>>>(p.qtot, p.qbase, nullptr, nullptr, p.nq);
     count_launch();
-    plan_cluster_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.corder, p.nlist,
-                                                                          p.QT, p.RR, p.cnt64, p.items_c);
+    plan_cluster_kernel<<<(unsigned)ceil_div(2 * p.nlist, 256), 256, 0, s>>>(p.cnt_c, p.list_off, p.corder, p.nlist,
+                                                                              p.QT, p.RR, p.cnt64, p.items_c);
     count_launch();
-    excl_scan_i64_kernel<<<dim3(1, 2), 1024, 0, s>>>(p.cnt64, p.qoff, p.items_c, p.item_off, p.nlist);
+    excl_scan_i64_kernel<<<dim3(1, 2), 1024, 0, s>>>(p.cnt64, p.qoff, p.items_c, p.item_off, 2 * p.nlist);
     count_launch();
-    plan_scatter_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(p.probe_c, p.nq, p.maxp, p.qoff, p.pos_c,
-                                                                       p.qlist, p.ck);
+    plan_scatter_kernel<<<(unsigned)ceil_div(pairs, 256), 256, 0, s>>>(p.probe_c, p.nq, p.maxp, p.nlist, p.two_phase,
+                                                                       p.qoff, p.pos_c, p.qlist, p.ck);
     return cudaGetLastError();
 }
 
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s) {
     count_launch();
-    plan_items_kernel<<<(unsigned)ceil_div(p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off, p.corder,
-                                                                       p.nlist, p.QT, p.RR, items, p.ck);
+    plan_items_kernel<<<(unsigned)ceil_div(2 * p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off,
+                                                                           p.corder, p.nlist, p.QT, p.RR, items, p.ck);
     return cudaGetLastError();
 }
 
@@ -745,13 +761,68 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     a.Qrot = L.Qrot; a.codes = L.codes; a.g_const = L.g_const; a.f_res = L.f_res; a.list_off = L.list_off;
     a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
     a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
-    a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip;
+    a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip; a.nlist = L.nlist;
     const size_t smem = scan_fp32_smem(L.kp);
     cudaError_t e = cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (L.grid <= 0) return cudaSuccess;
     count_launch();
     scan_fp32_kernel<<<L.grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (id, value) pairs <-> candidate keys, for merging and re-ranking candidate
+// lists given by the caller (e.g. the lists of several index shards).
+// ---------------------------------------------------------------------------
+// Empty key for ids < 0 or >= id_limit (id_limit > 0); the inner-product
+// metric ranks by -value.  vals may be null (value 0: re-rank by id only).
+__global__ void make_keys_kernel(const int64_t* __restrict__ ids, const float* __restrict__ vals, int64_t n,
+                                 int64_t id_limit, int neg, uint64_t* __restrict__ keys) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t id = ids[t];
+    const bool empty = id < 0 || id > 0xfffffffell || (id_limit > 0 && id >= id_limit);
+    const float v = vals ? (neg ? -vals[t] : vals[t]) : 0.f;
+    keys[t] = empty ? kEmptyKey : make_key(v, (uint32_t)id);
+}
+
+// Keys -> (id, value): empty keys give -1 and +inf (-inf for the inner-product metric).
+__global__ void keys_to_pairs_kernel(const uint64_t* __restrict__ keys, int64_t n, int neg, int64_t* __restrict__ ids,
+                                     float* __restrict__ vals) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint64_t k = keys[t];
+    const float sgn = neg ? -1.f : 1.f;
+    ids[t] = k == kEmptyKey ? -1 : (int64_t)key_id(k);
+    vals[t] = sgn * (k == kEmptyKey ? INFINITY : key_value(k));
+}
+
+// One list per query: counts[q] = m, offsets[q] = q.
+__global__ void one_list_per_query_kernel(int64_t nq, int m, int32_t* __restrict__ counts, int64_t* __restrict__ off) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= nq) off[t] = t;
+    if (t < nq) counts[t] = m;
+}
+
+cudaError_t launch_make_keys(const int64_t* ids, const float* vals, int64_t n, int64_t id_limit, int neg,
+                             uint64_t* keys, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    make_keys_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(ids, vals, n, id_limit, neg, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_to_pairs(const uint64_t* keys, int64_t n, int neg, int64_t* ids, float* vals, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    keys_to_pairs_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(keys, n, neg, ids, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_one_list_per_query(int64_t nq, int m, int32_t* counts, int64_t* off, cudaStream_t s) {
+    count_launch();
+    one_list_per_query_kernel<<<(unsigned)ceil_div(nq + 1, 256), 256, 0, s>>>(nq, m, counts, off);
     return cudaGetLastError();
 }
 

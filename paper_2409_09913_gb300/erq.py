@@ -27,7 +27,7 @@ EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
            "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total",
            "erq_autotune", "erq_set_scan_config", "erq_scan_config", "erq_estimate_metric",
-           "erq_search_backward_metric"]
+           "erq_search_backward_metric", "erq_merge_topk", "erq_rerank_ids", "erq_set_wait_limit"]
 
 
 class ErqError(RuntimeError):
@@ -39,7 +39,7 @@ class ErqError(RuntimeError):
 class BuildParams(ct.Structure):
     _fields_ = [("B", ct.c_int32), ("nlist", ct.c_int32), ("P", ct.c_void_p), ("assign", ct.c_void_p),
                 ("kmeans_iters", ct.c_int32), ("kmeans_sample", ct.c_int32), ("seed", ct.c_uint64),
-                ("keep_raw", ct.c_int32), ("reserved", ct.c_int32)]
+                ("keep_raw", ct.c_int32), ("reserved", ct.c_int32), ("centroids", ct.c_void_p)]
 
 
 class SearchParams(ct.Structure):
@@ -96,6 +96,9 @@ def lib(path: str | None = None):
     L.erq_kernel_launches.restype = ct.c_uint64
     L.erq_search_stats.argtypes = [vp, ct.POINTER(ct.c_int64), i32]
     L.erq_search_backward_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+    L.erq_merge_topk.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
+    L.erq_rerank_ids.argtypes = [vp, vp, i64, i32, vp, i32, i32, vp, vp, vp]
+    L.erq_set_wait_limit.argtypes = [vp, ct.c_uint64, i64]
     for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
                  "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
                  "erq_index_save", "erq_index_load", "erq_search_timing",
@@ -145,6 +148,22 @@ def _check_out(out, like, name="out"):
     if not out.is_cuda or out.device != like.device:
         raise ValueError(f"{name} must be on {like.device}, got {out.device}")
     return out
+
+
+def merge_topk(cand_ids, values, k, metric="l2"):
+    """erq_merge_topk: per row, the k best (value, id) pairs of the candidate
+    lists (device [nq, m] int64 ids, -1 = empty, and float32 values), ascending
+    for "l2", descending for "ip"; returns (ids [nq, k], values [nq, k])."""
+    cand_ids = _dev(cand_ids, torch.int64, "cand_ids", 2)
+    values = _dev(values, torch.float32, "values", 2)
+    if tuple(values.shape) != tuple(cand_ids.shape):
+        raise ValueError("cand_ids and values must have the same shape")
+    nq, m = cand_ids.shape
+    ids = torch.empty((nq, k), dtype=torch.int64, device=cand_ids.device)
+    vals = torch.empty((nq, k), dtype=torch.float32, device=cand_ids.device)
+    _check(lib().erq_merge_topk(_ptr(cand_ids), _ptr(values), nq, m, int(k), METRIC[metric], _ptr(ids), _ptr(vals),
+                                _stream()))
+    return ids, vals
 
 
 def kernel_launches() -> int:
@@ -333,6 +352,25 @@ class Index:
                                                  _ptr(out), _stream()))
         return out
 
+    def rerank_ids(self, Q, ids, k, metric="l2"):
+        """erq_rerank_ids: exact re-rank of the given ids (device [nq, nc] int64,
+        ids this index does not hold are skipped); returns (ids, distances or
+        inner products) [nq, k]."""
+        Q = _dev(Q, torch.float32, "Q", 2)
+        ids = _dev(ids, torch.int64, "ids", 2)
+        nq, nc = ids.shape
+        out_i = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        out_d = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        _check(lib().erq_rerank_ids(self._h, _ptr(Q), nq, nc, _ptr(ids), int(k), METRIC[metric], _ptr(out_i),
+                                    _ptr(out_d), _stream()))
+        return out_i, out_d
+
+    def set_wait_limit(self, ns, stall_stage=-1):
+        """Limit of the scan's bounded device-side waits in ns (0 = default 2 s);
+        stall_stage >= 0 makes later scans wait at that stage on a barrier that
+        nothing arrives on (a test of the ERQ_ETIMEOUT path)."""
+        _check(lib().erq_set_wait_limit(self._h, int(ns), int(stall_stage)))
+
     def export(self, field):
         inf = self.info()
         N, D, nl = inf["N"], inf["D"], inf["nlist"]
@@ -361,8 +399,11 @@ class Index:
         return Index(h.value)
 
 
-def build_index(X, P, B, nlist=1, *, assign=None, keep_raw=True, kmeans_iters=10, kmeans_sample=0, seed=0):
-    """Build an IVF + extended-RaBitQ index from device rows X [N, D]."""
+def build_index(X, P, B, nlist=1, *, assign=None, keep_raw=True, kmeans_iters=10, kmeans_sample=0, seed=0,
+                centroids=None):
+    """Build an IVF + extended-RaBitQ index from device rows X [N, D].
+    ``centroids`` (device [nlist, D], with ``assign``): use these instead of the
+    means of the rows (an index over one shard of a larger index's lists)."""
     X = _dev(X, torch.float32, "X", 2)
     P = _dev(P, torch.float32, "P", 2)
     bp = BuildParams()
@@ -370,6 +411,11 @@ def build_index(X, P, B, nlist=1, *, assign=None, keep_raw=True, kmeans_iters=10
     if assign is not None:
         assign = _dev(assign, torch.int32, "assign", 1)
         bp.assign = assign.data_ptr()
+    if centroids is not None:
+        centroids = _dev(centroids, torch.float32, "centroids", 2)
+        if tuple(centroids.shape) != (int(nlist), X.shape[1]):
+            raise ValueError(f"centroids must have shape ({int(nlist)}, {X.shape[1]})")
+        bp.centroids = centroids.data_ptr()
     bp.kmeans_iters, bp.kmeans_sample, bp.seed, bp.keep_raw = int(kmeans_iters), int(kmeans_sample), int(seed), \
         int(bool(keep_raw))
     h = ct.c_void_p()
