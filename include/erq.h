@@ -282,14 +282,14 @@ erq_status erq_search_stats(const erq_index* index, int64_t* out, int32_t n);
  * queries_per_item of the queries that probe it, up to rows_per_item of its
  * rows); on the tensor-core path queries_per_item is the MMA's N extent.
  * erq_autotune: times erq_search over the caller's query batch and params for
- * every supported shape (queries_per_item 32 or 64 for k' <= 32, 32 for larger k',
+ * every supported shape (queries_per_item 32, 64 or 128 for k' <= 32, 32 for larger k',
  * rows_per_item in {2048, 4096, 8192}), reps searches each after one warm-up,
  * and keeps the fastest for later searches on this index whose nq * nprobe is
  * within 4x of the tuned one (one entry for k' <= 32, one for larger k');
  * best_out (optional, host [2]) receives it.  Synchronises the stream.  Errors
  * as erq_search; EUNSUPPORTED for the FP32 path.
  * erq_set_scan_config: force the shape (0 = automatic) for later searches;
- * EINVAL for values other than 0/32/64 and 0 or multiples of 256.
+ * EINVAL for values other than 0/32/64/128 and 0 or multiples of 256.
  * erq_scan_config: out[0..1] = the shape used by the last search. */
 erq_status erq_autotune(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params, int32_t reps,
                         void* stream, int32_t* best_out);

@@ -447,8 +447,9 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
 // Search
 // ---------------------------------------------------------------------------
 // Work-item shape of the scan: queries per item (the tensor-core MMA's N
-// extent) and rows per item.  Heuristic: 64 queries per item for k' <= 32,
-// else 32, and 4,096 rows; the autotuned or forced shape wins.
+// extent) and rows per item.  Heuristic for k' <= 32: 128 queries per item when
+// a probed cluster has more than 96 probing queries on average, else 64; for
+// larger k' 32; 4,096 rows; the autotuned or forced shape wins.
 static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq, int maxp, int* qn, int* rr) {
     if (prec == ERQ_PREC_FP32) {
         *qn = 64;
@@ -457,7 +458,7 @@ static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq,
     }
     const int cls = kp <= 32 ? 0 : 1;
     const int64_t work = nq * (int64_t)maxp;
-    int q = cls == 0 ? 64 : 32, r = 4096;
+    int q = cls == 0 ? ((double)work / ix->nlist > 96.0 ? 128 : 64) : 32, r = 4096;
     const erq_index::ScanTune& t = ix->tune[cls];
     if (t.valid && work <= 4 * t.work && 4 * work >= t.work) {
         q = t.qn;
@@ -1015,8 +1016,8 @@ extern "C" erq_status erq_search_timing_total(erq_index* ix, float* ms, int32_t 
 
 extern "C" erq_status erq_set_scan_config(erq_index* ix, int32_t queries_per_item, int32_t rows_per_item) {
     if (!ix) return fail(ERQ_EINVAL, "erq_set_scan_config: null index");
-    if (queries_per_item != 0 && queries_per_item != 32 && queries_per_item != 64)
-        return fail(ERQ_EINVAL, "erq_set_scan_config: queries_per_item must be 0, 32 or 64");
+    if (queries_per_item != 0 && queries_per_item != 32 && queries_per_item != 64 && queries_per_item != 128)
+        return fail(ERQ_EINVAL, "erq_set_scan_config: queries_per_item must be 0, 32, 64 or 128");
     if (rows_per_item != 0 && (rows_per_item < 256 || rows_per_item % 256 != 0 || rows_per_item > (1 << 20)))
         return fail(ERQ_EINVAL, "erq_set_scan_config: rows_per_item must be 0 or a multiple of 256 in [256, 2^20]");
     ix->force_qn = queries_per_item;
@@ -1040,7 +1041,7 @@ extern "C" erq_status erq_autotune(erq_index* ix, const float* Q, int64_t nq, co
     const int kp = std::max(p->k, p->rerank_k);
     const int cls = kp <= 32 ? 0 : 1;
     const int maxp = p->probe ? p->nprobe : (ix->nlist == 1 ? 1 : p->nprobe);
-    const int qns[2] = {32, 64};
+    const int qns[3] = {32, 64, 128};
     const int rrs[3] = {2048, 4096, 8192};
     int64_t* ids = nullptr;
     float* dists = nullptr;
@@ -1058,7 +1059,7 @@ extern "C" erq_status erq_autotune(erq_index* ix, const float* Q, int64_t nq, co
     pp.flags &= ~ERQ_SEARCH_TIMING;
     pp.cand_ids = nullptr;
     pp.cand_est = nullptr;
-    for (int qi = 0; qi < 2 && st == ERQ_OK; ++qi) {
+    for (int qi = 0; qi < 3 && st == ERQ_OK; ++qi) {
         if (!scan_tc_shape_ok(qns[qi], kp)) continue;
         for (int ri = 0; ri < 3 && st == ERQ_OK; ++ri) {
             ix->force_qn = qns[qi];

@@ -25,14 +25,15 @@
 // One persistent CTA per SM takes work items from a global counter (items are
 // ordered by decreasing cluster size).  A stage group is up to RP = 2 row
 // blocks of 128 rows that share the stage's query tile; a stage is one
-// 64-coordinate K block of the group.  Warp roles (26 warps):
+// 64-coordinate K block of the group.  Warp roles (27 warps):
 //   warps 0-3    estimate tiles: warp w reads TMEM lanes 32w .. 32w + 31 (its
 //                32 rows, all queries) of each finished row-block accumulator,
 //                stores g + (f_res/2) acc into one of EB query-major tiles in
 //                shared memory and frees the accumulator;
-//   warps 4-11   converters: warp w unpacks the codes of rows 32 (w % 4) ..
-//                + 31 of row block (w - 4) / 4 from the raw stage in shared
-//                memory into FP16 (or e4m3) values in the stage's TMEM columns;
+//   warps 4-11   converters, two sets of four that take alternate stages:
+//                warp w unpacks the codes of rows 32 (w % 4) .. + 31 of both
+//                row blocks of its stages from the raw stage in shared memory
+//                into FP16 (or e4m3) values in the stage's TMEM columns;
 //   warp 12      code loader: publishes the items, per row block a bulk copy of
 //                the rows' factors and ids, per stage one TMA load of the packed
 //                codes per row block into a raw ring that is released as soon as
@@ -78,9 +79,7 @@ static_assert(MR == 128, "four 32-row lane quarters per row block");
 constexpr int KB = 64;           // FP16 elements per K block (one 128-byte swizzle row)
 constexpr int RP = 2;            // row blocks per stage group (one accumulator and one issuer each)
 constexpr int MS = 8;            // row-factor buffers
-constexpr int EB = 2;            // estimate tiles (the filters work on one while the other fills)
 constexpr int RSMAX = 8;         // raw-code ring slots at most
-constexpr int RAW_BYTES = 64 * 1024;
 constexpr int W_CV = 4;          // converter warps 4..11 (row block (w - 4) / 4, lane quarter w % 4)
 constexpr int W_LD = 12;         // code loader and item publisher
 constexpr int W_QL = 13;         // query-tile loaders 13 .. 13 + NQL - 1 (stage g: loader g % NQL)
@@ -95,22 +94,27 @@ constexpr int KCAP = 128;        // largest k' of the tensor-core path
 
 // Work-item capacities: QN queries per item at most (the MMA's N extent), KC
 // list entries per query, NBUF accumulator buffers per row block, LS stages of
-// query tiles and TMEM code columns.
-template <int QN_, int KC_, int NBUF_, int LS_>
+// query tiles and TMEM code columns, EB estimate tiles (with two the filters
+// work on one while the other fills), RAWK KB of raw-code ring, and LG: the
+// per-query candidate lists live in the item's output list slots in global
+// memory (LG = 1) instead of shared memory.
+template <int QN_, int KC_, int NBUF_, int LS_, int EB_, int RAWK_, int LG_>
 struct Cfg {
-    static constexpr int QN = QN_, KC = KC_, NBUF = NBUF_, LS = LS_;
+    static constexpr int QN = QN_, KC = KC_, NBUF = NBUF_, LS = LS_, EB = EB_, LG = LG_;
+    static constexpr int RAW_BYTES = RAWK_ * 1024;
     static constexpr int KS = KC <= 64 ? 64 : 256;   // sort width of a list compaction
     static constexpr int TILE_Q = QN * 128;          // one stage's query tile: QN rows of 128 bytes
     static constexpr int ACOL = NBUF * RP * QN;      // first TMEM column of the code stages
     static_assert(ACOL + LS * RP * (KB / 2) <= TMEM_COLS, "tensor memory budget");
+    static_assert(LS % 2 == 0, "the two converter sets take alternate stages and must own whole slots");
     static_assert(QN % 32 == 0 && KC >= 64 && (QN + NFX - 1) / NFX <= 32, "item shape");
     struct Smem {
         // offsets in bytes from a 1024-aligned base
         static constexpr int q = 0;                              // LS x [QN][128 B] query tiles, swizzled
         static constexpr int raw = q + LS * TILE_Q;              // raw-code ring (RS slots of RP x B KB)
         static constexpr int est = raw + RAW_BYTES;              // EB x [QN][MR] f32 g + (f_res/2) acc
-        static constexpr int lists = est + EB * QN * MR * 4;     // [QN][KC] u64 candidate keys
-        static constexpr int meta = lists + QN * KC * 8;         // MS x [MR] float4 {g, f_res/2, id, 0}
+        static constexpr int lists = est + EB * QN * MR * 4;     // [QN][KC] u64 candidate keys (LG = 0)
+        static constexpr int meta = lists + (LG ? 0 : QN * KC * 8);   // MS x [MR] float4 {g, f_res/2, id, 0}
         static constexpr int iq = meta + MS * MR * 16;           // 2 x [QN] int4 {query row, dqc bits, list lo, hi}
         static constexpr int tq = iq + 2 * QN * 16;              // 2 x [QN] u64 query-wide threshold at publication
         static constexpr int qsc = tq + 2 * QN * 8;              // 2 x [QN] f32 query scale (e4m3 path)
@@ -144,8 +148,9 @@ struct Cfg {
     static constexpr int b_tile_full(int t) { return 8 * (B0 + 2 * MS + 6 + t); }
     static constexpr int b_tile_empty(int t) { return 8 * (B0 + 2 * MS + 6 + EB + t); }
 };
-using CfgA = Cfg<64, 64, 2, 4>;     // k' <= 32, up to 64 queries per item
-using CfgB = Cfg<32, 160, 2, 4>;    // k' <= 128, up to 32 queries per item
+using CfgA = Cfg<64, 64, 2, 4, 2, 64, 0>;    // k' <= 32, up to 64 queries per item
+using CfgW = Cfg<128, 64, 1, 4, 1, 48, 1>;   // k' <= 32, up to 128 queries per item (twice the MMA width)
+using CfgB = Cfg<32, 160, 2, 4, 2, 64, 0>;   // k' <= 128, up to 32 queries per item
 
 // arrivals that complete a phase of the item-release barrier: every lane of the
 // query loader, the converters, the two issuers, the tile warps and the filters
@@ -331,6 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, const __grid_constant__ CUtensorMap q_map,
                    tc::Args a) {
     constexpr int QN = C::QN, KC = C::KC, LS = C::LS, NBUF = C::NBUF, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
+    constexpr int EB = C::EB, RAW_BYTES = C::RAW_BYTES;
     using Smem = typename C::Smem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (tid == 0) {
         for (int s = 0; s < RSMAX; ++s) {
             mbar_init(bars + C::b_full_raw(s), 1);
-            mbar_init(bars + C::b_empty_raw(s), 32 * 8);
+            mbar_init(bars + C::b_empty_raw(s), 128);     // the converter set of the stage
         }
         for (int s = 0; s < LS; ++s) {
             mbar_init(bars + C::b_full_q(s), 1);
@@ -523,9 +529,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
     } else if (warp >= W_CV && warp < W_CV + 8) {
         // ------------------------------------------------------------ converters
-        // Set b (warps 8 + 4b .. 11 + 4b) converts row block b of every stage;
-        // thread = one row of the block (TMEM lane).
-        const int b = (warp - W_CV) >> 2, qt = warp & 3;
+        // Two sets of four warps take alternate stages (set cs the stages with
+        // g % 2 == cs) and convert both row blocks of each: thread = one row of a
+        // block (TMEM lane 32 (w % 4) + lane); the TMEM stores of the two blocks
+        // are waited for once, while the other set converts the next stage.
+        const int cs = (warp - W_CV) >> 2, qt = warp & 3;
         const int r = qt * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(qt * 32) << 16;
         const int B = a.B;
@@ -539,8 +547,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (d.w < 0) break;
             const int nrows = d.z;
             for (int r0 = 0; r0 < nrows && ok; r0 += RP * MR) {
-                const bool has = b < min(RP, (nrows - r0 + MR - 1) / MR);
+                const int nb = min(RP, (nrows - r0 + MR - 1) / MR);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    if ((int)(g & 1) != cs) continue;
                     const int s = g % LS, rs = g % RS;
                     // the stage's TMEM columns are free (its previous MMAs completed)
                     // and its raw codes have landed
@@ -550,9 +559,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    uint32_t w[32];
-                    if (has) {
-                        const unsigned char* src = sm + Smem::raw + rs * slot_bytes + b * blk * (F8 ? 2 : 1) + roff;
+                    for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
+                        uint32_t w[32];
+                        const unsigned char* src = sm + Smem::raw + rs * slot_bytes + bb * blk * (F8 ? 2 : 1) + roff;
                         if (F8) {
                             // two packed blocks -> 128 e4m3 codes, four per column
 #pragma unroll
@@ -567,14 +576,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                         } else {
                             unpack_codes_b(B, src, w);
                         }
+                        ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + bb) * (KB / 2), w);
                     }
                     mbar_arrive(bars + C::b_empty_raw(rs));        // the raw slot may be refilled
-                    if (has) {
-                        ERQ_TMEM_ST32(tmem + lane_addr + ACOL + (s * RP + b) * (KB / 2), w);
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     tc_fence_before();
-                    mbar_arrive(bars + C::b_full_a(s, b));
+                    mbar_arrive(bars + C::b_full_a(s, 0));
+                    mbar_arrive(bars + C::b_full_a(s, 1));
                 }
             }
             if (!ok) break;
@@ -716,7 +724,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         // is never below its final k'-th key, so each list stays a superset of
         // what the item contributes to the query's top-k'.
         const float* s_est = reinterpret_cast<const float*>(sm + Smem::est);
-        uint64_t* lists = reinterpret_cast<uint64_t*>(sm + Smem::lists);
+        uint64_t* lists_s = reinterpret_cast<uint64_t*>(sm + Smem::lists);
+        // query q's candidate list: shared memory, or its output slot of the item
+        auto list_of = [&](const int4* iq, int q) -> uint64_t* {
+            if (C::LG) return a.inter + ((int64_t)(uint32_t)iq[q].z | ((int64_t)iq[q].w << 32)) * KC;
+            return lists_s + q * KC;
+        };
         const uint32_t* s_ids = reinterpret_cast<const uint32_t*>(sm + Smem::ids);
         int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
         uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
@@ -773,7 +786,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (cnt + __popc(msk) > KC) {
                             // full: keep the k' smallest (KC - k' >= 32 leaves
                             // room for a group), then test the group again
-                            tau = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
+                            tau = compact_list<C::KS>(list_of(iq, q), cnt, kp, lane);
                             tf = key_value(tau);
                             cnt = kp;
                             // k' keys of this query are now <= tau and stay in
@@ -784,7 +797,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             msk = __ballot_sync(0xffffffffu, pass);
                             if (msk == 0u) continue;
                         }
-                        if (pass) lists[q * KC + cnt + __popc(msk & below)] = key;
+                        if (pass) list_of(iq, q)[cnt + __popc(msk & below)] = key;
                         cnt += __popc(msk);
                         __syncwarp();
                     }
@@ -800,14 +813,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int q = fw; q < nqi; q += NFX) {               // write this warp's lists
                 int cnt = s_cnt[q];
                 if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
-                    const uint64_t th = compact_list<C::KS>(lists + q * KC, cnt, kp, lane);
+                    const uint64_t th = compact_list<C::KS>(list_of(iq, q), cnt, kp, lane);
                     cnt = kp;
                     if (lane == 0) atomicMin(a.tq + iq[q].x, (unsigned long long)th);
                 }
                 const int64_t L = (int64_t)(uint32_t)iq[q].z | ((int64_t)iq[q].w << 32);
                 if (!ERQ_DCHECK(L >= 0 && L < a.ck.lists && cnt >= 0 && cnt <= KC, a.ck.status, 6)) continue;
                 uint64_t* dst = a.inter + L * KC;
-                for (int e = lane; e < cnt; e += 32) dst[e] = lists[q * KC + e];
+                if (!C::LG)
+                    for (int e = lane; e < cnt; e += 32) dst[e] = lists_s[q * KC + e];
                 if (lane == 0) a.inter_cnt[L] = cnt;
             }
             __syncwarp();
@@ -829,7 +843,7 @@ bool tc_available(int precision, int D, int kp) {
 
 // Work-item query counts the tensor-core scan is built for, given k'.
 bool scan_tc_shape_ok(int qn, int kp) {
-    return (kp <= 32 && (qn == 32 || qn == CfgA::QN)) || (kp <= KCAP && qn == CfgB::QN);
+    return (kp <= 32 && (qn == 32 || qn == CfgA::QN || qn == CfgW::QN)) || (kp <= KCAP && qn == CfgB::QN);
 }
 
 // Capacity (stride) of the per-(query, item) candidate lists written by the scan.
@@ -1051,6 +1065,8 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     a.stall_stage = L.stall_stage;
     const void* qb = f8 ? L.Q8 : L.Qh;
     const int64_t qrow = f8 ? L.Dq : 2 * (int64_t)L.D;
+    if (L.kp <= 32 && L.qn > CfgA::QN)
+        return f8 ? scan_tc_launch<CfgW, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgW, false>(L, a, qb, qrow, s);
     if (L.kp <= 32) return f8 ? scan_tc_launch<CfgA, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgA, false>(L, a, qb, qrow, s);
     return f8 ? scan_tc_launch<CfgB, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgB, false>(L, a, qb, qrow, s);
 }

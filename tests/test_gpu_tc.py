@@ -108,7 +108,7 @@ def test_tc_rejects_large_k(erq):
         gx.search(Q, 10, rerank_k=129, nprobe=2, precision="fp16")
 
 
-@pytest.mark.parametrize("qn,rr", [(32, 2048), (64, 4096), (64, 8192), (32, 256), (64, 512)])
+@pytest.mark.parametrize("qn,rr", [(32, 2048), (64, 4096), (128, 8192), (128, 256), (64, 512)])
 def test_tc_scan_shapes_agree(erq, qn, rr):
     """Every work-item shape (queries per item = the MMA's N extent, rows per
     item) computes the same estimates and selects the same candidates: each
@@ -132,7 +132,7 @@ def test_autotune_picks_a_shape(erq):
     Q = to_dev(S.mixture(1200, 128, 16, 3601, comp_seed=3600, scale="aniso")[0])
     ref = gx.search(Q, 10, rerank_k=20, nprobe=12, precision="fp16")
     best = gx.autotune(Q, 10, rerank_k=20, nprobe=12, precision="fp16", reps=2)
-    assert best[0] in (32, 64) and best[1] in (2048, 4096, 8192)
+    assert best[0] in (32, 64, 128) and best[1] in (2048, 4096, 8192)
     got = gx.search(Q, 10, rerank_k=20, nprobe=12, precision="fp16")
     torch.cuda.synchronize()
     assert gx.scan_config() == best
@@ -140,7 +140,7 @@ def test_autotune_picks_a_shape(erq):
     with pytest.raises(erq.ErqError):
         gx.set_scan_config(48, 0)
     with pytest.raises(erq.ErqError):
-        gx.set_scan_config(128, 0)
+        gx.set_scan_config(256, 0)
     with pytest.raises(erq.ErqError):
         gx.set_scan_config(0, 1000)
 
