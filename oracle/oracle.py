@@ -15,6 +15,9 @@ TEST INFRASTRUCTURE ONLY.  Follows arXiv 2409.09913:
   gradient w.r.t. the raw query.
 * ``brute_force_quantize``      -- exhaustive argmax of Eq. 3.2 (optimization) over the
   whole grid G, for tiny D and B (pin for Algorithm 1).
+* ``two_stage_search``          -- Section 4.2: estimates from the most significant bits
+  (the 1-bit RaBitQ code, Lemma 2.1 estimator and bound) prune the probed rows,
+  Eq. 4.2 completes the survivors' estimates; numpy, FP64.
 """
 from __future__ import annotations
 
@@ -29,7 +32,7 @@ from . import build as _build
 __all__ = [
     "lib", "centroids", "rotate", "quantize", "build_index", "search", "estimate_rows",
     "backward", "rerank", "centroid_dists", "brute_force_quantize", "exact_knn", "num_threads",
-    "stored_factors",
+    "stored_factors", "two_stage_search", "two_stage_rows",
 ]
 
 _lib = None
@@ -281,3 +284,106 @@ def brute_force_quantize(op, B):
     tol = 4 * np.spacing(abs(best))
     hits = grid[cos >= best - tol] + (2 ** B - 1) / 2.0
     return best, hits.astype(np.int64)
+
+
+def two_stage_rows(ix, q, c, rows, eps0):
+    """Per-row quantities of the two-stage search for one query q and one
+    cluster c (stored rows ``rows`` of that cluster), FP64:
+
+    * est1: Lemma 2.1's estimate from the row's most significant bits, which
+      form the 1-bit RaBitQ code of the same residual (Section 4.2): with
+      xbar = 2 msb - 1 (+-1 per coordinate), obar_0 = P xbar / sqrt(D) and the
+      unit residual o, <o, q^> ~ <obar_0, q^> / <obar_0, o>, where
+      <obar_0, o> = sum_i |o'_i| / (sqrt(D) ||o'||);
+    * bound: Lemma 2.1's error bound carried to the squared distance
+      ||o'||^2 + ||q_r - c||^2 - 2 ||o'|| ||q_r - c|| <o, q^>:
+      2 ||o'|| ||q_r - c|| sqrt(1 - a^2) / a * eps0 / sqrt(D - 1), a = <obar_0, o>;
+    * est: the full B-bit estimate (Eq. 3.3, Eq. (eq:dis to ip)) with
+      <ybar_u, q'> assembled by Eq. 4.2 from the stage-1 product of the MSB
+      code and the product of the remaining bits;
+    * ip_msb: <msb, q'> (q' the unit rotated residual query), reused by Eq. 4.2.
+    Rows with o' = 0 (reading R8) estimate ||q_r - c||^2 with bound 0."""
+    d, B = ix["d"], ix["B"]
+    codes = ix["codes"][rows].astype(np.float64)
+    st = ix["stats"][rows]
+    qn = np.asarray(q, np.float64) - ix["C"][c].astype(np.float64)
+    qc = np.sqrt(qn @ qn)
+    if qc > 0:
+        qn = qn / qc
+    qp = qn @ ix["P"].astype(np.float64)                 # P^{-1} q^ (P orthogonal)
+    sum_qp = qp.sum()
+    msb = np.floor(codes / 2 ** (B - 1))                 # the MSB plane, 0/1
+    last = codes - 2 ** (B - 1) * msb                    # the remaining B-1 bits
+    ip_msb = msb @ qp
+    ipu = 2 ** (B - 1) * ip_msb + last @ qp              # Eq. 4.2
+    op = ix["Rp"][ix["list_ids"][rows]].astype(np.float64)
+    nr2 = (op * op).sum(1)
+    nr = np.sqrt(nr2)
+    pos = nr2 > 0
+    safe = np.where(pos, nr, 1.0)
+    a = np.abs(op).sum(1) / (np.sqrt(d) * safe)          # <obar_0, o>
+    # 1-bit estimate: ||ybar_1|| <obar_0, q^> = <msb, q'> - sum q' / 2 with ||ybar_1|| = sqrt(D)/2
+    ip1 = np.where(pos, (ip_msb - 0.5 * sum_qp) / (0.5 * np.sqrt(d) * np.where(pos, a, 1.0)), 0.0)
+    est1 = nr2 + qc * qc - 2.0 * nr * qc * ip1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        bound = np.where(pos, 2.0 * nr * qc * np.sqrt(np.maximum(1.0 - a * a, 0.0)) / np.where(pos, a, 1.0)
+                         * eps0 / np.sqrt(d - 1), 0.0)
+    # full estimate from the stored stats (as the search): ||ybar|| <obar, q^> * 1/(||ybar|| <o, obar>)
+    obar_q = ipu - 0.5 * (2 ** B - 1) * sum_qp
+    o_obar = np.where(pos, st[:, 2] / safe, 1.0)
+    inv = np.where(pos, 1.0 / (np.sqrt(st[:, 1]) * o_obar), 0.0)
+    est = nr2 + qc * qc - 2.0 * nr * qc * obar_q * inv
+    return dict(est1=est1, bound=bound, est=est, ip_msb=ip_msb)
+
+
+def two_stage_search(ix, Q, k, kprime, nprobe=None, probe=None, eps0=1.9):
+    """Two-stage (MSB-first) search of Section 4.2, FP64 with numpy (metric l2).
+
+    Per query: the probe of ``search``; stage 1 gives every probed row its
+    1-bit estimate est1 and Lemma 2.1 bound (two_stage_rows).  Pruning rule
+    (reading): tau = the k'-th smallest upper bound est1 + bound over the
+    query's probed rows (+inf with fewer than k' rows); when every bound holds,
+    at least k' rows have a true distance <= tau, so no row of the true top-k'
+    has est1 - bound > tau, and only those rows are dropped.  Stage 2: the
+    survivors' full estimates (Eq. 4.2), their top-k' by (estimate, id), the
+    exact re-rank and top-k as in ``search``.  eps0 = inf keeps every row
+    (the single-stage search); eps0 = 0 keeps the k' smallest est1.
+
+    Returns dict(ids, dists, cand_ids, cand_est, tau, survivors, rows, probe)."""
+    Q = _q64(Q)
+    nq = Q.shape[0]
+    kp = kprime if kprime > 0 else k
+    pr = search(ix, Q, k, kprime, nprobe=nprobe, probe=probe)["probe"]
+    cand_ids = np.full((nq, kp), -1, np.int64)
+    cand_est = np.full((nq, kp), np.inf)
+    tau = np.full(nq, np.inf)
+    surv = np.zeros(nq, np.int64)
+    nrows = np.zeros(nq, np.int64)
+    for i in range(nq):
+        ids, e1, bd, est = [], [], [], []
+        for c in pr[i]:
+            if c < 0:
+                continue
+            rows = np.arange(ix["list_off"][c], ix["list_off"][c + 1])
+            if len(rows) == 0:
+                continue
+            r = two_stage_rows(ix, Q[i], c, rows, eps0)
+            ids.append(ix["list_ids"][rows])
+            e1.append(r["est1"])
+            bd.append(r["bound"])
+            est.append(r["est"])
+        if not ids:
+            continue
+        ids, e1, bd, est = map(np.concatenate, (ids, e1, bd, est))
+        nrows[i] = len(ids)
+        ub = e1 + bd
+        if len(ub) >= kp:
+            tau[i] = np.sort(ub)[kp - 1]
+        keep = ~(e1 - bd > tau[i])
+        surv[i] = keep.sum()
+        o = np.lexsort((ids[keep], est[keep]))[:kp]
+        cand_ids[i, :len(o)] = ids[keep][o]
+        cand_est[i, :len(o)] = est[keep][o]
+    rids, rd = rerank(ix["X"], Q, cand_ids, k)
+    return dict(ids=rids, dists=rd, cand_ids=cand_ids, cand_est=cand_est, tau=tau, survivors=surv, rows=nrows,
+                probe=pr)
