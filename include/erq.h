@@ -55,9 +55,10 @@ typedef enum {
     ERQ_PREC_FP16 = 1,       /* tcgen05 kind::f16: codes exact, rotated query in FP16,
                                 FP32 accumulation in tensor memory                       */
     ERQ_PREC_FP8 = 2,        /* tcgen05 kind::f8f6f4: query rounded to e4m3 after a
-                                per-query power-of-two scale, centred codes in e4m3
-                                (exact; needs B <= 4, else ERQ_EUNSUPPORTED), FP32
-                                accumulation in tensor memory                            */
+                                per-query power-of-two scale, centred codes exact in
+                                e4m3 (B <= 4 directly; B = 5..8 as 16 hc + lc, two
+                                e4m3 parts of magnitude <= 15 each, Section 3.3),
+                                FP32 accumulation in tensor memory                       */
     ERQ_PREC_INT8 = 3        /* int8 tensor MMA: unavailable on sm_103a (ptxas rejects
                                 tcgen05 kind::i8) -> ERQ_EUNSUPPORTED                    */
 } erq_precision;
@@ -209,6 +210,29 @@ erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_
  * (precision), ENOMEM (workspace), ECUDA, ETIMEOUT (device status). */
 erq_status erq_search(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params,
                       int64_t* ids, float* dists, void* stream);
+
+/* Two-stage (MSB-first) search of Section 4.2, for few queries per probed
+ * cluster, on CUDA cores in FP32 (params->precision is ignored; metric l2).
+ * The probe is erq_search's.  Stage 1 reads only the most significant bit
+ * plane of every probed row -- the 1-bit RaBitQ code of its residual -- and
+ * forms Lemma 2.1's estimate est1 and error bound eps0 * err1 * ||q_r - c||
+ * (err1 = 2 ||o'|| sqrt(1 - a^2) / (a sqrt(D - 1)), a = sum|o'_i| / (sqrt(D) ||o'||)).
+ * Per query, tau = the k'-th smallest est1 + bound over its probed rows (+inf
+ * with fewer rows); rows with est1 - bound > tau are dropped.  Stage 2 reads
+ * the other B - 1 bits of the survivors and completes their estimate by
+ * Eq. 4.2; the k' = max(k, rerank_k) smallest (estimate, id) survivors are
+ * re-ranked as in erq_search (cand_ids / cand_est as there).  eps0 = INFINITY
+ * keeps every row (erq_search's result up to FP32 rounding); eps0 = 0 keeps
+ * the k' smallest est1.
+ * stats: optional HOST int64_t[2] out = {probed rows, survivors} summed over
+ * the queries (reading them synchronises the stream).  The first call on an
+ * index computes the stage-1 factors (16 bytes per row, kept) from the raw
+ * rows.  The call synchronises the stream (the row count sizes its buffers).
+ * Errors: EINVAL (as erq_search; eps0 < 0 or NaN; no raw rows),
+ * EUNSUPPORTED (metric ip; B = 4, whose top bit sits inside the packed nibble
+ * words), ENOMEM, ECUDA. */
+erq_status erq_search_two_stage(erq_index* index, const float* Q, int64_t nq, const erq_search_params* params,
+                                float eps0, int64_t* ids, float* dists, int64_t* stats, void* stream);
 
 /* The same search from HOST buffers: Q_host[nq][D] is copied to the device,
  * searched, and ids_host/dists_host are copied back before the call returns.

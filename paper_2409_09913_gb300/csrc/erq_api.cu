@@ -60,7 +60,7 @@ void free_index_arrays(erq_index* ix) {
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_p,
-                    ix->dstats, ix->PT_hi, ix->C_hi, ix->dctr};   // PT_lo / C_lo live inside those blocks
+                    ix->dstats, ix->PT_hi, ix->C_hi, ix->dctr, ix->rowmeta1};   // PT_lo / C_lo live inside those blocks
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
@@ -470,8 +470,110 @@ static void choose_scan_shape(const erq_index* ix, int prec, int kp, int64_t nq,
     *rr = r;
 }
 
+// Stage 1, pruning, stage 2 and the selection of the two-stage search
+// (k_two_stage.cu), after the probe, then the exact re-rank.
+static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p, int64_t* ids,
+                                 float* dists, cudaStream_t s, float eps0, int64_t* stats_out, const int32_t* probe_c,
+                                 const float* dqc, const float* Qrot, int maxp, int kp, int k, bool do_rerank,
+                                 uint64_t* cand, const DevChecks& ck) {
+    const int D = ix->D;
+    int32_t* rbase = nullptr;
+    int64_t *qrows = nullptr, *qoffr = nullptr;
+    void* big = nullptr;
+    auto release = [&]() {
+        for (void* ptr : {(void*)rbase, (void*)qrows, (void*)qoffr, big})
+            if (ptr) cudaFreeAsync(ptr, s);
+    };
+    auto bail = [&](erq_status st) {
+        release();
+        return st;
+    };
+    if (cudaMallocAsync((void**)&rbase, sizeof(int32_t) * (size_t)nq * maxp, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&qrows, sizeof(int64_t) * (size_t)nq, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&qoffr, sizeof(int64_t) * (size_t)(nq + 1), s) != cudaSuccess)
+        return bail(fail(ERQ_ENOMEM, "two-stage: row offsets"));
+    cudaError_t e;
+    if ((e = launch_two_stage_rows(probe_c, nq, maxp, ix->list_off, rbase, qrows, s)) != cudaSuccess ||
+        (e = launch_excl_scan_i64(qrows, qoffr, nq, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "two-stage: row offsets"));
+    int64_t rows = 0;
+    if ((e = cudaMemcpyAsync(&rows, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail(cuda_fail(e, "two-stage: row count"));
+    // one block: ub, lb, s1 [rows] f32 | skey [rows] u64 | T [nq][4D] f32 | tau [nq] f32 | scnt [nq] i32
+    // (every part starts on a 256-byte boundary: the tables are read as float4)
+    const size_t r = (size_t)std::max<int64_t>(rows, 1);
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t off_skey = up(12 * r), off_T = up(off_skey + 8 * r);
+    const size_t off_tau = up(off_T + (size_t)nq * 16 * D), off_cnt = up(off_tau + 4 * (size_t)nq);
+    if (cudaMallocAsync(&big, off_cnt + 4 * (size_t)nq, s) != cudaSuccess) return bail(fail(ERQ_ENOMEM, "two-stage"));
+    char* b = (char*)big;
+    TwoStageLaunch L;
+    L.probe_c = probe_c; L.dqc = dqc; L.list_off = ix->list_off; L.poff = ix->poff; L.codes_p = ix->codes_p;
+    L.rowmeta = ix->rowmeta; L.meta1 = ix->rowmeta1; L.Qrot = Qrot; L.T = (float*)(b + off_T);
+    L.rbase = rbase; L.qoffr = qoffr;
+    L.ub = (float*)b; L.lb = (float*)b + r; L.s1 = (float*)b + 2 * r;   // 4-byte elements
+    L.skey = (uint64_t*)(b + off_skey); L.scratch = (uint32_t*)(b + off_skey);
+    L.tau = (float*)(b + off_tau); L.scnt = (int32_t*)(b + off_cnt); L.cand = cand;
+    L.nq = nq; L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.eps0 = eps0;
+    if ((e = launch_two_stage(L, s)) != cudaSuccess) return bail(cuda_fail(e, "two-stage"));
+    if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, 0, ids, dists, p->cand_ids, p->cand_est,
+                           ck, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "two-stage: rerank"));
+    if (stats_out) {
+        std::vector<int32_t> cnt((size_t)nq);
+        if ((e = cudaMemcpyAsync(cnt.data(), L.scnt, sizeof(int32_t) * (size_t)nq, cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bail(cuda_fail(e, "two-stage: survivors"));
+        int64_t sv = 0;
+        for (int32_t v : cnt) sv += v;
+        stats_out[0] = rows;
+        stats_out[1] = sv;
+    }
+    release();
+    return ERQ_OK;
+}
+
+// Two-stage search request (erq_search_two_stage): Lemma 2.1's eps0 and an
+// optional host output {probed rows, survivors} summed over the queries.
+struct TwoStageReq {
+    float eps0;
+    int64_t* stats;
+};
+
+// Stage-1 factors of every stored row (rowmeta1), from the rotated residuals
+// of the raw rows (the same FP64 rotation as the build).
+static erq_status ensure_stage1(erq_index* ix, cudaStream_t s) {
+    if (ix->rowmeta1) return ERQ_OK;
+    const int D = ix->D;
+    const size_t np = (size_t)std::max<int64_t>(ix->Np, 32);
+    if (cudaMalloc(&ix->rowmeta1, sizeof(float4) * np) != cudaSuccess) {
+        ix->rowmeta1 = nullptr;
+        return fail(ERQ_ENOMEM, "cudaMalloc two-stage factors");
+    }
+    ix->device_bytes += (int64_t)(16 * np);
+    ERQ_CHECK_CUDA(cudaMemsetAsync(ix->rowmeta1, 0, sizeof(float4) * np, s));
+    const int64_t N = ix->N;
+    const int64_t chunk = std::min<int64_t>(N, std::max<int64_t>(4096, (int64_t)(1ll << 30) / (4ll * D)));
+    ERQ_TRY(ensure_ws(&ix->ws, &ix->ws_bytes, (size_t)std::max<int64_t>(chunk, 1) * D * 4));
+    float* R = (float*)ix->ws;
+    cudaError_t e;
+    for (int64_t r0 = 0; r0 < N; r0 += chunk) {
+        const int64_t m = std::min(chunk, N - r0);
+        if ((e = launch_rotate_fp64(ix->X, ix->list_ids + r0, ix->C, ix->cl_of_row + r0, ix->P, R, m, D, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "two-stage factors: rotate residuals");
+        if ((e = launch_stage1_factors(R, r0, m, D, ix->B, ix->codes, ix->f_add, ix->Cp, ix->cl_of_row, ix->list_off,
+                                       ix->poff, ix->rowmeta1, s)) != cudaSuccess)
+            return cuda_fail(e, "two-stage factors");
+    }
+    ERQ_CHECK_CUDA(cudaStreamSynchronize(s));   // the workspace is carved by the search next
+    return ERQ_OK;
+}
+
 static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p, int64_t* ids,
-                              float* dists, cudaStream_t s) {
+                              float* dists, cudaStream_t s, const TwoStageReq* ts = nullptr) {
     const int D = ix->D, nlist = ix->nlist;
     const int k = p->k;
     const int kp = std::max(p->k, p->rerank_k);
@@ -480,7 +582,10 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     const bool explicit_probe = p->probe != nullptr;
     const int prec = p->precision;
     const int ip = p->metric == ERQ_METRIC_IP ? 1 : 0;   // rank by -<o_r, q_r> (probe: -<q_r, c_j>)
-    const int64_t Dq = (D + 127) / 128 * 128;           // e4m3 query rows, padded to whole 128-byte stages
+    // e4m3 query rows: padded to whole 128-byte stages (B <= 4), or every
+    // 64-coordinate block twice for the split form of wider codes
+    const int split8 = ix->B > 4;
+    const int64_t Dq = split8 ? 2 * (int64_t)D : (D + 127) / 128 * 128;
     // ---- phase A workspace (sizes known on the host)
     // queries per work item of the scan kernels
     int QT = 64, RR = 4096;
@@ -591,7 +696,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
         qh_done = qh != nullptr;
     }
     if (prec == ERQ_PREC_FP8 &&
-        (e = launch_quant_e4m3(Qrot, nq, D, (int)Dq, (unsigned char*)sl[26], (float*)sl[27], s)) != cudaSuccess)
+        (e = launch_quant_e4m3(Qrot, nq, D, (int)Dq, split8, (unsigned char*)sl[26], (float*)sl[27], s)) != cudaSuccess)
         return cuda_fail(e, "query e4m3");
     if (prec == ERQ_PREC_FP16 && !qh_done &&
         (e = launch_to_half(Qrot, (__half*)sl[20], (int64_t)nq * D, s)) != cudaSuccess)
@@ -653,6 +758,8 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     // dqc needs the validated probe ids
     if (!dqc_from_probe && (e = launch_dqc(Q, ix->C, pa.probe_c, npr, nq, maxp, D, ip, dqc, s)) != cudaSuccess)
         return cuda_fail(e, "dqc");
+    if (ts) return two_stage_tail(ix, Q, nq, p, ids, dists, s, ts->eps0, ts->stats, pa.probe_c, dqc, Qrot, maxp, kp,
+                                  k, do_rerank, cand, ck);
     int64_t Ltot = 0, nitems = 0;
     const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0;
     if (async) {
@@ -732,7 +839,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    L.grid = (int)std::min<int64_t>(nitems, (int64_t)sms * (prec == ERQ_PREC_FP32 ? 2 : 1));
+    L.grid = (int)std::min<int64_t>(nitems, (int64_t)sms * (prec == ERQ_PREC_FP32 ? scan_fp32_blocks_per_sm(kp) : 1));
     if (prec == ERQ_PREC_FP32) {
         if ((e = launch_scan_fp32(L, s)) != cudaSuccess) return cuda_fail(e, "scan fp32");
     } else {
@@ -755,7 +862,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
 }
 
 static erq_status validate_search(const erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p,
-                                  const void* ids, const void* dists) {
+                                  const void* ids, const void* dists, bool two_stage = false) {
     if (!ix || !p) return fail(ERQ_EINVAL, "erq_search: null index or params");
     if (nq < 0) return fail(ERQ_EINVAL, "erq_search: nq < 0");
     if (nq > 0 && (!Q || !ids || !dists)) return fail(ERQ_EINVAL, "erq_search: null Q/ids/dists");
@@ -771,13 +878,19 @@ static erq_status validate_search(const erq_index* ix, const float* Q, int64_t n
     } else if (ix->nlist > 1 && (p->nprobe < 1 || p->nprobe > ix->nlist)) {
         return fail(ERQ_EINVAL, "erq_search: nprobe must be in [1, nlist]");
     }
+    if (two_stage) {
+        if (p->metric != ERQ_METRIC_L2) return fail(ERQ_EUNSUPPORTED, "erq_search_two_stage: metric l2 only");
+        if (ix->B == 4)
+            return fail(ERQ_EUNSUPPORTED, "erq_search_two_stage: B = 4 keeps its top bit inside the nibble words "
+                                          "of the packed layout (no separate plane to read first)");
+        if (!ix->keep_raw) return fail(ERQ_EINVAL, "erq_search_two_stage: needs keep_raw (stage-1 factors)");
+        return ERQ_OK;
+    }
     if (p->precision == ERQ_PREC_INT8)
         return fail(ERQ_EUNSUPPORTED, "erq_search: int8 tensor MMA (tcgen05 kind::i8) is not available on sm_103a");
     if (p->precision < 0 || p->precision > ERQ_PREC_INT8) return fail(ERQ_EINVAL, "erq_search: unknown precision");
     if (p->precision != ERQ_PREC_FP32 && !tc_available(p->precision, ix->D, kp))
         return fail(ERQ_EUNSUPPORTED, "erq_search: tensor-core path unavailable for this D / k'");
-    if (p->precision == ERQ_PREC_FP8 && ix->B > 4)
-        return fail(ERQ_EUNSUPPORTED, "erq_search: fp8 scan needs B <= 4 (centred codes exact in e4m3)");
     if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
         return fail(ERQ_EUNSUPPORTED, "erq_search: k' too large for the FP32 scan");
     if (p->metric != ERQ_METRIC_L2 && p->metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_search: unknown metric");
@@ -789,6 +902,21 @@ extern "C" erq_status erq_search(erq_index* ix, const float* Q, int64_t nq, cons
     ERQ_TRY(validate_search(ix, Q, nq, p, ids, dists));
     if (nq == 0) return ERQ_OK;
     return search_impl(ix, Q, nq, p, ids, dists, (cudaStream_t)stream);
+}
+
+extern "C" erq_status erq_search_two_stage(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p,
+                                           float eps0, int64_t* ids, float* dists, int64_t* stats, void* stream) {
+    ERQ_TRY(validate_search(ix, Q, nq, p, ids, dists, true));
+    if (!(eps0 >= 0.f)) return fail(ERQ_EINVAL, "erq_search_two_stage: eps0 must be >= 0");
+    if (stats) stats[0] = stats[1] = 0;
+    if (nq == 0) return ERQ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    ERQ_TRY(ensure_stage1(ix, s));
+    erq_search_params q = *p;
+    q.precision = ERQ_PREC_FP32;          // the probe's FP32 path; no tensor-core query copies
+    q.flags &= ~(ERQ_SEARCH_ASYNC | ERQ_SEARCH_TIMING);
+    TwoStageReq ts{eps0, stats};
+    return search_impl(ix, Q, nq, &q, ids, dists, s, &ts);
 }
 
 extern "C" erq_status erq_search_host(erq_index* ix, const float* Q_host, int64_t nq, const erq_search_params* p,

@@ -133,6 +133,8 @@ struct erq_index {
     int64_t* poff = nullptr;     // [nlist+1] padded list offsets
     uint64_t* codes_p = nullptr; // [Np * D * B / 64] packed, tiled codes of the tensor-core scan
     float4* rowmeta = nullptr;   // [Np] {g, f_res/2, id, 0} per padded row (zeros for padding)
+    float4* rowmeta1 = nullptr;  // [Np] {g1, f1/2, err1, 0}: 1-bit (MSB) factors of the two-stage search,
+                                 //      computed at its first use from the raw rows
     float* X = nullptr;          // [N][D] raw rows, original order (keep_raw)
     uint32_t* status = nullptr;  // device status word
     std::vector<int64_t>* host_list_off = nullptr;  // host copy of list_off

@@ -80,12 +80,46 @@ struct ScanLaunch {
     DevChecks ck;
 };
 
+// Two-stage (MSB-first) search, k_two_stage.cu.
+struct TwoStageLaunch {
+    const int32_t* probe_c;     // [nq][maxp] validated probes (-1: none)
+    const float* dqc;           // [nq][maxp] ||q_r - c||^2
+    const int64_t* list_off;
+    const int64_t* poff;
+    const uint64_t* codes_p;
+    const float4* rowmeta;      // [Np] {g, f_res / 2, id, 0}
+    const float4* meta1;        // [Np] {g1, f1 / 2, err1, 0} (stage-1 factors)
+    const float* Qrot;          // [nq][D]
+    float* T;                   // [nq][D / 4][16] workspace: plane-word nibble tables
+    const int32_t* rbase;       // [nq][maxp] first row of each probe within its query
+    const int64_t* qoffr;       // [nq + 1] first row slot of each query
+    float* ub;                  // [rows] workspace
+    float* lb;                  // [rows] workspace
+    float* s1;                  // [rows] workspace
+    float* tau;                 // [nq] out: pruning thresholds
+    int32_t* scnt;              // [nq] out: survivors
+    uint64_t* skey;             // [rows] workspace (also the threshold selection's scratch)
+    uint32_t* scratch;          // [rows] u32 scratch (may alias skey)
+    uint64_t* cand;             // [nq][kp] out: the k' best survivors' keys, ascending
+    int64_t nq;
+    int maxp, D, B, kp;
+    float eps0;
+};
+cudaError_t launch_stage1_factors(const float* R, int64_t r0, int64_t m, int D, int B, const uint8_t* codes,
+                                  const float* f_add, const float* Cp, const int32_t* cl_of_row,
+                                  const int64_t* list_off, const int64_t* poff, float4* meta1, cudaStream_t s);
+cudaError_t launch_two_stage_rows(const int32_t* probe_c, int64_t nq, int maxp, const int64_t* list_off,
+                                  int32_t* rbase, int64_t* qrows, cudaStream_t s);
+cudaError_t launch_two_stage(const TwoStageLaunch& L, cudaStream_t s);
+cudaError_t launch_excl_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
 cudaError_t launch_dqc(const float* Q, const float* C, const int32_t* probe, const int32_t* npr, int64_t nq, int maxp,
                        int D, int ip, float* dqc, cudaStream_t s);
 cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s);
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
 size_t scan_fp32_smem(int kp);
+int scan_fp32_blocks_per_sm(int kp);   // resident FP32-scan blocks per SM at this k'
 int merge_sortn(int kp, int lstride);
 cudaError_t launch_make_keys(const int64_t* ids, const float* vals, int64_t n, int64_t id_limit, int neg,
                              uint64_t* keys, cudaStream_t s);
@@ -103,7 +137,8 @@ bool scan_tc_shape_ok(int qn, int kp);
 cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float* f_res, const int64_t* ids,
                                const int64_t* list_off, const int64_t* poff, int nlist, int64_t Np, int D, int B,
                                uint64_t* codes_p, float4* rowmeta, cudaStream_t s);
-cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s);
+cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, int dup, unsigned char* y, float* scale,
+                              cudaStream_t s);
 cudaError_t launch_rerank(const uint64_t* cand, int64_t nq, int kp, const float* X, const float* Q, int D, int k,
                           int do_rerank, int ip, int64_t* ids, float* dists, int64_t* cand_ids, float* cand_est,
                           const DevChecks& ck, cudaStream_t s);

@@ -232,9 +232,69 @@ __device__ __forceinline__ void unpack_codes_b(int B, const unsigned char* base,
 // Two FP16 values holding odd integers |x| <= 15 (exact in e4m3) -> their
 // e4m3 encodings in bytes 0 and 2: the e4m3 exponent is the FP16 one minus 8
 // (biases 15 and 7) and the three mantissa bits are the FP16 mantissa's top
-// three (the lower seven are zero for these values).
+// three (the lower seven are zero for these values).  With X16 the encodings
+// are those of 16 x (exponent + 4; at most 240, below e4m3's 448).
+template <bool X16 = false>
 __device__ __forceinline__ uint32_t half2_to_e4m3_pair(uint32_t w) {
-    return (((w >> 7) & 0x00FF00FFu) - 0x00400040u) | ((w >> 8) & 0x00800080u);
+    constexpr uint32_t sub = X16 ? 0x00200020u : 0x00400040u;
+    return (((w >> 7) & 0x00FF00FFu) - sub) | ((w >> 8) & 0x00800080u);
+}
+
+// Four byte lanes holding 2x (x < 16) -> the e4m3 encodings of 2x - off
+// (odd, |2x - off| <= 15), times 16 with X16, in byte lanes 0..3.
+template <bool X16>
+__device__ __forceinline__ uint32_t lanes_to_e4m3(uint32_t V, __half2 c) {
+    const uint32_t p0 = __byte_perm(V, 0x6464u, 0x4140u);   // {x0, 0x64, x1, 0x64}: FP16 1024 + 2x
+    const uint32_t p1 = __byte_perm(V, 0x6464u, 0x4342u);
+    const __half2 h0 = __hsub2(*reinterpret_cast<const __half2*>(&p0), c);
+    const __half2 h1 = __hsub2(*reinterpret_cast<const __half2*>(&p1), c);
+    return __byte_perm(half2_to_e4m3_pair<X16>(*reinterpret_cast<const uint32_t*>(&h0)),
+                       half2_to_e4m3_pair<X16>(*reinterpret_cast<const uint32_t*>(&h1)), 0x6420u);
+}
+
+// Split e4m3 form of B = 5..8 codes (Section 3.3 remarks that a B-bit code
+// can be handled as parts of fewer bits).  With u = 16 h + l, l < 16,
+//   2u - (2^B - 1) = 16 (2h - (2^(B-4) - 1)) + (2l - 15),
+// and both brackets are odd integers of magnitude <= 15, so 16 hc and lc are
+// exact in e4m3.  Output: 32 columns for one 64-coordinate block, w[m] the
+// four values 16 hc of coordinates 4m..4m+3 and w[16 + m] their lc; the
+// stage's query tile holds the block's e4m3 queries twice (bytes 0-63 and
+// 64-127), so the four K = 32 MMAs of the stage sum 16 hc q + lc q exactly.
+// Packed layout as at unpack_codes (B >= 4: nibble words 0-3, planes 4..B-1).
+template <int B>
+__device__ __forceinline__ void unpack_split(const unsigned char* base, uint32_t (&w)[32]) {
+    static_assert(B >= 5 && B <= 8, "split form is for B = 5..8");
+    uint2 W[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) W[j] = *reinterpret_cast<const uint2*>(base + 256 * j);
+    const float offh = (float)((1 << (B - 4)) - 1);
+    const __half2 ch = __floats2half2_rn(1024.f + offh, 1024.f + offh);
+    const __half2 cl = __floats2half2_rn(1039.f, 1039.f);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int h = m >> 1;
+        const uint32_t N = (h & 1) ? W[h >> 1].y : W[h >> 1].x;
+        const uint32_t L = (m & 1) ? (N >> 3) & 0x1E1E1E1Eu : (N << 1) & 0x1E1E1E1Eu;   // 2l per byte lane
+        uint32_t H = 0;                                                                 // 2h per byte lane
+#pragma unroll
+        for (int b = 4; b < B; ++b) {
+            const uint32_t P = m < 8 ? W[b].x : W[b].y;
+            const int sh = (b - 3) - (m & 7);
+            const uint32_t x = sh >= 0 ? P << sh : P >> (-sh);
+            H |= x & (0x01010101u << (b - 3));
+        }
+        w[m] = lanes_to_e4m3<true>(H, ch);
+        w[16 + m] = lanes_to_e4m3<false>(L, cl);
+    }
+}
+
+__device__ __forceinline__ void unpack_split_b(int B, const unsigned char* base, uint32_t (&w)[32]) {
+    switch (B) {
+        case 5: unpack_split<5>(base, w); break;
+        case 6: unpack_split<6>(base, w); break;
+        case 7: unpack_split<7>(base, w); break;
+        default: unpack_split<8>(base, w); break;
+    }
 }
 
 struct Args {
@@ -251,6 +311,8 @@ struct Args {
     uint32_t* status;
     int D, B, kp, nkb;            // nkb: stages per row group (64 FP16 or 128 e4m3 coordinates each)
     int ip;                       // inner-product metric: est = -<c, q_r> + (f_res / 4) * acc
+    int codes_shared;             // items of one cluster share its rows (queries > QN): codes stay in L2 normally,
+                                  // else they are loaded evict-first
     unsigned long long wait_ns;   // limit of every bounded wait
     long long stall_stage;        // >= 0: the first issuer waits at this stage on a barrier nothing arrives on
     DevChecks ck;
@@ -327,14 +389,18 @@ __device__ __noinline__ uint64_t compact_list(uint64_t* list, int cnt, int kp, i
     return th;
 }
 
-// F8: queries in e4m3 with a per-query scale, codes in e4m3 (B <= 4),
-// tcgen05.mma kind::f8f6f4 (K = 32); a stage then covers 128 coordinates (two
-// packed 64-coordinate blocks), which occupy the same 128 bytes per row in
-// tensor memory and in the query tile as 64 FP16 coordinates.
-template <class C, bool F8>
+// P selects the operand form: 0 FP16 codes and queries (kind::f16, K = 16);
+// 1 e4m3 codes (B <= 4) and queries with a per-query scale (kind::f8f6f4,
+// K = 32), a stage covering 128 coordinates (two packed 64-coordinate blocks)
+// in the same 128 bytes per row of tensor memory and query tile as 64 FP16
+// coordinates; 2 the split e4m3 form of B = 5..8 codes (unpack_split), a
+// stage covering 64 coordinates whose query tile holds them twice.
+template <class C, int P>
 __global__ void __launch_bounds__(THREADS, 1)
-    scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, const __grid_constant__ CUtensorMap q_map,
-                   tc::Args a) {
+    scan_tc_kernel(const __grid_constant__ CUtensorMap codes_map, const __grid_constant__ CUtensorMap codes_map1,
+                   const __grid_constant__ CUtensorMap q_map, tc::Args a) {
+    constexpr bool F8 = P != 0;       // e4m3 operands
+    constexpr bool W2 = P == 1;       // two packed blocks per stage
     constexpr int QN = C::QN, KC = C::KC, LS = C::LS, NBUF = C::NBUF, TILE_Q = C::TILE_Q, ACOL = C::ACOL;
     constexpr int EB = C::EB, RAW_BYTES = C::RAW_BYTES;
     using Smem = typename C::Smem;
@@ -353,7 +419,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nkb = a.nkb;
     const uint32_t blk = (uint32_t)(MR / 32) * 256u * (uint32_t)a.B;    // packed codes of one 128-row K block
-    const uint32_t slot_bytes = (uint32_t)RP * blk * (F8 ? 2u : 1u);
+    const uint32_t slot_bytes = (uint32_t)RP * blk * (W2 ? 2u : 1u);
     const int RS = min(RSMAX, (int)(RAW_BYTES / slot_bytes));
     int64_t nitems = *a.n_items;
     if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 7)) nitems = 0;   // uniform: every thread reads it
@@ -405,7 +471,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t g = 0, rbg = 0, li = 0;
         bool ok = true;
         int64_t item = blockIdx.x;
-        const uint64_t pol_codes = l2_evict_first();
+        const uint64_t pol_codes = a.codes_shared ? l2_evict_normal() : l2_evict_first();
         for (;; ++li) {
             const int ib = li & 1;
             if (!mbar_wait_warp(bars + C::b_empty_item(ib), ((li >> 1) & 1) ^ 1, abort_flag, wlim)) {
@@ -451,16 +517,28 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(bars + C::b_full_raw(s), (uint32_t)nb * blk * (F8 ? 2u : 1u));
+                        // whole 32-row tiles of the item's rows only: a block of
+                        // fewer than 128 rows takes its tiles one by one (the rows
+                        // past them are never admitted: the filters test rr < nr)
+                        const int rem = nrows - r;
+                        const uint32_t tiles = (uint32_t)min(RP * MR / 32, (rem + 31) >> 5);
+                        mbar_arrive_expect_tx(bars + C::b_full_raw(s), tiles * 256u * (uint32_t)a.B * (W2 ? 2u : 1u));
                         for (int bb = 0; bb < nb; ++bb) {
-                            const uint32_t dst = smem_u32(sm + Smem::raw + s * slot_bytes + bb * blk * (F8 ? 2 : 1));
+                            const uint32_t dst = smem_u32(sm + Smem::raw + s * slot_bytes + bb * blk * (W2 ? 2 : 1));
                             const int tile = (int)((rb0 + r + bb * MR) >> 5);
-                            // (the second block of the last F8 stage may lie past D: the TMA fills zeros)
-                            tma_load_3d_hint(dst, &codes_map, 0, F8 ? 2 * kb : kb, tile, bars + C::b_full_raw(s),
-                                             pol_codes);
-                            if (F8)
-                                tma_load_3d_hint(dst + blk, &codes_map, 0, 2 * kb + 1, tile, bars + C::b_full_raw(s),
-                                                 pol_codes);
+                            const int nt = min(MR / 32, ((rem - bb * MR) + 31) >> 5);
+                            // (the second block of the last P = 1 stage may lie past D: the TMA fills zeros)
+                            for (int h = 0; h < (W2 ? 2 : 1); ++h) {
+                                const int kk = W2 ? 2 * kb + h : kb;
+                                if (nt == MR / 32) {
+                                    tma_load_3d_hint(dst + h * blk, &codes_map, 0, kk, tile, bars + C::b_full_raw(s),
+                                                     pol_codes);
+                                } else {
+                                    for (int t = 0; t < nt; ++t)
+                                        tma_load_3d_hint(dst + h * blk + t * 256u * (uint32_t)a.B, &codes_map1, 0, kk,
+                                                         tile + t, bars + C::b_full_raw(s), pol_codes);
+                                }
+                            }
                         }
                     }
                     __syncwarp();
@@ -561,8 +639,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_fence_after();
                     for (int bb = 0; bb < nb; ++bb) {                  // warp-uniform
                         uint32_t w[32];
-                        const unsigned char* src = sm + Smem::raw + rs * slot_bytes + bb * blk * (F8 ? 2 : 1) + roff;
-                        if (F8) {
+                        const unsigned char* src = sm + Smem::raw + rs * slot_bytes + bb * blk * (W2 ? 2 : 1) + roff;
+                        if (W2) {
                             // two packed blocks -> 128 e4m3 codes, four per column
 #pragma unroll
                             for (int hb = 0; hb < 2; ++hb) {
@@ -573,6 +651,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                                     w[16 * hb + c] = __byte_perm(half2_to_e4m3_pair(h[2 * c]),
                                                                  half2_to_e4m3_pair(h[2 * c + 1]), 0x6420u);
                             }
+                        } else if (P == 2) {
+                            unpack_split_b(B, src, w);
                         } else {
                             unpack_codes_b(B, src, w);
                         }
@@ -980,7 +1060,7 @@ cudaError_t launch_scan_layout(const uint8_t* codes, const float* g, const float
 // 3-D view of the packed codes in 8-byte elements: (32 B words of a tile and
 // K block, K block, tile); a box of (32 B, 1, 4) is the 128 rows x 8 B bytes
 // of one stage, four contiguous tiles.
-static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np, int D, int B) {
+static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np, int D, int B, int box_tiles) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -994,7 +1074,7 @@ static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np
     const int nkb = D / KB;
     const cuuint64_t dims[3] = {(cuuint64_t)(32 * B), (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
     const cuuint64_t strides[2] = {(cuuint64_t)256 * B, (cuuint64_t)256 * B * nkb};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 * B), 1, MR / 32};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * B), 1, (cuuint32_t)box_tiles};
     const cuuint32_t estr[3] = {1, 1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)codes_p, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1024,32 +1104,42 @@ static bool make_query_map(CUtensorMap* map, const void* base, int64_t nq, int64
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class C, bool F8>
+template <class C, int P>
 static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, const void* qbase, int64_t qrow_bytes,
                                  cudaStream_t s) {
     const int smem = C::Smem::total;
-    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
-    CUtensorMap cmap, qmap;
+    CUtensorMap cmap, cmap1, qmap;
     if (!L.codes_p || ((uintptr_t)L.codes_p & 15) != 0 || (L.D % KB) != 0 || L.B < 1 || L.B > 8 ||
-        !make_codes_map(&cmap, L.codes_p, L.Np, L.D, L.B))
+        !make_codes_map(&cmap, L.codes_p, L.Np, L.D, L.B, MR / 32) ||
+        !make_codes_map(&cmap1, L.codes_p, L.Np, L.D, L.B, 1))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
     if (!qbase || ((uintptr_t)qbase & 15) != 0 || qrow_bytes % 128 != 0 || L.nq < 1 ||
         !make_query_map(&qmap, qbase, L.nq, qrow_bytes))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the query array");
     count_launch();
-    scan_tc_kernel<C, F8><<<L.grid, THREADS, smem, s>>>(cmap, qmap, a);
+    scan_tc_kernel<C, P><<<L.grid, THREADS, smem, s>>>(cmap, cmap1, qmap, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc launch");
     return ERQ_OK;
+}
+
+template <class C>
+static erq_status scan_tc_form(int P, const ScanLaunch& L, const tc::Args& a, const void* qb, int64_t qrow,
+                               cudaStream_t s) {
+    if (P == 1) return scan_tc_launch<C, 1>(L, a, qb, qrow, s);
+    if (P == 2) return scan_tc_launch<C, 2>(L, a, qb, qrow, s);
+    return scan_tc_launch<C, 0>(L, a, qb, qrow, s);
 }
 
 erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     if (!tc_available(precision, L.D, L.kp))
         return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 or fp8 and k' <= 128");
     const bool f8 = precision == ERQ_PREC_FP8;
-    if (f8 && L.B > 4) return fail(ERQ_EUNSUPPORTED, "tensor-core scan: e4m3 holds the centred codes only for B <= 4");
+    const int P = f8 ? (L.B <= 4 ? 1 : 2) : 0;
+    if (P == 2 && L.Dq != 2 * (int64_t)L.D) return fail(ERQ_EINVAL, "tensor-core scan: split e4m3 needs doubled query rows");
     if (!(f8 ? (L.Q8 && L.qscale) : L.Qh != nullptr)) return fail(ERQ_EINVAL, "tensor-core scan: queries missing");
     if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq || !L.work_ctr)
         return fail(ERQ_EINVAL, "tensor-core scan: item tables missing");
@@ -1060,15 +1150,17 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
     a.work_ctr = L.work_ctr;
     a.inter = L.inter; a.inter_cnt = L.inter_cnt; a.tq = L.tq; a.qscale = L.qscale; a.status = L.status;
     a.D = L.D; a.B = L.B; a.kp = L.kp; a.ip = L.ip;
-    a.nkb = f8 ? (int)(L.Dq / 128) : L.D / KB;
+    a.nkb = P == 1 ? (int)(L.Dq / 128) : L.D / KB;
     a.wait_ns = L.wait_ns ? L.wait_ns : kWaitNs;
+    // a cluster probed by more queries than one item holds is read by several
+    // items at about the same time (items are ordered row range first)
+    a.codes_shared = L.nq * (int64_t)L.maxp > (int64_t)L.qn * L.nlist ? 1 : 0;
     a.stall_stage = L.stall_stage;
     const void* qb = f8 ? L.Q8 : L.Qh;
     const int64_t qrow = f8 ? L.Dq : 2 * (int64_t)L.D;
-    if (L.kp <= 32 && L.qn > CfgA::QN)
-        return f8 ? scan_tc_launch<CfgW, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgW, false>(L, a, qb, qrow, s);
-    if (L.kp <= 32) return f8 ? scan_tc_launch<CfgA, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgA, false>(L, a, qb, qrow, s);
-    return f8 ? scan_tc_launch<CfgB, true>(L, a, qb, qrow, s) : scan_tc_launch<CfgB, false>(L, a, qb, qrow, s);
+    if (L.kp <= 32 && L.qn > CfgA::QN) return scan_tc_form<CfgW>(P, L, a, qb, qrow, s);
+    if (L.kp <= 32) return scan_tc_form<CfgA>(P, L, a, qb, qrow, s);
+    return scan_tc_form<CfgB>(P, L, a, qb, qrow, s);
 }
 
 // Rotated queries -> e4m3 for the kind::f8f6f4 scan.  Per query row a power of
@@ -1078,6 +1170,8 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
 // 23-bit mantissa keeps its top 3 bits (carry into the exponent on overflow),
 // below it y is a multiple of 2^-9 after rounding |y| * 2^9 to an integer
 // (8 then being the smallest normal's code).  Columns D .. Dq-1 are zero.
+// With dup (the split form of B = 5..8 codes, Dq = 2 D) every 64-coordinate
+// block is written twice: byte 128 j + t holds coordinate 64 j + (t mod 64).
 // One warp per query row.
 __device__ __forceinline__ uint32_t e4m3_rn(float y) {
     const uint32_t bits = __float_as_uint(y);
@@ -1108,8 +1202,8 @@ __device__ __forceinline__ uint32_t e4m3_rn(float y) {
     return sign | code;
 }
 
-__global__ void quant_e4m3_kernel(const float* __restrict__ X, int64_t n, int D, int Dq, unsigned char* __restrict__ Y,
-                                  float* __restrict__ scale) {
+__global__ void quant_e4m3_kernel(const float* __restrict__ X, int64_t n, int D, int Dq, int dup,
+                                  unsigned char* __restrict__ Y, float* __restrict__ scale) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
@@ -1129,16 +1223,20 @@ __global__ void quant_e4m3_kernel(const float* __restrict__ X, int64_t n, int D,
     for (int i = lane * 4; i < Dq; i += 128) {
         uint32_t w = 0u;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (i + j < D) w |= e4m3_rn(x[i + j] * inv) << (8 * j);
+        for (int j = 0; j < 4; ++j) {
+            const int c = dup ? (((i + j) >> 7) << 6) | ((i + j) & 63) : i + j;
+            if (c < D) w |= e4m3_rn(x[c] * inv) << (8 * j);
+        }
         *reinterpret_cast<uint32_t*>(y + i) = w;
     }
 }
 
-cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, unsigned char* y, float* scale, cudaStream_t s) {
+cudaError_t launch_quant_e4m3(const float* x, int64_t n, int D, int Dq, int dup, unsigned char* y, float* scale,
+                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    if (Dq % 4 != 0 || (dup && Dq != 2 * D) || (!dup && Dq < D)) return cudaErrorInvalidValue;
     count_launch();
-    quant_e4m3_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, s>>>(x, n, D, Dq, y, scale);
+    quant_e4m3_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, s>>>(x, n, D, Dq, dup, y, scale);
     return cudaGetLastError();
 }
 

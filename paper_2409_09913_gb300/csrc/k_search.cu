@@ -266,13 +266,22 @@ __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64
 }
 
 // ---------------------------------------------------------------------------
-// FP32 CUDA-core scan.
-// Item = (cluster c, query chunk, row range).  Tile: 64 queries x 64 rows,
-// 256 threads with 4x4 outputs each, K step 32.  After a tile's dot products
-// the estimates go to shared memory and 64 threads (one per query) push them
-// through their query's max-heap of the k' best (estimate, id) keys.
+// FP32 CUDA-core scan: Eq. 3.3's <2 ybar - (2^B - 1), q'> by FFMA.
+// Item = (cluster c, query chunk, row range).  Tile: 64 queries x 128 rows,
+// 128 threads with 8 x 8 outputs each (queries 4 tq .. 4 tq + 3 and 32 + 4 tq
+// .. + 3, rows 4 tr .. + 3 and 64 + 4 tr .. + 3: four 16-byte shared loads per
+// 64 FFMA), K step 32.  The operands of step k + 1 are loaded from global
+// memory into registers while step k is multiplied out of the other shared
+// buffer (one barrier per step); codes are widened to 2 ybar - (2^B - 1) as
+// they are stored.  After a tile the estimates go to shared memory (over the
+// operand buffers) and 64 threads (one per query) push those that beat their
+// heap's root through the query's max-heap of the k' best (estimate, id) keys.
 // ---------------------------------------------------------------------------
-constexpr int SC_QT = 64, SC_RB = 64, SC_BK = 32;
+constexpr int SC_QT = 64, SC_RB = 128, SC_BK = 32, SC_THREADS = 128;
+constexpr int SC_QS = SC_QT + 4, SC_CS = SC_RB + 4;      // padded rows of the transposed operand tiles
+constexpr int SC_OPS = 2 * SC_BK * (SC_QS + SC_CS) * 4;  // two buffers of both operands, bytes
+constexpr int SC_EST = SC_QT * (SC_RB + 1) * 4;          // estimate tile (aliases the operand buffers)
+static_assert(SC_EST <= SC_OPS, "estimate tile fits the operand buffers");
 
 struct ScanArgs {
     const float* Qrot;          // [nq][D]
@@ -290,19 +299,50 @@ struct ScanArgs {
     const int64_t* qbase;       // [nq+1]
     uint64_t* inter;            // [L][kp]
     int32_t* inter_cnt;         // [L]
+    int64_t nq, N;              // extents of Qrot and of the stored rows (device-side checks)
     int maxp, D, B, kp, RR, nlist;
     int ip;                     // inner-product metric: est = -<c, q_r> + (f_res / 4) <2 ybar, q'>
     DevChecks ck;
 };
 
-__global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
+// Register-staged operands of one K step: 16 query values of query (tid & 63)
+// at k0 + 16 (tid >> 6), and the 32 codes of row tid at k0.
+struct Fp32Stage {
+    float4 q[4];
+    uint4 c[2];
+};
+
+__device__ __forceinline__ void fp32_load(Fp32Stage& st, const float* qrow, const uint8_t* crow, int k0, int tid) {
+    const int kq = (tid >> 6) * 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        st.q[j] = qrow ? __ldg(reinterpret_cast<const float4*>(qrow + k0 + kq) + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        st.c[j] = crow ? __ldg(reinterpret_cast<const uint4*>(crow + k0) + j) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ void fp32_store(const Fp32Stage& st, float* qs, float* cs, int tid, float off) {
+    const int qi = tid & 63, kq = (tid >> 6) * 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        qs[(kq + 4 * j + 0) * SC_QS + qi] = st.q[j].x;
+        qs[(kq + 4 * j + 1) * SC_QS + qi] = st.q[j].y;
+        qs[(kq + 4 * j + 2) * SC_QS + qi] = st.q[j].z;
+        qs[(kq + 4 * j + 3) * SC_QS + qi] = st.q[j].w;
+    }
+    const uint32_t w[8] = {st.c[0].x, st.c[0].y, st.c[0].z, st.c[0].w, st.c[1].x, st.c[1].y, st.c[1].z, st.c[1].w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cs[(4 * j + b) * SC_CS + tid] = fmaf(2.f, (float)((w[j] >> (8 * b)) & 0xffu), -off);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float (*qs)[SC_QT + 4] = reinterpret_cast<float (*)[SC_QT + 4]>(smem);                         // [BK][QT+4]
-    float (*cs)[SC_RB + 4] = reinterpret_cast<float (*)[SC_RB + 4]>(smem + SC_BK * (SC_QT + 4) * 4); // [BK][RB+4]
-    float (*E)[SC_RB + 1] = reinterpret_cast<float (*)[SC_RB + 1]>(smem + SC_BK * (SC_QT + 4) * 4 +
-                                                                   SC_BK * (SC_RB + 4) * 4);        // [QT][RB+1]
-    uint64_t* heap = reinterpret_cast<uint64_t*>(smem + SC_BK * (SC_QT + 4) * 4 + SC_BK * (SC_RB + 4) * 4 +
-                                                 SC_QT * (SC_RB + 1) * 4 + 16);                     // [kp][QT]
+    float* ops = reinterpret_cast<float*>(smem);     // buffer b: queries at b * BK * (QS + CS), codes after them
+    float (*E)[SC_RB + 1] = reinterpret_cast<float (*)[SC_RB + 1]>(smem);
+    uint64_t* heap = reinterpret_cast<uint64_t*>(smem + SC_OPS + 16);                      // [kp][QT]
     __shared__ int64_t s_q[SC_QT];
     __shared__ int64_t s_list[SC_QT];
     __shared__ float s_dqc[SC_QT];
@@ -311,7 +351,7 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
     __shared__ uint32_t s_id[SC_RB];
 
     const int tid = threadIdx.x;
-    const int tq = tid % 16, tr = tid / 16;
+    const int tq = tid & 7, tr = tid >> 3;
     const int D = a.D;
     const float off = (float)((1 << a.B) - 1);
     int64_t nitems = *a.n_items;
@@ -325,86 +365,82 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
         const int64_t rb0 = a.list_off[c] + (int64_t)item.z * a.RR;
         const int64_t rb1 = imin64(a.list_off[c + 1], rb0 + a.RR);
         if (tid < SC_QT) {
-            if (tid < nqi) {
+            s_q[tid] = -1;
+            if (tid < nqi && ERQ_DCHECK(qb + tid >= 0 && qb + tid < a.ck.qlist, a.ck.status, 5)) {
                 const int64_t e = a.qlist[qb + tid];
                 const int64_t q = e / a.maxp;
-                s_q[tid] = q;
-                s_dqc[tid] = a.dqc[e];
-                s_list[tid] = a.qbase[q] + a.slot_off[e] + item.z;
-            } else {
-                s_q[tid] = -1;
+                if (ERQ_DCHECK(q >= 0 && q < a.nq, a.ck.status, 5)) {
+                    s_q[tid] = q;
+                    s_dqc[tid] = a.dqc[e];
+                    s_list[tid] = a.qbase[q] + a.slot_off[e] + item.z;
+                }
             }
             s_hsize[tid] = 0;
         }
         __syncthreads();
+        const int64_t qsel = s_q[tid & 63];
+        const float* qrow = qsel >= 0 ? a.Qrot + qsel * D : nullptr;
         for (int64_t r0 = rb0; r0 < rb1; r0 += SC_RB) {
             const int nr = (int)imin64(SC_RB, rb1 - r0);
-            if (tid < SC_RB) {
-                if (tid < nr) {
-                    s_g[tid] = a.ip ? 0.f : a.g_const[r0 + tid];
-                    s_fh[tid] = (a.ip ? 0.25f : 0.5f) * a.f_res[r0 + tid];
-                    s_id[tid] = (uint32_t)a.list_ids[r0 + tid];
-                }
+            const bool row_ok = tid < nr && ERQ_DCHECK(r0 + tid >= 0 && r0 + tid < a.N, a.ck.status, 5);
+            if (row_ok) {
+                s_g[tid] = a.ip ? 0.f : a.g_const[r0 + tid];
+                s_fh[tid] = (a.ip ? 0.25f : 0.5f) * a.f_res[r0 + tid];
+                s_id[tid] = (uint32_t)a.list_ids[r0 + tid];
             }
-            float acc[4][4];
+            const uint8_t* crow = row_ok ? a.codes + (r0 + tid) * D : nullptr;
+            float acc[8][8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            for (int k0 = 0; k0 < D; k0 += SC_BK) {
-                // queries: 64 x 32 floats, 8 per thread
-                {
-                    const int qi = tid / 4, kk = (tid % 4) * 8;
-                    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                    if (qi < nqi) {
-                        const float* src = a.Qrot + s_q[qi] * D + k0 + kk;
-                        v0 = *reinterpret_cast<const float4*>(src);
-                        v1 = *reinterpret_cast<const float4*>(src + 4);
-                    }
-                    qs[kk + 0][qi] = v0.x; qs[kk + 1][qi] = v0.y; qs[kk + 2][qi] = v0.z; qs[kk + 3][qi] = v0.w;
-                    qs[kk + 4][qi] = v1.x; qs[kk + 5][qi] = v1.y; qs[kk + 6][qi] = v1.z; qs[kk + 7][qi] = v1.w;
-                }
-                // codes: 64 rows x 32 bytes, 8 per thread, centred 2*ybar
-                {
-                    const int ri = tid / 4, kk = (tid % 4) * 8;
-                    uint2 u = make_uint2(0u, 0u);
-                    if (ri < nr) u = *reinterpret_cast<const uint2*>(a.codes + (r0 + ri) * D + k0 + kk);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        cs[kk + b][ri] = 2.f * (float)((u.x >> (8 * b)) & 0xffu) - off;
-                        cs[kk + 4 + b][ri] = 2.f * (float)((u.y >> (8 * b)) & 0xffu) - off;
-                    }
-                }
-                __syncthreads();
-#pragma unroll 8
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            Fp32Stage st;
+            fp32_load(st, qrow, crow, 0, tid);
+            fp32_store(st, ops, ops + SC_BK * SC_QS, tid, off);
+            __syncthreads();
+            int buf = 0;
+            for (int k0 = 0; k0 < D; k0 += SC_BK, buf ^= 1) {
+                const bool more = k0 + SC_BK < D;
+                if (more) fp32_load(st, qrow, crow, k0 + SC_BK, tid);
+                const float* qs = ops + buf * SC_BK * (SC_QS + SC_CS);
+                const float* cs = qs + SC_BK * SC_QS;
+#pragma unroll 4
                 for (int kk = 0; kk < SC_BK; ++kk) {
-                    const float4 qv = *reinterpret_cast<const float4*>(&qs[kk][tq * 4]);
-                    const float4 cv = *reinterpret_cast<const float4*>(&cs[kk][tr * 4]);
-                    const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-                    const float ca[4] = {cv.x, cv.y, cv.z, cv.w};
+                    const float4 q0 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + tq * 4);
+                    const float4 q1 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + 32 + tq * 4);
+                    const float4 c0 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + tr * 4);
+                    const float4 c1 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + 64 + tr * 4);
+                    const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                    const float ca[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                }
+                if (more) {
+                    float* nq = ops + (buf ^ 1) * SC_BK * (SC_QS + SC_CS);
+                    fp32_store(st, nq, nq + SC_BK * SC_QS, tid, off);
                 }
                 __syncthreads();
             }
-            // estimates to shared memory
+            // estimates to shared memory (the operand buffers are free: the
+            // last step ended with a barrier)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int qi = tq * 4 + i, ri = tr * 4 + j;
+                for (int j = 0; j < 8; ++j) {
+                    const int qi = (i < 4 ? 0 : 32) + tq * 4 + (i & 3), ri = (j < 4 ? 0 : 64) + tr * 4 + (j & 3);
                     float e = INFINITY;
                     if (qi < nqi && ri < nr) e = s_dqc[qi] + s_g[ri] + s_fh[ri] * acc[i][j];
                     E[qi][ri] = e;
                 }
             __syncthreads();
             // heap update, one thread per query
-            if (tid < nqi) {
+            if (tid < nqi && s_q[tid] >= 0) {
                 const int q = tid;
                 int hs = s_hsize[q];
                 const int kp = a.kp;
+                uint64_t root = hs > 0 ? heap[q] : 0ull;
                 for (int r = 0; r < nr; ++r) {
                     const uint64_t key = make_key(E[q][r], s_id[r]);
                     if (hs < kp) {  // sift up into a max-heap
@@ -417,7 +453,8 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
                             j = p;
                         }
                         heap[j * SC_QT + q] = key;
-                    } else if (key < heap[q]) {  // replace the root, sift down
+                        root = heap[q];
+                    } else if (key < root) {  // replace the root, sift down
                         int j = 0;
                         for (;;) {
                             const int l = 2 * j + 1;
@@ -433,6 +470,7 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
                             j = m;
                         }
                         heap[j * SC_QT + q] = key;
+                        root = heap[q];
                     }
                 }
                 s_hsize[q] = hs;
@@ -440,7 +478,7 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
             __syncthreads();
         }
         // write the item's lists
-        if (tid < nqi && ERQ_DCHECK(s_list[tid] >= 0 && s_list[tid] < a.ck.lists, a.ck.status, 4)) {
+        if (tid < nqi && s_q[tid] >= 0 && ERQ_DCHECK(s_list[tid] >= 0 && s_list[tid] < a.ck.lists, a.ck.status, 4)) {
             const int hs = s_hsize[tid];
             const int64_t L = s_list[tid];
             uint64_t* dst = a.inter + L * a.kp;
@@ -451,9 +489,15 @@ __global__ void __launch_bounds__(256) scan_fp32_kernel(ScanArgs a) {
     }
 }
 
-size_t scan_fp32_smem(int kp) {
-    return (size_t)SC_BK * (SC_QT + 4) * 4 + (size_t)SC_BK * (SC_RB + 4) * 4 + (size_t)SC_QT * (SC_RB + 1) * 4 + 16 +
-           (size_t)kp * SC_QT * 8;
+size_t scan_fp32_smem(int kp) { return (size_t)SC_OPS + 16 + (size_t)kp * SC_QT * 8; }
+
+int scan_fp32_blocks_per_sm(int kp) {
+    int n = 1;
+    const size_t smem = scan_fp32_smem(kp);
+    if (cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_fp32_kernel, SC_THREADS, smem) != cudaSuccess || n < 1)
+        return 1;
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -748,6 +792,12 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_excl_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+    count_launch();
+    excl_scan_i64_kernel<<<dim3(1, 1), 1024, 0, s>>>(in, out, nullptr, nullptr, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s) {
     count_launch();
     plan_items_kernel<<<(unsigned)ceil_div(2 * p.nlist, 256), 256, 0, s>>>(p.cnt64, p.list_off, p.item_off,
@@ -762,12 +812,14 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
     a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
     a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip; a.nlist = L.nlist;
+    a.nq = L.nq; a.N = L.N;
     const size_t smem = scan_fp32_smem(L.kp);
     cudaError_t e = cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (L.grid <= 0) return cudaSuccess;
+    if (L.D % SC_BK != 0) return cudaErrorInvalidValue;
     count_launch();
-    scan_fp32_kernel<<<L.grid, 256, smem, s>>>(a);
+    scan_fp32_kernel<<<L.grid, SC_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ["erq_version", "erq_last_error", "erq_build_index", "erq_free_index",
            "erq_search_backward", "erq_index_export", "erq_index_save", "erq_index_load", "erq_search_timing",
            "erq_kernel_launches", "erq_search_stats", "erq_search_backward_noalloc", "erq_search_timing_total",
            "erq_autotune", "erq_set_scan_config", "erq_scan_config", "erq_estimate_metric",
-           "erq_search_backward_metric", "erq_merge_topk", "erq_rerank_ids", "erq_set_wait_limit"]
+           "erq_search_backward_metric", "erq_merge_topk", "erq_rerank_ids", "erq_set_wait_limit",
+           "erq_search_two_stage"]
 
 
 class ErqError(RuntimeError):
@@ -99,6 +100,7 @@ def lib(path: str | None = None):
     L.erq_merge_topk.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
     L.erq_rerank_ids.argtypes = [vp, vp, i64, i32, vp, i32, i32, vp, vp, vp]
     L.erq_set_wait_limit.argtypes = [vp, ct.c_uint64, i64]
+    L.erq_search_two_stage.argtypes = [vp, vp, i64, ct.POINTER(SearchParams), ct.c_float, vp, vp, vp, vp]
     for name in ("erq_build_index", "erq_index_info_get", "erq_index_status", "erq_rotate", "erq_encode",
                  "erq_search", "erq_search_host", "erq_estimate", "erq_search_backward", "erq_index_export",
                  "erq_index_save", "erq_index_load", "erq_search_timing",
@@ -254,6 +256,41 @@ class Index:
         if return_candidates:
             return ids, dists, cand_ids, cand_est
         return ids, dists
+
+    def search_two_stage(self, Q, k, *, rerank_k=0, nprobe=1, eps0=1.9, probe=None, nprobe_per_query=None,
+                         return_candidates=False, return_stats=False):
+        """erq_search_two_stage (Section 4.2, metric l2): MSB-plane estimates
+        with Lemma 2.1's bound (eps0) prune the probed rows, Eq. 4.2 completes
+        the survivors.  return_stats adds (probed rows, survivors)."""
+        Q = _dev(Q, torch.float32, "Q", 2)
+        nq = Q.shape[0]
+        sp = SearchParams()
+        sp.k, sp.rerank_k, sp.nprobe, sp.precision = int(k), int(rerank_k), int(nprobe), PREC["fp32"]
+        keep = []
+        if nprobe_per_query is not None:
+            nprobe_per_query = _dev(nprobe_per_query, torch.int32, "nprobe_per_query", 1)
+            keep.append(nprobe_per_query)
+            sp.nprobe_per_query = nprobe_per_query.data_ptr()
+        if probe is not None:
+            probe = _dev(probe, torch.int32, "probe", 2)
+            keep.append(probe)
+            sp.probe = probe.data_ptr()
+            sp.probe_stride = probe.shape[1]
+        kc = max(int(k), int(rerank_k))
+        cand_ids = cand_est = None
+        if return_candidates:
+            cand_ids = torch.empty((nq, kc), dtype=torch.int64, device=Q.device)
+            cand_est = torch.empty((nq, kc), dtype=torch.float32, device=Q.device)
+            sp.cand_ids, sp.cand_est = cand_ids.data_ptr(), cand_est.data_ptr()
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        st = (ct.c_int64 * 2)()
+        _check(lib().erq_search_two_stage(self._h, _ptr(Q), nq, ct.byref(sp), ct.c_float(eps0), _ptr(ids),
+                                          _ptr(dists), st if return_stats else None, _stream()))
+        out = (ids, dists) + ((cand_ids, cand_est) if return_candidates else ())
+        if return_stats:
+            out = out + ((int(st[0]), int(st[1])),)
+        return out
 
     def timing(self):
         """Per-phase device ms of the last timed search: rotate, probe, plan, scan, merge, rerank."""

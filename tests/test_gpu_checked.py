@@ -31,7 +31,7 @@ SCRIPT = textwrap.dedent("""
                              assign=torch.from_numpy(assign).to(dev))
         Q = torch.from_numpy(S.mixture(700, D, 16, 4203, comp_seed=4200 + D, scale="aniso")[0]).to(dev)
         npr = torch.from_numpy(np.random.default_rng(4204).integers(1, 13, 700).astype(np.int32)).to(dev)
-        precs = ("fp32", "fp16", "fp8") if B <= 4 else ("fp32", "fp16")
+        precs = ("fp32", "fp16", "fp8")
         for prec in precs:
             for kp in (20, 100):
                 for am in (False, True):

@@ -135,9 +135,11 @@ def test_ip_full_probe_rerank_is_exact_mips(erq):
     compare_topk_ids(ids.cpu().numpy(), ref, refv, what="exact MIPS", radius=1.5 * RTOL * np.repeat(sc, 11, 1))
 
 
-def test_ip_fp8_recall_close_to_fp32(erq):
-    """The e4m3 scan (B <= 4) ranks by the same inner-product estimate."""
-    X, gx, ox = _pair(erq, 20000, 128, 4, 32, 4500)
+@pytest.mark.parametrize("B", [4, 6])
+def test_ip_fp8_recall_close_to_fp32(erq, B):
+    """The e4m3 scan (B = 4 direct, B = 6 split) ranks by the same
+    inner-product estimate."""
+    X, gx, ox = _pair(erq, 20000, 128, B, 32, 4500)
     Q, _ = S.mixture(300, 128, 16, 4501, comp_seed=4500, scale="aniso")
     a, _ = gx.search(to_dev(Q), 10, rerank_k=32, nprobe=6, precision="fp32", metric="ip")
     b, _ = gx.search(to_dev(Q), 10, rerank_k=32, nprobe=6, precision="fp8", metric="ip")

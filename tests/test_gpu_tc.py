@@ -224,12 +224,15 @@ def _bound_fp8(ox, Q, ids):
     return 0.5 * np.abs(f_res[rows]).astype(np.float64) * t
 
 
-@pytest.mark.parametrize("D,B,kp", [(128, 4, 32), (960, 4, 24), (128, 2, 100), (192, 3, 32)])
+@pytest.mark.parametrize("D,B,kp", [(128, 4, 32), (960, 4, 24), (128, 2, 100), (192, 3, 32),
+                                    (128, 5, 32), (192, 7, 24), (256, 8, 100), (128, 6, 32), (960, 7, 32)])
 def test_fp8_scan_within_e4m3_bound(erq, D, B, kp):
-    """kind::f8f6f4 scan (e4m3 codes and queries, 128 coordinates per stage; D =
-    960 and 192 end in half a stage): every candidate estimate lies within the
-    query-rounding bound of the oracle's exact estimate, and the re-ranked
-    top-10 equals the oracle's exact re-rank of the same candidates."""
+    """kind::f8f6f4 scan (e4m3 queries; B <= 4: e4m3 codes, 128 coordinates
+    per stage, D = 960 and 192 ending in half a stage; B = 5..8: codes split
+    into 16 hc + lc, 64 coordinates per stage): every candidate estimate lies
+    within the query-rounding bound of the oracle's exact estimate, the
+    selected set is valid, and the re-ranked top-10 equals the exact re-rank of
+    the same candidates."""
     X, P, gx, ox = _index(erq, 12000, D, B, 32, 3900 + D + B)
     Q, _ = S.mixture(400, D, 16, 3901 + D, comp_seed=3900 + D + B, scale="aniso")
     probe = S.random_probe_lists(400, 32, 6, 3902 + D)
@@ -273,8 +276,14 @@ def test_fp8_recall_close_to_fp32(erq):
     assert rb >= ra - 0.01, (ra, rb)
 
 
-def test_fp8_rejects_wide_codes(erq):
-    X, P, gx, ox = _index(erq, 3000, 128, 5, 8, 4100)
-    Q = to_dev(S.mixture(4, 128, 16, 4101, comp_seed=4100, scale="aniso")[0])
-    with pytest.raises(erq.ErqError, match="B <= 4"):
-        gx.search(Q, 10, rerank_k=20, nprobe=2, precision="fp8")
+def test_fp8_split_recall_close_to_fp32(erq):
+    """B = 7 (the precision workload's code width) in the split e4m3 form:
+    recall@10 after the exact re-rank stays within 0.01 of the FP32 scan's."""
+    X, P, gx, ox = _index(erq, 30000, 256, 7, 32, 4100)
+    Q, _ = S.mixture(500, 256, 16, 4101, comp_seed=4100, scale="aniso")
+    a_ids, _ = gx.search(to_dev(Q), 10, rerank_k=40, nprobe=6, precision="fp32")
+    b_ids, _ = gx.search(to_dev(Q), 10, rerank_k=40, nprobe=6, precision="fp8")
+    gt, _ = oracle.exact_knn(X, Q, 10)
+    rec = lambda ids: np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy(), gt)])
+    ra, rb = rec(a_ids), rec(b_ids)
+    assert rb >= ra - 0.01, (ra, rb)
