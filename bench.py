@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--metric", default="l2", choices=["l2", "ip"],
                     help="l2: nearest by squared distance; ip: largest inner product (recall against exact MIPS)")
     ap.add_argument("--cpu-sample", type=int, default=16, help="at most this many queries in the timed oracle sample")
+    ap.add_argument("--cpu-sample-rows", type=int, default=256,
+                    help="rows of the oracle's timed sample in --workload encoder_table4")
     ap.add_argument("--cpu-rows", type=int, default=150_000,
                     help="the oracle sample takes queries in order while the rows of their probed clusters stay "
                          "within this many (at least one query)")
@@ -407,6 +409,14 @@ def run_encoder_sweep(args):
     R = erq.rotate(Xc, P, accurate=True)          # the rotation Table 4 includes (FP64 accumulation)
     torch.cuda.synchronize()
     rot_s = 1e6 * (time.perf_counter() - t0) / n
+    # the oracle's rotation and Algorithm 1 on the host cores, on a bounded sample of the same rows
+    import oracle
+    m = min(n, args.cpu_sample_rows)
+    Xs = Xc[:m].cpu().numpy()
+    Ps = P.cpu().numpy()
+    t0 = time.perf_counter()
+    Rs = oracle.rotate(Xs, Ps)
+    orot_s = 1e6 * (time.perf_counter() - t0) / m
     for B in range(1, 9):
         erq.encode(R[:1024], B)
         torch.cuda.synchronize()
@@ -414,10 +424,18 @@ def run_encoder_sweep(args):
         erq.encode(R, B)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.quantize(Rs, B)
+        odt = time.perf_counter() - t0
         print(json.dumps({"metric": "encoder rows/s (Algorithm 1, D = 3072)", "B": B, "value": n / dt,
                           "unit": "rows/s", "rows": n, "critical_values_per_s": n * d * (2 ** (B - 1) - 1) / dt,
                           "seconds_per_1e6_rows": 1e6 * dt / n, "rotate_seconds_per_1e6_rows": rot_s,
                           "rotate_plus_encode_seconds_per_1e6_rows": rot_s + 1e6 * dt / n,
+                          "cpu_baseline": {"value": m / odt, "unit": "rows/s", "cores": oracle.num_threads(),
+                                           "kind": "oracle", "sample": f"{m} of the same rows",
+                                           "seconds_per_1e6_rows": 1e6 * odt / m,
+                                           "rotate_seconds_per_1e6_rows": orot_s,
+                                           "rotate_plus_encode_seconds_per_1e6_rows": orot_s + 1e6 * odt / m},
                           "data": "synthetic"}), flush=True)
     return 0
 

@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
 
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 item = a.items[it];
+        if (!ERQ_DCHECK(item.x >= 0 && item.x < 2 * a.nlist, a.ck.status, 5)) continue;   // block-uniform
         const int v = item.x, c = v % a.nlist;                  // phase cluster -> cluster
         const int64_t qb = a.qoff[v] + (int64_t)item.y * SC_QT;
         const int nqi = (int)imin64(SC_QT, a.qoff[v + 1] - qb);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
             if (tid < nqi && ERQ_DCHECK(qb + tid >= 0 && qb + tid < a.ck.qlist, a.ck.status, 5)) {
                 const int64_t e = a.qlist[qb + tid];
                 const int64_t q = e / a.maxp;
-                if (ERQ_DCHECK(q >= 0 && q < a.nq, a.ck.status, 5)) {
+                if (ERQ_DCHECK(e >= 0 && e < a.ck.qlist && q < a.nq, a.ck.status, 5)) {
                     s_q[tid] = q;
                     s_dqc[tid] = a.dqc[e];
                     s_list[tid] = a.qbase[q] + a.slot_off[e] + item.z;
