@@ -153,10 +153,10 @@ static orc_event heap_pop(orc_event* h, int* n, const double* a)
 }
 
 /* Quantize one rotated residual rp[0..d-1] with B bits per coordinate.
- * Writes the unsigned code ybar_u (one byte per coordinate, B <= 8) and
+ * Writes the unsigned code ybar_u (16 bits per coordinate, B <= 9) and
  * stats[0..4] = { <ybar,|o'|> (ip at the optimum), ||ybar||^2, v_max,
  * ||o'||^2, number of events }. */
-void orc_quantize(const float* rp, int d, int B, uint8_t* code, double* stats)
+void orc_quantize(const float* rp, int d, int B, uint16_t* code, double* stats)
 {
     const int M = (1 << (B - 1)) - 1;           /* events per coordinate */
     const int half = 1 << (B - 1);
@@ -201,7 +201,7 @@ void orc_quantize(const float* rp, int d, int B, uint8_t* code, double* stats)
     }
     /* ybar_u = ybar + (2^B-1)/2: +(m+1/2) -> half+m, -(m+1/2) -> half-1-m (R6). */
     for (int i = 0; i < d; ++i)
-        code[i] = (uint8_t)(rp[i] >= 0.0f ? half + m[i] : half - 1 - m[i]);
+        code[i] = (uint16_t)(rp[i] >= 0.0f ? half + m[i] : half - 1 - m[i]);
     stats[0] = ip_best;
     stats[1] = n2_best;
     stats[2] = vmax;
@@ -212,7 +212,7 @@ void orc_quantize(const float* rp, int d, int B, uint8_t* code, double* stats)
     free(heap);
 }
 
-void orc_quantize_batch(const float* Rp, int64_t n, int d, int B, uint8_t* codes, double* stats)
+void orc_quantize_batch(const float* Rp, int64_t n, int d, int B, uint16_t* codes, double* stats)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i)
@@ -258,7 +258,7 @@ static void query_side(const double* q, const float* c, const float* P, int d,
     *sum_qp = s;
 }
 
-static double estimate_one(const uint8_t* code, const double* st, int d, int B,
+static double estimate_one(const uint16_t* code, const double* st, int d, int B,
                            const double* qp, double sum_qp, double qc_norm)
 {
     double nr, inv;
@@ -273,7 +273,7 @@ static double estimate_one(const uint8_t* code, const double* st, int d, int B,
 
 /* R9: estimated inner product <o_r, q_r>.  qp = P^{-1} q^ with q^ = q_r/||q_r||
  * (query_ip_side), sum_qp = sum_i qp[i], q_norm = ||q_r||, c_q = <c, q_r>. */
-static double estimate_ip_one(const uint8_t* code, const double* st, int d, int B,
+static double estimate_ip_one(const uint16_t* code, const double* st, int d, int B,
                               const double* qp, double sum_qp, double q_norm, double c_q)
 {
     double nr, inv;
@@ -314,7 +314,7 @@ typedef struct {
     const float* C;
     const int64_t* list_off;
     const int64_t* list_ids;
-    const uint8_t* codes;
+    const uint16_t* codes;
     const double* stats;
     const float* X;
 } orc_index;
@@ -389,7 +389,7 @@ static void search_one(const orc_index* ix, const double* q, int nprobe, const i
         else
             query_side(q, ix->C + (size_t)c * d, ix->P, d, qn, qp, &sum_qp, &qc_norm);
         for (int64_t r = ix->list_off[c]; r < ix->list_off[c + 1]; ++r) {
-            const uint8_t* code = ix->codes + (size_t)r * d;
+            const uint16_t* code = ix->codes + (size_t)r * d;
             const double* st = ix->stats + (size_t)r * 5;
             cand[w].key = metric ? -estimate_ip_one(code, st, d, ix->B, qp, sum_qp, q_norm, c_q)
                                  : estimate_one(code, st, d, ix->B, qp, sum_qp, qc_norm);
@@ -419,7 +419,7 @@ static void search_one(const orc_index* ix, const double* q, int nprobe, const i
 }
 
 void orc_search(int d, int B, int nlist, const float* P, const float* C, const int64_t* list_off,
-                const int64_t* list_ids, const uint8_t* codes, const double* stats, const float* X,
+                const int64_t* list_ids, const uint16_t* codes, const double* stats, const float* X,
                 const double* Q, int64_t nq, const int32_t* nprobe, const int32_t* probe_in, int max_probe,
                 int kprime, int k, int metric, int64_t* ids, double* dists, int64_t* cand_ids, double* cand_est,
                 int32_t* probe_out)
@@ -449,7 +449,7 @@ void orc_centroid_dists(const float* C, int nlist, int d, const double* Q, int64
 /* Estimated distance (metric 0) or inner product (metric 1, R9) for explicit
  * (query, stored row) pairs; rows index the cluster-major arrays and cl gives
  * the cluster of each row. */
-void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint8_t* codes, const double* stats,
+void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint16_t* codes, const double* stats,
                        const double* Q, int64_t nq, int nc, const int64_t* rows, const int32_t* cl, int metric,
                        double* out)
 {
@@ -483,7 +483,7 @@ void orc_estimate_rows(int d, int B, const float* P, const float* C, const uint8
  *   est = ||o'||^2 + ||q_r - c||^2 + f * <ybar, P^T (q_r - c)>,
  *   f   = -2 ||o_r - c|| * inv,  ybar = ybar_u - (2^B-1)/2,
  * so d est / d q_r = 2 (q_r - c) + f * P ybar.  grad_q = sum_j g_j d est_j/d q_r. */
-void orc_backward(int d, int B, const float* P, const float* C, const uint8_t* codes, const double* stats,
+void orc_backward(int d, int B, const float* P, const float* C, const uint16_t* codes, const double* stats,
                   const double* Q, int64_t nq, int nc, const int64_t* rows, const int32_t* cl,
                   const double* g, int metric, double* grad)
 {
@@ -502,7 +502,7 @@ void orc_backward(int d, int B, const float* P, const float* C, const uint8_t* c
                 vec_factors(stats + (size_t)r * 5, &nr, &inv);
                 const double f = -2.0 * nr * inv;
                 const float* c = C + (size_t)cl[r] * d;
-                const uint8_t* code = codes + (size_t)r * d;
+                const uint16_t* code = codes + (size_t)r * d;
                 for (int k = 0; k < d; ++k) v[k] = (double)code[k] - 0.5 * (double)((1 << B) - 1);
                 for (int k = 0; k < d; ++k) {
                     double pv = 0.0;                /* (P ybar)[k] */

@@ -41,7 +41,7 @@ _f32 = _P(np.float32, flags="C_CONTIGUOUS")
 _f64 = _P(np.float64, flags="C_CONTIGUOUS")
 _i32 = _P(np.int32, flags="C_CONTIGUOUS")
 _i64 = _P(np.int64, flags="C_CONTIGUOUS")
-_u8 = _P(np.uint8, flags="C_CONTIGUOUS")
+_u16 = _P(np.uint16, flags="C_CONTIGUOUS")
 
 
 class _Opt:
@@ -63,14 +63,14 @@ def lib():
         L = ct.CDLL(path)
         L.orc_centroids.argtypes = [_f32, ct.c_int64, ct.c_int, _i32, ct.c_int, _f32]
         L.orc_rotate.argtypes = [_f32, _Opt(np.float32), _Opt(np.int32), ct.c_int64, ct.c_int, _f32, _f32]
-        L.orc_quantize_batch.argtypes = [_f32, ct.c_int64, ct.c_int, ct.c_int, _u8, _f64]
-        L.orc_search.argtypes = [ct.c_int, ct.c_int, ct.c_int, _f32, _f32, _i64, _i64, _u8, _f64, _f32,
+        L.orc_quantize_batch.argtypes = [_f32, ct.c_int64, ct.c_int, ct.c_int, _u16, _f64]
+        L.orc_search.argtypes = [ct.c_int, ct.c_int, ct.c_int, _f32, _f32, _i64, _i64, _u16, _f64, _f32,
                                  _f64, ct.c_int64, _i32, _Opt(np.int32), ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                  _i64, _f64, _Opt(np.int64), _Opt(np.float64), _Opt(np.int32)]
         L.orc_centroid_dists.argtypes = [_f32, ct.c_int, ct.c_int, _f64, ct.c_int64, _f64]
-        L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
+        L.orc_estimate_rows.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u16, _f64, _f64, ct.c_int64, ct.c_int,
                                         _i64, _i32, ct.c_int, _f64]
-        L.orc_backward.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u8, _f64, _f64, ct.c_int64, ct.c_int,
+        L.orc_backward.argtypes = [ct.c_int, ct.c_int, _f32, _f32, _u16, _f64, _f64, ct.c_int64, ct.c_int,
                                    _i64, _i32, _f64, ct.c_int, _f64]
         L.orc_num_threads.restype = ct.c_int
         _lib = L
@@ -103,11 +103,11 @@ def rotate(X, P, C=None, assign=None):
 
 
 def quantize(Rp, B):
-    """Algorithm 1 on each row.  Returns (codes uint8 [n,d], stats float64 [n,5]);
+    """Algorithm 1 on each row.  Returns (codes uint16 [n,d], stats float64 [n,5]);
     stats = (<ybar,|o'|>, ||ybar||^2, v_max, ||o'||^2, events)."""
     Rp = _c32(np.atleast_2d(Rp))
     n, d = Rp.shape
-    codes = np.empty((n, d), np.uint8)
+    codes = np.empty((n, d), np.uint16)
     stats = np.empty((n, 5), np.float64)
     lib().orc_quantize_batch(Rp, n, d, int(B), codes, stats)
     return codes, stats

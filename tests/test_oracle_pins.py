@@ -56,6 +56,24 @@ def test_alg1_equals_brute_force(B, d):
             assert any((h == codes[i]).all() for h in hits), (kind, R[i], codes[i], hits)
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_alg1_b9_equals_brute_force(d):
+    """B = 9 (Section 5.1 evaluates B up to 9 and more): Algorithm 1 against
+    enumeration of all 2^(9 D) grid vectors (512 and 262,144)."""
+    n = 60 if d == 2 else 200
+    for kind, seed in (("gauss", 15), ("ties", 16), ("sparse", 17)):
+        R = S.random_rotated_residuals(n, d, seed + 100 * d, kind=kind)
+        codes, st = oracle.quantize(R, 9)
+        assert codes.max() <= 511
+        for i in range(n):
+            if not np.any(R[i]):
+                continue
+            best, hits = oracle.brute_force_quantize(R[i], 9)
+            v = st[i, 2] / math.sqrt(st[i, 3])
+            assert v == pytest.approx(best, rel=1e-13, abs=1e-15), (kind, R[i], codes[i])
+            assert any((h == codes[i]).all() for h in hits), (kind, R[i], codes[i], hits)
+
+
 def test_alg1_b1_is_rabitq_sign_code():
     """B = 1: the codebook is RaBitQ's (Section 3.1) -- code = sign bits of o',
     <obar,o> = sum|o'| / (sqrt(D) ||o'||) (Section 2.2)."""
@@ -68,7 +86,7 @@ def test_alg1_b1_is_rabitq_sign_code():
     assert (st[:, 4] == 0).all()          # no critical values when B = 1
 
 
-@pytest.mark.parametrize("B", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("B", [2, 3, 4, 5, 6, 7, 8, 9])
 def test_alg1_msb_is_sign_and_event_count(B):
     """Section 4.2: the most significant bits of ybar_u form the RaBitQ code of
     o'.  Section 3.1: each non-zero coordinate has 2^(B-1)-1 critical values."""
@@ -80,7 +98,7 @@ def test_alg1_msb_is_sign_and_event_count(B):
     assert (st[:, 4] == nz * (2 ** (B - 1) - 1)).all()
 
 
-@pytest.mark.parametrize("B", [2, 3, 5, 7])
+@pytest.mark.parametrize("B", [2, 3, 5, 7, 9])
 def test_lemma_3_1_nearest_grid_point(B):
     """Lemma 3.1 with the proof's t = ||ybar||^2 / <o', ybar>: ybar is a
     nearest point of G to t*o' (G is a product set, so coordinate-wise)."""
@@ -227,13 +245,13 @@ def test_error_decays_as_empirical_formula():
         o, q = _unit_pairs(n, d, 70 + d)
         P = S.random_orthogonal(d, 71)
         true = (o.astype(np.float64) * q).sum(1)
-        for B in range(1, 9):
+        for B in range(1, 10):
             err = np.abs(_ip_estimates(o, q, B, P) - true)
             q999[d, B] = np.quantile(err, 0.999)
             assert q999[d, B] < 1.25 * 5.75 * 2.0 ** -B / math.sqrt(d), (d, B, q999[d, B])
-        slope = np.polyfit(np.arange(1, 9), np.log2([q999[d, B] for B in range(1, 9)]), 1)[0]
+        slope = np.polyfit(np.arange(1, 10), np.log2([q999[d, B] for B in range(1, 10)]), 1)[0]
         assert -1.1 < slope < -0.9, slope
-    d_slope = np.mean([np.log2(q999[256, B] / q999[64, B]) / 2 for B in range(1, 9)])
+    d_slope = np.mean([np.log2(q999[256, B] / q999[64, B]) / 2 for B in range(1, 10)])
     assert -0.6 < d_slope < -0.4, d_slope
 
 

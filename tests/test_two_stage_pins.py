@@ -22,7 +22,7 @@ def _setup(n=4000, d=64, nlist=8, B=5, seed=0):
     return X, P, assign, ix, Q
 
 
-@pytest.mark.parametrize("B", [2, 3, 5, 8])
+@pytest.mark.parametrize("B", [2, 3, 5, 8, 9])
 def test_msb_plane_is_the_one_bit_code(B):
     """Section 4.2: the most significant bits of the B-bit code are the 1-bit
     RaBitQ code of the same rotated residual, and the stage-1 factor
@@ -49,7 +49,7 @@ def test_stage_one_is_the_one_bit_estimate():
             np.testing.assert_allclose(r["est1"], ref, rtol=1e-10, atol=1e-9 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("B", [1, 3, 5, 7])
+@pytest.mark.parametrize("B", [1, 3, 5, 7, 9])
 def test_stage_two_is_the_full_estimate(B):
     """Eq. 4.2 (MSB product reused, remaining bits added) gives the C oracle's
     full B-bit estimate."""
