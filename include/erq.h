@@ -18,7 +18,7 @@
  *    ends in _host.  The library never frees caller memory.
  *  - Matrices are row-major and contiguous: X[N][D], P[D][D], Q[nq][D].
  *  - D must be a multiple of 64 (the paper pads to a multiple of 64,
- *    Section 5.1) and at most 4096; B is 1..8; N < 2^31.
+ *    Section 5.1) and at most 4096; B is 1..9; N < 2^31.
  *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *    default stream).  Host-side validation errors return before any work is
  *    queued.  Device-side errors (a wait that ran out, a bound that failed) are
@@ -57,8 +57,9 @@ typedef enum {
     ERQ_PREC_FP8 = 2,        /* tcgen05 kind::f8f6f4: query rounded to e4m3 after a
                                 per-query power-of-two scale, centred codes exact in
                                 e4m3 (B <= 4 directly; B = 5..8 as 16 hc + lc, two
-                                e4m3 parts of magnitude <= 15 each, Section 3.3),
-                                FP32 accumulation in tensor memory                       */
+                                e4m3 parts of magnitude <= 15 each, Section 3.3;
+                                B = 9 -> ERQ_EUNSUPPORTED), FP32 accumulation in
+                                tensor memory                                            */
     ERQ_PREC_INT8 = 3        /* int8 tensor MMA: unavailable on sm_103a (ptxas rejects
                                 tcgen05 kind::i8) -> ERQ_EUNSUPPORTED                    */
 } erq_precision;
@@ -67,7 +68,7 @@ typedef struct erq_index erq_index;   /* opaque; owns all of its device memory *
 
 /* Index construction parameters (Section 3.3 workflow, Section 4.1 IVF). */
 typedef struct {
-    int32_t B;                /* bits per coordinate, 1..8                               */
+    int32_t B;                /* bits per coordinate, 1..9                               */
     int32_t nlist;            /* IVF clusters; 1 = no IVF (one cluster, c = mean of X)   */
     const float* P;           /* device [D][D] orthogonal matrix (the method's random
                                  draw, Section 3.1 Eq. equ:rotation); required            */
@@ -133,7 +134,7 @@ typedef enum {
     ERQ_FIELD_ROT_CENTROIDS = 1,  /* float  [nlist][D]  c'_j = P^T c_j (FP64 accumulated)  */
     ERQ_FIELD_LIST_OFFSETS = 2,   /* int64  [nlist+1]   first stored row of each cluster   */
     ERQ_FIELD_LIST_IDS = 3,       /* int64  [N]         original row id of each stored row */
-    ERQ_FIELD_CODES = 4,          /* uint8  [N][D]      ybar_u, one byte per coordinate    */
+    ERQ_FIELD_CODES = 4,          /* [N][D] ybar_u: uint8 (B <= 8) or little-endian uint16 (B = 9) */
     ERQ_FIELD_F_ADD = 5,          /* float  [N]         ||o'||^2                           */
     ERQ_FIELD_F_RES = 6,          /* float  [N]         -2 ||o'||^2 / <ybar, |o'|>          */
     ERQ_FIELD_P = 7,              /* float  [D][D]                                         */
@@ -181,13 +182,14 @@ erq_status erq_rotate(const float* X, int64_t n, int32_t D, const float* P, floa
                       void* stream);
 
 /* Algorithm 1 (Section 3.1) on each row of Rrot (device [n][D], rotated
- * residuals o', any scale).  Writes codes[n][D] (ybar_u, one byte per
- * coordinate), f_add[n] = fl32(||o'||^2), f_res[n] = fl32(-2 ||o'||^2 / ip*) with
+ * residuals o', any scale).  Writes codes[n][D] (ybar_u: one byte per
+ * coordinate for B <= 8, a little-endian 16-bit word per coordinate for
+ * B = 9, i.e. 2 n D bytes), f_add[n] = fl32(||o'||^2), f_res[n] = fl32(-2 ||o'||^2 / ip*) with
  * ip* = <ybar, |o'|> at the optimum (0 for o' = 0), and optionally stats[n][2] =
  * (ip*, ||ybar||^2) in FP64.  Critical values are visited in ascending exact
  * rational order, ties by coordinate; <y_cur,o'> accumulates in FP64 in that
  * order; the first state of maximal <y/||y||, o'> wins.
- * Errors: EINVAL (B, D), ECUDA. */
+ * Errors: EINVAL (B outside 1..9, D), ECUDA. */
 erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add,
                       float* f_res, double* stats, void* stream);
 

@@ -228,7 +228,7 @@ extern "C" erq_status erq_rotate(const float* X, int64_t n, int32_t D, const flo
 extern "C" erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add, float* f_res,
                       double* stats, void* stream) {
     if (n < 0 || !valid_d(D)) return fail(ERQ_EINVAL, "erq_encode: D must be a multiple of 64 in [64, 4096], n >= 0");
-    if (B < 1 || B > 8) return fail(ERQ_EINVAL, "erq_encode: B must be in [1, 8]");
+    if (B < 1 || B > 9) return fail(ERQ_EINVAL, "erq_encode: B must be in [1, 9]");
     if (n == 0) return ERQ_OK;
     if (!Rrot || !codes || !f_add || !f_res) return fail(ERQ_EINVAL, "erq_encode: null pointer");
     uint32_t* status = nullptr;
@@ -331,7 +331,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     if (!p || !X || !p->P) return fail(ERQ_EINVAL, "erq_build_index: X, params and params->P are required");
     if (N < 1 || N >= (1ll << 31)) return fail(ERQ_EINVAL, "erq_build_index: N must be in [1, 2^31)");
     if (!valid_d(D)) return fail(ERQ_EINVAL, "erq_build_index: D must be a multiple of 64 in [64, 4096]");
-    if (p->B < 1 || p->B > 8) return fail(ERQ_EINVAL, "erq_build_index: B must be in [1, 8]");
+    if (p->B < 1 || p->B > 9) return fail(ERQ_EINVAL, "erq_build_index: B must be in [1, 9]");
     if (p->centroids && (!p->assign || p->nlist < 2))
         return fail(ERQ_EINVAL, "erq_build_index: explicit centroids need an explicit assignment and nlist >= 2");
     if (p->nlist < 1 || p->nlist > 65536 || (p->nlist > N && !p->centroids))
@@ -361,7 +361,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     ALLOC(list_ids, N);
     ALLOC(row_of, N);
     ALLOC(cl_of_row, N);
-    ALLOC(codes, (size_t)N * D);
+    ALLOC(codes, (size_t)N * D * code_bytes(p->B));
     ALLOC(f_add, N);
     ALLOC(f_res, N);
     ALLOC(g_const, N);
@@ -421,7 +421,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
             if ((e = launch_rotate_fp64(X, ix->list_ids + r0, ix->C, ix->cl_of_row + r0, ix->P, R, m, D, s)) !=
                 cudaSuccess)
                 return bail2(cuda_fail(e, "rotate residuals"));
-            if ((e = launch_encode(R, m, D, ix->B, ix->codes + r0 * D, ix->f_add + r0, ix->f_res + r0, nullptr,
+            if ((e = launch_encode(R, m, D, ix->B, ix->codes + r0 * D * code_bytes(ix->B), ix->f_add + r0, ix->f_res + r0, nullptr,
                                    ix->status, s)) != cudaSuccess)
                 return bail2(cuda_fail(e, "encode"));
         }
@@ -839,7 +839,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    L.grid = (int)std::min<int64_t>(nitems, (int64_t)sms * (prec == ERQ_PREC_FP32 ? scan_fp32_blocks_per_sm(kp) : 1));
+    L.grid = (int)std::min<int64_t>(nitems, (int64_t)sms * (prec == ERQ_PREC_FP32 ? scan_fp32_blocks_per_sm(kp, ix->B) : 1));
     if (prec == ERQ_PREC_FP32) {
         if ((e = launch_scan_fp32(L, s)) != cudaSuccess) return cuda_fail(e, "scan fp32");
     } else {
@@ -889,6 +889,8 @@ static erq_status validate_search(const erq_index* ix, const float* Q, int64_t n
     if (p->precision == ERQ_PREC_INT8)
         return fail(ERQ_EUNSUPPORTED, "erq_search: int8 tensor MMA (tcgen05 kind::i8) is not available on sm_103a");
     if (p->precision < 0 || p->precision > ERQ_PREC_INT8) return fail(ERQ_EINVAL, "erq_search: unknown precision");
+    if (p->precision == ERQ_PREC_FP8 && ix->B > 8)
+        return fail(ERQ_EUNSUPPORTED, "erq_search: fp8 holds the split code parts (16 hc + lc) only for B <= 8");
     if (p->precision != ERQ_PREC_FP32 && !tc_available(p->precision, ix->D, kp))
         return fail(ERQ_EUNSUPPORTED, "erq_search: tensor-core path unavailable for this D / k'");
     if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
@@ -1006,7 +1008,7 @@ static FieldDesc field_of(const erq_index* ix, int f) {
         case ERQ_FIELD_ROT_CENTROIDS: return {ix->Cp, nl * D * 4};
         case ERQ_FIELD_LIST_OFFSETS: return {ix->list_off, (nl + 1) * 8};
         case ERQ_FIELD_LIST_IDS: return {ix->list_ids, N * 8};
-        case ERQ_FIELD_CODES: return {ix->codes, N * D};
+        case ERQ_FIELD_CODES: return {ix->codes, N * D * code_bytes(ix->B)};
         case ERQ_FIELD_F_ADD: return {ix->f_add, N * 4};
         case ERQ_FIELD_F_RES: return {ix->f_res, N * 4};
         case ERQ_FIELD_P: return {ix->P, D * D * 4};
@@ -1037,7 +1039,7 @@ extern "C" erq_status erq_index_save(const erq_index* ix, const char* path) {
                             ix->cl_of_row, ix->codes, ix->f_add, ix->f_res, ix->g_const, ix->X};
     const size_t N = ix->N, D = ix->D, nl = ix->nlist;
     const size_t sizes[] = {D * D * 4, nl * D * 4, nl * D * 4, nl * 4, (nl + 1) * 8, N * 8, N * 8,
-                            N * 4, N * D, N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
+                            N * 4, N * D * code_bytes(ix->B), N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
     std::vector<char> host;
     for (int i = 0; i < 13 && ok; ++i) {
         if (!sizes[i]) continue;
@@ -1071,7 +1073,7 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
     ix->keep_raw = (int32_t)hdr[4];
     ix->max_list = hdr[5];
     ix->host_list_off = new std::vector<int64_t>(ix->nlist + 1);
-    if (ix->N < 1 || !valid_d(ix->D) || ix->B < 1 || ix->B > 8 || ix->nlist < 1) {
+    if (ix->N < 1 || !valid_d(ix->D) || ix->B < 1 || ix->B > 9 || ix->nlist < 1) {
         fclose(f);
         erq_free_index(ix);
         return fail(ERQ_EIO, "erq_index_load: corrupt header");
@@ -1082,7 +1084,7 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
                     (void**)&ix->list_ids, (void**)&ix->row_of, (void**)&ix->cl_of_row, (void**)&ix->codes,
                     (void**)&ix->f_add, (void**)&ix->f_res, (void**)&ix->g_const, (void**)&ix->X};
     const size_t sizes[] = {D * D * 4, nl * D * 4, nl * D * 4, nl * 4, (nl + 1) * 8, N * 8, N * 8,
-                            N * 4, N * D, N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
+                            N * 4, N * D * code_bytes(ix->B), N * 4, N * 4, N * 4, ix->keep_raw ? N * D * 4 : 0};
     std::vector<char> host;
     for (int i = 0; i < 13 && st == ERQ_OK; ++i) {
         if (!sizes[i]) continue;

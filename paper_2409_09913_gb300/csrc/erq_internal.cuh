@@ -91,6 +91,15 @@ constexpr uint64_t kEmptyKey = ~0ull;
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Stored codes ybar_u: one byte per coordinate for B <= 8, a little-endian
+// 16-bit word per coordinate for B = 9.
+__host__ __device__ inline int code_bytes(int B) { return B > 8 ? 2 : 1; }
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t load_code(const uint8_t* codes, int B, int64_t i) {
+    return B > 8 ? (uint32_t)reinterpret_cast<const uint16_t*>(codes)[i] : (uint32_t)codes[i];
+}
+#endif
+
 // Process-wide count of kernel launches issued by the library.
 void count_launch();
 

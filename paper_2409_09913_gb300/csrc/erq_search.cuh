@@ -119,7 +119,7 @@ cudaError_t launch_plan(const PlanArgs& p, cudaStream_t s);
 cudaError_t launch_plan_items(const PlanArgs& p, int4* items, cudaStream_t s);
 cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s);
 size_t scan_fp32_smem(int kp);
-int scan_fp32_blocks_per_sm(int kp);   // resident FP32-scan blocks per SM at this k'
+int scan_fp32_blocks_per_sm(int kp, int B);   // resident FP32-scan blocks per SM at this k' and code width
 int merge_sortn(int kp, int lstride);
 cudaError_t launch_make_keys(const int64_t* ids, const float* vals, int64_t n, int64_t id_limit, int neg,
                              uint64_t* keys, cudaStream_t s);

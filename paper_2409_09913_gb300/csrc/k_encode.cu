@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
         }
 
         // ---- final state and code
-        uint8_t* code = codes + v * D;
+        uint8_t* code = codes + v * D * code_bytes(B);
         const double abest = best_i >= 0 ? (double)sm.a[best_i] : 0.0;
         for (int i = lane; i < D; i += 32) {
             int mi = 0;
@@ -413,7 +413,9 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 mi = j;
             }
             const float x = r[i];
-            code[i] = (uint8_t)(x >= 0.f ? half + mi : half - 1 - mi);
+            const int u = x >= 0.f ? half + mi : half - 1 - mi;
+            if (B > 8) reinterpret_cast<uint16_t*>(code)[i] = (uint16_t)u;
+            else code[i] = (uint8_t)u;
         }
         if (lane == 0) {
             f_add[v] = __double2float_rn(nr2);
@@ -468,13 +470,12 @@ __global__ void gconst_kernel(const uint8_t* __restrict__ codes, const float* __
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
-    const uint8_t* code = codes + w * D;
     const float* c = Cp + (int64_t)cl_of_row[w] * D;
     const double off = 0.5 * (double)((1 << B) - 1);
     // lanes form exact products; lane 0 adds them in ascending order
     double acc = 0.0;
     for (int k0 = 0; k0 < D; k0 += 32) {
-        const double prod = ((double)code[k0 + lane] - off) * (double)c[k0 + lane];  // exact
+        const double prod = ((double)load_code(codes, B, w * D + k0 + lane) - off) * (double)c[k0 + lane];  // exact
         for (int j = 0; j < 32; ++j) {
             const double pj = __shfl_sync(0xffffffffu, prod, j);
             if (lane == 0) acc = __dadd_rn(acc, pj);

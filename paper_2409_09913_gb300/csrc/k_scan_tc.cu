@@ -28,8 +28,9 @@
 // 64-coordinate K block of the group.  Warp roles (27 warps):
 //   warps 0-3    estimate tiles: warp w reads TMEM lanes 32w .. 32w + 31 (its
 //                32 rows, all queries) of each finished row-block accumulator,
-//                stores g + (f_res/2) acc into one of EB query-major tiles in
-//                shared memory and frees the accumulator;
+//                frees the accumulator as soon as its last columns are in
+//                registers, and stores g + (f_res/2) acc into one of EB
+//                query-major tiles in shared memory;
 //   warps 4-11   converters, two sets of four that take alternate stages:
 //                warp w unpacks the codes of rows 32 (w % 4) .. + 31 of both
 //                row blocks of its stages from the raw stage in shared memory
@@ -38,15 +39,17 @@
 //                the rows' factors and ids, per stage one TMA load of the packed
 //                codes per row block into a raw ring that is released as soon as
 //                the converters have read it (so loads run up to RS stages
-//                ahead, independent of the tensor cores);
-//   warps 13-16  query loaders: per stage the item's query rows (128 bytes
+//                ahead, independent of the tensor cores; RS is even, so that
+//                each raw slot is always converted by the same converter set
+//                and its phases are awaited in order);
+//   warps 13-14  query loaders: per stage the item's query rows (128 bytes
 //                each) by TMA gather4 into the stage's swizzled B tile, the
-//                stages taken in turn by the four warps;
-//   warps 17, 18 MMA issuers of row blocks 0 and 1 (one elected thread each;
-//                warp 17 owns the tensor memory); each commits once per stage to
+//                stages taken in turn by the two warps;
+//   warps 15, 16 MMA issuers of row blocks 0 and 1 (one elected thread each;
+//                warp 15 owns the tensor memory); each commits once per stage to
 //                the stage's release barrier, which frees the query tile and the
 //                stage's TMEM code columns;
-//   warps 19-26  filters (NFX = 8), pipelined behind the tiles through full /
+//   warps 17-26  filters (NFX = 10), pipelined behind the tiles through full /
 //                empty tile barriers: warp f owns the query slots f + NFX j and
 //                filters their rows (float pre-filter against the threshold,
 //                exact keys, ballots) into per-query candidate lists; a full
@@ -60,6 +63,7 @@
 // the kernel records ERQ_ETIMEOUT in the status word, every role stops at its
 // next wait (the abort flag), the copies and MMAs already issued are drained
 // (bounded), TMEM is freed and the kernel returns.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -83,10 +87,10 @@ constexpr int RSMAX = 8;         // raw-code ring slots at most
 constexpr int W_CV = 4;          // converter warps 4..11 (row block (w - 4) / 4, lane quarter w % 4)
 constexpr int W_LD = 12;         // code loader and item publisher
 constexpr int W_QL = 13;         // query-tile loaders 13 .. 13 + NQL - 1 (stage g: loader g % NQL)
-constexpr int NQL = 4;
+constexpr int NQL = 2;
 constexpr int W_MMA = W_QL + NQL;   // MMA issuers (row block 0, TMEM owner; row block 1)
 constexpr int W_FX = W_MMA + 2;     // filter warps W_FX .. W_FX + NFX - 1
-constexpr int NFX = 8;
+constexpr int NFX = 10;
 constexpr int NWARP = W_FX + NFX;
 constexpr int THREADS = 32 * NWARP;
 constexpr int TMEM_COLS = 512;
@@ -216,6 +220,42 @@ __device__ __forceinline__ void unpack_codes(const unsigned char* base, uint32_t
     }
 }
 
+// B = 9: bits 0-7 assembled in byte lanes as for B = 8 (nibble words 0-3,
+// planes 4-7) and bit 8 from plane 8; placed under 0x64 with bit 8 in the high
+// byte's lowest bit, each 16-bit lane is the FP16 value 1024 + u (u < 512,
+// exact), and 2 (1024 + u) - 2048 - 511 = 2u - 511 (each step exact).
+__device__ __forceinline__ void unpack_codes9(const unsigned char* base, uint32_t (&w)[32]) {
+    uint2 W[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) W[j] = *reinterpret_cast<const uint2*>(base + 256 * j);
+    const __half2 off2 = __floats2half2_rn(511.f, 511.f);
+    const __half2 two = __floats2half2_rn(2.f, 2.f);
+    const __half2 m2048 = __floats2half2_rn(-2048.f, -2048.f);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int h = m >> 1;
+        const uint32_t N = (h & 1) ? W[h >> 1].y : W[h >> 1].x;
+        uint32_t V = (m & 1) ? (N >> 4) & 0x0F0F0F0Fu : N & 0x0F0F0F0Fu;
+#pragma unroll
+        for (int b = 4; b < 8; ++b) {
+            const uint32_t P = m < 8 ? W[b].x : W[b].y;
+            const int sh = b - (m & 7);
+            const uint32_t x = sh >= 0 ? P << sh : P >> (-sh);
+            V |= x & (0x01010101u << b);
+        }
+        const uint32_t P8 = m < 8 ? W[8].x : W[8].y;
+        const uint32_t H = ((P8 >> (m & 7)) & 0x01010101u) | 0x64646464u;   // 0x64 | bit 8, per byte lane
+        const uint32_t p0 = __byte_perm(V, H, 0x5140u);   // {u0 lo, 0x64 | u0 bit 8, u1 lo, ...}
+        const uint32_t p1 = __byte_perm(V, H, 0x7362u);
+        __half2 h0 = *reinterpret_cast<const __half2*>(&p0);
+        __half2 h1 = *reinterpret_cast<const __half2*>(&p1);
+        h0 = __hsub2(__hfma2(h0, two, m2048), off2);
+        h1 = __hsub2(__hfma2(h1, two, m2048), off2);
+        w[2 * m] = *reinterpret_cast<uint32_t*>(&h0);
+        w[2 * m + 1] = *reinterpret_cast<uint32_t*>(&h1);
+    }
+}
+
 __device__ __forceinline__ void unpack_codes_b(int B, const unsigned char* base, uint32_t (&w)[32]) {
     switch (B) {
         case 1: unpack_codes<1>(base, w); break;
@@ -225,7 +265,8 @@ __device__ __forceinline__ void unpack_codes_b(int B, const unsigned char* base,
         case 5: unpack_codes<5>(base, w); break;
         case 6: unpack_codes<6>(base, w); break;
         case 7: unpack_codes<7>(base, w); break;
-        default: unpack_codes<8>(base, w); break;
+        case 8: unpack_codes<8>(base, w); break;
+        default: unpack_codes9(base, w); break;
     }
 }
 
@@ -420,7 +461,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int nkb = a.nkb;
     const uint32_t blk = (uint32_t)(MR / 32) * 256u * (uint32_t)a.B;    // packed codes of one 128-row K block
     const uint32_t slot_bytes = (uint32_t)RP * blk * (W2 ? 2u : 1u);
-    const int RS = min(RSMAX, (int)(RAW_BYTES / slot_bytes));
+    // an even number of raw slots: stage g uses slot g % RS and converter set
+    // g % 2, so every slot belongs to one set, which awaits its phases in order
+    // (with an odd RS a set could test a slot's parity one phase early)
+    const int RS = min(RSMAX, (int)(RAW_BYTES / slot_bytes)) & ~1;
     int64_t nitems = *a.n_items;
     if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 7)) nitems = 0;   // uniform: every thread reads it
 
@@ -531,12 +575,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                             for (int h = 0; h < (W2 ? 2 : 1); ++h) {
                                 const int kk = W2 ? 2 * kb + h : kb;
                                 if (nt == MR / 32) {
-                                    tma_load_3d_hint(dst + h * blk, &codes_map, 0, kk, tile, bars + C::b_full_raw(s),
-                                                     pol_codes);
+                                    tma_load_4d_hint(dst + h * blk, &codes_map, 0, 0, kk, tile,
+                                                     bars + C::b_full_raw(s), pol_codes);
                                 } else {
                                     for (int t = 0; t < nt; ++t)
-                                        tma_load_3d_hint(dst + h * blk + t * 256u * (uint32_t)a.B, &codes_map1, 0, kk,
-                                                         tile + t, bars + C::b_full_raw(s), pol_codes);
+                                        tma_load_4d_hint(dst + h * blk + t * 256u * (uint32_t)a.B, &codes_map1, 0, 0,
+                                                         kk, tile + t, bars + C::b_full_raw(s), pol_codes);
                                 }
                             }
                         }
@@ -773,6 +817,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         uint32_t v[32];
                         ERQ_TMEM_LD32(tacc + cc, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (cc + 32 >= npad) {                     // the last columns are in registers:
+                            tc_fence_before();                     // the accumulator is free
+                            mbar_arrive(bars + C::b_tempty(buf, rb));
+                        }
                         if (F8) {                                  // e4m3 queries carry a power-of-two scale (exact)
                             const float* sc = s_qsc + ib * QN + cc;
 #pragma unroll
@@ -783,8 +831,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                             for (int i = 0; i < 32; ++i) est_t[(cc + i) * MR + row] = fmaf(mt.y, __uint_as_float(v[i]), mt.x);
                         }
                     }
-                    tc_fence_before();
-                    mbar_arrive(bars + C::b_tempty(buf, rb));       // the accumulator is free
                     ++u[rb];
                     mbar_arrive(bars + C::b_empty_meta(m));
                     mbar_arrive(bars + C::b_tile_full(t));
@@ -1017,11 +1063,27 @@ __global__ void scan_layout_kernel(const uint8_t* __restrict__ codes, const floa
     const int64_t j = p - poff[lo];
     const bool valid = j < list_off[lo + 1] - list_off[lo];
     const int64_t src = list_off[lo] + j;
-    uint32_t u[16];                              // 64 codes, four per word (byte i of u[k] = code 4k + i)
+    uint32_t u[16];                              // 64 codes, four per word (byte i of u[k] = bits 0-7 of code 4k + i)
+    uint32_t h8[16] = {};                        // B = 9: byte i of h8[k] = bit 8 of code 4k + i
+    if (B <= 8) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + src * D + kb * 64)[x] : make_uint4(0u, 0u, 0u, 0u);
-        u[4 * x] = v.x; u[4 * x + 1] = v.y; u[4 * x + 2] = v.z; u[4 * x + 3] = v.w;
+        for (int x = 0; x < 4; ++x) {
+            const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + src * D + kb * 64)[x] : make_uint4(0u, 0u, 0u, 0u);
+            u[4 * x] = v.x; u[4 * x + 1] = v.y; u[4 * x + 2] = v.z; u[4 * x + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {            // 16-bit codes: eight per uint4
+            const uint4 v = valid ? reinterpret_cast<const uint4*>(codes + (src * D + kb * 64) * 2)[x]
+                                  : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {        // codes 8x + 4h .. + 3 -> word 2x + h
+                const uint32_t a = w[2 * h], b = w[2 * h + 1];
+                u[2 * x + h] = __byte_perm(a, b, 0x6420u);
+                h8[2 * x + h] = __byte_perm(a, b, 0x7531u) & 0x01010101u;
+            }
+        }
     }
     uint64_t* dst = codes_p + (tk * B) * 32 + r;
     const int bs = B >= 4 ? 4 : 0;
@@ -1038,7 +1100,7 @@ __global__ void scan_layout_kernel(const uint8_t* __restrict__ codes, const floa
         uint32_t P[2] = {0u, 0u};
 #pragma unroll
         for (int m = 0; m < 16; ++m)
-            P[m >> 3] |= ((u[m] >> b) & 0x01010101u) << (m & 7);
+            P[m >> 3] |= (b < 8 ? (u[m] >> b) & 0x01010101u : h8[m]) << (m & 7);
         dst[b * 32] = (uint64_t)P[0] | ((uint64_t)P[1] << 32);
     }
     if (kb == 0)
@@ -1071,12 +1133,14 @@ static bool make_codes_map(CUtensorMap* map, const uint64_t* codes_p, int64_t Np
             return false;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
+    // 4-D view [tiles][K blocks][B words][32 rows] of u64 (a box extent is at most 256 elements,
+    // so the 32 B words of a tile and K block are two dimensions, not one of 32 B)
     const int nkb = D / KB;
-    const cuuint64_t dims[3] = {(cuuint64_t)(32 * B), (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
-    const cuuint64_t strides[2] = {(cuuint64_t)256 * B, (cuuint64_t)256 * B * nkb};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 * B), 1, (cuuint32_t)box_tiles};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)codes_p, dims, strides, box, estr,
+    const cuuint64_t dims[4] = {32, (cuuint64_t)B, (cuuint64_t)nkb, (cuuint64_t)((Np + 31) / 32)};
+    const cuuint64_t strides[3] = {256, (cuuint64_t)256 * B, (cuuint64_t)256 * B * nkb};
+    const cuuint32_t box[4] = {32, (cuuint32_t)B, 1, (cuuint32_t)box_tiles};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, (void*)codes_p, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1108,11 +1172,16 @@ template <class C, int P>
 static erq_status scan_tc_launch(const ScanLaunch& L, const tc::Args& a, const void* qbase, int64_t qrow_bytes,
                                  cudaStream_t s) {
     const int smem = C::Smem::total;
+    {   // the kernel's raw-code ring must hold an even number (>= 2) of stage slots
+        const int64_t slot = (int64_t)RP * (MR / 32) * 256 * L.B * (P == 1 ? 2 : 1);
+        if ((std::min<int64_t>(RSMAX, C::RAW_BYTES / slot) & ~1ll) < 2)
+            return fail(ERQ_EUNSUPPORTED, "tensor-core scan: raw-code ring too small for this code width");
+    }
     cudaError_t e = cudaFuncSetAttribute(scan_tc_kernel<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "scan_tc smem attribute");
     if (L.grid <= 0) return ERQ_OK;
     CUtensorMap cmap, cmap1, qmap;
-    if (!L.codes_p || ((uintptr_t)L.codes_p & 15) != 0 || (L.D % KB) != 0 || L.B < 1 || L.B > 8 ||
+    if (!L.codes_p || ((uintptr_t)L.codes_p & 15) != 0 || (L.D % KB) != 0 || L.B < 1 || L.B > 9 ||
         !make_codes_map(&cmap, L.codes_p, L.Np, L.D, L.B, MR / 32) ||
         !make_codes_map(&cmap1, L.codes_p, L.Np, L.D, L.B, 1))
         return fail(ERQ_ECUDA, "tensor-core scan: cuTensorMapEncodeTiled failed for the code array");
@@ -1139,6 +1208,8 @@ erq_status scan_tc(const ScanLaunch& L, int precision, cudaStream_t s) {
         return fail(ERQ_EUNSUPPORTED, "tensor-core scan: needs precision fp16 or fp8 and k' <= 128");
     const bool f8 = precision == ERQ_PREC_FP8;
     const int P = f8 ? (L.B <= 4 ? 1 : 2) : 0;
+    if (P == 2 && L.B > 8)
+        return fail(ERQ_EUNSUPPORTED, "tensor-core scan: e4m3 holds the split code parts only for B <= 8");
     if (P == 2 && L.Dq != 2 * (int64_t)L.D) return fail(ERQ_EINVAL, "tensor-core scan: split e4m3 needs doubled query rows");
     if (!(f8 ? (L.Q8 && L.qscale) : L.Qh != nullptr)) return fail(ERQ_EINVAL, "tensor-core scan: queries missing");
     if (!L.itemd || !L.itemq || !L.rowmeta || !L.tq || !L.work_ctr)

@@ -306,23 +306,27 @@ struct ScanArgs {
 };
 
 // Register-staged operands of one K step: 16 query values of query (tid & 63)
-// at k0 + 16 (tid >> 6), and the 32 codes of row tid at k0.
+// at k0 + 16 (tid >> 6), and the 32 codes of row tid at k0 (CB bytes each:
+// 1 for B <= 8, 2 for B = 9).
+template <int CB>
 struct Fp32Stage {
     float4 q[4];
-    uint4 c[2];
+    uint4 c[2 * CB];
 };
 
-__device__ __forceinline__ void fp32_load(Fp32Stage& st, const float* qrow, const uint8_t* crow, int k0, int tid) {
+template <int CB>
+__device__ __forceinline__ void fp32_load(Fp32Stage<CB>& st, const float* qrow, const uint8_t* crow, int k0, int tid) {
     const int kq = (tid >> 6) * 16;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
         st.q[j] = qrow ? __ldg(reinterpret_cast<const float4*>(qrow + k0 + kq) + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
-        st.c[j] = crow ? __ldg(reinterpret_cast<const uint4*>(crow + k0) + j) : make_uint4(0u, 0u, 0u, 0u);
+    for (int j = 0; j < 2 * CB; ++j)
+        st.c[j] = crow ? __ldg(reinterpret_cast<const uint4*>(crow + (int64_t)k0 * CB) + j) : make_uint4(0u, 0u, 0u, 0u);
 }
 
-__device__ __forceinline__ void fp32_store(const Fp32Stage& st, float* qs, float* cs, int tid, float off) {
+template <int CB>
+__device__ __forceinline__ void fp32_store(const Fp32Stage<CB>& st, float* qs, float* cs, int tid, float off) {
     const int qi = tid & 63, kq = (tid >> 6) * 16;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -331,13 +335,26 @@ __device__ __forceinline__ void fp32_store(const Fp32Stage& st, float* qs, float
         qs[(kq + 4 * j + 2) * SC_QS + qi] = st.q[j].z;
         qs[(kq + 4 * j + 3) * SC_QS + qi] = st.q[j].w;
     }
-    const uint32_t w[8] = {st.c[0].x, st.c[0].y, st.c[0].z, st.c[0].w, st.c[1].x, st.c[1].y, st.c[1].z, st.c[1].w};
+    if constexpr (CB == 1) {
+        const uint32_t w[8] = {st.c[0].x, st.c[0].y, st.c[0].z, st.c[0].w, st.c[1].x, st.c[1].y, st.c[1].z, st.c[1].w};
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < 8; ++j)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) cs[(4 * j + b) * SC_CS + tid] = fmaf(2.f, (float)((w[j] >> (8 * b)) & 0xffu), -off);
+            for (int b = 0; b < 4; ++b) cs[(4 * j + b) * SC_CS + tid] = fmaf(2.f, (float)((w[j] >> (8 * b)) & 0xffu), -off);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t w[4] = {st.c[j].x, st.c[j].y, st.c[j].z, st.c[j].w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+                    cs[(8 * j + 2 * h + b) * SC_CS + tid] = fmaf(2.f, (float)((w[h] >> (16 * b)) & 0xffffu), -off);
+        }
+    }
 }
 
+template <int CB>
 __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     float* ops = reinterpret_cast<float*>(smem);     // buffer b: queries at b * BK * (QS + CS), codes after them
@@ -389,13 +406,13 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
                 s_fh[tid] = (a.ip ? 0.25f : 0.5f) * a.f_res[r0 + tid];
                 s_id[tid] = (uint32_t)a.list_ids[r0 + tid];
             }
-            const uint8_t* crow = row_ok ? a.codes + (r0 + tid) * D : nullptr;
+            const uint8_t* crow = row_ok ? a.codes + (r0 + tid) * D * CB : nullptr;
             float acc[8][8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-            Fp32Stage st;
+            Fp32Stage<CB> st;
             fp32_load(st, qrow, crow, 0, tid);
             fp32_store(st, ops, ops + SC_BK * SC_QS, tid, off);
             __syncthreads();
@@ -492,14 +509,19 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
 
 size_t scan_fp32_smem(int kp) { return (size_t)SC_OPS + 16 + (size_t)kp * SC_QT * 8; }
 
-int scan_fp32_blocks_per_sm(int kp) {
+template <int CB>
+static int fp32_blocks_per_sm(int kp) {
     int n = 1;
     const size_t smem = scan_fp32_smem(kp);
-    if (cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_fp32_kernel, SC_THREADS, smem) != cudaSuccess || n < 1)
+    if (cudaFuncSetAttribute(scan_fp32_kernel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_fp32_kernel<CB>, SC_THREADS, smem) != cudaSuccess ||
+        n < 1)
         return 1;
     return n;
 }
+
+int scan_fp32_blocks_per_sm(int kp, int B) { return B > 8 ? fp32_blocks_per_sm<2>(kp) : fp32_blocks_per_sm<1>(kp); }
 
 // ---------------------------------------------------------------------------
 // Merge: per query the k' smallest keys over its lists, ascending.
@@ -691,7 +713,6 @@ __global__ void estimate_kernel(const float* __restrict__ Q, const float* __rest
     const float* c = C + (int64_t)cl_of_row[row] * D;
     const float* x = Q + q * D;
     const float* xr = Qrot + q * D;
-    const uint8_t* code = codes + row * D;
     const float off = (float)((1 << B) - 1);
     float dq = 0.f, ip = 0.f;
     for (int k = lane; k < D; k += 32) {
@@ -701,7 +722,7 @@ __global__ void estimate_kernel(const float* __restrict__ Q, const float* __rest
             const float d = x[k] - c[k];
             dq = fmaf(d, d, dq);
         }
-        ip = fmaf(2.f * (float)code[k] - off, xr[k], ip);
+        ip = fmaf(2.f * (float)load_code(codes, B, row * D + k) - off, xr[k], ip);
     }
     dq = warp_sum(dq);
     ip = warp_sum(ip);
@@ -743,7 +764,7 @@ __global__ void __launch_bounds__(256) backward_gather_kernel(const float* __res
             }
             const float g = gs[q * nc + j];
             const int64_t row = row_of[id];
-            const float yb = (float)codes[row * D + k] - off;
+            const float yb = (float)load_code(codes, B, row * D + k) - off;
             v = fmaf(g * (fs * f_res[row]), yb, v);
             wc = fmaf(g, C[(int64_t)cl_of_row[row] * D + k], wc);
             G += g;
@@ -815,12 +836,15 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip; a.nlist = L.nlist;
     a.nq = L.nq; a.N = L.N;
     const size_t smem = scan_fp32_smem(L.kp);
-    cudaError_t e = cudaFuncSetAttribute(scan_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool wide = L.B > 8;                    // 16-bit codes
+    cudaError_t e = wide ? cudaFuncSetAttribute(scan_fp32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(scan_fp32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (L.grid <= 0) return cudaSuccess;
     if (L.D % SC_BK != 0) return cudaErrorInvalidValue;
     count_launch();
-    scan_fp32_kernel<<<L.grid, SC_THREADS, smem, s>>>(a);
+    if (wide) scan_fp32_kernel<2><<<L.grid, SC_THREADS, smem, s>>>(a);
+    else scan_fp32_kernel<1><<<L.grid, SC_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

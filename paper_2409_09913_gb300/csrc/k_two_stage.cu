@@ -50,12 +50,11 @@ __global__ void stage1_factors_kernel(const float* __restrict__ R, int64_t r0, i
     const int64_t w = r0 + i;
     const int c = cl_of_row[w];
     const float* o = R + i * D;
-    const uint8_t* code = codes + w * D;
     const float* cp = Cp + (int64_t)c * D;
     double sabs = 0.0, yc = 0.0;
     for (int k = lane; k < D; k += 32) {
         sabs += fabs((double)o[k]);
-        yc += ((double)(code[k] >> (B - 1)) - 0.5) * (double)cp[k];
+        yc += ((double)(load_code(codes, B, w * D + k) >> (B - 1)) - 0.5) * (double)cp[k];
     }
     for (int s = 16; s > 0; s >>= 1) {
         sabs += __shfl_xor_sync(0xffffffffu, sabs, s);
@@ -277,7 +276,8 @@ __device__ float last_bits_row_b(int B, const uint64_t* w0, int nkb, const float
         case 5: return last_bits_row<5>(w0, nkb, x);
         case 6: return last_bits_row<6>(w0, nkb, x);
         case 7: return last_bits_row<7>(w0, nkb, x);
-        default: return last_bits_row<8>(w0, nkb, x);
+        case 8: return last_bits_row<8>(w0, nkb, x);
+        default: return last_bits_row<9>(w0, nkb, x);
     }
 }
 
@@ -377,7 +377,7 @@ cudaError_t launch_two_stage_rows(const int32_t* probe_c, int64_t nq, int maxp, 
 
 cudaError_t launch_two_stage(const TwoStageLaunch& L, cudaStream_t s) {
     if (L.nq <= 0) return cudaSuccess;
-    if (L.D % 64 != 0 || L.B < 1 || L.B > 8 || L.B == 4 || L.kp < 1 || L.kp > 1024) return cudaErrorInvalidValue;
+    if (L.D % 64 != 0 || L.B < 1 || L.B > 9 || L.B == 4 || L.kp < 1 || L.kp > 1024) return cudaErrorInvalidValue;
     // the tables are read as float4, the keys as u64
     if (((uintptr_t)L.T & 15) != 0 || ((uintptr_t)L.skey & 7) != 0 || ((uintptr_t)L.meta1 & 15) != 0)
         return cudaErrorInvalidValue;

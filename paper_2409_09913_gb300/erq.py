@@ -186,10 +186,11 @@ def rotate(X, P, accurate=False, out=None):
 
 
 def encode(R, B, with_stats=False):
-    """Algorithm 1 on each row of R (rotated residuals) -> (codes, f_add, f_res[, stats])."""
+    """Algorithm 1 on each row of R (rotated residuals) -> (codes, f_add, f_res[, stats]);
+    codes are uint8 for B <= 8 and 16-bit (int16, values < 512) for B = 9."""
     R = _dev(R, torch.float32, "R", 2)
     n, d = R.shape
-    codes = torch.empty((n, d), dtype=torch.uint8, device=R.device)
+    codes = torch.empty((n, d), dtype=torch.int16 if int(B) > 8 else torch.uint8, device=R.device)
     f_add = torch.empty(n, dtype=torch.float32, device=R.device)
     f_res = torch.empty(n, dtype=torch.float32, device=R.device)
     stats = torch.empty((n, 2), dtype=torch.float64, device=R.device) if with_stats else None
@@ -413,7 +414,8 @@ class Index:
         N, D, nl = inf["N"], inf["D"], inf["nlist"]
         shapes = {"centroids": ((nl, D), torch.float32), "rot_centroids": ((nl, D), torch.float32),
                   "list_offsets": ((nl + 1,), torch.int64), "list_ids": ((N,), torch.int64),
-                  "codes": ((N, D), torch.uint8), "f_add": ((N,), torch.float32), "f_res": ((N,), torch.float32),
+                  "codes": ((N, D), torch.int16 if inf["B"] > 8 else torch.uint8), "f_add": ((N,), torch.float32),
+                  "f_res": ((N,), torch.float32),
                   "P": ((D, D), torch.float32), "raw": ((N, D), torch.float32)}
         if field == "packed_codes":      # clusters padded to 32-row tiles, B bits per coordinate
             off = self.export("list_offsets")

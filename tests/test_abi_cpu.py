@@ -48,7 +48,7 @@ def test_host_validation_rejects_bad_shapes(L):
     assert L.erq_rotate(_vp(8), 4, 63, _vp(8), _vp(8), 0, _vp()) == erq.ERQ_EINVAL
     assert b"multiple of 64" in L.erq_last_error()
     # B out of range
-    assert L.erq_encode(_vp(8), 4, 64, 9, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
+    assert L.erq_encode(_vp(8), 4, 64, 10, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
     assert L.erq_encode(_vp(8), 4, 64, 0, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
     # null pointers
     assert L.erq_encode(_vp(0), 4, 64, 4, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
@@ -62,7 +62,7 @@ def test_host_validation_build_params(L):
     bp = erq.BuildParams()
     bp.B, bp.nlist, bp.P = 4, 1, 0
     assert L.erq_build_index(_vp(8), 100, 64, ct.byref(bp), _vp(), ct.byref(out)) == erq.ERQ_EINVAL
-    bp.P, bp.B = 8, 9
+    bp.P, bp.B = 8, 10
     assert L.erq_build_index(_vp(8), 100, 64, ct.byref(bp), _vp(), ct.byref(out)) == erq.ERQ_EINVAL
     bp.B, bp.nlist = 4, 101
     assert L.erq_build_index(_vp(8), 100, 64, ct.byref(bp), _vp(), ct.byref(out)) == erq.ERQ_EINVAL

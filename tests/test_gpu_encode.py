@@ -27,7 +27,7 @@ def _check_encode(erq, R, B):
     np.testing.assert_array_equal(fr.view(np.uint32), fr_o.view(np.uint32))
 
 
-@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("kind", ["gauss", "ties", "sparse", "wide"])
 def test_encode_bit_exact_d128(erq, B, kind):
     R = S.random_rotated_residuals(300, 128, 1000 + B, kind=kind)
@@ -35,7 +35,7 @@ def test_encode_bit_exact_d128(erq, B, kind):
 
 
 @pytest.mark.parametrize("D,B,n", [(64, 5, 400), (960, 3, 200), (960, 5, 200), (960, 7, 60), (1536, 7, 40),
-                                   (768, 5, 150), (1024, 4, 150), (4096, 2, 20)])
+                                   (768, 5, 150), (1024, 4, 150), (4096, 2, 20), (960, 9, 20)])
 def test_encode_bit_exact_paper_shapes(erq, D, B, n):
     R = S.random_rotated_residuals(n, D, 2000 + D + B)
     _check_encode(erq, R, B)

@@ -75,7 +75,7 @@ def test_bruteforce_config_small(erq):
     assert recall > 0.98
 
 
-@pytest.mark.parametrize("B", [3, 5, 7])
+@pytest.mark.parametrize("B", [3, 5, 7, 9])
 def test_ivf_explicit_probe(erq, B):
     """IVF with probe lists drawn by the generator (both sides scan the same clusters)."""
     X, P, assign, gx, ox = _build_pair(erq, 20000, 128, B, 64, 500 + B, n_comp=16, scale="aniso")

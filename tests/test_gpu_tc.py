@@ -176,7 +176,7 @@ def _pack_reference(codes, off, B):
     return np.ascontiguousarray(W.transpose(0, 1, 3, 2)).view(np.uint8).ravel()   # [tile, kb, word, r]
 
 
-@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_packed_scan_layout_bit_exact(erq, B):
     """The scan's packed copy holds exactly the index's codes, B bits each."""
     X, lab = S.mixture(3000, 128, 8, 3700 + B, scale="aniso")
@@ -191,7 +191,7 @@ def test_packed_scan_layout_bit_exact(erq, B):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("B", [1, 2, 6, 8])
+@pytest.mark.parametrize("B", [1, 2, 6, 8, 9])
 def test_tc_scan_every_code_width(erq, B):
     """Estimates from the packed codes stay within the FP16 query-rounding
     bound for code widths the larger tests do not cover."""
@@ -274,6 +274,15 @@ def test_fp8_recall_close_to_fp32(erq):
     rec = lambda ids: np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy(), gt)])
     ra, rb = rec(a_ids), rec(b_ids)
     assert rb >= ra - 0.01, (ra, rb)
+
+
+def test_fp8_rejects_nine_bit_codes(erq):
+    """B = 9: the split parts would need 5 bits (16 hc with |hc| <= 31), which
+    e4m3 does not hold exactly; the search refuses instead of rounding codes."""
+    X, P, gx, ox = _index(erq, 3000, 128, 9, 8, 4150)
+    Q = to_dev(S.mixture(4, 128, 16, 4151, comp_seed=4150, scale="aniso")[0])
+    with pytest.raises(erq.ErqError, match="B <= 8"):
+        gx.search(Q, 10, rerank_k=20, nprobe=2, precision="fp8")
 
 
 def test_fp8_split_recall_close_to_fp32(erq):

@@ -44,7 +44,7 @@ def _oracle_rows(ox, Q, probe, eps0):
 
 
 @pytest.mark.parametrize("D,B,kp,eps0", [(128, 5, 40, 1.9), (192, 7, 24, 1.9), (128, 3, 32, 1.0), (64, 8, 100, 2.5),
-                                         (128, 1, 20, 1.9), (256, 6, 40, 0.5)])
+                                         (128, 1, 20, 1.9), (256, 6, 40, 0.5), (128, 9, 32, 1.9)])
 def test_two_stage_matches_oracle(erq, D, B, kp, eps0):
     X, gx, ox = _index(erq, 20000, D, B, 64, 5000 + D + B)
     nq, nprobe, k = 200, 6, 10
