@@ -303,7 +303,7 @@ def run_reference(args):
                                              "rerank_k": kp, "precision": "fp64 (oracle)", "nprobe": nprobe,
                                              "similarity": args.metric,
                                              "l2": "inputs larger than L2 (codes > 129 MB)"},
-            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle", "host": host_info(),
                              "sample": f"{len(Qs)} queries of {args.workload} per step, nprobe "
                                        f"{describe_nprobe(npq)}, {len(rows)} rows encoded"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -387,7 +387,7 @@ def run_backward(args, emit=True, steps=None):
 
 def run_encoder_sweep(args):
     """Algorithm 1 throughput at the paper's Table 4 shape (D = 3072, unit-norm
-    embedding-like rows), B = 1..8: one JSON line per B with rows/s on a
+    embedding-like rows), B = 1..9: one JSON line per B with rows/s on a
     sample of rotated residuals (the same kernel erq_build_index runs), the
     implied time for 10^6 rows, and the same with the exact rotation added
     (Table 4 times rotation plus quantization)."""
@@ -417,7 +417,7 @@ def run_encoder_sweep(args):
     t0 = time.perf_counter()
     Rs = oracle.rotate(Xs, Ps)
     orot_s = 1e6 * (time.perf_counter() - t0) / m
-    for B in range(1, 9):
+    for B in range(1, 10):
         erq.encode(R[:1024], B)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -432,7 +432,7 @@ def run_encoder_sweep(args):
                           "seconds_per_1e6_rows": 1e6 * dt / n, "rotate_seconds_per_1e6_rows": rot_s,
                           "rotate_plus_encode_seconds_per_1e6_rows": rot_s + 1e6 * dt / n,
                           "cpu_baseline": {"value": m / odt, "unit": "rows/s", "cores": oracle.num_threads(),
-                                           "kind": "oracle", "sample": f"{m} of the same rows",
+                                           "kind": "oracle", "sample": f"{m} of the same rows", "host": host_info(),
                                            "seconds_per_1e6_rows": 1e6 * odt / m,
                                            "rotate_seconds_per_1e6_rows": orot_s,
                                            "rotate_plus_encode_seconds_per_1e6_rows": orot_s + 1e6 * odt / m},
@@ -752,9 +752,27 @@ def search_workload(args, env, erq, steps, warmup, headline):
         t_cpu = time_oracle(ox, Qs, args, npq, kp)
         import oracle
         cpu = {"value": len(Qs) / t_cpu, "unit": "queries/s", "cores": min(oracle.num_threads(), len(Qs)),
-               "kind": "oracle", "sample": f"{len(Qs)} queries, nprobe {describe_nprobe(npq)}, {len(rows)} rows encoded"}
+               "kind": "oracle", "host": host_info(),
+               "sample": f"{len(Qs)} queries, nprobe {describe_nprobe(npq)}, {len(rows)} rows encoded"}
     out["cpu"] = cpu
     return out
+
+
+def host_info():
+    """The host cores the oracle runs on: count, architecture, CPU model."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "cpu implementer"):
+                    model = (model + " " + line.split(":", 1)[1].strip()).strip()
+                    if k == "model name" or model.count(" ") >= 1:
+                        break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model or platform.processor()}
 
 
 def describe_nprobe(npq):

@@ -78,7 +78,10 @@ typedef struct {
     int32_t kmeans_sample;    /* rows sampled for k-means training, 0 = all              */
     uint64_t seed;            /* k-means initialisation seed                             */
     int32_t keep_raw;         /* keep the FP32 rows in the index (exact re-rank needs it)*/
-    int32_t reserved;
+    int32_t normalize;        /* 1: scale every row to unit length first (FP64 norm, one
+                                 rounding), so that ERQ_METRIC_COS searches are the
+                                 inner product of unit vectors; kept raw rows are the
+                                 scaled ones                                              */
     const float* centroids;   /* optional device [nlist][D] centroids to use instead of the
                                  means of the rows (requires assign; lists may then be
                                  empty): an index over one shard of a larger index's lists
@@ -107,7 +110,12 @@ typedef struct {
 /* erq_search_params.metric */
 typedef enum {
     ERQ_METRIC_L2 = 0,        /* squared Euclidean distance, smallest first               */
-    ERQ_METRIC_IP = 1         /* inner product, largest first (see erq_search)            */
+    ERQ_METRIC_IP = 1,        /* inner product, largest first (see erq_search)            */
+    ERQ_METRIC_COS = 2        /* cosine similarity, largest first: the inner product of
+                                 unit vectors.  Needs an index built with normalize = 1;
+                                 the query is scaled to unit length, then searched as
+                                 ERQ_METRIC_IP; dists / cand_est hold cosines.  Search
+                                 only (erq_search, erq_search_host)                       */
 } erq_metric;
 
 /* erq_search_params.flags */

@@ -343,9 +343,12 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     ix->B = p->B;
     ix->nlist = p->nlist;
     ix->keep_raw = p->keep_raw ? 1 : 0;
+    ix->normalized = p->normalize ? 1 : 0;
     ix->host_list_off = new std::vector<int64_t>();
+    float* Xn = nullptr;                 // rows scaled to unit length (normalize = 1)
     auto bail = [&](erq_status st) {
         cudaStreamSynchronize(s);
+        if (Xn && Xn != ix->X) cudaFree(Xn);
         erq_free_index(ix);
         return st;
     };
@@ -370,9 +373,19 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
 #undef ALLOC
     cudaError_t e;
     if ((e = cudaMemsetAsync(ix->status, 0, 4, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if (ix->normalized) {                // every later step sees the unit rows
+        if (ix->keep_raw) {
+            Xn = ix->X;
+        } else if (cudaMalloc(&Xn, sizeof(float) * (size_t)N * D) != cudaSuccess) {
+            Xn = nullptr;
+            return bail(fail(ERQ_ENOMEM, "erq_build_index: unit-row copy"));
+        }
+        if ((e = launch_normalize_rows(X, N, D, Xn, s)) != cudaSuccess) return bail(cuda_fail(e, "normalize rows"));
+        X = Xn;
+    }
     if ((e = cudaMemcpyAsync(ix->P, p->P, sizeof(float) * D * D, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return bail(cuda_fail(e, "copy P"));
-    if (ix->keep_raw &&
+    if (ix->keep_raw && X != ix->X &&
         (e = cudaMemcpyAsync(ix->X, X, sizeof(float) * (size_t)N * D, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return bail(cuda_fail(e, "copy X"));
     // --- assignment
@@ -436,6 +449,7 @@ extern "C" erq_status erq_build_index(const float* X, int64_t N, int32_t D, cons
     if ((st = check_status(ix, s)) != ERQ_OK) return bail2(st);
     if ((st = derive_gemm_arrays(ix, s)) != ERQ_OK) return bail2(st);
     cudaFree(assign);
+    if (Xn && Xn != ix->X) cudaFree(Xn);   // (derive_gemm_arrays synchronised the stream)
     int64_t mx = 0;
     for (int j = 0; j < nlist; ++j) mx = std::max(mx, (*ix->host_list_off)[j + 1] - (*ix->host_list_off)[j]);
     ix->max_list = mx;
@@ -895,7 +909,10 @@ static erq_status validate_search(const erq_index* ix, const float* Q, int64_t n
         return fail(ERQ_EUNSUPPORTED, "erq_search: tensor-core path unavailable for this D / k'");
     if (scan_fp32_smem(kp) > 220 * 1024 && p->precision == ERQ_PREC_FP32)
         return fail(ERQ_EUNSUPPORTED, "erq_search: k' too large for the FP32 scan");
-    if (p->metric != ERQ_METRIC_L2 && p->metric != ERQ_METRIC_IP) return fail(ERQ_EINVAL, "erq_search: unknown metric");
+    if (p->metric != ERQ_METRIC_L2 && p->metric != ERQ_METRIC_IP && p->metric != ERQ_METRIC_COS)
+        return fail(ERQ_EINVAL, "erq_search: unknown metric");
+    if (p->metric == ERQ_METRIC_COS && !ix->normalized)
+        return fail(ERQ_EINVAL, "erq_search: the cosine metric needs an index built with normalize = 1");
     return ERQ_OK;
 }
 
@@ -903,7 +920,19 @@ extern "C" erq_status erq_search(erq_index* ix, const float* Q, int64_t nq, cons
                                  float* dists, void* stream) {
     ERQ_TRY(validate_search(ix, Q, nq, p, ids, dists));
     if (nq == 0) return ERQ_OK;
-    return search_impl(ix, Q, nq, p, ids, dists, (cudaStream_t)stream);
+    if (p->metric != ERQ_METRIC_COS) return search_impl(ix, Q, nq, p, ids, dists, (cudaStream_t)stream);
+    // cosine: the inner-product search of the unit query over the unit rows
+    cudaStream_t s = (cudaStream_t)stream;
+    float* Qn = nullptr;
+    ERQ_CHECK_CUDA(cudaMallocAsync((void**)&Qn, sizeof(float) * (size_t)nq * ix->D, s));
+    erq_search_params q = *p;
+    q.metric = ERQ_METRIC_IP;
+    cudaError_t e = launch_normalize_rows(Q, nq, ix->D, Qn, s);
+    const erq_status st = e == cudaSuccess ? search_impl(ix, Qn, nq, &q, ids, dists, s) : cuda_fail(e, "normalize query");
+    const cudaError_t ef = cudaFreeAsync(Qn, s);
+    if (st != ERQ_OK) return st;
+    if (ef != cudaSuccess) return cuda_fail(ef, "erq_search: cudaFreeAsync");
+    return ERQ_OK;
 }
 
 extern "C" erq_status erq_search_two_stage(erq_index* ix, const float* Q, int64_t nq, const erq_search_params* p,
@@ -933,7 +962,13 @@ extern "C" erq_status erq_search_host(erq_index* ix, const float* Q_host, int64_
     int64_t* idd = (int64_t*)(base + (qb + 255) / 256 * 256);
     float* dd = (float*)((char*)idd + (ib + 255) / 256 * 256);
     ERQ_CHECK_CUDA(cudaMemcpyAsync(Qd, Q_host, qb, cudaMemcpyHostToDevice, s));
-    ERQ_TRY(search_impl(ix, Qd, nq, p, idd, dd, s));
+    erq_search_params q = *p;
+    if (p->metric == ERQ_METRIC_COS) {   // the unit query, in place in the staging buffer
+        q.metric = ERQ_METRIC_IP;
+        cudaError_t e = launch_normalize_rows(Qd, nq, ix->D, Qd, s);
+        if (e != cudaSuccess) return cuda_fail(e, "normalize query");
+    }
+    ERQ_TRY(search_impl(ix, Qd, nq, &q, idd, dd, s));
     ERQ_CHECK_CUDA(cudaMemcpyAsync(ids_host, idd, ib, cudaMemcpyDeviceToHost, s));
     ERQ_CHECK_CUDA(cudaMemcpyAsync(dists_host, dd, db, cudaMemcpyDeviceToHost, s));
     ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -1027,14 +1062,14 @@ extern "C" erq_status erq_index_export(const erq_index* ix, int32_t field, void*
     return ERQ_OK;
 }
 
-static const char kMagic[8] = {'E', 'R', 'Q', 'I', 'D', 'X', '0', '1'};
+static const char kMagic[8] = {'E', 'R', 'Q', 'I', 'D', 'X', '0', '2'};
 
 extern "C" erq_status erq_index_save(const erq_index* ix, const char* path) {
     if (!ix || !path) return fail(ERQ_EINVAL, "erq_index_save: null argument");
     FILE* f = fopen(path, "wb");
     if (!f) return fail(ERQ_EIO, std::string("erq_index_save: cannot open ") + path);
-    int64_t hdr[6] = {ix->N, ix->D, ix->B, ix->nlist, ix->keep_raw, ix->max_list};
-    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 8, 6, f) == 6;
+    int64_t hdr[7] = {ix->N, ix->D, ix->B, ix->nlist, ix->keep_raw, ix->max_list, ix->normalized};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 8, 7, f) == 7;
     const void* arrays[] = {ix->P, ix->C, ix->Cp, ix->cnorm2, ix->list_off, ix->list_ids, ix->row_of,
                             ix->cl_of_row, ix->codes, ix->f_add, ix->f_res, ix->g_const, ix->X};
     const size_t N = ix->N, D = ix->D, nl = ix->nlist;
@@ -1060,8 +1095,8 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
     FILE* f = fopen(path, "rb");
     if (!f) return fail(ERQ_EIO, std::string("erq_index_load: cannot open ") + path);
     char magic[8];
-    int64_t hdr[6];
-    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 8, 6, f) != 6) {
+    int64_t hdr[7];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 8, 7, f) != 7) {
         fclose(f);
         return fail(ERQ_EIO, "erq_index_load: not an index file (bad magic or header)");
     }
@@ -1072,6 +1107,7 @@ extern "C" erq_status erq_index_load(const char* path, void* stream, erq_index**
     ix->nlist = (int32_t)hdr[3];
     ix->keep_raw = (int32_t)hdr[4];
     ix->max_list = hdr[5];
+    ix->normalized = (int32_t)hdr[6];
     ix->host_list_off = new std::vector<int64_t>(ix->nlist + 1);
     if (ix->N < 1 || !valid_d(ix->D) || ix->B < 1 || ix->B > 9 || ix->nlist < 1) {
         fclose(f);

@@ -115,6 +115,7 @@ struct DeviceBuffer {
 struct erq_index {
     int64_t N = 0;
     int32_t D = 0, B = 0, nlist = 0, keep_raw = 0;
+    int32_t normalized = 0;      // rows scaled to unit length at build (cosine metric)
     int64_t max_list = 0;
     float* P = nullptr;          // [D][D]
     float* PT = nullptr;         // [D][D] transpose of P (B operand of q' = P^T q)

@@ -52,6 +52,7 @@ cudaError_t launch_sgemm(bool nt, const float* A, const float* B, float* C, int6
 cudaError_t launch_sqdist(const float* Q, const float* qn, const float* C, const float* cn, float* out, int64_t nq,
                           int nc, int D, cudaStream_t s);
 cudaError_t launch_row_sqnorm(const float* X, int64_t n, int D, float* out, cudaStream_t s);
+cudaError_t launch_normalize_rows(const float* X, int64_t n, int D, float* Y, cudaStream_t s);
 cudaError_t launch_centroids(const float* X, const int64_t* list_off, const int64_t* list_ids, int nlist, int D,
                              float* C, int keep_empty, cudaStream_t s);
 cudaError_t launch_group(const int32_t* assign, int64_t n, int nlist, int64_t* list_off, int64_t* list_ids,

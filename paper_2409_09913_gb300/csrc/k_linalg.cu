@@ -286,6 +286,30 @@ __global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int D,
     if (lane == 0) out[w] = s;
 }
 
+// Rows scaled to unit length (cosine similarity as the inner product of unit
+// vectors): y = fl32(x / sqrt(sum x^2)) with the sum in FP64, one warp per
+// row; a zero row stays zero.  X and Y may be the same array (each thread
+// rewrites only the elements it read).
+__global__ void normalize_rows_kernel(const float* X, int64_t n, int D, float* Y) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float* x = X + r * D;
+    double s = 0.0;
+    for (int k = lane; k < D; k += 32) s += (double)x[k] * (double)x[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double nrm = sqrt(s);
+    float* y = Y + r * D;
+    for (int k = lane; k < D; k += 32) y[k] = nrm > 0.0 ? (float)((double)x[k] / nrm) : 0.f;
+}
+
+cudaError_t launch_normalize_rows(const float* X, int64_t n, int D, float* Y, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    normalize_rows_kernel<<<(unsigned)ceil_div(n * 32, 256), 256, 0, s>>>(X, n, D, Y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_row_sqnorm(const float* X, int64_t n, int D, float* out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     count_launch();

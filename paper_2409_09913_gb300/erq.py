@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liberq.so")
 
 ERQ_OK, ERQ_EINVAL, ERQ_ENOMEM, ERQ_ECUDA, ERQ_ETIMEOUT, ERQ_EUNSUPPORTED, ERQ_EIO = range(7)
 PREC = {"fp32": 0, "fp16": 1, "fp8": 2, "int8": 3}
-METRIC = {"l2": 0, "ip": 1}
+METRIC = {"l2": 0, "ip": 1, "cos": 2}
 FIELDS = {"centroids": 0, "rot_centroids": 1, "list_offsets": 2, "list_ids": 3, "codes": 4, "f_add": 5,
           "f_res": 6, "P": 7, "raw": 8, "packed_codes": 9}
 
@@ -40,7 +40,7 @@ class ErqError(RuntimeError):
 class BuildParams(ct.Structure):
     _fields_ = [("B", ct.c_int32), ("nlist", ct.c_int32), ("P", ct.c_void_p), ("assign", ct.c_void_p),
                 ("kmeans_iters", ct.c_int32), ("kmeans_sample", ct.c_int32), ("seed", ct.c_uint64),
-                ("keep_raw", ct.c_int32), ("reserved", ct.c_int32), ("centroids", ct.c_void_p)]
+                ("keep_raw", ct.c_int32), ("normalize", ct.c_int32), ("centroids", ct.c_void_p)]
 
 
 class SearchParams(ct.Structure):
@@ -439,14 +439,17 @@ class Index:
 
 
 def build_index(X, P, B, nlist=1, *, assign=None, keep_raw=True, kmeans_iters=10, kmeans_sample=0, seed=0,
-                centroids=None):
+                centroids=None, normalize=False):
     """Build an IVF + extended-RaBitQ index from device rows X [N, D].
     ``centroids`` (device [nlist, D], with ``assign``): use these instead of the
-    means of the rows (an index over one shard of a larger index's lists)."""
+    means of the rows (an index over one shard of a larger index's lists).
+    ``normalize``: scale the rows to unit length first (searches with
+    metric "cos")."""
     X = _dev(X, torch.float32, "X", 2)
     P = _dev(P, torch.float32, "P", 2)
     bp = BuildParams()
     bp.B, bp.nlist, bp.P = int(B), int(nlist), P.data_ptr()
+    bp.normalize = 1 if normalize else 0
     if assign is not None:
         assign = _dev(assign, torch.int32, "assign", 1)
         bp.assign = assign.data_ptr()

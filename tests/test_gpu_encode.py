@@ -81,7 +81,7 @@ def test_encode_empty_and_invalid(erq):
     with pytest.raises(erq.ErqError):
         erq.encode(torch.zeros((2, 65), device="cuda"), 4)
     with pytest.raises(erq.ErqError):
-        erq.encode(torch.zeros((2, 64), device="cuda"), 9)
+        erq.encode(torch.zeros((2, 64), device="cuda"), 10)
 
 
 @pytest.mark.parametrize("D", [64, 960])

@@ -157,3 +157,39 @@ def test_ip_rejects_unknown_metric(erq):
     rc = erq.lib().erq_search(gx._h, ct.c_void_p(Q.data_ptr()), 4, ct.byref(sp), ct.c_void_p(ids.data_ptr()),
                               ct.c_void_p(d.data_ptr()), None)
     assert rc == erq.ERQ_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_cosine_is_the_inner_product_of_unit_vectors(erq, precision):
+    """Cosine similarity (Section 7: the method adapts to cosine as RaBitQ
+    does): an index built with normalize = 1 holds unit rows (FP64 norm, one
+    rounding), the query is scaled to unit length and the inner-product search
+    runs; the answer equals the oracle's inner-product search over the same
+    unit rows and unit queries, and the values are the exact cosines."""
+    X, lab = S.mixture(20000, 128, 16, 4700, scale="aniso")
+    assign = S.kmeans_assign(X, 32, 4, 4707)
+    P = S.random_orthogonal(128, 4701)
+    gx = erq.build_index(to_dev(X), to_dev(P), 5, 32, assign=to_dev(assign), normalize=True)
+    Xn = gx.export("raw").numpy()
+    X64 = X.astype(np.float64)
+    ref_n = (X64 / np.linalg.norm(X64, axis=1, keepdims=True)).astype(np.float32)
+    assert np.abs(Xn.astype(np.float64) - ref_n).max() <= 6e-8      # one rounding of the FP64 quotient
+    Q, _ = S.mixture(200, 128, 16, 4702, comp_seed=4700, scale="aniso")
+    Q = Q * np.float32(3.5)                                          # any query scale
+    probe = S.random_probe_lists(200, 32, 6, 4703)
+    ids, vals = gx.search(to_dev(Q), 10, rerank_k=40, probe=to_dev(probe), nprobe=6, precision=precision,
+                          metric="cos")
+    torch.cuda.synchronize()
+    Qn = Q.astype(np.float64) / np.linalg.norm(Q.astype(np.float64), axis=1, keepdims=True)
+    exact = Qn @ Xn.astype(np.float64).T                             # cosines of the unit rows
+    got_i, got_v = ids.cpu().numpy(), vals.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got_v, np.take_along_axis(exact, got_i, 1), atol=2e-6)
+    ox = oracle.build_index(Xn, P, assign, 32, 5)
+    ref = oracle.search(ox, Qn, 10, kprime=40, probe=probe, metric="ip")
+    agree = (got_i == ref["ids"]).mean()
+    assert agree >= 0.97, agree                     # differences only where estimates tie at the k'-th candidate
+    same = (got_i == ref["ids"]).all(1)
+    np.testing.assert_allclose(got_v[same], ref["dists"][same], atol=2e-6)
+    gx2 = erq.build_index(to_dev(X[:3000]), to_dev(P), 5, 4, assign=to_dev(assign[:3000] % 4))
+    with pytest.raises(erq.ErqError, match="normalize"):
+        gx2.search(to_dev(Q[:4]), 10, rerank_k=20, nprobe=2, metric="cos")
