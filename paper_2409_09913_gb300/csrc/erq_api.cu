@@ -849,7 +849,7 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     L.wait_ns = ix->wait_ns;
     L.stall_stage = ix->stall_stage;
     if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(L.tq, 0xff, sizeof(uint64_t) * nq, s));
-    if (tcp) ERQ_CHECK_CUDA(cudaMemsetAsync(ix->dctr, 0, sizeof(unsigned int), s));
+    ERQ_CHECK_CUDA(cudaMemsetAsync(ix->dctr, 0, sizeof(unsigned int), s));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

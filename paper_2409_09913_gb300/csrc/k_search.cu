@@ -300,6 +300,7 @@ struct ScanArgs {
     uint64_t* inter;            // [L][kp]
     int32_t* inter_cnt;         // [L]
     int64_t nq, N;              // extents of Qrot and of the stored rows (device-side checks)
+    unsigned int* work_ctr;     // items taken after the first grid-size ones (zero at launch)
     int maxp, D, B, kp, RR, nlist;
     int ip;                     // inner-product metric: est = -<c, q_r> + (f_res / 4) <2 ybar, q'>
     DevChecks ck;
@@ -354,6 +355,16 @@ __device__ __forceinline__ void fp32_store(const Fp32Stage<CB>& st, float* qs, f
     }
 }
 
+// The next work item of a block: the first grid-size items go to the blocks
+// in order, the rest to whichever block asks first (items come by decreasing
+// list size, so this balances the tail).
+__device__ __forceinline__ int64_t fp32_next_item(unsigned int* ctr, int64_t* s_next) {
+    __syncthreads();                              // every thread has read the previous value
+    if (threadIdx.x == 0) *s_next = (int64_t)gridDim.x + atomicAdd(ctr, 1u);
+    __syncthreads();
+    return *s_next;
+}
+
 template <int CB>
 __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -366,6 +377,7 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
     __shared__ int s_hsize[SC_QT];
     __shared__ float s_g[SC_RB], s_fh[SC_RB];
     __shared__ uint32_t s_id[SC_RB];
+    __shared__ int64_t s_next;
 
     const int tid = threadIdx.x;
     const int tq = tid & 7, tr = tid >> 3;
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
     int64_t nitems = *a.n_items;
     if (!ERQ_DCHECK(nitems >= 0 && nitems <= a.ck.items, a.ck.status, 5)) nitems = 0;
 
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < nitems; it = fp32_next_item(a.work_ctr, &s_next)) {
         const int4 item = a.items[it];
         if (!ERQ_DCHECK(item.x >= 0 && item.x < 2 * a.nlist, a.ck.status, 5)) continue;   // block-uniform
         const int v = item.x, c = v % a.nlist;                  // phase cluster -> cluster
@@ -834,7 +846,8 @@ cudaError_t launch_scan_fp32(const ScanLaunch& L, cudaStream_t s) {
     a.list_ids = L.list_ids; a.qlist = L.qlist; a.qoff = L.qoff; a.items = L.items; a.n_items = L.n_items;
     a.dqc = L.dqc; a.slot_off = L.slot_off; a.qbase = L.qbase; a.inter = L.inter; a.inter_cnt = L.inter_cnt;
     a.maxp = L.maxp; a.D = L.D; a.B = L.B; a.kp = L.kp; a.RR = L.RR; a.ip = L.ip; a.nlist = L.nlist;
-    a.nq = L.nq; a.N = L.N;
+    a.nq = L.nq; a.N = L.N; a.work_ctr = L.work_ctr;
+    if (!a.work_ctr) return cudaErrorInvalidValue;
     const size_t smem = scan_fp32_smem(L.kp);
     const bool wide = L.B > 8;                    // 16-bit codes
     cudaError_t e = wide ? cudaFuncSetAttribute(scan_fp32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
