@@ -367,16 +367,14 @@ erq_status erq_set_wait_limit(erq_index* index, uint64_t ns, int64_t stall_stage
 
 /* Allocation-free variant of erq_search_backward (no counterpart in the paper;
  * an interface for callers that cannot allocate device memory while they run,
- * e.g. a training step being recorded into a CUDA graph, where stream capture
- * forbids cudaMalloc, or a host that owns all device memory through its own
- * pool).  Same arguments, result and errors as erq_search_backward.  Its
+ * e.g. a host that owns all device memory through its own pool).  Same arguments, result and errors as erq_search_backward.  Its
  * intermediates (2 * nq * D floats and nq ints) live in one static device array
  * of ERQ_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
  * keeps until the process exits; requests with 8*nq*D + 4*nq + 512 bytes above
  * that size are rejected with ERQ_EINVAL (at D = 1024: nq <= 2046).  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and keeps it for the life of the process; it should be made before any
- * stream capture, and the kept address is no longer valid once the device's
+ * and keeps it for the life of the process; the kept address is no longer
+ * valid once the device's
  * primary context is destroyed (cudaDeviceReset), after which this entry point
  * must not be called again in that process.  All calls share the array and the previous call's
  * contents are never read, but calls that can overlap on the GPU (different

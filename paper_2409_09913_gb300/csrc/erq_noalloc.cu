@@ -1,7 +1,6 @@
 // erq_search_backward_noalloc: the query gradient of erq_search_backward for
-// callers that cannot allocate device memory while they run.  Examples are a
-// training step being recorded into a CUDA graph (stream capture forbids
-// cudaMalloc) and hosts that hand all device memory out of their own pool.
+// callers that cannot allocate device memory while they run, for example
+// hosts that hand all device memory out of their own pool.
 //
 // The intermediate matrices of the backward pass (V, Wv and V's row
 // exponents) live in one statically sized array in device global memory,

@@ -1,8 +1,8 @@
 """The allocation-free backward entry point.
 
 erq_search_backward_noalloc serves callers that cannot allocate device memory
-during the call (a step being recorded into a CUDA graph, where stream capture
-forbids cudaMalloc, or a host whose device memory comes from its own pool).
+during the call (for example a host whose device memory comes from its own
+pool).
 It must give the same gradient as erq_search_backward, which allocates its
 workspace, on consecutive calls that share the fixed scratch array, and it
 must refuse requests larger than that array."""
