@@ -270,7 +270,7 @@ __global__ void plan_items_kernel(const int64_t* __restrict__ cnt64, const int64
 // Item = (cluster c, query chunk, row range).  Tile: 64 queries x 128 rows,
 // 128 threads with 8 x 8 outputs each (queries 4 tq .. 4 tq + 3 and 32 + 4 tq
 // .. + 3, rows 4 tr .. + 3 and 64 + 4 tr .. + 3: four 16-byte shared loads per
-// 64 FFMA), K step 32.  The operands of step k + 1 are loaded from global
+// 64 FFMA; an item of at most 32 queries skips the upper half), K step 32.  The operands of step k + 1 are loaded from global
 // memory into registers while step k is multiplied out of the other shared
 // buffer (one barrier per step); codes are widened to 2 ybar - (2^B - 1) as
 // they are stored.  After a tile the estimates go to shared memory (over the
@@ -434,18 +434,33 @@ __global__ void __launch_bounds__(SC_THREADS) scan_fp32_kernel(ScanArgs a) {
                 if (more) fp32_load(st, qrow, crow, k0 + SC_BK, tid);
                 const float* qs = ops + buf * SC_BK * (SC_QS + SC_CS);
                 const float* cs = qs + SC_BK * SC_QS;
+                if (nqi > 32) {
 #pragma unroll 4
-                for (int kk = 0; kk < SC_BK; ++kk) {
-                    const float4 q0 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + tq * 4);
-                    const float4 q1 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + 32 + tq * 4);
-                    const float4 c0 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + tr * 4);
-                    const float4 c1 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + 64 + tr * 4);
-                    const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                    const float ca[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                    for (int kk = 0; kk < SC_BK; ++kk) {
+                        const float4 q0 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + tq * 4);
+                        const float4 q1 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + 32 + tq * 4);
+                        const float4 c0 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + tr * 4);
+                        const float4 c1 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + 64 + tr * 4);
+                        const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                        const float ca[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
+                        for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                    }
+                } else {                                   // queries 32..63 are padding: half the FMAs
+#pragma unroll 4
+                    for (int kk = 0; kk < SC_BK; ++kk) {
+                        const float4 q0 = *reinterpret_cast<const float4*>(qs + kk * SC_QS + tq * 4);
+                        const float4 c0 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + tr * 4);
+                        const float4 c1 = *reinterpret_cast<const float4*>(cs + kk * SC_CS + 64 + tr * 4);
+                        const float qa[4] = {q0.x, q0.y, q0.z, q0.w};
+                        const float ca[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(qa[i], ca[j], acc[i][j]);
+                    }
                 }
                 if (more) {
                     float* nq = ops + (buf ^ 1) * SC_BK * (SC_QS + SC_CS);
