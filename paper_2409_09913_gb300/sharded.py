@@ -107,13 +107,29 @@ def _to_local(glob, g2l):
     return out
 
 
-def sharded_search(backend, Q, k, kp, gids, n_total, group=None):
+class _DistComm:
+    """The exchange over a torch.distributed group (NCCL across GPUs, gloo on CPU)."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist, self.group = dist, group
+
+    def world_size(self):
+        return self.dist.get_world_size(self.group)
+
+    def all_gather(self, out, t):
+        self.dist.all_gather(out, t, group=self.group)
+
+
+def sharded_search(backend, Q, k, kp, gids, n_total, group=None, comm=None):
     """Steps 1-5 above on this rank; every rank returns the same (ids, values)
     [nq, k] with global ids.  ``gids``: global id of each local row (torch,
-    on the backend's device); ``n_total``: rows of the whole index."""
+    on the backend's device); ``n_total``: rows of the whole index.
+    ``comm``: the exchange (world_size(), all_gather(list, tensor)); by
+    default torch.distributed on ``group``."""
     import torch
-    import torch.distributed as dist
-    world = dist.get_world_size(group)
+    comm = comm or _DistComm(group)
+    world = comm.world_size()
     dev = gids.device
     g2l = torch.full((n_total,), -1, dtype=torch.int64, device=dev)
     g2l[gids] = torch.arange(len(gids), dtype=torch.int64, device=dev)
@@ -121,13 +137,13 @@ def sharded_search(backend, Q, k, kp, gids, n_total, group=None):
     cid = _to_global(lid.to(torch.int64), gids)
     all_i = [torch.empty_like(cid) for _ in range(world)]          # 2. exchange
     all_v = [torch.empty_like(lest) for _ in range(world)]
-    dist.all_gather(all_i, cid.contiguous(), group=group)
-    dist.all_gather(all_v, lest.contiguous(), group=group)
+    comm.all_gather(all_i, cid.contiguous())
+    comm.all_gather(all_v, lest.contiguous())
     mid, _ = backend.merge(torch.cat(all_i, 1), torch.cat(all_v, 1), kp)   # 3. global top-k'
     rid, rd = backend.rerank(Q, _to_local(mid, g2l), k)           # 4. exact, rows held here
     rid = _to_global(rid, gids)
     all_i = [torch.empty_like(rid) for _ in range(world)]
     all_v = [torch.empty_like(rd) for _ in range(world)]
-    dist.all_gather(all_i, rid.contiguous(), group=group)
-    dist.all_gather(all_v, rd.contiguous(), group=group)
+    comm.all_gather(all_i, rid.contiguous())
+    comm.all_gather(all_v, rd.contiguous())
     return backend.merge(torch.cat(all_i, 1), torch.cat(all_v, 1), k)   # 5. the answer
