@@ -126,7 +126,9 @@ typedef enum {
                                     sized from host-side upper bounds, so the call can be
                                     recorded into a CUDA graph once a first call with the
                                     same (nq, nprobe, k') has sized them; device-side errors
-                                    surface at the next synchronous call or erq_index_status */
+                                    surface at the next synchronous call or erq_index_status.
+                                    Ignored with explicit probe lists, which are sized from a
+                                    read-back (their distinctness is not checked)          */
 
 /* Read-only description of an index. */
 typedef struct {

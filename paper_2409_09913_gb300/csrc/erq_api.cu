@@ -510,10 +510,25 @@ static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, cons
     if ((e = launch_two_stage_rows(probe_c, nq, maxp, ix->list_off, rbase, qrows, s)) != cudaSuccess ||
         (e = launch_excl_scan_i64(qrows, qoffr, nq, s)) != cudaSuccess)
         return bail(cuda_fail(e, "two-stage: row offsets"));
+    // slots for every probed row: bounded on the host (nq x the rows of the maxp
+    // largest lists) so that nothing is read back, unless the bound would take
+    // more than 2 GB of scratch, when the exact count is read back instead
     int64_t rows = 0;
-    if ((e = cudaMemcpyAsync(&rows, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return bail(cuda_fail(e, "two-stage: row count"));
+    {
+        const std::vector<int64_t>& off = *ix->host_list_off;
+        std::vector<int64_t> sz((size_t)ix->nlist);
+        for (int c = 0; c < ix->nlist; ++c) sz[c] = off[c + 1] - off[c];
+        const int top = std::min(maxp, ix->nlist);
+        std::partial_sort(sz.begin(), sz.begin() + top, sz.end(), std::greater<int64_t>());
+        int64_t per_q = 0;
+        for (int i = 0; i < top; ++i) per_q += sz[i];
+        rows = nq * per_q;
+    }
+    if (p->probe || rows * 20 > (1ll << 31)) {          // (explicit lists: distinctness is not checked)
+        if ((e = cudaMemcpyAsync(&rows, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bail(cuda_fail(e, "two-stage: row count"));
+    }
     // one block: ub, lb, s1 [rows] f32 | skey [rows] u64 | T [nq][4D] f32 | tau [nq] f32 | scnt [nq] i32
     // (every part starts on a 256-byte boundary: the tables are read as float4)
     const size_t r = (size_t)std::max<int64_t>(rows, 1);
@@ -536,13 +551,15 @@ static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, cons
         return bail(cuda_fail(e, "two-stage: rerank"));
     if (stats_out) {
         std::vector<int32_t> cnt((size_t)nq);
+        int64_t total = 0;
         if ((e = cudaMemcpyAsync(cnt.data(), L.scnt, sizeof(int32_t) * (size_t)nq, cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess ||
+            (e = cudaMemcpyAsync(&total, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return bail(cuda_fail(e, "two-stage: survivors"));
         int64_t sv = 0;
         for (int32_t v : cnt) sv += v;
-        stats_out[0] = rows;
+        stats_out[0] = total;
         stats_out[1] = sv;
     }
     release();
@@ -775,7 +792,9 @@ static erq_status search_impl(erq_index* ix, const float* Q, int64_t nq, const e
     if (ts) return two_stage_tail(ix, Q, nq, p, ids, dists, s, ts->eps0, ts->stats, pa.probe_c, dqc, Qrot, maxp, kp,
                                   k, do_rerank, cand, ck);
     int64_t Ltot = 0, nitems = 0;
-    const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0;
+    // host-side bounds assume distinct probed lists per query, which the
+    // centroid search guarantees; explicit probe lists are sized exactly
+    const bool async = (p->flags & ERQ_SEARCH_ASYNC) != 0 && !explicit_probe;
     if (async) {
         // upper bounds from the cluster sizes (no read-back):
         //   items <= maxR * ceil(nq * maxp / QT) + sum_c nr_c,  lists <= nq * (sum of the maxp largest nr_c)
