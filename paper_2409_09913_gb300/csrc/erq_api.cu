@@ -60,7 +60,7 @@ void free_index_arrays(erq_index* ix) {
                     ix->P,     ix->C,     ix->Cp,      ix->cnorm2, ix->list_off, ix->list_ids,
                     ix->row_of, ix->cl_of_row, ix->codes, ix->f_add, ix->f_res,  ix->g_const,
                     ix->X,     ix->status, ix->ws,      ix->ws_b,   ix->io,    ix->rowmeta, ix->poff, ix->codes_p,
-                    ix->dstats, ix->PT_hi, ix->C_hi, ix->dctr, ix->rowmeta1};   // PT_lo / C_lo live inside those blocks
+                    ix->dstats, ix->PT_hi, ix->C_hi, ix->dctr, ix->rowmeta1, ix->ws_ts};   // PT_lo / C_lo live inside those blocks
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ix->pinned) cudaFreeHost(ix->pinned);
@@ -491,28 +491,11 @@ static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, cons
                                  const float* dqc, const float* Qrot, int maxp, int kp, int k, bool do_rerank,
                                  uint64_t* cand, const DevChecks& ck) {
     const int D = ix->D;
-    int32_t* rbase = nullptr;
-    int64_t *qrows = nullptr, *qoffr = nullptr;
-    void* big = nullptr;
-    auto release = [&]() {
-        for (void* ptr : {(void*)rbase, (void*)qrows, (void*)qoffr, big})
-            if (ptr) cudaFreeAsync(ptr, s);
-    };
-    auto bail = [&](erq_status st) {
-        release();
-        return st;
-    };
-    if (cudaMallocAsync((void**)&rbase, sizeof(int32_t) * (size_t)nq * maxp, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&qrows, sizeof(int64_t) * (size_t)nq, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&qoffr, sizeof(int64_t) * (size_t)(nq + 1), s) != cudaSuccess)
-        return bail(fail(ERQ_ENOMEM, "two-stage: row offsets"));
     cudaError_t e;
-    if ((e = launch_two_stage_rows(probe_c, nq, maxp, ix->list_off, rbase, qrows, s)) != cudaSuccess ||
-        (e = launch_excl_scan_i64(qrows, qoffr, nq, s)) != cudaSuccess)
-        return bail(cuda_fail(e, "two-stage: row offsets"));
     // slots for every probed row: bounded on the host (nq x the rows of the maxp
-    // largest lists) so that nothing is read back, unless the bound would take
-    // more than 2 GB of scratch, when the exact count is read back instead
+    // largest lists) so that nothing is read back, unless the probe lists are
+    // explicit (their distinctness is not checked) or the bound would take more
+    // than 2 GB of scratch, when the exact count is read back instead
     int64_t rows = 0;
     {
         const std::vector<int64_t>& off = *ix->host_list_off;
@@ -524,31 +507,52 @@ static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, cons
         for (int i = 0; i < top; ++i) per_q += sz[i];
         rows = nq * per_q;
     }
-    if (p->probe || rows * 20 > (1ll << 31)) {          // (explicit lists: distinctness is not checked)
+    const bool exact = p->probe != nullptr || rows * 20 > (1ll << 31);
+    // one index-owned scratch block (kept between calls):
+    //   rbase [nq][maxp] i32 | qrows [nq] i64 | qoffr [nq+1] i64 | ub, lb, s1 [rows] f32 |
+    //   skey [rows] u64 | T [nq][4D] f32 | tau [nq] f32 | scnt [nq] i32
+    // (every part starts on a 256-byte boundary: the tables are read as float4)
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t off_qrows = up(4 * (size_t)nq * maxp), off_qoffr = up(off_qrows + 8 * (size_t)nq);
+    const size_t off_rows = up(off_qoffr + 8 * (size_t)(nq + 1));
+    ERQ_TRY(ensure_ws(&ix->ws_ts, &ix->ws_ts_bytes, off_rows));
+    int32_t* rbase = (int32_t*)ix->ws_ts;
+    int64_t* qrows = (int64_t*)((char*)ix->ws_ts + off_qrows);
+    int64_t* qoffr = (int64_t*)((char*)ix->ws_ts + off_qoffr);
+    if ((e = launch_two_stage_rows(probe_c, nq, maxp, ix->list_off, rbase, qrows, s)) != cudaSuccess ||
+        (e = launch_excl_scan_i64(qrows, qoffr, nq, s)) != cudaSuccess)
+        return cuda_fail(e, "two-stage: row offsets");
+    if (exact) {
         if ((e = cudaMemcpyAsync(&rows, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return bail(cuda_fail(e, "two-stage: row count"));
+            return cuda_fail(e, "two-stage: row count");
     }
-    // one block: ub, lb, s1 [rows] f32 | skey [rows] u64 | T [nq][4D] f32 | tau [nq] f32 | scnt [nq] i32
-    // (every part starts on a 256-byte boundary: the tables are read as float4)
     const size_t r = (size_t)std::max<int64_t>(rows, 1);
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t off_skey = up(12 * r), off_T = up(off_skey + 8 * r);
+    const size_t off_skey = up(off_rows + 12 * r), off_T = up(off_skey + 8 * r);
     const size_t off_tau = up(off_T + (size_t)nq * 16 * D), off_cnt = up(off_tau + 4 * (size_t)nq);
-    if (cudaMallocAsync(&big, off_cnt + 4 * (size_t)nq, s) != cudaSuccess) return bail(fail(ERQ_ENOMEM, "two-stage"));
-    char* b = (char*)big;
+    const size_t need = off_cnt + 4 * (size_t)nq;
+    if (ix->ws_ts_bytes < need) {        // growing replaces the block: keep the offsets computed so far
+        ERQ_CHECK_CUDA(cudaStreamSynchronize(s));
+        std::vector<char> head(off_rows);
+        ERQ_CHECK_CUDA(cudaMemcpy(head.data(), ix->ws_ts, off_rows, cudaMemcpyDeviceToHost));
+        ERQ_TRY(ensure_ws(&ix->ws_ts, &ix->ws_ts_bytes, need));
+        ERQ_CHECK_CUDA(cudaMemcpy(ix->ws_ts, head.data(), off_rows, cudaMemcpyHostToDevice));
+        rbase = (int32_t*)ix->ws_ts;
+        qoffr = (int64_t*)((char*)ix->ws_ts + off_qoffr);
+    }
+    char* b = (char*)ix->ws_ts;          // the offsets are from the block's start
     TwoStageLaunch L;
     L.probe_c = probe_c; L.dqc = dqc; L.list_off = ix->list_off; L.poff = ix->poff; L.codes_p = ix->codes_p;
     L.rowmeta = ix->rowmeta; L.meta1 = ix->rowmeta1; L.Qrot = Qrot; L.T = (float*)(b + off_T);
     L.rbase = rbase; L.qoffr = qoffr;
-    L.ub = (float*)b; L.lb = (float*)b + r; L.s1 = (float*)b + 2 * r;   // 4-byte elements
+    L.ub = (float*)(b + off_rows); L.lb = L.ub + r; L.s1 = L.ub + 2 * r;   // 4-byte elements
     L.skey = (uint64_t*)(b + off_skey); L.scratch = (uint32_t*)(b + off_skey);
     L.tau = (float*)(b + off_tau); L.scnt = (int32_t*)(b + off_cnt); L.cand = cand;
     L.nq = nq; L.maxp = maxp; L.D = D; L.B = ix->B; L.kp = kp; L.eps0 = eps0;
-    if ((e = launch_two_stage(L, s)) != cudaSuccess) return bail(cuda_fail(e, "two-stage"));
+    if ((e = launch_two_stage(L, s)) != cudaSuccess) return cuda_fail(e, "two-stage");
     if ((e = launch_rerank(cand, nq, kp, ix->X, Q, D, k, do_rerank ? 1 : 0, 0, ids, dists, p->cand_ids, p->cand_est,
                            ck, s)) != cudaSuccess)
-        return bail(cuda_fail(e, "two-stage: rerank"));
+        return cuda_fail(e, "two-stage: rerank");
     if (stats_out) {
         std::vector<int32_t> cnt((size_t)nq);
         int64_t total = 0;
@@ -556,13 +560,12 @@ static erq_status two_stage_tail(erq_index* ix, const float* Q, int64_t nq, cons
                 cudaSuccess ||
             (e = cudaMemcpyAsync(&total, qoffr + nq, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return bail(cuda_fail(e, "two-stage: survivors"));
+            return cuda_fail(e, "two-stage: survivors");
         int64_t sv = 0;
         for (int32_t v : cnt) sv += v;
         stats_out[0] = total;
         stats_out[1] = sv;
     }
-    release();
     return ERQ_OK;
 }
 

@@ -153,6 +153,8 @@ struct erq_index {
     void* ws = nullptr;          // phase-A / build workspace
     size_t ws_bytes = 0;
     void* ws_b = nullptr;        // phase-B workspace (data-dependent sizes)
+    void* ws_ts = nullptr;       // two-stage search scratch (grown on demand, kept)
+    size_t ws_ts_bytes = 0;
     size_t ws_b_bytes = 0;
     void* io = nullptr;          // device staging of erq_search_host
     size_t io_bytes = 0;
