@@ -387,7 +387,7 @@ def run_backward(args, emit=True, steps=None):
 
 def run_encoder_sweep(args):
     """Algorithm 1 throughput at the paper's Table 4 shape (D = 3072, unit-norm
-    embedding-like rows), B = 1..9: one JSON line per B with rows/s on a
+    embedding-like rows), B = 1..10: one JSON line per B with rows/s on a
     sample of rotated residuals (the same kernel erq_build_index runs), the
     implied time for 10^6 rows, and the same with the exact rotation added
     (Table 4 times rotation plus quantization)."""
@@ -417,7 +417,7 @@ def run_encoder_sweep(args):
     t0 = time.perf_counter()
     Rs = oracle.rotate(Xs, Ps)
     orot_s = 1e6 * (time.perf_counter() - t0) / m
-    for B in range(1, 10):
+    for B in range(1, 11):
         erq.encode(R[:1024], B)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -445,7 +445,7 @@ def run_two_stage_sweep(args):
     few-queries regime: the 1M x 960 workload (B = 5, 4,096 lists, nprobe 16,
     k' = 20), batches of nq in {1, 16, 256, 1024} queries; per arm the median
     latency of a batch (host clock around the call with a device synchronise,
-    since the two-stage call synchronises to size its buffers), recall@10 and
+    the same for every arm), recall@10 and
     the surviving fraction of the probed rows."""
     import torch
     from paper_2409_09913_gb300 import build as erq_build

@@ -194,12 +194,15 @@ erq_status erq_rotate(const float* X, int64_t n, int32_t D, const float* P, floa
 /* Algorithm 1 (Section 3.1) on each row of Rrot (device [n][D], rotated
  * residuals o', any scale).  Writes codes[n][D] (ybar_u: one byte per
  * coordinate for B <= 8, a little-endian 16-bit word per coordinate for
- * B = 9, i.e. 2 n D bytes), f_add[n] = fl32(||o'||^2), f_res[n] = fl32(-2 ||o'||^2 / ip*) with
+ * B = 9 and 10, i.e. 2 n D bytes), f_add[n] = fl32(||o'||^2), f_res[n] = fl32(-2 ||o'||^2 / ip*) with
  * ip* = <ybar, |o'|> at the optimum (0 for o' = 0), and optionally stats[n][2] =
  * (ip*, ||ybar||^2) in FP64.  Critical values are visited in ascending exact
  * rational order, ties by coordinate; <y_cur,o'> accumulates in FP64 in that
- * order; the first state of maximal <y/||y||, o'> wins.
- * Errors: EINVAL (B outside 1..9, D), ECUDA. */
+ * order; the first state of maximal <y/||y||, o'> wins.  B = 10 (the widest
+ * code of Table 4) is accepted here, for the encoder alone; an index stores
+ * at most B = 9 bits per coordinate (erq_build_index).
+ * Errors: EINVAL (B outside 1..10, D), EUNSUPPORTED (a row whose non-zero
+ * magnitudes span more than 2^118), ECUDA. */
 erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add,
                       float* f_res, double* stats, void* stream);
 

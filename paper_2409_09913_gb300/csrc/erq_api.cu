@@ -228,7 +228,7 @@ extern "C" erq_status erq_rotate(const float* X, int64_t n, int32_t D, const flo
 extern "C" erq_status erq_encode(const float* Rrot, int64_t n, int32_t D, int32_t B, uint8_t* codes, float* f_add, float* f_res,
                       double* stats, void* stream) {
     if (n < 0 || !valid_d(D)) return fail(ERQ_EINVAL, "erq_encode: D must be a multiple of 64 in [64, 4096], n >= 0");
-    if (B < 1 || B > 9) return fail(ERQ_EINVAL, "erq_encode: B must be in [1, 9]");
+    if (B < 1 || B > 10) return fail(ERQ_EINVAL, "erq_encode: B must be in [1, 10]");
     if (n == 0) return ERQ_OK;
     if (!Rrot || !codes || !f_add || !f_res) return fail(ERQ_EINVAL, "erq_encode: null pointer");
     uint32_t* status = nullptr;

@@ -41,10 +41,17 @@ namespace erq {
 
 namespace {
 
+// event word: the FP32 key in the high half, then the coordinate i (22 bits)
+// and the level m (10 bits: m <= 2^(B-1) - 2 = 510 at B = 10)
+constexpr int EV_MBITS = 10;
+constexpr uint64_t EV_MMASK = (1u << EV_MBITS) - 1, EV_IMASK = (1u << (32 - EV_MBITS)) - 1;
+__device__ __forceinline__ int ev_i(uint64_t x) { return (int)((x >> EV_MBITS) & EV_IMASK); }
+__device__ __forceinline__ int ev_m(uint64_t x) { return (int)(x & EV_MMASK); }
+
 struct EncSmem {
     float* a;         // [D] |o'_i|
-    uint8_t* cnt;     // [D] events of coordinate i already consumed
-    uint64_t* keys;   // [W] (key32 << 32) | (i << 8) | m
+    uint16_t* cnt;    // [D] events of coordinate i already consumed
+    uint64_t* keys;   // [W] (key32 << 32) | (i << EV_MBITS) | m
 };
 
 // Exponent of the lowest mantissa bit of a positive FP32 value.
@@ -113,12 +120,12 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const size_t per_warp = (size_t)W * 8 + (size_t)D * 5 + 64;
+    const size_t per_warp = (size_t)W * 8 + (size_t)D * 6 + 64;
     unsigned char* base = smem_raw + (size_t)warp * ((per_warp + 15) / 16 * 16);
     EncSmem sm;
     sm.keys = reinterpret_cast<uint64_t*>(base);
     sm.a = reinterpret_cast<float*>(base + (size_t)W * 8);
-    sm.cnt = reinterpret_cast<uint8_t*>(base + (size_t)W * 8 + (size_t)D * 4);
+    sm.cnt = reinterpret_cast<uint16_t*>(base + (size_t)W * 8 + (size_t)D * 4);
 
     const int M = (1 << (B - 1)) - 1;
     const int half = 1 << (B - 1);
@@ -142,6 +149,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
         frexpf(amax, &e2);                       // amax in [2^(e2-1), 2^e2)
         const float sc = ldexpf(1.f, e2 - 1), inv_sc = ldexpf(1.f, 1 - e2);  // both finite for any FP32 amax
         // keys stay finite when every non-zero magnitude is >= 2^-118 * amax
+        // (k + 1 <= 2^9 and sc <= amax bound every key by 2^127)
         bool small = false;
         for (int i = lane; i < D; i += 32) small |= (sm.a[i] > 0.f && sm.a[i] < ldexpf(amax, -118));
         if (__any_sync(0xffffffffu, small)) {
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
 
         // initial state: all |y_i| = 1/2
         double ip_run = __dmul_rn(0.5, sum_a);    // exact scaling
-        int n2q_run = D;                           // 4 * ||y||^2
+        int64_t n2q_run = D;                       // 4 * ||y||^2 (above 2^31 at B = 10, D = 4096)
         // integer units of the running sum: u = 2^ue divides every |o'_i| / 2
         int le = 1 << 30;
         for (int i = lane; i < D; i += 32)
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
         int64_t S_int = in_range ? __double2ll_rn(ldexp(ip_run, -ue)) : 0;
         double vmax = __ddiv_rn(ip_run, __dsqrt_rn(0.25 * (double)D));
         double ip_best = ip_run;
-        int n2q_best = D;
+        int64_t n2q_best = D;
         int best_i = -1, best_m = -1;
         int64_t remaining = (int64_t)nz * M;
         float T_prev = 0.f;
@@ -241,9 +249,9 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 const int c0 = sm.cnt[i], c1 = events_upto(T, ai, sc, inv_sc, M);
                 for (int k = c0; k < c1; ++k) {
                     const uint32_t kb = __float_as_uint(ev_key(k, ai, sc));
-                    sm.keys[pos++] = ((uint64_t)kb << 32) | ((uint64_t)i << 8) | (uint64_t)k;
+                    sm.keys[pos++] = ((uint64_t)kb << 32) | ((uint64_t)i << EV_MBITS) | (uint64_t)k;
                 }
-                sm.cnt[i] = (uint8_t)c1;
+                sm.cnt[i] = (uint16_t)c1;
             }
             int np2 = 32;
             while (np2 < cnt) np2 <<= 1;
@@ -273,11 +281,11 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 while (e < cnt && (uint32_t)(sm.keys[e] >> 32) == kj) ++e;
                 for (int h = j + 1; h < e; ++h) {
                     const uint64_t x = sm.keys[h];
-                    const int ix = (int)((x >> 8) & 0xffffffu), mx = (int)(x & 0xffu);
+                    const int ix = ev_i(x), mx = ev_m(x);
                     int g = h - 1;
                     while (g >= j) {
                         const uint64_t y = sm.keys[g];
-                        const int iy = (int)((y >> 8) & 0xffffffu), my = (int)(y & 0xffu);
+                        const int iy = ev_i(y), my = ev_m(y);
                         if (!ev_before(sm.a, ix, mx, iy, my)) break;
                         sm.keys[g + 1] = y;
                         --g;
@@ -294,9 +302,9 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
             int sumN = 0, gmin = 64;
             for (int j = c0; j < c1; ++j) {
                 const uint64_t x = sm.keys[j];
-                sumN += 8 * ((int)(x & 0xffu) + 1);         // 4 * ((m + 3/2)^2 - (m + 1/2)^2)
+                sumN += 8 * (ev_m(x) + 1);                  // 4 * ((m + 3/2)^2 - (m + 1/2)^2)
                 if (in_range) {
-                    const int64_t A = units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
+                    const int64_t A = units_of(sm.a[ev_i(x)], ue);
                     sumA += A;
                     gmin = min(gmin, __ffsll(A) - 1);
                 }
@@ -314,16 +322,17 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 fast = 64 - __clzll(Pend) <= 53 + g;
             }
             double bv = -1.0, bip = 0.0;                        // best cosine and its exact <y, o'>
-            int bj = 0x7fffffff, bn = 0;
+            int bj = 0x7fffffff;
+            int64_t bn = 0;
             if (fast) {
                 const float vmax_u = (float)ldexp(vmax, -ue);  // cosine bounds in units of u (scale-free)
                 float lmax = 0.f;
                 int64_t P = S_int + baseA;
-                int N = n2q_run + baseN;
+                int64_t N = n2q_run + baseN;
                 for (int j = c0; j < c1; ++j) {
                     const uint64_t x = sm.keys[j];
-                    P += units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
-                    N += 8 * ((int)(x & 0xffu) + 1);
+                    P += units_of(sm.a[ev_i(x)], ue);
+                    N += 8 * (ev_m(x) + 1);
                     lmax = fmaxf(lmax, (float)P * rsqrtf(0.25f * (float)N));
                 }
                 const float thr = fmaxf(warp_max(lmax), vmax_u) * (1.0f - 1e-5f);
@@ -331,8 +340,8 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 N = n2q_run + baseN;
                 for (int j = c0; j < c1; ++j) {
                     const uint64_t x = sm.keys[j];
-                    P += units_of(sm.a[(int)((x >> 8) & 0xffffffu)], ue);
-                    N += 8 * ((int)(x & 0xffu) + 1);
+                    P += units_of(sm.a[ev_i(x)], ue);
+                    N += 8 * (ev_m(x) + 1);
                     if ((float)P * rsqrtf(0.25f * (float)N) >= thr) {
                         const double ipj = ldexp(__ll2double_rn(P), ue);   // exact: P has <= 53 significant bits
                         const double ve = __ddiv_rn(ipj, __dsqrt_rn(0.25 * (double)N));
@@ -343,11 +352,11 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 // serial FP64 walk, every addition rounded (two passes: bound, then exact check)
                 float lmax = 0.f;
                 double ip = ip_run;
-                int N = n2q_run;
+                int64_t N = n2q_run;
                 for (int j = 0; j < cnt; ++j) {
                     const uint64_t x = sm.keys[j];
-                    ip = __dadd_rn(ip, (double)sm.a[(int)((x >> 8) & 0xffffffu)]);
-                    N += 8 * ((int)(x & 0xffu) + 1);
+                    ip = __dadd_rn(ip, (double)sm.a[ev_i(x)]);
+                    N += 8 * (ev_m(x) + 1);
                     lmax = fmaxf(lmax, (float)ip * rsqrtf(0.25f * (float)N));
                 }
                 const float thr = fmaxf(lmax, (float)vmax) * (1.0f - 1e-5f);
@@ -355,8 +364,8 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 N = n2q_run;
                 for (int j = 0; j < cnt; ++j) {
                     const uint64_t x = sm.keys[j];
-                    ip = __dadd_rn(ip, (double)sm.a[(int)((x >> 8) & 0xffffffu)]);
-                    N += 8 * ((int)(x & 0xffu) + 1);
+                    ip = __dadd_rn(ip, (double)sm.a[ev_i(x)]);
+                    N += 8 * (ev_m(x) + 1);
                     if ((float)ip * rsqrtf(0.25f * (float)N) >= thr) {
                         const double ve = __ddiv_rn(ip, __dsqrt_rn(0.25 * (double)N));
                         if (ve > bv) { bv = ve; bip = ip; bj = j; bn = N; }
@@ -369,14 +378,14 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const double oip = __shfl_xor_sync(0xffffffffu, bip, o);
                 const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                const int on = __shfl_xor_sync(0xffffffffu, bn, o);
+                const int64_t on = __shfl_xor_sync(0xffffffffu, bn, o);
                 if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bip = oip; bj = oj; bn = on; }
             }
             if (bv > vmax) {
                 vmax = bv;
                 const uint64_t x = sm.keys[bj];
-                best_i = (int)((x >> 8) & 0xffffffu);
-                best_m = (int)(x & 0xffu);
+                best_i = ev_i(x);
+                best_m = ev_m(x);
                 ip_best = bip;
                 n2q_best = bn;
             }
@@ -439,7 +448,7 @@ cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* c
                           double* stats, uint32_t* status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int W = enc_window(D);
-    const size_t per_warp = ((size_t)W * 8 + (size_t)D * 5 + 64 + 15) / 16 * 16;
+    const size_t per_warp = ((size_t)W * 8 + (size_t)D * 6 + 64 + 15) / 16 * 16;
     int warps = (int)((200 * 1024) / per_warp);
     warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
     const size_t smem = per_warp * warps;

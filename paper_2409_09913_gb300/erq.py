@@ -187,7 +187,7 @@ def rotate(X, P, accurate=False, out=None):
 
 def encode(R, B, with_stats=False):
     """Algorithm 1 on each row of R (rotated residuals) -> (codes, f_add, f_res[, stats]);
-    codes are uint8 for B <= 8 and 16-bit (int16, values < 512) for B = 9."""
+    codes are uint8 for B <= 8 and 16-bit (int16, values < 2^B) for B = 9, 10."""
     R = _dev(R, torch.float32, "R", 2)
     n, d = R.shape
     codes = torch.empty((n, d), dtype=torch.int16 if int(B) > 8 else torch.uint8, device=R.device)

@@ -48,7 +48,7 @@ def test_host_validation_rejects_bad_shapes(L):
     assert L.erq_rotate(_vp(8), 4, 63, _vp(8), _vp(8), 0, _vp()) == erq.ERQ_EINVAL
     assert b"multiple of 64" in L.erq_last_error()
     # B out of range
-    assert L.erq_encode(_vp(8), 4, 64, 10, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
+    assert L.erq_encode(_vp(8), 4, 64, 11, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
     assert L.erq_encode(_vp(8), 4, 64, 0, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL
     # null pointers
     assert L.erq_encode(_vp(0), 4, 64, 4, _vp(8), _vp(8), _vp(8), _vp(), _vp()) == erq.ERQ_EINVAL

@@ -27,7 +27,7 @@ def _check_encode(erq, R, B):
     np.testing.assert_array_equal(fr.view(np.uint32), fr_o.view(np.uint32))
 
 
-@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("kind", ["gauss", "ties", "sparse", "wide"])
 def test_encode_bit_exact_d128(erq, B, kind):
     R = S.random_rotated_residuals(300, 128, 1000 + B, kind=kind)
@@ -35,13 +35,14 @@ def test_encode_bit_exact_d128(erq, B, kind):
 
 
 @pytest.mark.parametrize("D,B,n", [(64, 5, 400), (960, 3, 200), (960, 5, 200), (960, 7, 60), (1536, 7, 40),
-                                   (768, 5, 150), (1024, 4, 150), (4096, 2, 20), (960, 9, 20)])
+                                   (768, 5, 150), (1024, 4, 150), (4096, 2, 20), (960, 9, 20),
+                                   (960, 10, 12), (4096, 10, 3)])
 def test_encode_bit_exact_paper_shapes(erq, D, B, n):
     R = S.random_rotated_residuals(n, D, 2000 + D + B)
     _check_encode(erq, R, B)
 
 
-@pytest.mark.parametrize("B", [4, 6, 8])
+@pytest.mark.parametrize("B", [4, 6, 8, 10])
 def test_encode_bit_exact_openai3072(erq, B):
     """The Table 4 shape (D = 3072), with a few very small coordinates planted
     in half of the rows: their events make FP64 additions of the running
@@ -62,7 +63,7 @@ def test_encode_degenerate_rows(erq):
     rows[3, :] = 1.0
     rows[4, 0], rows[4, 1:] = 2.0 ** -101, 0.5
     rows[5, 0], rows[5, 1:] = 1e30, 1.0
-    for B in (1, 2, 4, 8):
+    for B in (1, 2, 4, 8, 9, 10):
         _check_encode(erq, rows, B)
 
 
@@ -81,7 +82,7 @@ def test_encode_empty_and_invalid(erq):
     with pytest.raises(erq.ErqError):
         erq.encode(torch.zeros((2, 65), device="cuda"), 4)
     with pytest.raises(erq.ErqError):
-        erq.encode(torch.zeros((2, 64), device="cuda"), 10)
+        erq.encode(torch.zeros((2, 64), device="cuda"), 11)
 
 
 @pytest.mark.parametrize("D", [64, 960])

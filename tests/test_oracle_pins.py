@@ -56,19 +56,20 @@ def test_alg1_equals_brute_force(B, d):
             assert any((h == codes[i]).all() for h in hits), (kind, R[i], codes[i], hits)
 
 
-@pytest.mark.parametrize("d", [1, 2])
-def test_alg1_b9_equals_brute_force(d):
-    """B = 9 (Section 5.1 evaluates B up to 9 and more): Algorithm 1 against
-    enumeration of all 2^(9 D) grid vectors (512 and 262,144)."""
+@pytest.mark.parametrize("d,B", [(1, 9), (2, 9), (1, 10), (2, 10)])
+def test_alg1_wide_codes_equal_brute_force(d, B):
+    """B = 9 and 10 (Section 5.1 evaluates B up to 9, Table 4 times B up to
+    10): Algorithm 1 against enumeration of all 2^(B D) grid vectors (512 to
+    1,048,576)."""
     n = 60 if d == 2 else 200
     for kind, seed in (("gauss", 15), ("ties", 16), ("sparse", 17)):
-        R = S.random_rotated_residuals(n, d, seed + 100 * d, kind=kind)
-        codes, st = oracle.quantize(R, 9)
-        assert codes.max() <= 511
+        R = S.random_rotated_residuals(n, d, seed + 100 * d + 1000 * (B - 9), kind=kind)
+        codes, st = oracle.quantize(R, B)
+        assert codes.max() <= 2 ** B - 1
         for i in range(n):
             if not np.any(R[i]):
                 continue
-            best, hits = oracle.brute_force_quantize(R[i], 9)
+            best, hits = oracle.brute_force_quantize(R[i], B)
             v = st[i, 2] / math.sqrt(st[i, 3])
             assert v == pytest.approx(best, rel=1e-13, abs=1e-15), (kind, R[i], codes[i])
             assert any((h == codes[i]).all() for h in hits), (kind, R[i], codes[i], hits)
@@ -86,7 +87,7 @@ def test_alg1_b1_is_rabitq_sign_code():
     assert (st[:, 4] == 0).all()          # no critical values when B = 1
 
 
-@pytest.mark.parametrize("B", [2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("B", [2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_alg1_msb_is_sign_and_event_count(B):
     """Section 4.2: the most significant bits of ybar_u form the RaBitQ code of
     o'.  Section 3.1: each non-zero coordinate has 2^(B-1)-1 critical values."""
@@ -98,7 +99,7 @@ def test_alg1_msb_is_sign_and_event_count(B):
     assert (st[:, 4] == nz * (2 ** (B - 1) - 1)).all()
 
 
-@pytest.mark.parametrize("B", [2, 3, 5, 7, 9])
+@pytest.mark.parametrize("B", [2, 3, 5, 7, 9, 10])
 def test_lemma_3_1_nearest_grid_point(B):
     """Lemma 3.1 with the proof's t = ||ybar||^2 / <o', ybar>: ybar is a
     nearest point of G to t*o' (G is a product set, so coordinate-wise)."""
