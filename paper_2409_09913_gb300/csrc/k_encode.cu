@@ -48,9 +48,13 @@ constexpr uint64_t EV_MMASK = (1u << EV_MBITS) - 1, EV_IMASK = (1u << (32 - EV_M
 __device__ __forceinline__ int ev_i(uint64_t x) { return (int)((x >> EV_MBITS) & EV_IMASK); }
 __device__ __forceinline__ int ev_m(uint64_t x) { return (int)(x & EV_MMASK); }
 
+// CntT: the per-coordinate event counter, one byte up to B = 9 (at most 255
+// events), two bytes at B = 10 (511); the narrow form leaves room for more
+// warps per block in shared memory.
+template <typename CntT>
 struct EncSmem {
     float* a;         // [D] |o'_i|
-    uint16_t* cnt;    // [D] events of coordinate i already consumed
+    CntT* cnt;        // [D] events of coordinate i already consumed
     uint64_t* keys;   // [W] (key32 << 32) | (i << EV_MBITS) | m
 };
 
@@ -104,7 +108,8 @@ __device__ __forceinline__ bool ev_before(const float* a, int ia, int ma, int ib
     return ia < ib;
 }
 
-__device__ int window_count(const EncSmem& sm, int D, int M, float T, float sc, float inv_sc) {
+template <typename CntT>
+__device__ int window_count(const EncSmem<CntT>& sm, int D, int M, float T, float sc, float inv_sc) {
     const int lane = threadIdx.x & 31;
     int c = 0;
     for (int i = lane; i < D; i += 32) c += events_upto(T, sm.a[i], sc, inv_sc, M) - (int)sm.cnt[i];
@@ -113,6 +118,7 @@ __device__ int window_count(const EncSmem& sm, int D, int M, float T, float sc, 
 
 }  // namespace
 
+template <typename CntT>
 __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ Rrot, int64_t n, int D, int B, int W,
                                                      uint8_t* __restrict__ codes, float* __restrict__ f_add,
                                                      float* __restrict__ f_res, double* __restrict__ stats,
@@ -120,12 +126,12 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const size_t per_warp = (size_t)W * 8 + (size_t)D * 6 + 64;
+    const size_t per_warp = (size_t)W * 8 + (size_t)D * (4 + sizeof(CntT)) + 64;
     unsigned char* base = smem_raw + (size_t)warp * ((per_warp + 15) / 16 * 16);
-    EncSmem sm;
+    EncSmem<CntT> sm;
     sm.keys = reinterpret_cast<uint64_t*>(base);
     sm.a = reinterpret_cast<float*>(base + (size_t)W * 8);
-    sm.cnt = reinterpret_cast<uint16_t*>(base + (size_t)W * 8 + (size_t)D * 4);
+    sm.cnt = reinterpret_cast<CntT*>(base + (size_t)W * 8 + (size_t)D * 4);
 
     const int M = (1 << (B - 1)) - 1;
     const int half = 1 << (B - 1);
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
 
         // initial state: all |y_i| = 1/2
         double ip_run = __dmul_rn(0.5, sum_a);    // exact scaling
-        int64_t n2q_run = D;                       // 4 * ||y||^2 (above 2^31 at B = 10, D = 4096)
+        uint32_t n2q_run = D;                      // 4 ||y||^2 <= D (2^B - 1)^2 < 2^32 (B <= 10, D <= 4096)
         // integer units of the running sum: u = 2^ue divides every |o'_i| / 2
         int le = 1 << 30;
         for (int i = lane; i < D; i += 32)
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
         int64_t S_int = in_range ? __double2ll_rn(ldexp(ip_run, -ue)) : 0;
         double vmax = __ddiv_rn(ip_run, __dsqrt_rn(0.25 * (double)D));
         double ip_best = ip_run;
-        int64_t n2q_best = D;
+        uint32_t n2q_best = D;
         int best_i = -1, best_m = -1;
         int64_t remaining = (int64_t)nz * M;
         float T_prev = 0.f;
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                     const uint32_t kb = __float_as_uint(ev_key(k, ai, sc));
                     sm.keys[pos++] = ((uint64_t)kb << 32) | ((uint64_t)i << EV_MBITS) | (uint64_t)k;
                 }
-                sm.cnt[i] = (uint16_t)c1;
+                sm.cnt[i] = (CntT)c1;
             }
             int np2 = 32;
             while (np2 < cnt) np2 <<= 1;
@@ -323,12 +329,12 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
             }
             double bv = -1.0, bip = 0.0;                        // best cosine and its exact <y, o'>
             int bj = 0x7fffffff;
-            int64_t bn = 0;
+            uint32_t bn = 0;
             if (fast) {
                 const float vmax_u = (float)ldexp(vmax, -ue);  // cosine bounds in units of u (scale-free)
                 float lmax = 0.f;
                 int64_t P = S_int + baseA;
-                int64_t N = n2q_run + baseN;
+                uint32_t N = n2q_run + (uint32_t)baseN;
                 for (int j = c0; j < c1; ++j) {
                     const uint64_t x = sm.keys[j];
                     P += units_of(sm.a[ev_i(x)], ue);
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 // serial FP64 walk, every addition rounded (two passes: bound, then exact check)
                 float lmax = 0.f;
                 double ip = ip_run;
-                int64_t N = n2q_run;
+                uint32_t N = n2q_run;
                 for (int j = 0; j < cnt; ++j) {
                     const uint64_t x = sm.keys[j];
                     ip = __dadd_rn(ip, (double)sm.a[ev_i(x)]);
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ R
                 const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const double oip = __shfl_xor_sync(0xffffffffu, bip, o);
                 const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                const int64_t on = __shfl_xor_sync(0xffffffffu, bn, o);
+                const uint32_t on = __shfl_xor_sync(0xffffffffu, bn, o);
                 if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bip = oip; bj = oj; bn = on; }
             }
             if (bv > vmax) {
@@ -444,15 +450,15 @@ static int enc_window(int D) {
     return W;
 }
 
-cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* codes, float* f_add, float* f_res,
-                          double* stats, uint32_t* status, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+template <typename CntT>
+static cudaError_t launch_encode_t(const float* Rrot, int64_t n, int D, int B, uint8_t* codes, float* f_add,
+                                   float* f_res, double* stats, uint32_t* status, cudaStream_t s) {
     const int W = enc_window(D);
-    const size_t per_warp = ((size_t)W * 8 + (size_t)D * 6 + 64 + 15) / 16 * 16;
+    const size_t per_warp = ((size_t)W * 8 + (size_t)D * (4 + sizeof(CntT)) + 64 + 15) / 16 * 16;
     int warps = (int)((200 * 1024) / per_warp);
     warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
     const size_t smem = per_warp * warps;
-    cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(encode_kernel<CntT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -461,8 +467,16 @@ cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* c
     const int64_t cap = (int64_t)sms * 4;
     if (blocks > cap) blocks = cap;
     count_launch();
-    encode_kernel<<<(unsigned)blocks, warps * 32, smem, s>>>(Rrot, n, D, B, W, codes, f_add, f_res, stats, status);
+    encode_kernel<CntT><<<(unsigned)blocks, warps * 32, smem, s>>>(Rrot, n, D, B, W, codes, f_add, f_res, stats,
+                                                                   status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const float* Rrot, int64_t n, int D, int B, uint8_t* codes, float* f_add, float* f_res,
+                          double* stats, uint32_t* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (B <= 9) return launch_encode_t<uint8_t>(Rrot, n, D, B, codes, f_add, f_res, stats, status, s);
+    return launch_encode_t<uint16_t>(Rrot, n, D, B, codes, f_add, f_res, stats, status, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -124,9 +124,7 @@ struct Cfg {
         static constexpr int qsc = tq + 2 * QN * 8;              // 2 x [QN] f32 query scale (e4m3 path)
         static constexpr int itd = qsc + 2 * QN * 4;             // 2 x int4 {rb0 lo, rb0 hi, rows, queries | -1}
         static constexpr int ids = itd + 2 * 16;                 // EB x [MR] u32 ids of the tile's rows
-        static constexpr int cnt = ids + EB * MR * 4;            // [QN] int list fill
-        static constexpr int tau = cnt + QN * 4;                 // [QN] u64 admission threshold
-        static constexpr int bars = tau + QN * 8;
+        static constexpr int bars = ids + EB * MR * 4;
         static constexpr int nbars = 2 * RSMAX + 2 * LS + LS * RP + 2 * NBUF * RP + 2 * MS + 4 + 2 + 2 * EB;
         static constexpr int tmem_slot = bars + nbars * 8;
         static constexpr int abort_flag = tmem_slot + 4;
@@ -857,8 +855,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             return lists_s + q * KC;
         };
         const uint32_t* s_ids = reinterpret_cast<const uint32_t*>(sm + Smem::ids);
-        int* s_cnt = reinterpret_cast<int*>(sm + Smem::cnt);
-        uint64_t* s_tau = reinterpret_cast<uint64_t*>(sm + Smem::tau);
         const int fw = warp - W_FX;
         const uint32_t below = (1u << lane) - 1u;
         const int kp = a.kp;
@@ -871,14 +867,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (d.w < 0) break;
             const int nrows = d.z, nqi = d.w;
             const int4* iq = s_iq + ib * QN;
-            if (lane < (QN + NFX - 1) / NFX) {
+            // lane j holds the state of the warp's j-th query slot q = fw + NFX j:
+            // its distance term, admission threshold (key and float) and list fill
+            const int nown = nqi > fw ? (nqi - fw + NFX - 1) / NFX : 0;
+            float my_dq = 0.f, my_tf = -INFINITY;
+            uint64_t my_tau = 0;
+            int my_cnt = 0;
+            if (lane < nown) {
                 const int q = fw + NFX * lane;
-                if (q < nqi) {
-                    s_cnt[q] = 0;
-                    s_tau[q] = s_tq[ib * QN + q];
-                }
+                my_dq = __int_as_float(iq[q].y);
+                my_tau = s_tq[ib * QN + q];
+                my_tf = my_tau == kEmptyKey ? INFINITY : key_value(my_tau);
             }
-            __syncwarp();
             for (int r = 0; r < nrows; r += MR, ++blk) {
                 const int nr = min(MR, nrows - r);
                 const int t = blk % EB;
@@ -888,18 +888,24 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 const float* est_t = s_est + t * (QN * MR);
                 const uint32_t* ids_t = s_ids + t * MR;
-                // the 128 rows of each owned query; the four 32-row groups'
-                // estimates are loaded together, compared as floats against
-                // the threshold's estimate (a superset of the key test), and
-                // only groups with a candidate form exact keys
-                for (int q = fw; q < nqi; q += NFX) {
-                    const float dq = __int_as_float(iq[q].y);
-                    uint64_t tau = s_tau[q];
-                    float tf = tau == kEmptyKey ? INFINITY : key_value(tau);
-                    int cnt = s_cnt[q];
+                // the 128 rows of each owned query: the four 32-row groups'
+                // estimates are compared as floats against the threshold's
+                // estimate (a superset of the key test) with one vote for the
+                // query, and only groups with a candidate form exact keys
+                for (int jj = 0; jj < nown; ++jj) {
+                    const int q = fw + NFX * jj;
+                    const float dq = __shfl_sync(0xffffffffu, my_dq, jj);
+                    float tf = __shfl_sync(0xffffffffu, my_tf, jj);
                     float e[MR / 32];
+                    bool any = false;
 #pragma unroll
-                    for (int j = 0; j < MR / 32; ++j) e[j] = dq + est_t[q * MR + j * 32 + lane];
+                    for (int j = 0; j < MR / 32; ++j) {
+                        e[j] = dq + est_t[q * MR + j * 32 + lane];
+                        any |= j * 32 + lane < nr && e[j] <= tf;
+                    }
+                    if (!__any_sync(0xffffffffu, any)) continue;
+                    uint64_t tau = shfl_u64(my_tau, jj);
+                    int cnt = __shfl_sync(0xffffffffu, my_cnt, jj);
 #pragma unroll
                     for (int j = 0; j < MR / 32; ++j) {
                         const int rr = j * 32 + lane;
@@ -927,17 +933,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                         cnt += __popc(msk);
                         __syncwarp();
                     }
-                    if (lane == 0) {
-                        s_cnt[q] = cnt;
-                        s_tau[q] = tau;
+                    if (lane == jj) {
+                        my_cnt = cnt;
+                        my_tau = tau;
+                        my_tf = tf;
                     }
-                    __syncwarp();
                 }
                 mbar_arrive(bars + C::b_tile_empty(t));
             }
             if (!ok) break;
-            for (int q = fw; q < nqi; q += NFX) {               // write this warp's lists
-                int cnt = s_cnt[q];
+            for (int jj = 0; jj < nown; ++jj) {                 // write this warp's lists
+                const int q = fw + NFX * jj;
+                int cnt = __shfl_sync(0xffffffffu, my_cnt, jj);
                 if (cnt >= kp) {                                 // keep the k' smallest; publish the k'-th
                     const uint64_t th = compact_list<C::KS>(list_of(iq, q), cnt, kp, lane);
                     cnt = kp;
