@@ -405,6 +405,15 @@ __device__ __forceinline__ void warp_sort(uint64_t (&v)[N / 32], int lane) {
     }
 }
 
+// A threshold on the estimate tile's values (g + (f_res/2) acc) that admits
+// every value v with fl(dq + v) <= tf: tf - dq, raised by 2^-20 of
+// |tf| + |dq| to cover the roundings of fl(dq + v) and of this expression
+// (each within 2^-24 of the magnitudes involved) and by 2^-120 for the
+// absolute error of subnormal results; +inf stays +inf.
+__device__ __forceinline__ float relaxed_threshold(float tf, float dq) {
+    return (tf - dq) + (0x1p-20f * (fabsf(tf) + fabsf(dq)) + 0x1p-120f);
+}
+
 // Keep the kp smallest keys of one query's list (cnt <= KS entries) in its
 // first kp slots, sorted; returns the new admission threshold (the kp-th key).
 template <int KS>
@@ -809,6 +818,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         mt.x = 0.f;
                         mt.y *= 0.5f;
                     }
+                    if (row >= min(MR, nrows - r0 - rb * MR)) {    // past the block's rows: NaN, which no
+                        mt.x = __int_as_float(0x7fc00000);         // threshold admits
+                        mt.y = 0.f;
+                    }
                     const uint32_t tacc = tmem + lane_base + (uint32_t)((buf * RP + rb) * QN);
 #pragma unroll 1
                     for (int cc = 0; cc < npad; cc += 32) {
@@ -868,9 +881,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int nrows = d.z, nqi = d.w;
             const int4* iq = s_iq + ib * QN;
             // lane j holds the state of the warp's j-th query slot q = fw + NFX j:
-            // its distance term, admission threshold (key and float) and list fill
+            // its distance term, admission threshold (key and float), list fill
+            // and the threshold relaxed into the estimate tile's units
             const int nown = nqi > fw ? (nqi - fw + NFX - 1) / NFX : 0;
-            float my_dq = 0.f, my_tf = -INFINITY;
+            float my_dq = 0.f, my_tf = -INFINITY, my_thr = -INFINITY;
             uint64_t my_tau = 0;
             int my_cnt = 0;
             if (lane < nown) {
@@ -878,6 +892,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 my_dq = __int_as_float(iq[q].y);
                 my_tau = s_tq[ib * QN + q];
                 my_tf = my_tau == kEmptyKey ? INFINITY : key_value(my_tau);
+                my_thr = relaxed_threshold(my_tf, my_dq);
             }
             for (int r = 0; r < nrows; r += MR, ++blk) {
                 const int nr = min(MR, nrows - r);
@@ -888,27 +903,24 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 const float* est_t = s_est + t * (QN * MR);
                 const uint32_t* ids_t = s_ids + t * MR;
-                // the 128 rows of each owned query: the four 32-row groups'
-                // estimates are compared as floats against the threshold's
-                // estimate (a superset of the key test) with one vote for the
-                // query, and only groups with a candidate form exact keys
+                // the 128 rows of each owned query, rows 4 lane .. 4 lane + 3 in
+                // lane `lane` (rows past the block are NaN): one vote against the
+                // relaxed threshold (a superset of the float test below, which is
+                // a superset of the key test), then per row group the float
+                // test and exact keys
                 for (int jj = 0; jj < nown; ++jj) {
                     const int q = fw + NFX * jj;
+                    const float thr = __shfl_sync(0xffffffffu, my_thr, jj);
+                    const float4 v4 = *reinterpret_cast<const float4*>(est_t + q * MR + 4 * lane);
+                    if (!__any_sync(0xffffffffu, v4.x <= thr || v4.y <= thr || v4.z <= thr || v4.w <= thr)) continue;
                     const float dq = __shfl_sync(0xffffffffu, my_dq, jj);
                     float tf = __shfl_sync(0xffffffffu, my_tf, jj);
-                    float e[MR / 32];
-                    bool any = false;
-#pragma unroll
-                    for (int j = 0; j < MR / 32; ++j) {
-                        e[j] = dq + est_t[q * MR + j * 32 + lane];
-                        any |= j * 32 + lane < nr && e[j] <= tf;
-                    }
-                    if (!__any_sync(0xffffffffu, any)) continue;
                     uint64_t tau = shfl_u64(my_tau, jj);
                     int cnt = __shfl_sync(0xffffffffu, my_cnt, jj);
+                    const float e[4] = {dq + v4.x, dq + v4.y, dq + v4.z, dq + v4.w};
 #pragma unroll
-                    for (int j = 0; j < MR / 32; ++j) {
-                        const int rr = j * 32 + lane;
+                    for (int j = 0; j < 4; ++j) {
+                        const int rr = 4 * lane + j;
                         const bool pre = rr < nr && e[j] <= tf;
                         if (!__any_sync(0xffffffffu, pre)) continue;
                         const uint64_t key = make_key(e[j], ids_t[rr]);
@@ -936,6 +948,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (lane == jj) {
                         my_cnt = cnt;
                         my_tau = tau;
+                        if (tf != my_tf) my_thr = relaxed_threshold(tf, dq);
                         my_tf = tf;
                     }
                 }
