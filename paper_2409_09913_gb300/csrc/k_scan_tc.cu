@@ -523,6 +523,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         int64_t item = blockIdx.x;
         const uint64_t pol_codes = a.codes_shared ? l2_evict_normal() : l2_evict_first();
+        // the descriptor and query slots of the item published next, fetched
+        // while the previous item streams (its thresholds are read when it is
+        // published, so they are as tight as possible)
+        constexpr int QPL = QN / 32;
+        int4 pd = make_int4(0, 0, 0, -1), pv[QPL];
+        auto prefetch = [&](int64_t it) {
+            if (it >= nitems) return;
+            pd = a.itemd[it];
+#pragma unroll
+            for (int k = 0; k < QPL; ++k) {
+                const int q = lane + 32 * k;
+                pv[k] = q < a.qn ? a.itemq[it * a.qn + q] : make_int4(-1, 0, 0, 0);
+            }
+        };
+        prefetch(item);
         for (;; ++li) {
             const int ib = li & 1;
             if (!mbar_wait_warp(bars + C::b_empty_item(ib), ((li >> 1) & 1) ^ 1, abort_flag, wlim)) {
@@ -532,9 +547,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             const bool have = item < nitems;
             int4 d = make_int4(0, 0, 0, -1);
             if (have) {
-                d = a.itemd[item];
-                for (int q = lane; q < QN; q += 32) {
-                    const int4 v = q < a.qn ? a.itemq[item * a.qn + q] : make_int4(-1, 0, 0, 0);
+                d = pd;
+#pragma unroll
+                for (int k = 0; k < QPL; ++k) {
+                    const int q = lane + 32 * k;
+                    const int4 v = pv[k];
                     s_iq[ib * QN + q] = v;
                     s_tq[ib * QN + q] = v.x >= 0 ? __ldcg(a.tq + v.x) : kEmptyKey;
                     if (F8) s_qsc[ib * QN + q] = v.x >= 0 ? a.qscale[v.x] : 0.f;
@@ -544,6 +561,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             mbar_arrive(bars + C::b_full_item(ib));
             if (!have) break;
+            {   // claim the next item now; its descriptor arrives while this one streams
+                int nx = 0;
+                if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
+                item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
+                prefetch(item);
+            }
             const int64_t rb0 = rb0_of(d);                 // first padded row (multiple of 32)
             const int nrows = d.z;
             for (int r = 0; r < nrows && ok; r += RP * MR) {
@@ -596,9 +619,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
-            int nx = 0;
-            if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
-            item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
         }
         // drain: every copy this warp issued has landed before the CTA exits
         for (uint32_t k = 0; k < (uint32_t)RS && k < g; ++k) {
