@@ -102,6 +102,25 @@ def test_ivf_computed_probe(erq):
     compare_topk_ids(gid, ref["cand_ids"], ref["cand_est"], 1.5 * max(err, 1e-7), "candidates", max_excluded=0.05)
 
 
+@pytest.mark.parametrize("nprobe", [40, 150])
+def test_ivf_computed_probe_wide(erq, nprobe):
+    """Probe lists longer than a warp (the block-per-query radix selection over
+    400 centroid distances): as above, probe sets equal the oracle's outside
+    FP32 noise at the cut."""
+    X, P, assign, gx, ox = _build_pair(erq, 20000, 128, 4, 400, 820, n_comp=40, scale="aniso")
+    Q, _ = S.mixture(150, 128, 40, 821, comp_seed=820, scale="aniso")
+    ids, dists, cids, cest = gx.search(to_dev(Q), 10, rerank_k=30, nprobe=nprobe, return_candidates=True)
+    cd = oracle.centroid_dists(ox["C"], Q)
+    srt = np.sort(cd, 1)
+    clean = (srt[:, nprobe] - srt[:, nprobe - 1]) > 1e-4 * srt[:, nprobe]
+    assert clean.sum() >= 100              # (the cut falls in a denser part of the distances at 150)
+    ref = oracle.search(ox, Q[clean], 10, kprime=31, nprobe=nprobe)
+    gid = cids.cpu().numpy()[clean]
+    oest = oracle.estimate_rows(ox, Q[clean], gid)
+    err = assert_close_rel(cest.cpu().numpy()[clean], oest, FP32_RTOL, "estimates")
+    compare_topk_ids(gid, ref["cand_ids"], ref["cand_est"], 1.5 * max(err, 1e-7), "candidates", max_excluded=0.05)
+
+
 def test_variable_nprobe_and_large_k(erq):
     """Per-query nprobe, k' larger than some probed clusters, -1 padding."""
     X, P, assign, gx, ox = _build_pair(erq, 3000, 64, 5, 40, 900)
