@@ -561,15 +561,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             mbar_arrive(bars + C::b_full_item(ib));
             if (!have) break;
-            {   // claim the next item now; its descriptor arrives while this one streams
-                int nx = 0;
-                if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
-                item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
-                prefetch(item);
-            }
             const int64_t rb0 = rb0_of(d);                 // first padded row (multiple of 32)
             const int nrows = d.z;
             for (int r = 0; r < nrows && ok; r += RP * MR) {
+                if (r + RP * MR >= nrows) {
+                    // the last stage group: claim the next item, whose descriptor
+                    // arrives while this group streams (claiming no earlier keeps
+                    // the items of one list on several SMs at about the same
+                    // time, sharing its codes in L2)
+                    int nx = 0;
+                    if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
+                    item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
+                    prefetch(item);
+                }
                 const int nb = min(RP, (nrows - r + MR - 1) / MR);     // row blocks in this stage group
                 for (int bb = 0; bb < nb && ok; ++bb, ++rbg) {
                     const int nr = min(MR, nrows - r - bb * MR);
