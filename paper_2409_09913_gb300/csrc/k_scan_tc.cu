@@ -563,17 +563,21 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!have) break;
             const int64_t rb0 = rb0_of(d);                 // first padded row (multiple of 32)
             const int nrows = d.z;
+            // the next item is claimed exactly once per published item: at the
+            // start of this item's last stage group, so that its descriptor
+            // arrives while the group streams (claiming no earlier keeps the
+            // items of one list on several SMs at about the same time, sharing
+            // its codes in L2), or below for an item without rows
+            bool claimed = false;
+            auto claim_next = [&]() {
+                int nx = 0;
+                if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
+                item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
+                prefetch(item);
+                claimed = true;
+            };
             for (int r = 0; r < nrows && ok; r += RP * MR) {
-                if (r + RP * MR >= nrows) {
-                    // the last stage group: claim the next item, whose descriptor
-                    // arrives while this group streams (claiming no earlier keeps
-                    // the items of one list on several SMs at about the same
-                    // time, sharing its codes in L2)
-                    int nx = 0;
-                    if (lane == 0) nx = (int)atomicAdd(a.work_ctr, 1u);
-                    item = (int64_t)gridDim.x + __shfl_sync(0xffffffffu, nx, 0);
-                    prefetch(item);
-                }
+                if (r + RP * MR >= nrows) claim_next();
                 const int nb = min(RP, (nrows - r + MR - 1) / MR);     // row blocks in this stage group
                 for (int bb = 0; bb < nb && ok; ++bb, ++rbg) {
                     const int nr = min(MR, nrows - r - bb * MR);
@@ -623,6 +627,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
+            if (!claimed) claim_next();
         }
         // drain: every copy this warp issued has landed before the CTA exits
         for (uint32_t k = 0; k < (uint32_t)RS && k < g; ++k) {
